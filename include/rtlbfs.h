@@ -1,0 +1,201 @@
+/*
+ * rtlbfs.h -- C ABI of the GB300 (sm_103a) solver for the reconstructed
+ * thermal lattice Boltzmann flux solver (RTLBFS) of arXiv 2202.13449, 2D,
+ * on a structured rectilinear (tensor-product, possibly stretched) mesh.
+ *
+ * One time step (Section 3.2 of the paper) is, per face: face values by
+ * inverse-distance weighting (Eq. 56), cell gradients by the discrete Gauss
+ * theorem (Eq. 55), a 9-node unit lattice at the face with node values by
+ * Eq. 29, the predicted variables of Eqs. 46-48, and the corrector fluxes
+ * of Eqs. 57-59 with their (tau - 1.5)(X* - X^n) dissipation terms; per
+ * cell: the explicit update of Eqs. 57-59 with the Boussinesq buoyancy of
+ * Eq. 64 and the steady residual (the L2 analogue of Eq. 65).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (RTLBFS_OK = 0 or a negative
+ *     RTLBFS_ERR_*) and never aborts or traps.  rtlbfs_last_error() gives a
+ *     human-readable reason for the last failure on a handle.
+ *   - Host arrays passed in are read during the call and never retained;
+ *     host arrays passed out are written during the call (the call
+ *     synchronises the handle's stream before returning).  The library
+ *     owns all device memory of a handle and frees it in *_destroy.
+ *   - Fields are row-major ny x nx (cell (i, j) at j*nx + i, i along x).
+ *   - A handle is not thread-safe: one host thread at a time.
+ *   - Lattice units: c = 1, c_s^2 = 1/3, c_p = 1, reference length L = the
+ *     domain width in x (for Rayleigh-Benard runs: the height, see
+ *     rtlbfs_set_params_ref).
+ */
+#ifndef RTLBFS_H
+#define RTLBFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RTLBFS_OK 0
+#define RTLBFS_ERR_ARG (-1)           /* bad argument (size, range, null) */
+#define RTLBFS_ERR_OOM (-2)           /* device or host allocation failed */
+#define RTLBFS_ERR_CUDA (-3)          /* a CUDA call failed */
+#define RTLBFS_ERR_DIVERGED (-4)      /* the residual became non-finite */
+#define RTLBFS_ERR_NOT_CONVERGED (-5) /* max_steps reached before tol */
+#define RTLBFS_ERR_TIMEOUT (-6)       /* wall-clock limit reached */
+#define RTLBFS_ERR_STATE (-7)         /* call not valid in this state */
+
+/* arithmetic of the bulk step */
+#define RTLBFS_FP64 0 /* every stage in FP64 */
+#define RTLBFS_FP32 1 /* FP32 bulk storing rho - 1, FP64 residual/Nusselt sums */
+
+/* sides and boundary kinds */
+#define RTLBFS_WEST 0
+#define RTLBFS_EAST 1
+#define RTLBFS_SOUTH 2
+#define RTLBFS_NORTH 3
+#define RTLBFS_WALL_DIRICHLET 0 /* no-slip wall, fixed temperature */
+#define RTLBFS_WALL_ADIABATIC 1 /* no-slip wall, zero heat flux */
+#define RTLBFS_PERIODIC 2       /* must be set on both opposite sides */
+
+/* Nusselt selectors of rtlbfs_nusselt */
+#define RTLBFS_NU_WEST 0  /* energy flux through the west wall / (chi dT) */
+#define RTLBFS_NU_EAST 1
+#define RTLBFS_NU_SOUTH 2
+#define RTLBFS_NU_NORTH 3
+#define RTLBFS_NU_AVG 4   /* Nu_a of Eq. 69 (Section 4.2) */
+#define RTLBFS_NU_HALF 5  /* Nu_1/2: energy flux through the x-face column x = L/2 (Tables 2-3); nx even */
+
+typedef struct rtlbfs_ctx* rtlbfs_t;
+
+/*
+ * Face coordinates of the tanh-stretched mesh of Eq. 74 (Section 4.4):
+ * out[i] = {tanh(phi) + tanh[2 phi (i/n - 1/2)]} L / (2 tanh(phi)),
+ * i = 0..n (out holds n+1 doubles, caller-owned).  phi <= 0 gives the
+ * uniform mesh out[i] = i L / n.  Host only.  ERR_ARG if n < 1, L <= 0.
+ */
+int rtlbfs_tanh_faces(int n, double L, double phi, double* out);
+
+/*
+ * Create a solver for an nx x ny cell mesh with face coordinates xf[0..nx],
+ * yf[0..ny] (strictly ascending, copied).  precision is RTLBFS_FP64 or
+ * RTLBFS_FP32.  Defaults: the differentially heated cavity of Section 3.3
+ * (west Dirichlet T = 1, east Dirichlet T = 0, south/north adiabatic, all
+ * no-slip at rest), Ra = 1e3, Pr = 0.71, Ma = 0.1, dt = half the smallest
+ * cell width, kappa = 1, and the initial state rho = 1, u = v = 0, T linear
+ * in x between the wall temperatures.  Allocates the device state
+ * (2 buffers x 4 fields) on the current CUDA device.  *out receives the
+ * handle.  ERR_ARG on bad sizes or non-ascending faces, ERR_OOM, ERR_CUDA.
+ */
+int rtlbfs_create_mesh(int nx, int ny, const double* xf, const double* yf, int precision,
+                       rtlbfs_t* out);
+
+/*
+ * Physical parameters (Eq. 63 with V_c = Ma, c = 1): nu = V_c L sqrt(Pr/Ra),
+ * chi = nu / Pr, beta_g = V_c^2 / (dT L) with L = xf[nx] - xf[0] and
+ * dT = 1; dt is the macroscopic time step Delta t of Eqs. 41-43 / 57-59.
+ * ERR_ARG unless all are positive.
+ */
+int rtlbfs_set_params(rtlbfs_t h, double Ra, double Pr, double Ma, double dt);
+
+/*
+ * As rtlbfs_set_params with an explicit reference length L (e.g. the
+ * height of a Rayleigh-Benard box), temperature difference dT and
+ * reference temperature T_ref of the Boussinesq term (Eq. 64).
+ */
+int rtlbfs_set_params_ref(rtlbfs_t h, double Ra, double Pr, double Ma, double dt, double L,
+                          double dT, double T_ref);
+
+/*
+ * Lattice spacing of the reconstructed unit lattice (Fig. 2): each face
+ * uses dt_f = kappa * min(width of its two cells normal to the face), and
+ * tau_f = nu / (c_s^2 dt_f) + 1/2, tau_g = chi / (c_s^2 dt_f) + 1/2
+ * (Eqs. 9-10).  kappa = 1 reproduces the paper's dt_f = dx = 1 runs.
+ * ERR_ARG unless kappa > 0.
+ */
+int rtlbfs_set_lattice(rtlbfs_t h, double kappa);
+
+/*
+ * Boundary condition of one side (RTLBFS_WEST..NORTH): kind is
+ * RTLBFS_WALL_DIRICHLET (wall at temperature T_wall), RTLBFS_WALL_ADIABATIC
+ * or RTLBFS_PERIODIC (must be set on both opposite sides before stepping);
+ * u_wall is the wall's tangential velocity (0 = no-slip at rest).
+ * Walls are ghost cells mirroring the adjacent cell; every wall face
+ * carries zero mass flux.  ERR_ARG on a bad side or kind.
+ */
+int rtlbfs_set_bc(rtlbfs_t h, int side, int kind, double T_wall, double u_wall);
+
+/* Body force per unit mass (fx, fy) added to the momentum source. */
+int rtlbfs_set_body_force(rtlbfs_t h, double fx, double fy);
+
+/*
+ * Override the parameter mapping: kinematic viscosity nu, thermal
+ * diffusivity chi and buoyancy coefficient beta_g (0 switches buoyancy
+ * off).  ERR_ARG unless nu > 0, chi > 0.
+ */
+int rtlbfs_set_physics(rtlbfs_t h, double nu, double chi, double beta_g);
+
+/*
+ * Copy a host state in (rho, u, v, T: ny*nx doubles each, caller-owned)
+ * and reset the step counter and residual.  In FP32 mode the fields are
+ * rounded to float, rho stored as rho - 1.
+ */
+int rtlbfs_set_state(rtlbfs_t h, const double* rho, const double* u, const double* v,
+                     const double* T);
+
+/* Copy the current state out to host arrays (ny*nx doubles each). */
+int rtlbfs_get_state(rtlbfs_t h, double* rho, double* u, double* v, double* T);
+
+/*
+ * Advance exactly nsteps explicit steps (no convergence stop).  The steps
+ * run as CUDA-graph replays on the handle's stream; the call returns after
+ * they complete.  ERR_DIVERGED if the residual became non-finite (the
+ * state is then left at the first non-finite step).
+ */
+int rtlbfs_step(rtlbfs_t h, long nsteps);
+
+/*
+ * Step until max(R_u, R_T) < tol, checked after every step on the device,
+ * where R_u = ||(|u|^{n+1} - |u|^n)||_2 / ||(|u|^{n+1})||_2 and R_T the
+ * same for T (L2 analogue of Eq. 65).  Stops exactly at the first step that
+ * meets tol.  max_steps bounds the steps of this call; timeout_s (<= 0: no
+ * limit) bounds its wall time, checked between chunks of steps.  Writes
+ * the steps taken by this call and the last (R_u, R_T) if the pointers are
+ * non-null.  Returns OK, ERR_NOT_CONVERGED, ERR_TIMEOUT or ERR_DIVERGED.
+ */
+int rtlbfs_run_to_steady(rtlbfs_t h, double tol, long max_steps, double timeout_s,
+                         long* steps_taken, double* residual);
+
+/* Residual (R_u, R_T) of the last step and the total step count. */
+int rtlbfs_residual(rtlbfs_t h, double* res2, long* steps);
+
+/*
+ * Nusselt number of the current state, summed in FP64 on the device:
+ * which = RTLBFS_NU_WEST..NORTH: the corrector's energy flux (Eq. 59 brace)
+ * through that wall's faces times the face areas, / (chi dT); RTLBFS_NU_AVG:
+ * Eq. 69 by the midpoint rule with Green-Gauss dT/dx; RTLBFS_NU_HALF: the
+ * energy flux through the x-face column i = nx/2 (requires nx even).
+ */
+int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch's current stream) for
+ * all later work of the handle; NULL restores the handle's own stream. */
+int rtlbfs_set_stream(rtlbfs_t h, void* stream);
+
+/* Wait for the handle's stream. */
+int rtlbfs_sync(rtlbfs_t h);
+
+/* Message of the last failure on h (static storage of the handle). */
+const char* rtlbfs_last_error(rtlbfs_t h);
+
+/* Free every device and host resource of h; NULL is ignored. */
+void rtlbfs_destroy(rtlbfs_t h);
+
+/* Number of kernel launches issued by the library since load (for the
+ * benchmark's launch count). */
+long long rtlbfs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTLBFS_H */

@@ -1,0 +1,217 @@
+"""ctypes binding of ``include/rtlbfs.h`` (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/librtlbfs.so``;
+this module only converts numpy arrays to pointers and status codes to
+exceptions.  There is no CPU fallback: if the library cannot be built or
+loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_STATE = (
+    -1, -2, -3, -4, -5, -6, -7)
+FP64, FP32 = 0, 1
+WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
+WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC = 0, 1, 2
+NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
+
+HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
+
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rtlbfs_tanh_faces": (C.c_int, [C.c_int, C.c_double, C.c_double, _dp]),
+    "rtlbfs_create_mesh": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_int, C.POINTER(_vp)]),
+    "rtlbfs_set_params": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs_set_params_ref": (C.c_int, [_vp] + [C.c_double] * 7),
+    "rtlbfs_set_lattice": (C.c_int, [_vp, C.c_double]),
+    "rtlbfs_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double]),
+    "rtlbfs_set_body_force": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "rtlbfs_set_physics": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs_set_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "rtlbfs_get_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "rtlbfs_step": (C.c_int, [_vp, C.c_long]),
+    "rtlbfs_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_long, C.c_double,
+                                       C.POINTER(C.c_long), _dp]),
+    "rtlbfs_residual": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
+    "rtlbfs_nusselt": (C.c_int, [_vp, C.c_int, _dp]),
+    "rtlbfs_set_stream": (C.c_int, [_vp, _vp]),
+    "rtlbfs_sync": (C.c_int, [_vp]),
+    "rtlbfs_last_error": (C.c_char_p, [_vp]),
+    "rtlbfs_destroy": (None, [_vp]),
+    "rtlbfs_launch_count": (C.c_longlong, []),
+}
+
+
+class RTLBFSError(RuntimeError):
+    def __init__(self, rc: int, msg: str):
+        super().__init__(f"rtlbfs error {rc}: {msg}")
+        self.rc = rc
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_needed: bool = True):
+    """Load the CUDA library (building it first if stale and nvcc exists)."""
+    global _lib
+    if _lib is None:
+        if build_if_needed and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError("librtlbfs.so is not built; run paper_2202_13449_gb300.build")
+        L = C.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in the public header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtlbfs_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, n: int) -> np.ndarray:
+    out = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if out.size != n:
+        raise ValueError(f"expected {n} values, got {out.size}")
+    return out
+
+
+def tanh_faces(n: int, L: float, phi: float) -> np.ndarray:
+    """Eq. 74 face coordinates from the library (host-only entry point)."""
+    out = np.empty(n + 1)
+    rc = lib().rtlbfs_tanh_faces(int(n), float(L), float(phi), _ptr(out))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs_tanh_faces")
+    return out
+
+
+def launch_count() -> int:
+    return int(lib().rtlbfs_launch_count())
+
+
+class Solver:
+    """One cavity on the GPU (a handle of ``include/rtlbfs.h``)."""
+
+    def __init__(self, xf, yf, precision: int = FP64):
+        L = lib()
+        self.xf = np.ascontiguousarray(xf, dtype=np.float64)
+        self.yf = np.ascontiguousarray(yf, dtype=np.float64)
+        self.nx, self.ny = len(self.xf) - 1, len(self.yf) - 1
+        self.precision = precision
+        h = _vp()
+        rc = L.rtlbfs_create_mesh(self.nx, self.ny, _ptr(self.xf), _ptr(self.yf), int(precision),
+                                  C.byref(h))
+        if rc:
+            raise RTLBFSError(rc, "rtlbfs_create_mesh")
+        self._h = h
+
+    # -- helpers
+    def _check(self, rc: int, what: str):
+        if rc:
+            msg = lib().rtlbfs_last_error(self._h)
+            raise RTLBFSError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rtlbfs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration
+    def set_params(self, Ra, Pr, Ma, dt):
+        self._check(lib().rtlbfs_set_params(self._h, Ra, Pr, Ma, dt), "set_params")
+
+    def set_params_ref(self, Ra, Pr, Ma, dt, L, dT=1.0, T_ref=0.5):
+        self._check(lib().rtlbfs_set_params_ref(self._h, Ra, Pr, Ma, dt, L, dT, T_ref),
+                    "set_params_ref")
+
+    def set_lattice(self, kappa):
+        self._check(lib().rtlbfs_set_lattice(self._h, kappa), "set_lattice")
+
+    def set_bc(self, side, kind, T_wall=0.0, u_wall=0.0):
+        self._check(lib().rtlbfs_set_bc(self._h, side, kind, T_wall, u_wall), "set_bc")
+
+    def set_body_force(self, fx, fy):
+        self._check(lib().rtlbfs_set_body_force(self._h, fx, fy), "set_body_force")
+
+    def set_physics(self, nu, chi, beta_g):
+        self._check(lib().rtlbfs_set_physics(self._h, nu, chi, beta_g), "set_physics")
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None."""
+        ptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self._check(lib().rtlbfs_set_stream(self._h, ptr), "set_stream")
+
+    # -- state
+    def set_state(self, rho, u, v, T):
+        n = self.nx * self.ny
+        arrs = [_f64(a, n) for a in (rho, u, v, T)]
+        self._check(lib().rtlbfs_set_state(self._h, *[_ptr(a) for a in arrs]), "set_state")
+
+    def get_state(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        self._check(lib().rtlbfs_get_state(self._h, *[_ptr(a) for a in out]), "get_state")
+        return tuple(out)
+
+    # -- stepping
+    def step(self, n: int):
+        self._check(lib().rtlbfs_step(self._h, int(n)), "step")
+
+    def run_to_steady(self, tol: float, max_steps: int, timeout_s: float = 0.0):
+        """Returns (rc, steps_taken, (R_u, R_T)); rc 0 = converged."""
+        steps = C.c_long(0)
+        res = np.full(2, np.nan)
+        rc = lib().rtlbfs_run_to_steady(self._h, float(tol), int(max_steps), float(timeout_s),
+                                        C.byref(steps), _ptr(res))
+        if rc not in (OK, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_DIVERGED):
+            self._check(rc, "run_to_steady")
+        return rc, int(steps.value), (float(res[0]), float(res[1]))
+
+    def residual(self):
+        res = np.full(2, np.nan)
+        steps = C.c_long(0)
+        self._check(lib().rtlbfs_residual(self._h, _ptr(res), C.byref(steps)), "residual")
+        return (float(res[0]), float(res[1])), int(steps.value)
+
+    def nusselt(self, which: int) -> float:
+        out = np.empty(1)
+        self._check(lib().rtlbfs_nusselt(self._h, int(which), _ptr(out)), "nusselt")
+        return float(out[0])
+
+    def sync(self):
+        self._check(lib().rtlbfs_sync(self._h), "sync")

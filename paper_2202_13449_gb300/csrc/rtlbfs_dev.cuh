@@ -1,0 +1,207 @@
+// rtlbfs_dev.cuh -- device-side data layout and the per-face arithmetic of
+// RTLBFS (arXiv 2202.13449, Section 3.2), templated on the storage type R
+// (double for the FP64 path, float for the FP32 bulk path).
+//
+// Every field is stored as (drho = rho - 1, u, v, T); in FP32 this keeps the
+// weakly compressible density perturbation in the mantissa, and the pressure
+// part c_s^2 rho of the momentum flux is formed from drho (the constant
+// c_s^2 * 1 cancels in every flux difference because the face areas of a
+// closed rectilinear cell sum to zero).
+#pragma once
+
+#include <cstdint>
+
+namespace rtlbfs {
+
+constexpr int kSideW = 0, kSideE = 1, kSideS = 2, kSideN = 3;
+constexpr int kDirichlet = 0, kAdiabatic = 1, kPeriodic = 2;
+
+// Status of a cavity's run, written by the device.
+constexpr int kRunning = 0, kConverged = 1, kMaxSteps = 2, kDiverged = 3;
+
+// Constants of one line of faces normal to an axis (all faces of an x-face
+// column share them): lattice spacing h = kappa*min(wL, wR) (per-face dt of
+// the reconstructed lattice), node offsets, transport coefficients.
+template <typename R>
+struct FaceLine {
+    R h;       // lattice spacing dt_f
+    R cL;      // wL - h : normal offset of node a = -1 from the left centre
+    R cR;      // h - wR : normal offset of node a = +1 from the right centre
+    R wL, wR;  // half widths of the two cells (centre-to-face distances)
+    R nu_2h;   // nu / (2 h): viscous term with a central difference over 2h
+    R chi_2h;  // chi / (2 h)
+    R tf15;    // tau_f - 1.5 = nu / (cs2 h) - 1   (Eqs. 9, 58)
+    R tg15;    // tau_g - 1.5 = chi / (cs2 h) - 1  (Eqs. 10, 59)
+};
+
+// Constants of one line of cells along an axis, ghosts included.
+template <typename R>
+struct CellLine {
+    R w;      // cell width (ghost: partner's width, periodic: opposite cell's)
+    R inv_w;  // 1 / width (Eq. 55: 1/dV times the face area)
+    R dt_w;   // Delta t / width
+    R a_next; // Eq. 56 weight of this cell in the face it shares with the
+              // next cell: w_next / (w + w_next)
+};
+
+// Read-only description of one cavity (one mesh) on the device.
+struct CavityDesc {
+    int nx, ny, pitch, ntiles;    // cells, row stride (elements), tiles of this cavity
+    int kind[4];                  // boundary kind per side W,E,S,N
+    int tiles_x, tiles_y, tile_begin, pad0;
+    double bcT[4], bcU[4];        // wall temperature, tangential wall velocity
+    double beta_g, T_ref, fx, fy, dt, dT, nu, chi;
+    void* f[2][4];                // two buffers of (drho, u, v, T)
+    const void* xline;            // FaceLine<R>[nx+1]
+    const void* yline;            // FaceLine<R>[ny+1]
+    const void* xcell;            // CellLine<R>[nx+4], index i+2 for cell i in [-2, nx+1]
+    const void* ycell;            // CellLine<R>[ny+4]
+};
+
+// Mutable per-cavity run control (device-written between steps).
+struct CavityCtl {
+    int cur;                  // buffer holding the current state
+    int done;                 // 1: this cavity takes no more steps
+    int status;               // kRunning, kConverged, kMaxSteps, kDiverged
+    unsigned int arrive;      // tiles of this cavity finished in this step
+    long long steps;          // steps taken since the last state upload
+    long long max_steps;      // done when steps reaches this
+    double tol;               // done when max(R_u, R_T) < tol (tol < 0: never)
+    double res[2];            // (R_u, R_T) of the last step
+    double acc[4];            // running sums of this step: sum (d|u|)^2, |u|^2, (dT)^2, T^2
+};
+
+template <typename R>
+struct Vec4 {
+    R x, y, z, w;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ R rconst(double v) { return static_cast<R>(v); }
+
+// -------------------------------------------------------------------------
+// One face in its own frame: normal n (the "x" of a node (a, b)), tangent t.
+// q[] = (drho, u_n, u_t, T) of a cell, gn/gt its gradients along n and t.
+// -------------------------------------------------------------------------
+template <typename R>
+struct CellNT {
+    R q[4];
+    R gn[4];
+    R gt[4];
+};
+
+// Eqs. 29, 46-48 and the braces of Eqs. 57-59 for one face.  Output
+// F = (mass, normal momentum, tangential momentum, energy) flux through the
+// face along +n, with the constant c_s^2 dropped from the normal momentum
+// flux (see the file comment).  wall: the face lies on a wall whose
+// tangential velocity is u_wall_t.
+//
+// Node values.  A cell's reconstruction plane restricted to a column of
+// nodes a = const is linear in b, so the three columns are c_a + b s_a:
+//   a = -1: left plane,  a = +1: right plane,  a = 0: mean of both (Eq. 29).
+// Central differences on the 9 nodes, written without the powers of h that
+// cancel in Eqs. 46-48 (d_x ~ 2h D_x, d_xx ~ h^2 D_xx, d_xy ~ 4h^2 D_xy).
+template <typename R>
+__device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& Rc,
+                                          const FaceLine<R>& fl, bool wall, R u_wall_t,
+                                          R F[4])
+{
+    const R half = rconst<R>(0.5);
+    const R one = rconst<R>(1.0);
+    const R cs2 = rconst<R>(1.0 / 3.0);
+    const R hh = fl.h * half;
+    R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = L.q[k] + L.gn[k] * fl.cL;
+        Sa[k] = L.gt[k] * fl.h;
+        B[k] = Rc.q[k] + Rc.gn[k] * fl.cR;
+        Sb[k] = Rc.gt[k] * fl.h;
+        M[k] = half * ((L.q[k] + L.gn[k] * fl.wL) + (Rc.q[k] - Rc.gn[k] * fl.wR));
+        Sm[k] = hh * (L.gt[k] + Rc.gt[k]);
+    }
+    // plus nodes: c = (0,0), w = (-1,0), e = (+1,0), s = (0,-1), n = (0,+1)
+    const R r0 = one + M[0], n0 = M[1], t0 = M[2], T0 = M[3];
+    const R rw = one + A[0], nw = A[1], tw = A[2], Tw = A[3];
+    const R re = one + B[0], ne = B[1], te = B[2], Te = B[3];
+    const R rs = one + (M[0] - Sm[0]), ns = M[1] - Sm[1], ts = M[2] - Sm[2], Ts = M[3] - Sm[3];
+    const R rn = one + (M[0] + Sm[0]), nn = M[1] + Sm[1], tn = M[2] + Sm[2], Tn = M[3] + Sm[3];
+
+    // node products (only those the predictor and the flux use)
+    const R mn0 = r0 * n0, mt0 = r0 * t0, E0 = r0 * T0;
+    const R Pnn0 = mn0 * n0, Pnt0 = mn0 * t0, Ptt0 = mt0 * t0, Qn0 = mn0 * T0, Qt0 = mt0 * T0;
+    const R mnw = rw * nw, mtw = rw * tw, Ew = rw * Tw, Pnnw = mnw * nw, Pntw = mnw * tw, Qnw = mnw * Tw;
+    const R mne = re * ne, mte = re * te, Ee = re * Te, Pnne = mne * ne, Pnte = mne * te, Qne = mne * Te;
+    const R mns = rs * ns, mts = rs * ts, Es = rs * Ts, Pnts = mns * ts, Ptts = mts * ts, Qts = mts * Ts;
+    const R mnn = rn * nn, mtn = rn * tn, En = rn * Tn, Pntn = mnn * tn, Pttn = mtn * tn, Qtn = mtn * Tn;
+    // corners (a, b): only rho u_n, rho u_t and rho u_n u_t enter (through d_xy)
+    R mnc[4], mtc[4], Pntc[4];  // order (-1,-1), (-1,+1), (+1,-1), (+1,+1)
+    {
+        const R rc[4] = {one + (A[0] - Sa[0]), one + (A[0] + Sa[0]), one + (B[0] - Sb[0]),
+                         one + (B[0] + Sb[0])};
+        const R nc[4] = {A[1] - Sa[1], A[1] + Sa[1], B[1] - Sb[1], B[1] + Sb[1]};
+        const R tc[4] = {A[2] - Sa[2], A[2] + Sa[2], B[2] - Sb[2], B[2] + Sb[2]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mnc[k] = rc[k] * nc[k];
+            mtc[k] = rc[k] * tc[k];
+            Pntc[k] = mnc[k] * tc[k];
+        }
+    }
+    const R two = rconst<R>(2.0);
+    // central differences
+    const R dx_mn = mne - mnw, dx_mt = mte - mtw, dx_E = Ee - Ew;
+    const R dy_mn = mnn - mns, dy_mt = mtn - mts;
+    const R dx_dr = B[0] - A[0];
+    const R dy_dr = two * Sm[0];
+    const R dxx_dr = (B[0] + A[0]) - two * M[0];
+    const R dxx_Pnn = (Pnne + Pnnw) - two * Pnn0;
+    const R dyy_Ptt = (Pttn + Ptts) - two * Ptt0;
+    const R dxy_Pnt = (Pntc[3] - Pntc[2]) - (Pntc[1] - Pntc[0]);
+    const R dxy_mn = (mnc[3] - mnc[2]) - (mnc[1] - mnc[0]);
+    const R dxy_mt = (mtc[3] - mtc[2]) - (mtc[1] - mtc[0]);
+    const R dxx_mn = (mne + mnw) - two * mn0, dyy_mn = (mnn + mns) - two * mn0;
+    const R dxx_mt = (mte + mtw) - two * mt0, dyy_mt = (mtn + mts) - two * mt0;
+    const R dxx_E = (Ee + Ew) - two * E0, dyy_E = (En + Es) - two * E0;
+    const R quarter = rconst<R>(0.25);
+    const R hcs2 = rconst<R>(0.5 / 3.0);  // c_s^2 / 2
+
+    // Eq. 46: rho* (as drho*)
+    const R drs = M[0] - half * (dx_mn + dy_mt) +
+                  half * (dxx_Pnn + cs2 * dxx_dr + dyy_Ptt) + quarter * dxy_Pnt;
+    // Eq. 47: (rho u_n)*, (rho u_t)*
+    R mns_ = mn0 - half * ((Pnne - Pnnw) + cs2 * dx_dr + (Pntn - Pnts)) +
+             hcs2 * (rconst<R>(3.0) * dxx_mn + dyy_mn + half * dxy_mt);
+    R mts_ = mt0 - half * ((Pnte - Pntw) + (Pttn - Ptts) + cs2 * dy_dr) +
+             hcs2 * (dxx_mt + rconst<R>(3.0) * dyy_mt + half * dxy_mn);
+    // Eq. 48: (rho T)*
+    const R Es_ = E0 - half * ((Qne - Qnw) + (Qtn - Qts)) + hcs2 * (dxx_E + dyy_E);
+
+    const R rho_s = one + drs;
+    if (wall) {  // no mass through a wall; the wall's tangential velocity
+        mns_ = rconst<R>(0.0);
+        mts_ = rho_s * u_wall_t;
+    }
+    const R inv = one / rho_s;
+    const R uns = mns_ * inv, uts = mts_ * inv, Tst = Es_ * inv;
+
+    // Eqs. 57-59 braces along the face normal
+    F[0] = mns_;
+    const R Xnn0 = Pnn0 + cs2 * M[0];
+    F[1] = Xnn0 - fl.nu_2h * (rconst<R>(3.0) * dx_mn + dy_mt) -
+           fl.tf15 * ((mns_ * uns + cs2 * drs) - Xnn0);
+    F[2] = Pnt0 - fl.nu_2h * (dx_mt + dy_mn) - fl.tf15 * (mns_ * uts - Pnt0);
+    F[3] = Qn0 - fl.chi_2h * dx_E - fl.tg15 * (mns_ * Tst - Qn0);
+    (void)Qt0;
+}
+
+// Parity of quantity k (0 drho, 1 u, 2 v, 3 T) about a wall of side s:
+// +1 even (mirror value), -1 odd about the wall value.
+__host__ __device__ __forceinline__ int wall_parity(int kind, int k)
+{
+    if (k == 0) return +1;
+    if (k == 1 || k == 2) return -1;
+    return kind == kDirichlet ? -1 : +1;
+}
+
+}  // namespace rtlbfs

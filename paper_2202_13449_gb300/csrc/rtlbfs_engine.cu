@@ -1,0 +1,594 @@
+// rtlbfs_engine.cu -- host side of the solver: per-cavity mesh lines, device
+// buffers, the tile list of the batched step kernel, CUDA graphs of step
+// launches, run control and the FP64 reductions.
+#include "rtlbfs_engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "rtlbfs.h"
+
+namespace rtlbfs {
+
+std::atomic<long long> g_launches{0};
+
+namespace {
+constexpr int kGraphChunk = 64;  // step launches per captured graph
+constexpr int kPartialMax = 2048;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Width of cell i in [-2, n+1] of a line with walls or periodic ends
+// (ghosts: a wall ghost has its partner's width; a periodic ghost the
+// opposite cell's).
+double line_width(const std::vector<double>& f, int i, bool periodic)
+{
+    const int n = (int)f.size() - 1;
+    int k = i;
+    if (periodic) {
+        k = ((i % n) + n) % n;
+    } else {
+        if (i < 0) k = -1 - i;        // -1 -> 0, -2 -> 1 (beyond the ghost: unused)
+        if (i >= n) k = 2 * n - 1 - i; // n -> n-1, n+1 -> n-2
+        k = std::min(std::max(k, 0), n - 1);
+    }
+    return f[k + 1] - f[k];
+}
+
+template <typename R>
+void build_lines(const Cavity& c, const std::vector<double>& f, bool periodic, double kappa,
+                 double nu, double chi, double dt, std::vector<FaceLine<R>>& fl,
+                 std::vector<CellLine<R>>& cl)
+{
+    const int n = (int)f.size() - 1;
+    (void)c;
+    fl.resize(n + 1);
+    for (int i = 0; i <= n; ++i) {
+        const double wl = line_width(f, i - 1, periodic), wr = line_width(f, i, periodic);
+        const double h = kappa * std::min(wl, wr);
+        FaceLine<R> x;
+        x.h = (R)h;
+        x.cL = (R)(0.5 * wl - h);
+        x.cR = (R)(h - 0.5 * wr);
+        x.wL = (R)(0.5 * wl);
+        x.wR = (R)(0.5 * wr);
+        x.nu_2h = (R)(nu / (2.0 * h));
+        x.chi_2h = (R)(chi / (2.0 * h));
+        x.tf15 = (R)(3.0 * nu / h - 1.0);
+        x.tg15 = (R)(3.0 * chi / h - 1.0);
+        fl[i] = x;
+    }
+    cl.resize(n + 4);
+    for (int i = -2; i <= n + 1; ++i) {
+        const double w = line_width(f, i, periodic), wn = line_width(f, i + 1, periodic);
+        CellLine<R> y;
+        y.w = (R)w;
+        y.inv_w = (R)(1.0 / w);
+        y.dt_w = (R)(dt / w);
+        y.a_next = (R)(wn / (w + wn));
+        cl[i + 2] = y;
+    }
+}
+}  // namespace
+
+Engine::Engine(int precision, int capacity)
+    : precision_(precision), capacity_(capacity),
+      rsize_(precision == RTLBFS_FP64 ? sizeof(double) : sizeof(float))
+{
+}
+
+Engine::~Engine()
+{
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    for (auto& c : slots_) {
+        if (c.d_fields) cudaFree(c.d_fields);
+        if (c.d_lines) cudaFree(c.d_lines);
+    }
+    cudaFree(d_desc_);
+    cudaFree(d_ctl_);
+    cudaFree(d_tiles_);
+    cudaFree(d_ntiles_);
+    cudaFree(d_partial_);
+    cudaFree(d_scalar_);
+    cudaFree(d_stage_);
+    if (h_scalar_) cudaFreeHost(h_scalar_);
+    if (own_stream_) cudaStreamDestroy(own_stream_);
+}
+
+int Engine::fail(int code, const std::string& msg)
+{
+    err_ = msg;
+    return code;
+}
+
+int Engine::cuda_fail(cudaError_t e, const char* what)
+{
+    err_ = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RTLBFS_ERR_OOM : RTLBFS_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+int Engine::init()
+{
+    if (precision_ != RTLBFS_FP64 && precision_ != RTLBFS_FP32)
+        return fail(RTLBFS_ERR_ARG, "precision must be RTLBFS_FP64 or RTLBFS_FP32");
+    if (capacity_ < 1) return fail(RTLBFS_ERR_ARG, "capacity must be >= 1");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
+    CK(step_prepare(precision_));
+    CK(step_occupancy(precision_, &occ_));
+    if (occ_ < 1) return fail(RTLBFS_ERR_CUDA, "step kernel does not fit on an SM");
+    CK(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
+    stream_ = own_stream_;
+    slots_.resize(capacity_);
+    h_desc_.resize(capacity_);
+    std::memset(h_desc_.data(), 0, sizeof(CavityDesc) * capacity_);
+    CK(cudaMalloc(&d_desc_, sizeof(CavityDesc) * capacity_));
+    CK(cudaMalloc(&d_ctl_, sizeof(CavityCtl) * capacity_));
+    CK(cudaMemset(d_ctl_, 0, sizeof(CavityCtl) * capacity_));
+    std::vector<CavityCtl> c0(capacity_);
+    for (auto& c : c0) {
+        std::memset(&c, 0, sizeof(c));
+        c.done = 1;
+        c.tol = -1.0;
+        c.res[0] = c.res[1] = INFINITY;
+    }
+    CK(cudaMemcpy(d_ctl_, c0.data(), sizeof(CavityCtl) * capacity_, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d_ntiles_, sizeof(int)));
+    CK(cudaMemset(d_ntiles_, 0, sizeof(int)));
+    partial_cap_ = kPartialMax;
+    CK(cudaMalloc(&d_partial_, sizeof(double) * partial_cap_));
+    CK(cudaMalloc(&d_scalar_, sizeof(double) * 8));
+    CK(cudaMallocHost(&h_scalar_, sizeof(double) * 8));
+    return RTLBFS_OK;
+}
+
+size_t Engine::bytes_for(int precision, int nx, int ny)
+{
+    const size_t rs = precision == RTLBFS_FP64 ? 8 : 4;
+    const size_t pitch = align_up((size_t)nx, 32);
+    const size_t fields = 8 * rs * pitch * (size_t)ny;
+    const size_t lines = (2 * (nx + ny) + 12) * (sizeof(FaceLine<double>) + sizeof(CellLine<double>)) + 8 * 256;
+    return fields + lines;
+}
+
+Cavity* Engine::cavity(int slot)
+{
+    if (slot < 0 || slot >= capacity_ || !slots_[slot].active) return nullptr;
+    return &slots_[slot];
+}
+
+int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_out)
+{
+    if (nx < 1 || ny < 1 || !xf || !yf) return fail(RTLBFS_ERR_ARG, "bad mesh size or null faces");
+    if ((long long)nx * ny > (1LL << 31)) return fail(RTLBFS_ERR_ARG, "mesh too large");
+    for (int i = 0; i < nx; ++i)
+        if (!(xf[i + 1] > xf[i])) return fail(RTLBFS_ERR_ARG, "xf must be strictly ascending");
+    for (int j = 0; j < ny; ++j)
+        if (!(yf[j + 1] > yf[j])) return fail(RTLBFS_ERR_ARG, "yf must be strictly ascending");
+    int slot = -1;
+    for (int k = 0; k < capacity_; ++k)
+        if (!slots_[k].active) {
+            slot = k;
+            break;
+        }
+    if (slot < 0) return fail(RTLBFS_ERR_STATE, "no free slot");
+    Cavity c;
+    c.nx = nx;
+    c.ny = ny;
+    c.pitch = (int)align_up((size_t)nx, 32);
+    c.xf.assign(xf, xf + nx + 1);
+    c.yf.assign(yf, yf + ny + 1);
+    double wmin = 1e300;
+    for (int i = 0; i < nx; ++i) wmin = std::min(wmin, xf[i + 1] - xf[i]);
+    for (int j = 0; j < ny; ++j) wmin = std::min(wmin, yf[j + 1] - yf[j]);
+    c.dt = 0.5 * wmin;
+    c.Lref = 0.0;  // 0: the domain width in x
+    c.fields_bytes = 8 * rsize_ * (size_t)c.pitch * ny;
+    // line layout: R lines, then FP64 lines, each block 256-byte aligned
+    const size_t fr = precision_ == RTLBFS_FP64 ? sizeof(FaceLine<double>) : sizeof(FaceLine<float>);
+    const size_t cr = precision_ == RTLBFS_FP64 ? sizeof(CellLine<double>) : sizeof(CellLine<float>);
+    size_t off = 0;
+    c.off_xl = off; off = align_up(off + fr * (nx + 1), 256);
+    c.off_yl = off; off = align_up(off + fr * (ny + 1), 256);
+    c.off_xc = off; off = align_up(off + cr * (nx + 4), 256);
+    c.off_yc = off; off = align_up(off + cr * (ny + 4), 256);
+    c.off_xld = off; off = align_up(off + sizeof(FaceLine<double>) * (nx + 1), 256);
+    c.off_yld = off; off = align_up(off + sizeof(FaceLine<double>) * (ny + 1), 256);
+    c.off_xcd = off; off = align_up(off + sizeof(CellLine<double>) * (nx + 4), 256);
+    c.off_ycd = off; off = align_up(off + sizeof(CellLine<double>) * (ny + 4), 256);
+    c.lines_bytes = off;
+    cudaError_t e = cudaMalloc(&c.d_fields, c.fields_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fields)");
+    e = cudaMalloc(&c.d_lines, c.lines_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(c.d_fields);
+        return cuda_fail(e, "cudaMalloc(lines)");
+    }
+    e = cudaMemsetAsync(c.d_fields, 0, c.fields_bytes, stream_);
+    if (e != cudaSuccess) {
+        cudaFree(c.d_fields);
+        cudaFree(c.d_lines);
+        return cuda_fail(e, "cudaMemset(fields)");
+    }
+    c.active = true;
+    c.dirty = true;
+    slots_[slot] = std::move(c);
+    tiles_dirty_ = true;
+    // reset the slot's run control: nothing to do until armed
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.done = 1;
+    z.tol = -1.0;
+    z.res[0] = z.res[1] = INFINITY;
+    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    *slot_out = slot;
+    return RTLBFS_OK;
+}
+
+int Engine::remove(int slot)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    CK(cudaStreamSynchronize(stream_));
+    cudaFree(c->d_fields);
+    cudaFree(c->d_lines);
+    slots_[slot] = Cavity();
+    tiles_dirty_ = true;
+    return RTLBFS_OK;
+}
+
+void Engine::touch(int slot)
+{
+    if (Cavity* c = cavity(slot)) c->dirty = true;
+}
+
+int Engine::resolve_params(Cavity& c)
+{
+    const double L = c.Lref > 0.0 ? c.Lref : (c.xf.back() - c.xf.front());
+    if (c.from_ra) {
+        if (!(c.Ra > 0 && c.Pr > 0 && c.Ma > 0 && c.dT > 0))
+            return fail(RTLBFS_ERR_ARG, "Ra, Pr, Ma and dT must be positive");
+        const double Vc = c.Ma;  // V_c = Ma * c with c = 1
+        c.nu = Vc * L * std::sqrt(c.Pr / c.Ra);
+        c.chi = c.nu / c.Pr;
+        c.beta_g = Vc * Vc / (c.dT * L);
+    }
+    if (!(c.nu > 0 && c.chi > 0)) return fail(RTLBFS_ERR_ARG, "nu and chi must be positive");
+    if (!(c.dt > 0) || !(c.kappa > 0)) return fail(RTLBFS_ERR_ARG, "dt and kappa must be positive");
+    const bool xp = c.kind[kSideW] == kPeriodic, xp2 = c.kind[kSideE] == kPeriodic;
+    const bool yp = c.kind[kSideS] == kPeriodic, yp2 = c.kind[kSideN] == kPeriodic;
+    if (xp != xp2 || yp != yp2)
+        return fail(RTLBFS_ERR_ARG, "periodic sides must come in opposite pairs");
+    return RTLBFS_OK;
+}
+
+int Engine::upload_lines(int slot)
+{
+    Cavity& c = slots_[slot];
+    int rc = resolve_params(c);
+    if (rc) return rc;
+    const bool xp = c.kind[kSideW] == kPeriodic, yp = c.kind[kSideS] == kPeriodic;
+    std::vector<unsigned char> buf(c.lines_bytes, 0);
+    auto put = [&](size_t off, const void* src, size_t n) { std::memcpy(buf.data() + off, src, n); };
+    {
+        std::vector<FaceLine<double>> fx, fy;
+        std::vector<CellLine<double>> cx, cy;
+        build_lines<double>(c, c.xf, xp, c.kappa, c.nu, c.chi, c.dt, fx, cx);
+        build_lines<double>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy);
+        put(c.off_xld, fx.data(), fx.size() * sizeof(fx[0]));
+        put(c.off_yld, fy.data(), fy.size() * sizeof(fy[0]));
+        put(c.off_xcd, cx.data(), cx.size() * sizeof(cx[0]));
+        put(c.off_ycd, cy.data(), cy.size() * sizeof(cy[0]));
+        if (precision_ == RTLBFS_FP64) {
+            put(c.off_xl, fx.data(), fx.size() * sizeof(fx[0]));
+            put(c.off_yl, fy.data(), fy.size() * sizeof(fy[0]));
+            put(c.off_xc, cx.data(), cx.size() * sizeof(cx[0]));
+            put(c.off_yc, cy.data(), cy.size() * sizeof(cy[0]));
+        }
+    }
+    if (precision_ == RTLBFS_FP32) {
+        std::vector<FaceLine<float>> fx, fy;
+        std::vector<CellLine<float>> cx, cy;
+        build_lines<float>(c, c.xf, xp, c.kappa, c.nu, c.chi, c.dt, fx, cx);
+        build_lines<float>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy);
+        put(c.off_xl, fx.data(), fx.size() * sizeof(fx[0]));
+        put(c.off_yl, fy.data(), fy.size() * sizeof(fy[0]));
+        put(c.off_xc, cx.data(), cx.size() * sizeof(cx[0]));
+        put(c.off_yc, cy.data(), cy.size() * sizeof(cy[0]));
+    }
+    // synchronous copy: buf is pageable and about to go out of scope
+    CK(cudaStreamSynchronize(stream_));
+    CK(cudaMemcpy(c.d_lines, buf.data(), c.lines_bytes, cudaMemcpyHostToDevice));
+
+    CavityDesc& d = h_desc_[slot];
+    std::memset(&d, 0, sizeof(d));
+    d.nx = c.nx;
+    d.ny = c.ny;
+    d.pitch = c.pitch;
+    for (int s = 0; s < 4; ++s) {
+        d.kind[s] = c.kind[s];
+        d.bcT[s] = c.bcT[s];
+        d.bcU[s] = c.bcU[s];
+    }
+    d.tiles_x = (c.nx + kTileX - 1) / kTileX;
+    d.tiles_y = (c.ny + kTileY - 1) / kTileY;
+    d.ntiles = d.tiles_x * d.tiles_y;
+    d.tile_begin = c.first_tile;
+    d.beta_g = c.beta_g;
+    d.T_ref = c.T_ref;
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.dt = c.dt;
+    d.dT = c.dT;
+    d.nu = c.nu;
+    d.chi = c.chi;
+    const size_t plane = rsize_ * (size_t)c.pitch * c.ny;
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 4; ++k)
+            d.f[b][k] = static_cast<unsigned char*>(c.d_fields) + (size_t)(4 * b + k) * plane;
+    unsigned char* L = static_cast<unsigned char*>(c.d_lines);
+    d.xline = L + c.off_xl;
+    d.yline = L + c.off_yl;
+    d.xcell = L + c.off_xc;
+    d.ycell = L + c.off_yc;
+    CK(cudaMemcpy(&d_desc_[slot], &d, sizeof(d), cudaMemcpyHostToDevice));
+    c.dirty = false;
+    return RTLBFS_OK;
+}
+
+int Engine::rebuild_tiles()
+{
+    std::vector<int4> t;
+    for (int s = 0; s < capacity_; ++s) {
+        Cavity& c = slots_[s];
+        if (!c.active) continue;
+        const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
+        c.first_tile = (int)t.size();
+        c.ntiles = tx * ty;
+        for (int j = 0; j < ty; ++j)
+            for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * kTileY, 0));
+        c.dirty = true;  // tile_begin lives in the descriptor
+    }
+    CK(cudaStreamSynchronize(stream_));
+    if ((int)t.size() > tile_cap_) {
+        cudaFree(d_tiles_);
+        d_tiles_ = nullptr;
+        tile_cap_ = std::max<int>((int)t.size(), 2 * tile_cap_);
+        CK(cudaMalloc(&d_tiles_, sizeof(int4) * tile_cap_));
+        if (gexec_) {  // the graph baked the old tile pointer
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+        }
+    }
+    if (!t.empty()) CK(cudaMemcpy(d_tiles_, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+    ntiles_ = (int)t.size();
+    CK(cudaMemcpy(d_ntiles_, &ntiles_, sizeof(int), cudaMemcpyHostToDevice));
+    tiles_dirty_ = false;
+    return RTLBFS_OK;
+}
+
+int Engine::prepare_launch()
+{
+    if (tiles_dirty_) {
+        int rc = rebuild_tiles();
+        if (rc) return rc;
+    }
+    for (int s = 0; s < capacity_; ++s)
+        if (slots_[s].active && slots_[s].dirty) {
+            int rc = upload_lines(s);
+            if (rc) return rc;
+        }
+    // persistent grid: every SM full, never more blocks than tiles
+    const int full = sms_ * occ_;
+    const int want = std::max(1, std::min(full, std::max(ntiles_, 1)));
+    if (want != grid_ && gexec_) {
+        cudaGraphExecDestroy(gexec_);
+        gexec_ = nullptr;
+    }
+    grid_ = want;
+    return RTLBFS_OK;
+}
+
+int Engine::set_stream(cudaStream_t s)
+{
+    CK(cudaStreamSynchronize(stream_));
+    stream_ = s ? s : own_stream_;
+    return RTLBFS_OK;
+}
+
+int Engine::sync()
+{
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::set_state(int slot, const double* rho, const double* u, const double* v,
+                      const double* T)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if (!rho || !u || !v || !T) return fail(RTLBFS_ERR_ARG, "null state array");
+    if (c->dirty) {
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
+    const size_t n = (size_t)c->nx * c->ny;
+    if (stage_cap_ < 4 * n) {
+        CK(cudaStreamSynchronize(stream_));
+        cudaFree(d_stage_);
+        d_stage_ = nullptr;
+        CK(cudaMalloc(&d_stage_, sizeof(double) * 4 * n));
+        stage_cap_ = 4 * n;
+    }
+    const double* src[4] = {rho, u, v, T};
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(d_stage_ + k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+                           stream_));
+    const CavityDesc& d = h_desc_[slot];
+    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0]));
+    g_launches++;
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.cur = 0;
+    z.done = 1;
+    z.tol = -1.0;
+    z.res[0] = z.res[1] = INFINITY;
+    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
+    CK(cudaStreamSynchronize(stream_));  // z lives on this stack frame
+    return RTLBFS_OK;
+}
+
+int Engine::get_state(int slot, double* rho, double* u, double* v, double* T)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if (!rho || !u || !v || !T) return fail(RTLBFS_ERR_ARG, "null state array");
+    if (c->dirty) {
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
+    CavityCtl ctl;
+    int rc = read_ctl(slot, &ctl);
+    if (rc) return rc;
+    const size_t n = (size_t)c->nx * c->ny;
+    if (stage_cap_ < 4 * n) {
+        cudaFree(d_stage_);
+        d_stage_ = nullptr;
+        CK(cudaMalloc(&d_stage_, sizeof(double) * 4 * n));
+        stage_cap_ = 4 * n;
+    }
+    const CavityDesc& d = h_desc_[slot];
+    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[ctl.cur & 1]));
+    g_launches++;
+    double* dst[4] = {rho, u, v, T};
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(dst[k], d_stage_ + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                           stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::set_conduction_state(int slot)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<double> r(n, 1.0), u(n, 0.0), v(n, 0.0), T(n, c->T_ref);
+    if (c->kind[kSideW] == kDirichlet && c->kind[kSideE] == kDirichlet) {
+        const double x0 = c->xf.front(), Lx = c->xf.back() - c->xf.front();
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                const double s = (0.5 * (c->xf[i] + c->xf[i + 1]) - x0) / Lx;
+                T[(size_t)j * c->nx + i] = c->bcT[kSideW] + (c->bcT[kSideE] - c->bcT[kSideW]) * s;
+            }
+    }
+    return set_state(slot, r.data(), u.data(), v.data(), T.data());
+}
+
+int Engine::arm(int slot, long long nsteps, double tol)
+{
+    if (!cavity(slot)) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if (nsteps < 0) return fail(RTLBFS_ERR_ARG, "negative step count");
+    int rc = prepare_launch();
+    if (rc) return rc;
+    CK(launch_arm(stream_, d_ctl_, slot, nsteps, tol, 0));
+    g_launches++;
+    return RTLBFS_OK;
+}
+
+int Engine::launch_steps(long long launches)
+{
+    int rc = prepare_launch();
+    if (rc) return rc;
+    if (ntiles_ == 0 || launches <= 0) return RTLBFS_OK;
+    long long left = launches;
+    if (left >= kGraphChunk) {
+        if (!gexec_) {
+            cudaStream_t cs = nullptr;
+            CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
+                    e = launch_step(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec_, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) return cuda_fail(e, "capturing the step graph");
+            gchunk_ = kGraphChunk;
+        }
+        while (left >= gchunk_) {
+            CK(cudaGraphLaunch(gexec_, stream_));
+            g_launches += gchunk_;
+            left -= gchunk_;
+        }
+    }
+    for (; left > 0; --left) {
+        CK(launch_step(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
+        g_launches++;
+    }
+    return RTLBFS_OK;
+}
+
+int Engine::read_ctl(int slot, CavityCtl* out)
+{
+    if (slot < 0 || slot >= capacity_) return fail(RTLBFS_ERR_ARG, "no such slot");
+    CK(cudaMemcpyAsync(out, &d_ctl_[slot], sizeof(CavityCtl), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::read_ctls(std::vector<CavityCtl>& out)
+{
+    out.resize(capacity_);
+    CK(cudaStreamSynchronize(stream_));
+    CK(cudaMemcpy(out.data(), d_ctl_, sizeof(CavityCtl) * capacity_, cudaMemcpyDeviceToHost));
+    return RTLBFS_OK;
+}
+
+int Engine::nusselt(int slot, int which, double* out)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if (which < kNuWest || which > kNuHalf) return fail(RTLBFS_ERR_ARG, "bad Nusselt selector");
+    if (which == kNuHalf && (c->nx % 2)) return fail(RTLBFS_ERR_ARG, "Nu_1/2 needs nx even");
+    int rc = prepare_launch();
+    if (rc) return rc;
+    const CavityDesc& d = h_desc_[slot];
+    unsigned char* L = static_cast<unsigned char*>(c->d_lines);
+    NuLines ln;
+    ln.xl = reinterpret_cast<const FaceLine<double>*>(L + c->off_xld);
+    ln.yl = reinterpret_cast<const FaceLine<double>*>(L + c->off_yld);
+    ln.xc = reinterpret_cast<const CellLine<double>*>(L + c->off_xcd);
+    ln.yc = reinterpret_cast<const CellLine<double>*>(L + c->off_ycd);
+    long long count;
+    double scale = 1.0 / (c->chi * c->dT);
+    if (which == kNuWest || which == kNuEast || which == kNuHalf) count = c->ny;
+    else if (which == kNuSouth || which == kNuNorth) count = c->nx;
+    else {
+        count = (long long)c->nx * c->ny;
+        scale /= (c->xf.back() - c->xf.front());
+    }
+    (void)d;
+    CK(launch_nusselt(precision_, stream_, d_desc_, d_ctl_, slot, ln, which, count, scale,
+                      d_partial_, partial_cap_, d_scalar_));
+    g_launches += 2;
+    CK(cudaMemcpyAsync(h_scalar_, d_scalar_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    *out = h_scalar_[0];
+    return RTLBFS_OK;
+}
+
+}  // namespace rtlbfs

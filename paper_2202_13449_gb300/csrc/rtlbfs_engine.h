@@ -1,0 +1,116 @@
+// rtlbfs_engine.h -- host-side engine shared by the single-cavity handle
+// and the batch API: device memory of the cavities, the tile list, CUDA
+// graphs of step launches and the run control.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "rtlbfs_dev.cuh"
+#include "rtlbfs_kernels.h"
+
+namespace rtlbfs {
+
+extern std::atomic<long long> g_launches;
+
+// Host record of one cavity.
+struct Cavity {
+    int nx = 0, ny = 0, pitch = 0;
+    std::vector<double> xf, yf;
+    // parameters
+    bool from_ra = true;
+    double Ra = 1e3, Pr = 0.71, Ma = 0.1, dt = 0.5, kappa = 1.0;
+    double Lref = 0.0, dT = 1.0, T_ref = 0.5;
+    double nu = 0.0, chi = 0.0, beta_g = 0.0, fx = 0.0, fy = 0.0;
+    int kind[4] = {kDirichlet, kDirichlet, kAdiabatic, kAdiabatic};
+    double bcT[4] = {1.0, 0.0, 0.0, 0.0};
+    double bcU[4] = {0.0, 0.0, 0.0, 0.0};
+    // device memory
+    void* d_fields = nullptr;  // 2 buffers x 4 fields x ny x pitch
+    void* d_lines = nullptr;   // R lines then FP64 lines
+    size_t fields_bytes = 0, lines_bytes = 0;
+    size_t off_xl = 0, off_yl = 0, off_xc = 0, off_yc = 0;          // R lines
+    size_t off_xld = 0, off_yld = 0, off_xcd = 0, off_ycd = 0;      // FP64 lines
+    bool dirty = true;  // parameters changed since the last upload
+    bool active = false;
+    int first_tile = 0, ntiles = 0;
+};
+
+class Engine {
+public:
+    Engine(int precision, int capacity);
+    ~Engine();
+    Engine(const Engine&) = delete;
+    Engine& operator=(const Engine&) = delete;
+
+    int init();  // device queries, buffers; returns status
+    int precision() const { return precision_; }
+    int capacity() const { return capacity_; }
+
+    // slots
+    int add(int nx, int ny, const double* xf, const double* yf, int* slot);
+    int remove(int slot);
+    Cavity* cavity(int slot);
+    static size_t bytes_for(int precision, int nx, int ny);
+
+    // parameters of a slot changed: lines are re-uploaded before the next step
+    void touch(int slot);
+    int resolve_params(Cavity& c);  // fills nu, chi, beta_g from Ra etc.
+
+    // state I/O (host arrays of ny*nx doubles each)
+    int set_state(int slot, const double* rho, const double* u, const double* v,
+                  const double* T);
+    int get_state(int slot, double* rho, double* u, double* v, double* T);
+    int set_conduction_state(int slot);
+
+    // run control: arm a slot for up to nsteps steps (tol < 0: no early stop)
+    int arm(int slot, long long nsteps, double tol);
+    // launch `launches` step kernels (graph replays where possible)
+    int launch_steps(long long launches);
+    int read_ctl(int slot, CavityCtl* out);          // synchronises
+    int read_ctls(std::vector<CavityCtl>& out);      // all slots, synchronises
+    int nusselt(int slot, int which, double* out);   // synchronises
+
+    int sync();
+    int set_stream(cudaStream_t s);
+    cudaStream_t stream() const { return stream_; }
+    const std::string& error() const { return err_; }
+    int fail(int code, const std::string& msg);
+    int cuda_fail(cudaError_t e, const char* what);
+    int active_tiles() const { return ntiles_; }
+    int grid() const { return grid_; }
+
+private:
+    int upload_lines(int slot);
+    int rebuild_tiles();
+    int prepare_launch();
+
+    int precision_;
+    int capacity_;
+    size_t rsize_;
+    int sms_ = 0, occ_ = 0, grid_ = 0;
+    cudaStream_t stream_ = nullptr, own_stream_ = nullptr;
+    std::vector<Cavity> slots_;
+    std::vector<CavityDesc> h_desc_;
+    CavityDesc* d_desc_ = nullptr;
+    CavityCtl* d_ctl_ = nullptr;
+    int4* d_tiles_ = nullptr;
+    int* d_ntiles_ = nullptr;
+    int tile_cap_ = 0, ntiles_ = 0;
+    bool tiles_dirty_ = true;
+    double* d_partial_ = nullptr;  // per-block partial sums of the FP64 reductions
+    int partial_cap_ = 0;
+    double* d_scalar_ = nullptr;
+    double* h_scalar_ = nullptr;   // pinned
+    double* d_stage_ = nullptr;
+    size_t stage_cap_ = 0;
+    cudaGraphExec_t gexec_ = nullptr;
+    int gchunk_ = 0;
+    cudaStream_t gstream_ = nullptr;
+    std::string err_;
+};
+
+}  // namespace rtlbfs

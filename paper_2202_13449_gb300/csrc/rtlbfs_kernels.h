@@ -1,0 +1,41 @@
+// rtlbfs_kernels.h -- launchers of the device kernels (rtlbfs_step.cu) as
+// seen from the host code of the library (rtlbfs_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rtlbfs_dev.cuh"
+
+namespace rtlbfs {
+
+constexpr int kStepThreads = 256;  // threads of a step block
+constexpr int kTileX = 32;         // cells of a tile along x (one warp row)
+constexpr int kTileY = 8;          // cells of a tile along y
+
+constexpr int kNuWest = 0, kNuEast = 1, kNuSouth = 2, kNuNorth = 3, kNuAvg = 4, kNuHalf = 5;
+
+// FP64 mesh lines of one cavity, for the FP64 reductions.
+struct NuLines {
+    const FaceLine<double>* xl;
+    const FaceLine<double>* yl;
+    const CellLine<double>* xc;
+    const CellLine<double>* yc;
+};
+
+size_t step_smem(int precision);
+cudaError_t step_prepare(int precision);
+cudaError_t step_occupancy(int precision, int* blocks_per_sm);
+cudaError_t launch_step(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
+                        CavityCtl* ctls, const int4* tiles, const int* ntiles);
+cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
+                           const CavityCtl* ctls, int slot, const NuLines& ln, int which,
+                           long long count, double scale, double* partial, int max_blocks,
+                           double* out);
+cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
+                            int pitch, void* const* f);
+cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny,
+                             int pitch, void* const* f);
+cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
+                       int reset_counter);
+
+}  // namespace rtlbfs

@@ -1,0 +1,657 @@
+// rtlbfs_step.cu -- the fused RTLBFS time step on sm_103a and the FP64
+// reductions (Nusselt numbers), for any list of cavities ("batch").
+//
+// One launch advances every listed cavity by one explicit step (Section 3.2
+// of arXiv 2202.13449).  Work unit: a tile of TX x TY cells of one cavity.
+// Per tile, in shared memory:
+//   1. the tile plus a 2-cell halo of (drho, u, v, T), with the boundary
+//      ghosts materialised (mirror rules at walls, wrap at periodic sides);
+//   2. Green-Gauss gradients (Eq. 55) with inverse-distance face values
+//      (Eq. 56) on the tile plus a 1-cell ring; wall ghosts mirror their
+//      partner's gradient;
+//   3. every x- and y-face of the tile: 9-node lattice (Eq. 29), predictor
+//      (Eqs. 46-48), corrector fluxes (Eqs. 57-59) -- face_flux();
+//   4. the explicit update with the Boussinesq source (Eq. 64) and the
+//      conservative -> primitive conversion;
+//   5. the residual sums of the steady criterion; the last tile of a cavity
+//      to finish turns them into (R_u, R_T), advances the step counter,
+//      flips the buffer and decides whether the cavity is done.
+// Face values and gradients never leave the SM; HBM sees one read and one
+// write of the four fields per cell per step (halo re-reads hit L2).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "rtlbfs_dev.cuh"
+#include "rtlbfs_kernels.h"
+
+namespace rtlbfs {
+
+template <typename R, int TX, int TY>
+struct TileSmem {
+    static constexpr int BX = TX + 4, BY = TY + 4;  // tile + 2-cell halo
+    static constexpr int GX = TX + 2, GY = TY + 2;  // gradient ring
+    Vec4<R> val[BY][BX];
+    Vec4<R> gx[GY][GX];
+    Vec4<R> gy[GY][GX];
+    Vec4<R> fx[TY][TX + 1];
+    Vec4<R> fy[TY + 1][TX];
+    FaceLine<R> xl[TX + 1];
+    FaceLine<R> yl[TY + 1];
+    CellLine<R> xc[BX];
+    CellLine<R> yc[BY];
+    double red[kStepThreads / 32][4];
+    int last;
+};
+
+// Resolve global cell (gi, gj) of a cavity, ghosts included: the source
+// cell (si, sj) to read, and the wall side whose mirror rule applies
+// (-1: none).  Returns false for positions no stencil uses (corner ghosts,
+// cells beyond the ghost layer of a wall, beyond a ragged tile edge).
+__device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj, int& si,
+                                             int& sj, int& mside)
+{
+    const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
+    si = gi;
+    sj = gj;
+    mside = -1;
+    if (gi < 0 || gi >= d.nx) {
+        if (xper) {
+            si = ((gi % d.nx) + d.nx) % d.nx;
+        } else if (gi == -1) {
+            si = 0;
+            mside = kSideW;
+        } else if (gi == d.nx) {
+            si = d.nx - 1;
+            mside = kSideE;
+        } else {
+            return false;
+        }
+    }
+    if (gj < 0 || gj >= d.ny) {
+        if (yper) {
+            sj = ((gj % d.ny) + d.ny) % d.ny;
+        } else if ((gj == -1 || gj == d.ny) && mside < 0) {
+            sj = gj < 0 ? 0 : d.ny - 1;
+            mside = gj < 0 ? kSideS : kSideN;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+// Ghost value of (drho, u, v, T) across wall `side` (mirror rules: rho
+// even, velocity odd about the wall velocity, T odd about T_wall on a
+// Dirichlet wall and even on an adiabatic one).
+template <typename R>
+__device__ __forceinline__ Vec4<R> mirror_value(const CavityDesc& d, int side, Vec4<R> v)
+{
+    const R two = rconst<R>(2.0);
+    const R uw = rconst<R>(d.bcU[side]);
+    if (side == kSideW || side == kSideE) {
+        v.y = -v.y;
+        v.z = two * uw - v.z;
+    } else {
+        v.z = -v.z;
+        v.y = two * uw - v.y;
+    }
+    if (d.kind[side] == kDirichlet) v.w = two * rconst<R>(d.bcT[side]) - v.w;
+    return v;
+}
+
+// Ghost gradient across wall `side`: even quantities negate the normal
+// component, odd ones the tangential component.
+template <typename R>
+__device__ __forceinline__ void mirror_grad(const CavityDesc& d, int side, Vec4<R>& gx,
+                                            Vec4<R>& gy)
+{
+    const bool nx_ = (side == kSideW || side == kSideE);
+    R* ax = &gx.x;
+    R* ay = &gy.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool even = wall_parity(d.kind[side], k) > 0;
+        // normal-x wall: even -> gx = -gx; odd -> gy = -gy.  normal-y: swapped.
+        if (nx_) {
+            if (even) ax[k] = -ax[k];
+            else ay[k] = -ay[k];
+        } else {
+            if (even) ay[k] = -ay[k];
+            else ax[k] = -ax[k];
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ Vec4<R> v4_lerp(R a, const Vec4<R>& p, const Vec4<R>& q)
+{
+    // a p + (1 - a) q  ==  q + a (p - q)
+    Vec4<R> r;
+    r.x = q.x + a * (p.x - q.x);
+    r.y = q.y + a * (p.y - q.y);
+    r.z = q.z + a * (p.z - q.z);
+    r.w = q.w + a * (p.w - q.w);
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ Vec4<R> v4_diff_scaled(const Vec4<R>& e, const Vec4<R>& w, R s)
+{
+    Vec4<R> r;
+    r.x = (e.x - w.x) * s;
+    r.y = (e.y - w.y) * s;
+    r.z = (e.z - w.z) * s;
+    r.w = (e.w - w.w) * s;
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(kStepThreads)
+step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
+            const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
+{
+    using S = TileSmem<R, TX, TY>;
+    constexpr int BX = S::BX, BY = S::BY, GX = S::GX, GY = S::GY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S& sm = *reinterpret_cast<S*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int ntiles = *ntiles_ptr;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tile = tiles[t];
+        const int slot = tile.x, i0 = tile.y, j0 = tile.z;
+        const CavityDesc& d = descs[slot];
+        CavityCtl* ctl = &ctls[slot];
+        if (ctl->done) continue;  // uniform across the block
+        const int cur = ctl->cur;
+        const R* fin[4];
+        R* fout[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            fin[k] = static_cast<const R*>(d.f[cur][k]);
+            fout[k] = static_cast<R*>(d.f[cur ^ 1][k]);
+        }
+        const int nx = d.nx, ny = d.ny, pitch = d.pitch;
+        const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
+
+        // ---- 1. lines and the haloed tile -------------------------------
+        {
+            const CellLine<R>* xc = static_cast<const CellLine<R>*>(d.xcell);
+            const CellLine<R>* yc = static_cast<const CellLine<R>*>(d.ycell);
+            const FaceLine<R>* xl = static_cast<const FaceLine<R>*>(d.xline);
+            const FaceLine<R>* yl = static_cast<const FaceLine<R>*>(d.yline);
+            for (int k = tid; k < BX; k += kStepThreads) sm.xc[k] = xc[min(i0 + k, nx + 3)];
+            for (int k = tid; k < BY; k += kStepThreads) sm.yc[k] = yc[min(j0 + k, ny + 3)];
+            for (int k = tid; k < TX + 1; k += kStepThreads) sm.xl[k] = xl[min(i0 + k, nx)];
+            for (int k = tid; k < TY + 1; k += kStepThreads) sm.yl[k] = yl[min(j0 + k, ny)];
+        }
+        for (int k = tid; k < BX * BY; k += kStepThreads) {
+            const int c = k % BX, r = k / BX;
+            int si, sj, ms;
+            Vec4<R> v = {R(0), R(0), R(0), R(0)};
+            if (resolve_cell(d, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+                const size_t o = (size_t)sj * pitch + si;
+                v.x = fin[0][o];
+                v.y = fin[1][o];
+                v.z = fin[2][o];
+                v.w = fin[3][o];
+                if (ms >= 0) v = mirror_value(d, ms, v);
+            }
+            sm.val[r][c] = v;
+        }
+        __syncthreads();
+
+        // ---- 2. gradients on the tile plus a 1-cell ring ----------------
+        for (int k = tid; k < GX * GY; k += kStepThreads) {
+            const int gc = k % GX, gr = k / GX;
+            int c = gc + 1, r = gr + 1;  // box position
+            int si, sj, ms;
+            Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
+            if (resolve_cell(d, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+                // a wall ghost takes its partner's gradient, mirrored
+                if (ms == kSideW) c += 1;
+                else if (ms == kSideE) c -= 1;
+                else if (ms == kSideS) r += 1;
+                else if (ms == kSideN) r -= 1;
+                const CellLine<R>& lx = sm.xc[c];
+                const CellLine<R>& ly = sm.yc[r];
+                const Vec4<R> p = sm.val[r][c];
+                const Vec4<R> fe = v4_lerp(lx.a_next, p, sm.val[r][c + 1]);
+                const Vec4<R> fw = v4_lerp(sm.xc[c - 1].a_next, sm.val[r][c - 1], p);
+                const Vec4<R> fn = v4_lerp(ly.a_next, p, sm.val[r + 1][c]);
+                const Vec4<R> fs = v4_lerp(sm.yc[r - 1].a_next, sm.val[r - 1][c], p);
+                gxv = v4_diff_scaled(fe, fw, lx.inv_w);
+                gyv = v4_diff_scaled(fn, fs, ly.inv_w);
+                if (ms >= 0) mirror_grad(d, ms, gxv, gyv);
+            }
+            sm.gx[gr][gc] = gxv;
+            sm.gy[gr][gc] = gyv;
+        }
+        __syncthreads();
+
+        // ---- 3. faces ----------------------------------------------------
+        constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+        for (int k = tid; k < NXF + NYF; k += kStepThreads) {
+            const bool isx = k < NXF;
+            int fc, fr;
+            if (isx) {
+                fc = k % (TX + 1);
+                fr = k / (TX + 1);
+            } else {
+                fc = (k - NXF) % TX;
+                fr = (k - NXF) / TX;
+            }
+            const int gi = i0 + fc, gj = j0 + fr;
+            const bool valid = isx ? (gi <= nx && gj < ny) : (gi < nx && gj <= ny);
+            Vec4<R> out = {R(0), R(0), R(0), R(0)};
+            if (valid) {
+                // left/right cells in box and gradient-ring coordinates
+                const int lc = isx ? fc + 1 : fc + 2, lr = isx ? fr + 2 : fr + 1;
+                const int rc = fc + 2, rr = fr + 2;
+                const Vec4<R> vl = sm.val[lr][lc], vr = sm.val[rr][rc];
+                const Vec4<R> gxl = sm.gx[lr - 1][lc - 1], gyl = sm.gy[lr - 1][lc - 1];
+                const Vec4<R> gxr = sm.gx[rr - 1][rc - 1], gyr = sm.gy[rr - 1][rc - 1];
+                CellNT<R> L, Rr;
+                if (isx) {
+                    L = {{vl.x, vl.y, vl.z, vl.w}, {gxl.x, gxl.y, gxl.z, gxl.w},
+                         {gyl.x, gyl.y, gyl.z, gyl.w}};
+                    Rr = {{vr.x, vr.y, vr.z, vr.w}, {gxr.x, gxr.y, gxr.z, gxr.w},
+                          {gyr.x, gyr.y, gyr.z, gyr.w}};
+                } else {
+                    L = {{vl.x, vl.z, vl.y, vl.w}, {gyl.x, gyl.z, gyl.y, gyl.w},
+                         {gxl.x, gxl.z, gxl.y, gxl.w}};
+                    Rr = {{vr.x, vr.z, vr.y, vr.w}, {gyr.x, gyr.z, gyr.y, gyr.w},
+                          {gxr.x, gxr.z, gxr.y, gxr.w}};
+                }
+                const FaceLine<R> fl = isx ? sm.xl[fc] : sm.yl[fr];
+                int wside = -1;
+                if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
+                if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
+                const R uw = wside >= 0 ? rconst<R>(d.bcU[wside]) : R(0);
+                R F[4];
+                face_flux<R>(L, Rr, fl, wside >= 0, uw, F);
+                if (isx) out = {F[0], F[1], F[2], F[3]};
+                else out = {F[0], F[2], F[1], F[3]};
+            }
+            if (isx) sm.fx[fr][fc] = out;
+            else sm.fy[fr][fc] = out;
+        }
+        __syncthreads();
+
+        // ---- 4. update, 5. residual sums --------------------------------
+        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+        for (int k = tid; k < TX * TY; k += kStepThreads) {
+            const int tc = k % TX, tr = k / TX;
+            const int gi = i0 + tc, gj = j0 + tr;
+            if (gi >= nx || gj >= ny) continue;
+            const Vec4<R> p = sm.val[tr + 2][tc + 2];
+            const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
+            const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
+            const R ax = sm.xc[tc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
+            const R one = rconst<R>(1.0);
+            const R rho = one + p.x;
+            const R dt = rconst<R>(d.dt);
+            const R src_x = rho * rconst<R>(d.fx);
+            const R src_y = rho * (rconst<R>(d.beta_g) * (p.w - rconst<R>(d.T_ref)) + rconst<R>(d.fy));
+            const R dr1 = p.x - ax * (Fe.x - Fw.x) - ay * (Fn.x - Fs.x);
+            const R mx1 = rho * p.y - ax * (Fe.y - Fw.y) - ay * (Fn.y - Fs.y) + dt * src_x;
+            const R my1 = rho * p.z - ax * (Fe.z - Fw.z) - ay * (Fn.z - Fs.z) + dt * src_y;
+            const R E1 = rho * p.w - ax * (Fe.w - Fw.w) - ay * (Fn.w - Fs.w);
+            const R inv = one / (one + dr1);
+            const R u1 = mx1 * inv, v1 = my1 * inv, T1 = E1 * inv;
+            const size_t o = (size_t)gj * pitch + gi;
+            fout[0][o] = dr1;
+            fout[1][o] = u1;
+            fout[2][o] = v1;
+            fout[3][o] = T1;
+            const R m0 = sqrt(p.y * p.y + p.z * p.z), m1 = sqrt(u1 * u1 + v1 * v1);
+            const R du = m1 - m0, dT = T1 - p.w;
+            s0 += du * du;
+            s1 += m1 * m1;
+            s2 += dT * dT;
+            s3 += T1 * T1;
+        }
+        // warp sums in R, then FP64 across warps and tiles
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        s3 = warp_sum(s3);
+        if ((tid & 31) == 0) {
+            sm.red[tid >> 5][0] = (double)s0;
+            sm.red[tid >> 5][1] = (double)s1;
+            sm.red[tid >> 5][2] = (double)s2;
+            sm.red[tid >> 5][3] = (double)s3;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < kStepThreads / 32; ++w)
+                for (int q = 0; q < 4; ++q) a[q] += sm.red[w][q];
+            for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
+            __threadfence();
+            const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+            sm.last = (prev == (unsigned)d.ntiles - 1u);
+            if (sm.last) {
+                __threadfence();
+                volatile double* acc = ctl->acc;
+                const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
+                const double ru = du > 0.0 ? sqrt(su) / sqrt(du) : INFINITY;
+                const double rT = dT > 0.0 ? sqrt(sT) / sqrt(dT) : INFINITY;
+                ctl->res[0] = ru;
+                ctl->res[1] = rT;
+                ctl->steps += 1;
+                ctl->cur = cur ^ 1;
+                int status = kRunning;
+                if (isnan(ru) || isnan(rT) || isnan(su) || isnan(sT)) status = kDiverged;
+                else if (fmax(ru, rT) < ctl->tol) status = kConverged;
+                else if (ctl->steps >= ctl->max_steps) status = kMaxSteps;
+                ctl->status = status;
+                if (status != kRunning) ctl->done = 1;
+                for (int q = 0; q < 4; ++q) acc[q] = 0.0;
+                ctl->arrive = 0u;
+                __threadfence();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 evaluation straight from global memory (Nusselt reductions).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ bool load_cell_d(const CavityDesc& d, const R* const* f, int gi, int gj,
+                            Vec4<double>& v)
+{
+    int si, sj, ms;
+    if (!resolve_cell(d, gi, gj, si, sj, ms)) return false;
+    const size_t o = (size_t)sj * d.pitch + si;
+    Vec4<double> x = {(double)f[0][o], (double)f[1][o], (double)f[2][o], (double)f[3][o]};
+    if (ms >= 0) x = mirror_value<double>(d, ms, x);
+    v = x;
+    return true;
+}
+
+// Green-Gauss gradient (Eqs. 55-56) of cell (gi, gj) in FP64; a wall ghost
+// mirrors its partner's.  xc/yc: FP64 cell lines (index i + 2).
+template <typename R>
+__device__ void grad_d(const CavityDesc& d, const R* const* f, const CellLine<double>* xc,
+                       const CellLine<double>* yc, int gi, int gj, Vec4<double>& gx,
+                       Vec4<double>& gy)
+{
+    int si, sj, ms;
+    gx = {0, 0, 0, 0};
+    gy = gx;
+    if (!resolve_cell(d, gi, gj, si, sj, ms)) return;
+    int ci = gi, cj = gj;
+    if (ms == kSideW) ci += 1;
+    else if (ms == kSideE) ci -= 1;
+    else if (ms == kSideS) cj += 1;
+    else if (ms == kSideN) cj -= 1;
+    Vec4<double> p, e, w, n, s;
+    load_cell_d(d, f, ci, cj, p);
+    load_cell_d(d, f, ci + 1, cj, e);
+    load_cell_d(d, f, ci - 1, cj, w);
+    load_cell_d(d, f, ci, cj + 1, n);
+    load_cell_d(d, f, ci, cj - 1, s);
+    const CellLine<double>& lx = xc[ci + 2];
+    const CellLine<double>& ly = yc[cj + 2];
+    gx = v4_diff_scaled(v4_lerp(lx.a_next, p, e), v4_lerp(xc[ci + 1].a_next, w, p), lx.inv_w);
+    gy = v4_diff_scaled(v4_lerp(ly.a_next, p, n), v4_lerp(yc[cj + 1].a_next, s, p), ly.inv_w);
+    if (ms >= 0) mirror_grad<double>(d, ms, gx, gy);
+}
+
+// Energy flux (Eq. 59 brace) through x-face (i, j) (nd = 0) or y-face
+// (nd = 1), in FP64.
+template <typename R>
+__device__ double energy_flux_d(const CavityDesc& d, const R* const* f, const NuLines& ln,
+                                int nd, int i, int j)
+{
+    const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
+    const int li = nd == 0 ? i - 1 : i, lj = nd == 0 ? j : j - 1;
+    Vec4<double> vl = {0, 0, 0, 0}, vr = vl, gxl, gyl, gxr, gyr;
+    load_cell_d(d, f, li, lj, vl);
+    load_cell_d(d, f, i, j, vr);
+    grad_d(d, f, ln.xc, ln.yc, li, lj, gxl, gyl);
+    grad_d(d, f, ln.xc, ln.yc, i, j, gxr, gyr);
+    CellNT<double> L, Rr;
+    if (nd == 0) {
+        L = {{vl.x, vl.y, vl.z, vl.w}, {gxl.x, gxl.y, gxl.z, gxl.w}, {gyl.x, gyl.y, gyl.z, gyl.w}};
+        Rr = {{vr.x, vr.y, vr.z, vr.w}, {gxr.x, gxr.y, gxr.z, gxr.w}, {gyr.x, gyr.y, gyr.z, gyr.w}};
+    } else {
+        L = {{vl.x, vl.z, vl.y, vl.w}, {gyl.x, gyl.z, gyl.y, gyl.w}, {gxl.x, gxl.z, gxl.y, gxl.w}};
+        Rr = {{vr.x, vr.z, vr.y, vr.w}, {gyr.x, gyr.z, gyr.y, gyr.w}, {gxr.x, gxr.z, gxr.y, gxr.w}};
+    }
+    int wside = -1;
+    if (nd == 0 && !xper) wside = i == 0 ? kSideW : (i == d.nx ? kSideE : -1);
+    if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
+    const FaceLine<double> fl = nd == 0 ? ln.xl[i] : ln.yl[j];
+    double F[4];
+    face_flux<double>(L, Rr, fl, wside >= 0, wside >= 0 ? d.bcU[wside] : 0.0, F);
+    return F[3];
+}
+
+// Partial sums of a Nusselt number: one partial per block, in block order.
+template <typename R>
+__global__ void __launch_bounds__(256)
+nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityCtl* __restrict__ ctls,
+                       int slot, NuLines ln, int which, double* __restrict__ partial)
+{
+    const CavityDesc& d = descs[slot];
+    const int cur = ctls[slot].cur;
+    const R* f[4] = {static_cast<const R*>(d.f[cur][0]), static_cast<const R*>(d.f[cur][1]),
+                     static_cast<const R*>(d.f[cur][2]), static_cast<const R*>(d.f[cur][3])};
+    long long count;
+    if (which == kNuWest || which == kNuEast || which == kNuHalf) count = d.ny;
+    else if (which == kNuSouth || which == kNuNorth) count = d.nx;
+    else count = (long long)d.nx * d.ny;
+    double s = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (which == kNuWest || which == kNuEast || which == kNuHalf) {
+            const int i = which == kNuWest ? 0 : (which == kNuEast ? d.nx : d.nx / 2);
+            const int j = (int)k;
+            s += energy_flux_d(d, f, ln, 0, i, j) * ln.yc[j + 2].w;
+        } else if (which == kNuSouth || which == kNuNorth) {
+            const int i = (int)k;
+            const int j = which == kNuSouth ? 0 : d.ny;
+            s += energy_flux_d(d, f, ln, 1, i, j) * ln.xc[i + 2].w;
+        } else {  // Eq. 69 integrand (u T - chi dT/dx) dV
+            const int i = (int)(k % d.nx), j = (int)(k / d.nx);
+            Vec4<double> p, gx, gy;
+            load_cell_d(d, f, i, j, p);
+            grad_d(d, f, ln.xc, ln.yc, i, j, gx, gy);
+            s += (p.y * p.w - d.chi * gx.w) * ln.xc[i + 2].w * ln.yc[j + 2].w;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int n, double scale,
+                                    double* __restrict__ out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += partial[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// State conversion: FP64 host-layout staging (rho, u, v, T planes of n
+// cells, row-major nx) <-> device fields (drho, u, v, T with row pitch).
+template <typename R>
+__global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, int pitch,
+                                R* f0, R* f1, R* f2, R* f3)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = k % nx, j = k / nx;
+        const size_t o = (size_t)j * pitch + i;
+        f0[o] = (R)(st[k] - 1.0);
+        f1[o] = (R)st[n + k];
+        f2[o] = (R)st[2 * n + k];
+        f3[o] = (R)st[3 * n + k];
+    }
+}
+
+template <typename R>
+__global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pitch,
+                                 const R* f0, const R* f1, const R* f2, const R* f3)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = k % nx, j = k / nx;
+        const size_t o = (size_t)j * pitch + i;
+        st[k] = 1.0 + (double)f0[o];
+        st[n + k] = (double)f1[o];
+        st[2 * n + k] = (double)f2[o];
+        st[3 * n + k] = (double)f3[o];
+    }
+}
+
+// Arm the run control of one cavity: take `nsteps` more steps (stop early
+// when max(R_u, R_T) < tol, tol < 0: never).
+__global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double tol,
+                           int reset_counter)
+{
+    CavityCtl* c = &ctls[slot];
+    if (reset_counter) {
+        c->steps = 0;
+        c->res[0] = c->res[1] = INFINITY;
+    }
+    c->max_steps = c->steps + nsteps;
+    c->tol = tol;
+    c->status = kRunning;
+    c->done = nsteps > 0 ? 0 : 1;
+    c->arrive = 0u;
+    for (int q = 0; q < 4; ++q) c->acc[q] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+static size_t step_smem_bytes()
+{
+    return sizeof(TileSmem<R, kTileX, kTileY>);
+}
+
+size_t step_smem(int precision)
+{
+    return precision == 0 ? step_smem_bytes<double>() : step_smem_bytes<float>();
+}
+
+cudaError_t step_prepare(int precision)
+{
+    if (precision == 0)
+        return cudaFuncSetAttribute(step_kernel<double, kTileX, kTileY>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)step_smem_bytes<double>());
+    return cudaFuncSetAttribute(step_kernel<float, kTileX, kTileY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_smem_bytes<float>());
+}
+
+cudaError_t step_occupancy(int precision, int* blocks_per_sm)
+{
+    if (precision == 0)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, step_kernel<double, kTileX, kTileY>, kStepThreads,
+            step_smem_bytes<double>());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, step_kernel<float, kTileX, kTileY>, kStepThreads,
+        step_smem_bytes<float>());
+}
+
+cudaError_t launch_step(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
+                        CavityCtl* ctls, const int4* tiles, const int* ntiles)
+{
+    if (precision == 0)
+        step_kernel<double, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<double>(), s>>>(
+            descs, ctls, tiles, ntiles);
+    else
+        step_kernel<float, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<float>(), s>>>(
+            descs, ctls, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
+                           const CavityCtl* ctls, int slot, const NuLines& ln, int which,
+                           long long count, double scale, double* partial, int max_blocks,
+                           double* out)
+{
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    if (precision == 0)
+        nusselt_partial_kernel<double><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
+    else
+        nusselt_partial_kernel<float><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
+    sum_partials_kernel<<<1, 256, 0, s>>>(partial, blocks, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
+                            int pitch, void* const* f)
+{
+    const long long n = (long long)nx * ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (precision == 0)
+        state_in_kernel<double><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (double*)f[0],
+                                                       (double*)f[1], (double*)f[2], (double*)f[3]);
+    else
+        state_in_kernel<float><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (float*)f[0],
+                                                      (float*)f[1], (float*)f[2], (float*)f[3]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny, int pitch,
+                             void* const* f)
+{
+    const long long n = (long long)nx * ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (precision == 0)
+        state_out_kernel<double><<<blocks, 256, 0, s>>>(
+            st, nx, ny, pitch, (const double*)f[0], (const double*)f[1], (const double*)f[2],
+            (const double*)f[3]);
+    else
+        state_out_kernel<float><<<blocks, 256, 0, s>>>(
+            st, nx, ny, pitch, (const float*)f[0], (const float*)f[1], (const float*)f[2],
+            (const float*)f[3]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
+                       int reset_counter)
+{
+    arm_kernel<<<1, 1, 0, s>>>(ctls, slot, nsteps, tol, reset_counter);
+    return cudaGetLastError();
+}
+
+}  // namespace rtlbfs

@@ -1,0 +1,42 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/rtlbfs.h, and its host-only entry points agree with the
+oracle; argument errors come back as status codes."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2202_13449_gb300 import capi
+
+
+def test_library_exports_every_declared_function():
+    L = capi.lib()
+    declared = capi.header_functions()
+    assert len(declared) >= 19
+    missing = [f for f in declared if not hasattr(L, f)]
+    assert missing == []
+
+
+@pytest.mark.parametrize("n,L,phi", [(512, 512.0, 2.0), (64, 64.0, 0.0), (80, 1.0, 1.8),
+                                     (33, 7.5, 2.5)])
+def test_tanh_faces_matches_oracle(orc, n, L, phi):
+    np.testing.assert_array_equal(capi.tanh_faces(n, L, phi), orc.tanh_faces(n, L, phi))
+
+
+def test_host_argument_errors_are_status_codes():
+    L = capi.lib()
+    out = np.empty(4)
+    assert L.rtlbfs_tanh_faces(0, 1.0, 1.0, out.ctypes.data_as(C.POINTER(C.c_double))) == capi.ERR_ARG
+    assert L.rtlbfs_tanh_faces(3, -1.0, 1.0, out.ctypes.data_as(C.POINTER(C.c_double))) == capi.ERR_ARG
+    # a null handle is rejected, never dereferenced
+    assert L.rtlbfs_step(None, 1) == capi.ERR_ARG
+    assert L.rtlbfs_set_params(None, 1e3, 0.71, 0.1, 0.5) == capi.ERR_ARG
+    assert L.rtlbfs_last_error(None) == b"null handle"
+    L.rtlbfs_destroy(None)
+    h = C.c_void_p()
+    xf = np.arange(5.0)
+    bad = np.array([0.0, 1.0, 1.0, 2.0, 3.0])
+    dp = C.POINTER(C.c_double)
+    assert L.rtlbfs_create_mesh(4, 4, xf.ctypes.data_as(dp), bad.ctypes.data_as(dp), 0,
+                                C.byref(h)) != capi.OK
+    assert not h.value

@@ -1,0 +1,244 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative to max(max|ref|, floor); floors: rho 1, u and v the
+velocity scale of the case, T the temperature difference):
+  FP64: <= 1e-12 after one step, <= 1e-11 after tens of steps, <= 1e-10 at
+        the steady state;
+  FP32 (rho - 1 stored): <= 1e-5 on u, v, T and 1e-6 absolute on rho.
+Cases span several 32 x 8 tiles with ragged tails, every boundary kind,
+stretched and irregular meshes, degenerate 1-cell meshes, and the full
+512 x 512 tanh mesh of the Ra = 1e8 cavity.
+"""
+import numpy as np
+import pytest
+
+from paper_2202_13449_gb300 import capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+D, A, P = capi.WALL_DIRICHLET, capi.WALL_ADIABATIC, capi.PERIODIC
+TOL = {capi.FP64: 1e-12, capi.FP32: 1e-5}
+
+
+def rel(a, b, floor):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(float(np.max(np.abs(b))), floor))
+
+
+def make_pair(orc, xf, yf, nu, chi, beta_g, dt, kappa, kinds, bcT, bcU, precision,
+              fx=0.0, fy=0.0, T_ref=0.5):
+    p = orc.Problem(xf=xf, yf=yf, nu=nu, chi=chi, beta_g=beta_g, T_ref=T_ref, dt=dt,
+                    kappa=kappa, fx=fx, fy=fy, bc_kind=kinds, bc_T=bcT, bc_u=bcU)
+    s = capi.Solver(xf, yf, precision)
+    s.set_params_ref(1e3, 0.71, 0.1, dt, 1.0, 1.0, T_ref)
+    s.set_physics(nu, chi, beta_g)
+    s.set_lattice(kappa)
+    s.set_body_force(fx, fy)
+    for side in range(4):
+        s.set_bc(side, kinds[side], bcT[side], bcU[side])
+    return p, s
+
+
+CASES = {
+    # name: (nx, ny, mesh, kinds, bcT, bcU, kappa, beta_g)
+    "cavity_irregular_lid": (37, 21, "random", (D, D, A, A), (1, 0, 0, 0), (0, 0, 0, 0.01), 1.0, 2e-3),
+    "rb_periodic_x_stretched_y": (45, 17, "tanh_y", (P, P, D, D), (0, 0, 1, 0), (0, 0, 0, 0), 0.7, 1e-3),
+    "all_periodic": (33, 9, "uniform", (P, P, P, P), (0, 0, 0, 0), (0, 0, 0, 0), 1.0, 5e-4),
+    "periodic_y_walls_x": (19, 26, "random", (D, A, P, P), (0.8, 0, 0, 0), (0.005, 0, 0, 0), 0.55, 1e-3),
+    "tiny_1x1": (1, 1, "uniform", (D, D, A, A), (1, 0, 0, 0), (0, 0, 0, 0), 1.0, 1e-3),
+    "tiny_1x5": (1, 5, "random", (D, A, D, A), (1, 0, 0.2, 0), (0, 0, 0, 0.01), 1.0, 1e-3),
+    "tiny_5x1_periodic": (5, 1, "uniform", (P, P, D, D), (0, 0, 1, 0), (0, 0, 0, 0), 0.8, 1e-3),
+    "two_by_three": (2, 3, "random", (A, D, A, D), (0, 0.3, 0, 0.9), (0.02, 0, 0, 0), 1.0, 1e-3),
+}
+
+
+def case_mesh(name, nx, ny, mesh):
+    if mesh == "uniform":
+        return inputs.uniform_faces(nx), inputs.uniform_faces(ny)
+    if mesh == "tanh_y":
+        import oracle
+        return inputs.uniform_faces(nx), oracle.tanh_faces(ny, float(ny), 2.0)
+    seed = sum(map(ord, name))
+    return inputs.random_faces(nx, seed), inputs.random_faces(ny, seed + 1)
+
+
+def run_case(orc, name, precision, nsteps):
+    nx, ny, mesh, kinds, bcT, bcU, kappa, bg = CASES[name]
+    xf, yf = case_mesh(name, nx, ny, mesh)
+    p, s = make_pair(orc, xf, yf, nu=0.04, chi=0.05, beta_g=bg, dt=0.25, kappa=kappa,
+                     kinds=kinds, bcT=bcT, bcU=bcU, precision=precision)
+    st = inputs.perturbed_state(nx, ny, seed=7 + nx * 31 + ny)
+    ref, _, rc = orc.step(p, st, nsteps)
+    assert rc == 0
+    s.set_state(*st)
+    s.step(nsteps)
+    got = s.get_state()
+    res_gpu, steps = s.residual()
+    s.close()
+    assert steps == nsteps
+    return ref, got, res_gpu
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_single_step_matches_oracle(orc, name, precision):
+    ref, got, _ = run_case(orc, name, precision, 1)
+    tol = TOL[precision]
+    if precision == capi.FP64:
+        assert rel(got[0], ref[0], 1.0) < tol
+    else:
+        assert np.max(np.abs(got[0] - ref[0])) < 1e-6
+    for q in (1, 2):
+        assert rel(got[q], ref[q], 1e-2) < tol, (q, rel(got[q], ref[q], 1e-2))
+    assert rel(got[3], ref[3], 1.0) < tol
+
+
+@pytest.mark.parametrize("name", ["cavity_irregular_lid", "rb_periodic_x_stretched_y",
+                                  "periodic_y_walls_x"])
+def test_thirty_steps_match_oracle_fp64(orc, name):
+    ref, got, res = run_case(orc, name, capi.FP64, 30)
+    for q, floor in ((0, 1.0), (1, 1e-2), (2, 1e-2), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < 1e-11, (q, rel(got[q], ref[q], floor))
+
+
+def test_residual_of_last_step_matches_oracle(orc):
+    nx, ny, mesh, kinds, bcT, bcU, kappa, bg = CASES["cavity_irregular_lid"]
+    xf, yf = case_mesh("cavity_irregular_lid", nx, ny, mesh)
+    p, s = make_pair(orc, xf, yf, 0.04, 0.05, bg, 0.25, kappa, kinds, bcT, bcU, capi.FP64)
+    st = inputs.perturbed_state(nx, ny, seed=99)
+    _, (ru, rT), _ = orc.step(p, st, 3)
+    s.set_state(*st)
+    s.step(3)
+    (gu, gT), steps = s.residual()
+    s.close()
+    assert gu == pytest.approx(ru, rel=1e-12) and gT == pytest.approx(rT, rel=1e-12)
+
+
+def config2_pair(orc, precision):
+    n = 512
+    xf = orc.tanh_faces(n, float(n), 2.0)
+    nu, chi, bg = orc.params_from_ra(1e8, 0.71, 0.1, float(n))
+    dt = 0.5 * float(np.min(np.diff(xf)))
+    return make_pair(orc, xf, xf.copy(), nu, chi, bg, dt, 1.0, (D, D, A, A), (1, 0, 0, 0),
+                     (0, 0, 0, 0), precision)
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_full_size_512_tanh_cavity_one_step(orc, precision):
+    """The Ra = 1e8, 512 x 512, tanh (phi = 2) cavity: one step from a
+    generic state, every cell compared."""
+    p, s = config2_pair(orc, precision)
+    st = inputs.perturbed_state(512, 512, seed=2024, amp_u=0.05)
+    ref, _, rc = orc.step(p, st, 1)
+    s.set_state(*st)
+    s.step(1)
+    got = s.get_state()
+    s.close()
+    tol = TOL[precision]
+    for q, floor in ((1, 0.1), (2, 0.1), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < tol, (q, rel(got[q], ref[q], floor))
+
+
+def test_mass_conserved_to_round_off_on_gpu(orc):
+    nx, ny = 40, 24
+    xf, yf = inputs.random_faces(nx, 5), inputs.random_faces(ny, 6)
+    _, s = make_pair(orc, xf, yf, 0.03, 0.04, 2e-3, 0.3, 1.0, (D, D, A, A), (1, 0, 0, 0),
+                     (0, 0, 0, 0), capi.FP64)
+    st = inputs.perturbed_state(nx, ny, seed=11)
+    dV = np.outer(np.diff(yf), np.diff(xf))
+    m0 = float(np.sum(st[0] * dV))
+    s.set_state(*st)
+    s.step(500)
+    m1 = float(np.sum(s.get_state()[0] * dV))
+    s.close()
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def cavity_solver(orc, n, Ra, precision):
+    p = orc.cavity_problem(n, Ra)
+    s = capi.Solver(p.xf, p.yf, precision)
+    s.set_params(Ra, 0.71, 0.1, p.dt)
+    return p, s
+
+
+def test_config1_run_to_steady_fp64(orc):
+    """64 x 64, Ra = 1e3, to max(R_u, R_T) < 1e-8: the GPU stops on the same
+    step as the oracle and the steady fields agree to 1e-10."""
+    p, s = cavity_solver(orc, 64, 1e3, capi.FP64)
+    st0 = inputs.conduction_state(p.xf, p.yf)
+    ref, n_ref, res_ref, rc = orc.run_to_steady(p, st0, 1e-8, 400000)
+    assert rc == 0
+    rc, n_gpu, res_gpu = s.run_to_steady(1e-8, 400000)
+    assert rc == capi.OK
+    assert abs(n_gpu - n_ref) <= 1, (n_gpu, n_ref)
+    if n_gpu != n_ref:  # compare at the oracle's step count
+        s.set_state(*st0)
+        s.step(n_ref)
+    got = s.get_state()
+    for q, floor in ((0, 1.0), (1, 0.1), (2, 0.1), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < 1e-10, (q, rel(got[q], ref[q], floor))
+    for which in (capi.NU_WEST, capi.NU_EAST, capi.NU_AVG, capi.NU_HALF):
+        assert s.nusselt(which) == pytest.approx(orc.nusselt(p, ref, which), rel=1e-10)
+    s.close()
+
+
+def test_config1_fp32_against_fp64_oracle(orc):
+    """FP32 bulk with FP64 reductions on the same case: fields within 1e-5 and
+    the mean wall Nusselt number within 1e-4 of the FP64 oracle."""
+    p, s = cavity_solver(orc, 64, 1e3, capi.FP32)
+    st0 = inputs.conduction_state(p.xf, p.yf)
+    ref, n_ref, _, rc = orc.run_to_steady(p, st0, 1e-8, 400000)
+    assert rc == 0
+    s.step(n_ref)
+    got = s.get_state()
+    for q, floor in ((1, 0.1), (2, 0.1), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < 1e-5, (q, rel(got[q], ref[q], floor))
+    nu_ref = 0.5 * (orc.nusselt(p, ref, 0) + orc.nusselt(p, ref, 1))
+    nu_gpu = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+    assert abs(nu_gpu - nu_ref) / nu_ref < 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_nusselt_of_generic_state(orc, precision):
+    nx, ny = 38, 22
+    xf, yf = inputs.random_faces(nx, 71), inputs.random_faces(ny, 72)
+    p, s = make_pair(orc, xf, yf, 0.03, 0.05, 1e-3, 0.3, 0.9, (D, D, D, D), (1, 0, 0.7, 0.2),
+                     (0, 0, 0, 0), precision)
+    st = inputs.perturbed_state(nx, ny, seed=73)
+    s.set_state(*st)
+    tol = 1e-12 if precision == capi.FP64 else 1e-4
+    for which in range(6):
+        want = orc.nusselt(p, st, which)
+        got = s.nusselt(which)
+        assert abs(got - want) <= tol * max(abs(want), 1.0), (which, got, want)
+    s.close()
+
+
+def test_divergence_is_reported_not_trapped(orc):
+    """Host-side fault injection: a NaN in the uploaded state makes the step
+    return RTLBFS_ERR_DIVERGED; the handle stays usable."""
+    p, s = cavity_solver(orc, 16, 1e4, capi.FP32)
+    st = list(inputs.conduction_state(p.xf, p.yf))
+    st[3] = st[3].copy()
+    st[3][5, 5] = np.nan
+    s.set_state(*st)
+    with pytest.raises(capi.RTLBFSError) as e:
+        s.step(10)
+    assert e.value.rc == capi.ERR_DIVERGED
+    s.set_state(*inputs.conduction_state(p.xf, p.yf))
+    s.step(10)
+    assert np.all(np.isfinite(s.get_state()[3]))
+    s.close()
+
+
+def test_run_controls(orc):
+    p, s = cavity_solver(orc, 16, 1e4, capi.FP64)
+    rc, n, _ = s.run_to_steady(1e-8, 0)
+    assert rc == capi.ERR_NOT_CONVERGED and n == 0
+    rc, n, _ = s.run_to_steady(1e-30, 300)
+    assert rc == capi.ERR_NOT_CONVERGED and n == 300
+    (r, _), steps = s.residual()
+    assert steps == 300
+    s.step(0)
+    assert s.residual()[1] == 300
+    s.close()
