@@ -9,6 +9,7 @@
 // closed rectilinear cell sum to zero).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace rtlbfs {
@@ -35,13 +36,18 @@ struct FaceLine {
 };
 
 // Constants of one line of cells along an axis, ghosts included.
+//
+// Eqs. 55-56 on a rectilinear mesh: with inverse-distance face values the
+// Green-Gauss derivative of cell c along a line is
+//   (phi_{c+1} - phi_c) / (w_c + w_{c+1}) + (phi_c - phi_{c-1}) / (w_{c-1} + w_c),
+// which is formed from neighbour differences (exact for the fixed-point
+// state) with is_next = 1 / (w_c + w_{c+1}).
 template <typename R>
 struct CellLine {
-    R w;      // cell width (ghost: partner's width, periodic: opposite cell's)
-    R inv_w;  // 1 / width (Eq. 55: 1/dV times the face area)
-    R dt_w;   // Delta t / width
-    R a_next; // Eq. 56 weight of this cell in the face it shares with the
-              // next cell: w_next / (w + w_next)
+    R w;        // cell width (ghost: partner's width, periodic: opposite cell's)
+    R is_next;  // 1 / (w + w_next)
+    R dt_w;     // Delta t / width
+    R pad;
 };
 
 // Read-only description of one cavity (one mesh) on the device.
@@ -81,7 +87,9 @@ __host__ __device__ __forceinline__ R rconst(double v) { return static_cast<R>(v
 
 // -------------------------------------------------------------------------
 // One face in its own frame: normal n (the "x" of a node (a, b)), tangent t.
-// q[] = (drho, u_n, u_t, T) of a cell, gn/gt its gradients along n and t.
+// q[] = (drho, u_n, u_t, T - Tbar) of a cell, gn/gt its gradients along n
+// and t.  Temperatures enter as deviations from a face reference Tbar so
+// that the O(1) energy rho*T never has to be differenced in FP32.
 // -------------------------------------------------------------------------
 template <typename R>
 struct CellNT {
@@ -101,8 +109,10 @@ struct CellNT {
 //   a = -1: left plane,  a = +1: right plane,  a = 0: mean of both (Eq. 29).
 // Central differences on the 9 nodes, written without the powers of h that
 // cancel in Eqs. 46-48 (d_x ~ 2h D_x, d_xx ~ h^2 D_xx, d_xy ~ 4h^2 D_xy).
+// The energy rho*T at a node is written Tbar + e with e = tau + drho*T,
+// tau = T - Tbar; every difference of rho*T is a difference of e.
 template <typename R>
-__device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& Rc,
+__device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& Rc, R Tbar,
                                           const FaceLine<R>& fl, bool wall, R u_wall_t,
                                           R F[4])
 {
@@ -120,20 +130,26 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
         M[k] = half * ((L.q[k] + L.gn[k] * fl.wL) + (Rc.q[k] - Rc.gn[k] * fl.wR));
         Sm[k] = hh * (L.gt[k] + Rc.gt[k]);
     }
-    // plus nodes: c = (0,0), w = (-1,0), e = (+1,0), s = (0,-1), n = (0,+1)
-    const R r0 = one + M[0], n0 = M[1], t0 = M[2], T0 = M[3];
-    const R rw = one + A[0], nw = A[1], tw = A[2], Tw = A[3];
-    const R re = one + B[0], ne = B[1], te = B[2], Te = B[3];
-    const R rs = one + (M[0] - Sm[0]), ns = M[1] - Sm[1], ts = M[2] - Sm[2], Ts = M[3] - Sm[3];
-    const R rn = one + (M[0] + Sm[0]), nn = M[1] + Sm[1], tn = M[2] + Sm[2], Tn = M[3] + Sm[3];
+    // plus nodes: c = (0,0), w = (-1,0), e = (+1,0), s = (0,-1), n = (0,+1);
+    // d* = rho - 1, t* = tangential velocity, a* = T - Tbar
+    const R d0 = M[0], n0 = M[1], t0 = M[2], a0 = M[3];
+    const R dw = A[0], nw = A[1], tw = A[2], aw = A[3];
+    const R de = B[0], ne = B[1], te = B[2], ae = B[3];
+    const R ds = M[0] - Sm[0], ns = M[1] - Sm[1], ts = M[2] - Sm[2], as = M[3] - Sm[3];
+    const R dn = M[0] + Sm[0], nn = M[1] + Sm[1], tn = M[2] + Sm[2], an = M[3] + Sm[3];
+    const R T0 = Tbar + a0, Tw = Tbar + aw, Te = Tbar + ae, Ts = Tbar + as, Tn = Tbar + an;
 
     // node products (only those the predictor and the flux use)
-    const R mn0 = r0 * n0, mt0 = r0 * t0, E0 = r0 * T0;
-    const R Pnn0 = mn0 * n0, Pnt0 = mn0 * t0, Ptt0 = mt0 * t0, Qn0 = mn0 * T0, Qt0 = mt0 * T0;
-    const R mnw = rw * nw, mtw = rw * tw, Ew = rw * Tw, Pnnw = mnw * nw, Pntw = mnw * tw, Qnw = mnw * Tw;
-    const R mne = re * ne, mte = re * te, Ee = re * Te, Pnne = mne * ne, Pnte = mne * te, Qne = mne * Te;
-    const R mns = rs * ns, mts = rs * ts, Es = rs * Ts, Pnts = mns * ts, Ptts = mts * ts, Qts = mts * Ts;
-    const R mnn = rn * nn, mtn = rn * tn, En = rn * Tn, Pntn = mnn * tn, Pttn = mtn * tn, Qtn = mtn * Tn;
+    const R mn0 = (one + d0) * n0, mt0 = (one + d0) * t0, e0 = a0 + d0 * T0;
+    const R Pnn0 = mn0 * n0, Pnt0 = mn0 * t0, Ptt0 = mt0 * t0, Qn0 = mn0 * T0;
+    const R mnw = (one + dw) * nw, mtw = (one + dw) * tw, ew = aw + dw * Tw;
+    const R Pnnw = mnw * nw, Pntw = mnw * tw, Qnw = mnw * Tw;
+    const R mne = (one + de) * ne, mte = (one + de) * te, ee = ae + de * Te;
+    const R Pnne = mne * ne, Pnte = mne * te, Qne = mne * Te;
+    const R mns = (one + ds) * ns, mts = (one + ds) * ts, es = as + ds * Ts;
+    const R Pnts = mns * ts, Ptts = mts * ts, Qts = mts * Ts;
+    const R mnn = (one + dn) * nn, mtn = (one + dn) * tn, en = an + dn * Tn;
+    const R Pntn = mnn * tn, Pttn = mtn * tn, Qtn = mtn * Tn;
     // corners (a, b): only rho u_n, rho u_t and rho u_n u_t enter (through d_xy)
     R mnc[4], mtc[4], Pntc[4];  // order (-1,-1), (-1,+1), (+1,-1), (+1,+1)
     {
@@ -150,7 +166,7 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
     }
     const R two = rconst<R>(2.0);
     // central differences
-    const R dx_mn = mne - mnw, dx_mt = mte - mtw, dx_E = Ee - Ew;
+    const R dx_mn = mne - mnw, dx_mt = mte - mtw, dx_e = ee - ew;
     const R dy_mn = mnn - mns, dy_mt = mtn - mts;
     const R dx_dr = B[0] - A[0];
     const R dy_dr = two * Sm[0];
@@ -162,7 +178,7 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
     const R dxy_mt = (mtc[3] - mtc[2]) - (mtc[1] - mtc[0]);
     const R dxx_mn = (mne + mnw) - two * mn0, dyy_mn = (mnn + mns) - two * mn0;
     const R dxx_mt = (mte + mtw) - two * mt0, dyy_mt = (mtn + mts) - two * mt0;
-    const R dxx_E = (Ee + Ew) - two * E0, dyy_E = (En + Es) - two * E0;
+    const R dxx_e = (ee + ew) - two * e0, dyy_e = (en + es) - two * e0;
     const R quarter = rconst<R>(0.25);
     const R hcs2 = rconst<R>(0.5 / 3.0);  // c_s^2 / 2
 
@@ -174,8 +190,8 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
              hcs2 * (rconst<R>(3.0) * dxx_mn + dyy_mn + half * dxy_mt);
     R mts_ = mt0 - half * ((Pnte - Pntw) + (Pttn - Ptts) + cs2 * dy_dr) +
              hcs2 * (dxx_mt + rconst<R>(3.0) * dyy_mt + half * dxy_mn);
-    // Eq. 48: (rho T)*
-    const R Es_ = E0 - half * ((Qne - Qnw) + (Qtn - Qts)) + hcs2 * (dxx_E + dyy_E);
+    // Eq. 48: (rho T)* - Tbar
+    const R es_ = e0 - half * ((Qne - Qnw) + (Qtn - Qts)) + hcs2 * (dxx_e + dyy_e);
 
     const R rho_s = one + drs;
     if (wall) {  // no mass through a wall; the wall's tangential velocity
@@ -183,16 +199,18 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
         mts_ = rho_s * u_wall_t;
     }
     const R inv = one / rho_s;
-    const R uns = mns_ * inv, uts = mts_ * inv, Tst = Es_ * inv;
+    const R uns = mns_ * inv, uts = mts_ * inv;
+    const R as_ = (es_ - drs * Tbar) * inv;  // T* - Tbar
 
     // Eqs. 57-59 braces along the face normal
     F[0] = mns_;
-    const R Xnn0 = Pnn0 + cs2 * M[0];
+    const R Xnn0 = Pnn0 + cs2 * d0;
     F[1] = Xnn0 - fl.nu_2h * (rconst<R>(3.0) * dx_mn + dy_mt) -
            fl.tf15 * ((mns_ * uns + cs2 * drs) - Xnn0);
     F[2] = Pnt0 - fl.nu_2h * (dx_mt + dy_mn) - fl.tf15 * (mns_ * uts - Pnt0);
-    F[3] = Qn0 - fl.chi_2h * dx_E - fl.tg15 * (mns_ * Tst - Qn0);
-    (void)Qt0;
+    // (rho u_n T)* - (rho u_n T)^n = Tbar (mn* - mn0) + mn* a* - mn0 a0
+    F[3] = Qn0 - fl.chi_2h * dx_e -
+           fl.tg15 * (Tbar * (mns_ - mn0) + (mns_ * as_ - mn0 * a0));
 }
 
 // Parity of quantity k (0 drho, 1 u, 2 v, 3 T) about a wall of side s:
@@ -203,5 +221,70 @@ __host__ __device__ __forceinline__ int wall_parity(int kind, int k)
     if (k == 1 || k == 2) return -1;
     return kind == kDirichlet ? -1 : +1;
 }
+
+// -------------------------------------------------------------------------
+// Storage of the state.  StoreD: FP64 values, FP64 arithmetic.  StoreQ:
+// FP32 arithmetic on a 32-bit fixed-point state (value = q * scale): an
+// explicit iteration stalls once its increments fall below half a unit of
+// the stored value, so the state keeps more bits than an FP32 mantissa for
+// these bounded fields at the same 4 bytes; increments are computed in FP32
+// and added exactly.  Ranges: rho - 1 in (-0.5, 0.5), u, v in (-1, 1),
+// T in (-2, 2); leaving a range is reported as divergence.
+// -------------------------------------------------------------------------
+struct StoreD {
+    using S = double;
+    using R = double;
+    static __host__ __device__ __forceinline__ R val(S s, int) { return s; }
+    static __host__ __device__ __forceinline__ R diff(S a, S b, int) { return a - b; }
+    static __host__ __device__ __forceinline__ S add(S s, R d, int) { return s + d; }
+    static __host__ __device__ __forceinline__ S from_double(double v, int) { return v; }
+    static __host__ __device__ __forceinline__ double to_double(S s, int) { return s; }
+    static __host__ __device__ __forceinline__ S mirror_odd(S wall2, S s) { return wall2 - s; }
+    static __host__ __device__ __forceinline__ S twice(S s) { return 2.0 * s; }
+    static __host__ __device__ __forceinline__ bool in_range(R v, int) { return v == v; }
+};
+
+struct StoreQ {
+    using S = int;
+    using R = float;
+    // scale of quantity k: 2^-32 (rho - 1), 2^-31 (u, v), 2^-30 (T)
+    static __host__ __device__ __forceinline__ double scale_d(int k)
+    {
+        return k == 0 ? 2.3283064365386963e-10 : (k == 3 ? 9.313225746154785e-10 : 4.656612873077393e-10);
+    }
+    static __host__ __device__ __forceinline__ float scale_f(int k) { return (float)scale_d(k); }
+    static __host__ __device__ __forceinline__ float limit(int k)
+    {
+        return k == 0 ? 0.49f : (k == 3 ? 1.98f : 0.99f);
+    }
+    static __host__ __device__ __forceinline__ R val(S s, int k) { return (float)s * scale_f(k); }
+    // exact integer difference (wrap-around subtraction is exact whenever the
+    // true difference fits in 32 bits), then one rounding to float
+    static __host__ __device__ __forceinline__ R diff(S a, S b, int k)
+    {
+        return (float)(int)((unsigned)a - (unsigned)b) * scale_f(k);
+    }
+    static __device__ __forceinline__ S add(S s, R d, int k)
+    {
+        return (int)((unsigned)s + (unsigned)__float2int_rn(d * (1.0f / scale_f(k))));
+    }
+    static __host__ __device__ __forceinline__ S from_double(double v, int k)
+    {
+        double q = v / scale_d(k);
+        q = q > 2147483000.0 ? 2147483000.0 : (q < -2147483000.0 ? -2147483000.0 : q);
+        return (int)(q < 0 ? q - 0.5 : q + 0.5);
+    }
+    static __host__ __device__ __forceinline__ double to_double(S s, int k) { return (double)s * scale_d(k); }
+    static __host__ __device__ __forceinline__ S mirror_odd(S wall2, S s)
+    {
+        return (int)((unsigned)wall2 - (unsigned)s);
+    }
+    // 2 s with wrap-around: exact for the mirror 2 s - x whenever that fits
+    static __host__ __device__ __forceinline__ S twice(S s) { return (int)(2u * (unsigned)s); }
+    static __host__ __device__ __forceinline__ bool in_range(R v, int k)
+    {
+        return fabsf(v) < limit(k);
+    }
+};
 
 }  // namespace rtlbfs

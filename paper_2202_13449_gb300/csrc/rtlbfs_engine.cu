@@ -64,9 +64,9 @@ void build_lines(const Cavity& c, const std::vector<double>& f, bool periodic, d
         const double w = line_width(f, i, periodic), wn = line_width(f, i + 1, periodic);
         CellLine<R> y;
         y.w = (R)w;
-        y.inv_w = (R)(1.0 / w);
+        y.is_next = (R)(1.0 / (w + wn));
         y.dt_w = (R)(dt / w);
-        y.a_next = (R)(wn / (w + wn));
+        y.pad = (R)0;
         cl[i + 2] = y;
     }
 }

@@ -28,11 +28,13 @@
 
 namespace rtlbfs {
 
-template <typename R, int TX, int TY>
+template <class P, int TX, int TY>
 struct TileSmem {
+    using S = typename P::S;
+    using R = typename P::R;
     static constexpr int BX = TX + 4, BY = TY + 4;  // tile + 2-cell halo
     static constexpr int GX = TX + 2, GY = TY + 2;  // gradient ring
-    Vec4<R> val[BY][BX];
+    Vec4<S> val[BY][BX];
     Vec4<R> gx[GY][GX];
     Vec4<R> gy[GY][GX];
     Vec4<R> fx[TY][TX + 1];
@@ -48,7 +50,7 @@ struct TileSmem {
 // Resolve global cell (gi, gj) of a cavity, ghosts included: the source
 // cell (si, sj) to read, and the wall side whose mirror rule applies
 // (-1: none).  Returns false for positions no stencil uses (corner ghosts,
-// cells beyond the ghost layer of a wall, beyond a ragged tile edge).
+// cells beyond the ghost layer of a wall).
 __device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj, int& si,
                                              int& sj, int& mside)
 {
@@ -82,22 +84,28 @@ __device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj
     return true;
 }
 
-// Ghost value of (drho, u, v, T) across wall `side` (mirror rules: rho
-// even, velocity odd about the wall velocity, T odd about T_wall on a
-// Dirichlet wall and even on an adiabatic one).
-template <typename R>
-__device__ __forceinline__ Vec4<R> mirror_value(const CavityDesc& d, int side, Vec4<R> v)
+// Ghost state across wall `side` in the storage type: rho even, velocity odd
+// about the wall velocity (normal component about 0), T odd about T_wall on
+// a Dirichlet wall and even on an adiabatic one.
+template <class P>
+__device__ __forceinline__ Vec4<typename P::S> mirror_state(const CavityDesc& d, int side,
+                                                            Vec4<typename P::S> v)
 {
-    const R two = rconst<R>(2.0);
-    const R uw = rconst<R>(d.bcU[side]);
-    if (side == kSideW || side == kSideE) {
-        v.y = -v.y;
-        v.z = two * uw - v.z;
+    using S = typename P::S;
+    const bool xn = (side == kSideW || side == kSideE);
+    const S zero2 = P::from_double(0.0, 1);
+    const S ut2 = P::from_double(2.0 * d.bcU[side], 1);
+    if (xn) {
+        v.y = P::mirror_odd(zero2, v.y);
+        v.z = P::mirror_odd(ut2, v.z);
     } else {
-        v.z = -v.z;
-        v.y = two * uw - v.y;
+        v.z = P::mirror_odd(zero2, v.z);
+        v.y = P::mirror_odd(ut2, v.y);
     }
-    if (d.kind[side] == kDirichlet) v.w = two * rconst<R>(d.bcT[side]) - v.w;
+    if (d.kind[side] == kDirichlet) {
+        const S Tw = P::from_double(d.bcT[side], 3);
+        v.w = P::mirror_odd(P::twice(Tw), v.w);
+    }
     return v;
 }
 
@@ -113,7 +121,6 @@ __device__ __forceinline__ void mirror_grad(const CavityDesc& d, int side, Vec4<
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool even = wall_parity(d.kind[side], k) > 0;
-        // normal-x wall: even -> gx = -gx; odd -> gy = -gy.  normal-y: swapped.
         if (nx_) {
             if (even) ax[k] = -ax[k];
             else ay[k] = -ay[k];
@@ -124,27 +131,32 @@ __device__ __forceinline__ void mirror_grad(const CavityDesc& d, int side, Vec4<
     }
 }
 
-template <typename R>
-__device__ __forceinline__ Vec4<R> v4_lerp(R a, const Vec4<R>& p, const Vec4<R>& q)
+template <class P>
+__device__ __forceinline__ typename P::S comp(const Vec4<typename P::S>& v, int k)
 {
-    // a p + (1 - a) q  ==  q + a (p - q)
-    Vec4<R> r;
-    r.x = q.x + a * (p.x - q.x);
-    r.y = q.y + a * (p.y - q.y);
-    r.z = q.z + a * (p.z - q.z);
-    r.w = q.w + a * (p.w - q.w);
-    return r;
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-template <typename R>
-__device__ __forceinline__ Vec4<R> v4_diff_scaled(const Vec4<R>& e, const Vec4<R>& w, R s)
+// Eqs. 55-56: Green-Gauss gradient from the four neighbour differences.
+template <class P>
+__device__ __forceinline__ void gg_gradient(const Vec4<typename P::S>& p,
+                                            const Vec4<typename P::S>& e,
+                                            const Vec4<typename P::S>& w,
+                                            const Vec4<typename P::S>& n,
+                                            const Vec4<typename P::S>& s, typename P::R ixe,
+                                            typename P::R ixw, typename P::R iyn,
+                                            typename P::R iys, Vec4<typename P::R>& gx,
+                                            Vec4<typename P::R>& gy)
 {
-    Vec4<R> r;
-    r.x = (e.x - w.x) * s;
-    r.y = (e.y - w.y) * s;
-    r.z = (e.z - w.z) * s;
-    r.w = (e.w - w.w) * s;
-    return r;
+    using R = typename P::R;
+    R* ax = &gx.x;
+    R* ay = &gy.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const auto pk = comp<P>(p, k);
+        ax[k] = P::diff(comp<P>(e, k), pk, k) * ixe + P::diff(pk, comp<P>(w, k), k) * ixw;
+        ay[k] = P::diff(comp<P>(n, k), pk, k) * iyn + P::diff(pk, comp<P>(s, k), k) * iys;
+    }
 }
 
 template <typename R>
@@ -155,15 +167,43 @@ __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
-template <typename R, int TX, int TY>
+// Build the two cells of a face in the face frame (normal along x for an
+// x-face, along y for a y-face); T enters as a deviation from Tbar = T_L.
+template <class P>
+__device__ __forceinline__ void face_cells(bool isx, const Vec4<typename P::S>& sl,
+                                           const Vec4<typename P::S>& sr,
+                                           const Vec4<typename P::R>& gxl,
+                                           const Vec4<typename P::R>& gyl,
+                                           const Vec4<typename P::R>& gxr,
+                                           const Vec4<typename P::R>& gyr,
+                                           CellNT<typename P::R>& L, CellNT<typename P::R>& Rr,
+                                           typename P::R& Tbar)
+{
+    using R = typename P::R;
+    Tbar = P::val(sl.w, 3);
+    const R tR = P::diff(sr.w, sl.w, 3);
+    const R dl = P::val(sl.x, 0), ul = P::val(sl.y, 1), vl = P::val(sl.z, 2);
+    const R dr = P::val(sr.x, 0), ur = P::val(sr.y, 1), vr = P::val(sr.z, 2);
+    if (isx) {
+        L = {{dl, ul, vl, R(0)}, {gxl.x, gxl.y, gxl.z, gxl.w}, {gyl.x, gyl.y, gyl.z, gyl.w}};
+        Rr = {{dr, ur, vr, tR}, {gxr.x, gxr.y, gxr.z, gxr.w}, {gyr.x, gyr.y, gyr.z, gyr.w}};
+    } else {
+        L = {{dl, vl, ul, R(0)}, {gyl.x, gyl.z, gyl.y, gyl.w}, {gxl.x, gxl.z, gxl.y, gxl.w}};
+        Rr = {{dr, vr, ur, tR}, {gyr.x, gyr.z, gyr.y, gyr.w}, {gxr.x, gxr.z, gxr.y, gxr.w}};
+    }
+}
+
+template <class P, int TX, int TY>
 __global__ void __launch_bounds__(kStepThreads)
 step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
 {
-    using S = TileSmem<R, TX, TY>;
-    constexpr int BX = S::BX, BY = S::BY, GX = S::GX, GY = S::GY;
+    using Sm = TileSmem<P, TX, TY>;
+    using S = typename P::S;
+    using R = typename P::R;
+    constexpr int BX = Sm::BX, BY = Sm::BY, GX = Sm::GX, GY = Sm::GY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S& sm = *reinterpret_cast<S*>(smem_raw);
+    Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
     const int ntiles = *ntiles_ptr;
 
@@ -174,12 +214,12 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         CavityCtl* ctl = &ctls[slot];
         if (ctl->done) continue;  // uniform across the block
         const int cur = ctl->cur;
-        const R* fin[4];
-        R* fout[4];
+        const S* fin[4];
+        S* fout[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            fin[k] = static_cast<const R*>(d.f[cur][k]);
-            fout[k] = static_cast<R*>(d.f[cur ^ 1][k]);
+            fin[k] = static_cast<const S*>(d.f[cur][k]);
+            fout[k] = static_cast<S*>(d.f[cur ^ 1][k]);
         }
         const int nx = d.nx, ny = d.ny, pitch = d.pitch;
         const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
@@ -198,14 +238,14 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         for (int k = tid; k < BX * BY; k += kStepThreads) {
             const int c = k % BX, r = k / BX;
             int si, sj, ms;
-            Vec4<R> v = {R(0), R(0), R(0), R(0)};
+            Vec4<S> v = {S(0), S(0), S(0), S(0)};
             if (resolve_cell(d, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
                 const size_t o = (size_t)sj * pitch + si;
                 v.x = fin[0][o];
                 v.y = fin[1][o];
                 v.z = fin[2][o];
                 v.w = fin[3][o];
-                if (ms >= 0) v = mirror_value(d, ms, v);
+                if (ms >= 0) v = mirror_state<P>(d, ms, v);
             }
             sm.val[r][c] = v;
         }
@@ -223,15 +263,9 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 else if (ms == kSideE) c -= 1;
                 else if (ms == kSideS) r += 1;
                 else if (ms == kSideN) r -= 1;
-                const CellLine<R>& lx = sm.xc[c];
-                const CellLine<R>& ly = sm.yc[r];
-                const Vec4<R> p = sm.val[r][c];
-                const Vec4<R> fe = v4_lerp(lx.a_next, p, sm.val[r][c + 1]);
-                const Vec4<R> fw = v4_lerp(sm.xc[c - 1].a_next, sm.val[r][c - 1], p);
-                const Vec4<R> fn = v4_lerp(ly.a_next, p, sm.val[r + 1][c]);
-                const Vec4<R> fs = v4_lerp(sm.yc[r - 1].a_next, sm.val[r - 1][c], p);
-                gxv = v4_diff_scaled(fe, fw, lx.inv_w);
-                gyv = v4_diff_scaled(fn, fs, ly.inv_w);
+                gg_gradient<P>(sm.val[r][c], sm.val[r][c + 1], sm.val[r][c - 1], sm.val[r + 1][c],
+                               sm.val[r - 1][c], sm.xc[c].is_next, sm.xc[c - 1].is_next,
+                               sm.yc[r].is_next, sm.yc[r - 1].is_next, gxv, gyv);
                 if (ms >= 0) mirror_grad(d, ms, gxv, gyv);
             }
             sm.gx[gr][gc] = gxv;
@@ -255,31 +289,20 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const bool valid = isx ? (gi <= nx && gj < ny) : (gi < nx && gj <= ny);
             Vec4<R> out = {R(0), R(0), R(0), R(0)};
             if (valid) {
-                // left/right cells in box and gradient-ring coordinates
                 const int lc = isx ? fc + 1 : fc + 2, lr = isx ? fr + 2 : fr + 1;
                 const int rc = fc + 2, rr = fr + 2;
-                const Vec4<R> vl = sm.val[lr][lc], vr = sm.val[rr][rc];
-                const Vec4<R> gxl = sm.gx[lr - 1][lc - 1], gyl = sm.gy[lr - 1][lc - 1];
-                const Vec4<R> gxr = sm.gx[rr - 1][rc - 1], gyr = sm.gy[rr - 1][rc - 1];
                 CellNT<R> L, Rr;
-                if (isx) {
-                    L = {{vl.x, vl.y, vl.z, vl.w}, {gxl.x, gxl.y, gxl.z, gxl.w},
-                         {gyl.x, gyl.y, gyl.z, gyl.w}};
-                    Rr = {{vr.x, vr.y, vr.z, vr.w}, {gxr.x, gxr.y, gxr.z, gxr.w},
-                          {gyr.x, gyr.y, gyr.z, gyr.w}};
-                } else {
-                    L = {{vl.x, vl.z, vl.y, vl.w}, {gyl.x, gyl.z, gyl.y, gyl.w},
-                         {gxl.x, gxl.z, gxl.y, gxl.w}};
-                    Rr = {{vr.x, vr.z, vr.y, vr.w}, {gyr.x, gyr.z, gyr.y, gyr.w},
-                          {gxr.x, gxr.z, gxr.y, gxr.w}};
-                }
+                R Tbar;
+                face_cells<P>(isx, sm.val[lr][lc], sm.val[rr][rc], sm.gx[lr - 1][lc - 1],
+                              sm.gy[lr - 1][lc - 1], sm.gx[rr - 1][rc - 1], sm.gy[rr - 1][rc - 1],
+                              L, Rr, Tbar);
                 const FaceLine<R> fl = isx ? sm.xl[fc] : sm.yl[fr];
                 int wside = -1;
                 if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
                 if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
                 const R uw = wside >= 0 ? rconst<R>(d.bcU[wside]) : R(0);
                 R F[4];
-                face_flux<R>(L, Rr, fl, wside >= 0, uw, F);
+                face_flux<R>(L, Rr, Tbar, fl, wside >= 0, uw, F);
                 if (isx) out = {F[0], F[1], F[2], F[3]};
                 else out = {F[0], F[2], F[1], F[3]};
             }
@@ -288,39 +311,53 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         }
         __syncthreads();
 
-        // ---- 4. update, 5. residual sums --------------------------------
+        // ---- 4. update (increment form), 5. residual sums ---------------
         R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+        const R one = rconst<R>(1.0);
+        const R dt = rconst<R>(d.dt), bg = rconst<R>(d.beta_g), Tr = rconst<R>(d.T_ref);
+        const R fxb = rconst<R>(d.fx), fyb = rconst<R>(d.fy);
+        bool bad = false;
         for (int k = tid; k < TX * TY; k += kStepThreads) {
             const int tc = k % TX, tr = k / TX;
             const int gi = i0 + tc, gj = j0 + tr;
             if (gi >= nx || gj >= ny) continue;
-            const Vec4<R> p = sm.val[tr + 2][tc + 2];
+            const Vec4<S> p = sm.val[tr + 2][tc + 2];
             const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
             const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
             const R ax = sm.xc[tc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
-            const R one = rconst<R>(1.0);
-            const R rho = one + p.x;
-            const R dt = rconst<R>(d.dt);
-            const R src_x = rho * rconst<R>(d.fx);
-            const R src_y = rho * (rconst<R>(d.beta_g) * (p.w - rconst<R>(d.T_ref)) + rconst<R>(d.fy));
-            const R dr1 = p.x - ax * (Fe.x - Fw.x) - ay * (Fn.x - Fs.x);
-            const R mx1 = rho * p.y - ax * (Fe.y - Fw.y) - ay * (Fn.y - Fs.y) + dt * src_x;
-            const R my1 = rho * p.z - ax * (Fe.z - Fw.z) - ay * (Fn.z - Fs.z) + dt * src_y;
-            const R E1 = rho * p.w - ax * (Fe.w - Fw.w) - ay * (Fn.w - Fs.w);
-            const R inv = one / (one + dr1);
-            const R u1 = mx1 * inv, v1 = my1 * inv, T1 = E1 * inv;
+            const R dr = P::val(p.x, 0), u = P::val(p.y, 1), v = P::val(p.z, 2), T = P::val(p.w, 3);
+            const R rho = one + dr;
+            // Dt/dV sum_k F_k dS_k for mass, momentum, energy
+            const R div0 = ax * (Fe.x - Fw.x) + ay * (Fn.x - Fs.x);
+            const R div1 = ax * (Fe.y - Fw.y) + ay * (Fn.y - Fs.y);
+            const R div2 = ax * (Fe.z - Fw.z) + ay * (Fn.z - Fs.z);
+            const R div3 = ax * (Fe.w - Fw.w) + ay * (Fn.w - Fs.w);
+            // Boussinesq source (Eq. 64, hot fluid rises) and body force
+            const R src_x = rho * fxb;
+            const R src_y = rho * (bg * (T - Tr) + fyb);
+            // rho^{n+1} = rho - div0; q^{n+1} - q = (q div0 - div_q + dt src) / rho^{n+1}
+            const R inv = one / (rho - div0);
+            const R du = (u * div0 - div1 + dt * src_x) * inv;
+            const R dv = (v * div0 - div2 + dt * src_y) * inv;
+            const R dT = (T * div0 - div3) * inv;
+            const R dr1 = dr - div0, u1 = u + du, v1 = v + dv, T1 = T + dT;
             const size_t o = (size_t)gj * pitch + gi;
-            fout[0][o] = dr1;
-            fout[1][o] = u1;
-            fout[2][o] = v1;
-            fout[3][o] = T1;
-            const R m0 = sqrt(p.y * p.y + p.z * p.z), m1 = sqrt(u1 * u1 + v1 * v1);
-            const R du = m1 - m0, dT = T1 - p.w;
-            s0 += du * du;
+            fout[0][o] = P::add(p.x, -div0, 0);
+            fout[1][o] = P::add(p.y, du, 1);
+            fout[2][o] = P::add(p.z, dv, 2);
+            fout[3][o] = P::add(p.w, dT, 3);
+            bad = bad || !(P::in_range(dr1, 0) && P::in_range(u1, 1) && P::in_range(v1, 2) &&
+                           P::in_range(T1, 3));
+            // |u|^{n+1} - |u|^n without cancellation
+            const R m0 = sqrt(u * u + v * v), m1 = sqrt(u1 * u1 + v1 * v1);
+            const R den = m0 + m1;
+            const R dm = den > R(0) ? (du * (u + u1) + dv * (v + v1)) / den : R(0);
+            s0 += dm * dm;
             s1 += m1 * m1;
             s2 += dT * dT;
             s3 += T1 * T1;
         }
+        if (bad) s0 = R(NAN);
         // warp sums in R, then FP64 across warps and tiles
         s0 = warp_sum(s0);
         s1 = warp_sum(s1);
@@ -340,8 +377,8 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
             __threadfence();
             const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-            sm.last = (prev == (unsigned)d.ntiles - 1u);
-            if (sm.last) {
+            if (prev == (unsigned)d.ntiles - 1u) {
+                // last tile of this cavity in this step: finalize
                 __threadfence();
                 volatile double* acc = ctl->acc;
                 const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
@@ -369,25 +406,25 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
 // ---------------------------------------------------------------------------
 // FP64 evaluation straight from global memory (Nusselt reductions).
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ bool load_cell_d(const CavityDesc& d, const R* const* f, int gi, int gj,
+template <class P>
+__device__ bool load_cell_d(const CavityDesc& d, const typename P::S* const* f, int gi, int gj,
                             Vec4<double>& v)
 {
     int si, sj, ms;
     if (!resolve_cell(d, gi, gj, si, sj, ms)) return false;
     const size_t o = (size_t)sj * d.pitch + si;
-    Vec4<double> x = {(double)f[0][o], (double)f[1][o], (double)f[2][o], (double)f[3][o]};
-    if (ms >= 0) x = mirror_value<double>(d, ms, x);
-    v = x;
+    Vec4<typename P::S> x = {f[0][o], f[1][o], f[2][o], f[3][o]};
+    if (ms >= 0) x = mirror_state<P>(d, ms, x);
+    v = {P::to_double(x.x, 0), P::to_double(x.y, 1), P::to_double(x.z, 2), P::to_double(x.w, 3)};
     return true;
 }
 
 // Green-Gauss gradient (Eqs. 55-56) of cell (gi, gj) in FP64; a wall ghost
 // mirrors its partner's.  xc/yc: FP64 cell lines (index i + 2).
-template <typename R>
-__device__ void grad_d(const CavityDesc& d, const R* const* f, const CellLine<double>* xc,
-                       const CellLine<double>* yc, int gi, int gj, Vec4<double>& gx,
-                       Vec4<double>& gy)
+template <class P>
+__device__ void grad_d(const CavityDesc& d, const typename P::S* const* f,
+                       const CellLine<double>* xc, const CellLine<double>* yc, int gi, int gj,
+                       Vec4<double>& gx, Vec4<double>& gy)
 {
     int si, sj, ms;
     gx = {0, 0, 0, 0};
@@ -398,59 +435,53 @@ __device__ void grad_d(const CavityDesc& d, const R* const* f, const CellLine<do
     else if (ms == kSideE) ci -= 1;
     else if (ms == kSideS) cj += 1;
     else if (ms == kSideN) cj -= 1;
-    Vec4<double> p, e, w, n, s;
-    load_cell_d(d, f, ci, cj, p);
-    load_cell_d(d, f, ci + 1, cj, e);
-    load_cell_d(d, f, ci - 1, cj, w);
-    load_cell_d(d, f, ci, cj + 1, n);
-    load_cell_d(d, f, ci, cj - 1, s);
-    const CellLine<double>& lx = xc[ci + 2];
-    const CellLine<double>& ly = yc[cj + 2];
-    gx = v4_diff_scaled(v4_lerp(lx.a_next, p, e), v4_lerp(xc[ci + 1].a_next, w, p), lx.inv_w);
-    gy = v4_diff_scaled(v4_lerp(ly.a_next, p, n), v4_lerp(yc[cj + 1].a_next, s, p), ly.inv_w);
-    if (ms >= 0) mirror_grad<double>(d, ms, gx, gy);
+    Vec4<double> p = {0, 0, 0, 0}, e = p, w = p, n = p, s = p;
+    load_cell_d<P>(d, f, ci, cj, p);
+    load_cell_d<P>(d, f, ci + 1, cj, e);
+    load_cell_d<P>(d, f, ci - 1, cj, w);
+    load_cell_d<P>(d, f, ci, cj + 1, n);
+    load_cell_d<P>(d, f, ci, cj - 1, s);
+    gg_gradient<StoreD>(p, e, w, n, s, xc[ci + 2].is_next, xc[ci + 1].is_next, yc[cj + 2].is_next,
+                        yc[cj + 1].is_next, gx, gy);
+    if (ms >= 0) mirror_grad(d, ms, gx, gy);
 }
 
 // Energy flux (Eq. 59 brace) through x-face (i, j) (nd = 0) or y-face
 // (nd = 1), in FP64.
-template <typename R>
-__device__ double energy_flux_d(const CavityDesc& d, const R* const* f, const NuLines& ln,
-                                int nd, int i, int j)
+template <class P>
+__device__ double energy_flux_d(const CavityDesc& d, const typename P::S* const* f,
+                                const NuLines& ln, int nd, int i, int j)
 {
     const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
     const int li = nd == 0 ? i - 1 : i, lj = nd == 0 ? j : j - 1;
     Vec4<double> vl = {0, 0, 0, 0}, vr = vl, gxl, gyl, gxr, gyr;
-    load_cell_d(d, f, li, lj, vl);
-    load_cell_d(d, f, i, j, vr);
-    grad_d(d, f, ln.xc, ln.yc, li, lj, gxl, gyl);
-    grad_d(d, f, ln.xc, ln.yc, i, j, gxr, gyr);
+    load_cell_d<P>(d, f, li, lj, vl);
+    load_cell_d<P>(d, f, i, j, vr);
+    grad_d<P>(d, f, ln.xc, ln.yc, li, lj, gxl, gyl);
+    grad_d<P>(d, f, ln.xc, ln.yc, i, j, gxr, gyr);
     CellNT<double> L, Rr;
-    if (nd == 0) {
-        L = {{vl.x, vl.y, vl.z, vl.w}, {gxl.x, gxl.y, gxl.z, gxl.w}, {gyl.x, gyl.y, gyl.z, gyl.w}};
-        Rr = {{vr.x, vr.y, vr.z, vr.w}, {gxr.x, gxr.y, gxr.z, gxr.w}, {gyr.x, gyr.y, gyr.z, gyr.w}};
-    } else {
-        L = {{vl.x, vl.z, vl.y, vl.w}, {gyl.x, gyl.z, gyl.y, gyl.w}, {gxl.x, gxl.z, gxl.y, gxl.w}};
-        Rr = {{vr.x, vr.z, vr.y, vr.w}, {gyr.x, gyr.z, gyr.y, gyr.w}, {gxr.x, gxr.z, gxr.y, gxr.w}};
-    }
+    double Tbar;
+    face_cells<StoreD>(nd == 0, vl, vr, gxl, gyl, gxr, gyr, L, Rr, Tbar);
     int wside = -1;
     if (nd == 0 && !xper) wside = i == 0 ? kSideW : (i == d.nx ? kSideE : -1);
     if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
     const FaceLine<double> fl = nd == 0 ? ln.xl[i] : ln.yl[j];
     double F[4];
-    face_flux<double>(L, Rr, fl, wside >= 0, wside >= 0 ? d.bcU[wside] : 0.0, F);
+    face_flux<double>(L, Rr, Tbar, fl, wside >= 0, wside >= 0 ? d.bcU[wside] : 0.0, F);
     return F[3];
 }
 
 // Partial sums of a Nusselt number: one partial per block, in block order.
-template <typename R>
+template <class P>
 __global__ void __launch_bounds__(256)
 nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityCtl* __restrict__ ctls,
                        int slot, NuLines ln, int which, double* __restrict__ partial)
 {
+    using S = typename P::S;
     const CavityDesc& d = descs[slot];
     const int cur = ctls[slot].cur;
-    const R* f[4] = {static_cast<const R*>(d.f[cur][0]), static_cast<const R*>(d.f[cur][1]),
-                     static_cast<const R*>(d.f[cur][2]), static_cast<const R*>(d.f[cur][3])};
+    const S* f[4] = {static_cast<const S*>(d.f[cur][0]), static_cast<const S*>(d.f[cur][1]),
+                     static_cast<const S*>(d.f[cur][2]), static_cast<const S*>(d.f[cur][3])};
     long long count;
     if (which == kNuWest || which == kNuEast || which == kNuHalf) count = d.ny;
     else if (which == kNuSouth || which == kNuNorth) count = d.nx;
@@ -461,16 +492,16 @@ nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityCtl* __
         if (which == kNuWest || which == kNuEast || which == kNuHalf) {
             const int i = which == kNuWest ? 0 : (which == kNuEast ? d.nx : d.nx / 2);
             const int j = (int)k;
-            s += energy_flux_d(d, f, ln, 0, i, j) * ln.yc[j + 2].w;
+            s += energy_flux_d<P>(d, f, ln, 0, i, j) * ln.yc[j + 2].w;
         } else if (which == kNuSouth || which == kNuNorth) {
             const int i = (int)k;
             const int j = which == kNuSouth ? 0 : d.ny;
-            s += energy_flux_d(d, f, ln, 1, i, j) * ln.xc[i + 2].w;
+            s += energy_flux_d<P>(d, f, ln, 1, i, j) * ln.xc[i + 2].w;
         } else {  // Eq. 69 integrand (u T - chi dT/dx) dV
             const int i = (int)(k % d.nx), j = (int)(k / d.nx);
-            Vec4<double> p, gx, gy;
-            load_cell_d(d, f, i, j, p);
-            grad_d(d, f, ln.xc, ln.yc, i, j, gx, gy);
+            Vec4<double> p = {0, 0, 0, 0}, gx, gy;
+            load_cell_d<P>(d, f, i, j, p);
+            grad_d<P>(d, f, ln.xc, ln.yc, i, j, gx, gy);
             s += (p.y * p.w - d.chi * gx.w) * ln.xc[i + 2].w * ln.yc[j + 2].w;
         }
     }
@@ -500,36 +531,38 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 }
 
 // State conversion: FP64 host-layout staging (rho, u, v, T planes of n
-// cells, row-major nx) <-> device fields (drho, u, v, T with row pitch).
-template <typename R>
+// cells, row-major nx) <-> device storage (rho - 1, u, v, T with row pitch).
+template <class P>
 __global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, int pitch,
-                                R* f0, R* f1, R* f2, R* f3)
+                                typename P::S* f0, typename P::S* f1, typename P::S* f2,
+                                typename P::S* f3)
 {
     const long long n = (long long)nx * ny;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
         const size_t o = (size_t)j * pitch + i;
-        f0[o] = (R)(st[k] - 1.0);
-        f1[o] = (R)st[n + k];
-        f2[o] = (R)st[2 * n + k];
-        f3[o] = (R)st[3 * n + k];
+        f0[o] = P::from_double(st[k] - 1.0, 0);
+        f1[o] = P::from_double(st[n + k], 1);
+        f2[o] = P::from_double(st[2 * n + k], 2);
+        f3[o] = P::from_double(st[3 * n + k], 3);
     }
 }
 
-template <typename R>
+template <class P>
 __global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pitch,
-                                 const R* f0, const R* f1, const R* f2, const R* f3)
+                                 const typename P::S* f0, const typename P::S* f1,
+                                 const typename P::S* f2, const typename P::S* f3)
 {
     const long long n = (long long)nx * ny;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
         const size_t o = (size_t)j * pitch + i;
-        st[k] = 1.0 + (double)f0[o];
-        st[n + k] = (double)f1[o];
-        st[2 * n + k] = (double)f2[o];
-        st[3 * n + k] = (double)f3[o];
+        st[k] = 1.0 + P::to_double(f0[o], 0);
+        st[n + k] = P::to_double(f1[o], 1);
+        st[2 * n + k] = P::to_double(f2[o], 2);
+        st[3 * n + k] = P::to_double(f3[o], 3);
     }
 }
 
@@ -554,47 +587,47 @@ __global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double t
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-template <typename R>
+template <class P>
 static size_t step_smem_bytes()
 {
-    return sizeof(TileSmem<R, kTileX, kTileY>);
+    return sizeof(TileSmem<P, kTileX, kTileY>);
 }
 
 size_t step_smem(int precision)
 {
-    return precision == 0 ? step_smem_bytes<double>() : step_smem_bytes<float>();
+    return precision == 0 ? step_smem_bytes<StoreD>() : step_smem_bytes<StoreQ>();
 }
 
 cudaError_t step_prepare(int precision)
 {
     if (precision == 0)
-        return cudaFuncSetAttribute(step_kernel<double, kTileX, kTileY>,
+        return cudaFuncSetAttribute(step_kernel<StoreD, kTileX, kTileY>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)step_smem_bytes<double>());
-    return cudaFuncSetAttribute(step_kernel<float, kTileX, kTileY>,
+                                    (int)step_smem_bytes<StoreD>());
+    return cudaFuncSetAttribute(step_kernel<StoreQ, kTileX, kTileY>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<float>());
+                                (int)step_smem_bytes<StoreQ>());
 }
 
 cudaError_t step_occupancy(int precision, int* blocks_per_sm)
 {
     if (precision == 0)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            blocks_per_sm, step_kernel<double, kTileX, kTileY>, kStepThreads,
-            step_smem_bytes<double>());
+            blocks_per_sm, step_kernel<StoreD, kTileX, kTileY>, kStepThreads,
+            step_smem_bytes<StoreD>());
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, step_kernel<float, kTileX, kTileY>, kStepThreads,
-        step_smem_bytes<float>());
+        blocks_per_sm, step_kernel<StoreQ, kTileX, kTileY>, kStepThreads,
+        step_smem_bytes<StoreQ>());
 }
 
 cudaError_t launch_step(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
                         CavityCtl* ctls, const int4* tiles, const int* ntiles)
 {
     if (precision == 0)
-        step_kernel<double, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<double>(), s>>>(
+        step_kernel<StoreD, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<StoreD>(), s>>>(
             descs, ctls, tiles, ntiles);
     else
-        step_kernel<float, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<float>(), s>>>(
+        step_kernel<StoreQ, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<StoreQ>(), s>>>(
             descs, ctls, tiles, ntiles);
     return cudaGetLastError();
 }
@@ -608,9 +641,9 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     if (precision == 0)
-        nusselt_partial_kernel<double><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
+        nusselt_partial_kernel<StoreD><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
     else
-        nusselt_partial_kernel<float><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
+        nusselt_partial_kernel<StoreQ><<<blocks, 256, 0, s>>>(descs, ctls, slot, ln, which, partial);
     sum_partials_kernel<<<1, 256, 0, s>>>(partial, blocks, scale, out);
     return cudaGetLastError();
 }
@@ -622,11 +655,11 @@ cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_in_kernel<double><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (double*)f[0],
+        state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (double*)f[0],
                                                        (double*)f[1], (double*)f[2], (double*)f[3]);
     else
-        state_in_kernel<float><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (float*)f[0],
-                                                      (float*)f[1], (float*)f[2], (float*)f[3]);
+        state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (int*)f[0], (int*)f[1],
+                                                       (int*)f[2], (int*)f[3]);
     return cudaGetLastError();
 }
 
@@ -637,13 +670,13 @@ cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, 
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_out_kernel<double><<<blocks, 256, 0, s>>>(
+        state_out_kernel<StoreD><<<blocks, 256, 0, s>>>(
             st, nx, ny, pitch, (const double*)f[0], (const double*)f[1], (const double*)f[2],
             (const double*)f[3]);
     else
-        state_out_kernel<float><<<blocks, 256, 0, s>>>(
-            st, nx, ny, pitch, (const float*)f[0], (const float*)f[1], (const float*)f[2],
-            (const float*)f[3]);
+        state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (const int*)f[0],
+                                                        (const int*)f[1], (const int*)f[2],
+                                                        (const int*)f[3]);
     return cudaGetLastError();
 }
 
