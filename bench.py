@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the RTLBFS time step (arXiv 2202.13449) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+One bench "step" is one pass of the whole hot path over the workload: for
+the single-cavity workloads, ``inner`` consecutive explicit time steps
+(fused face sweep, update, boundary conditions and the FP64 residual
+reduction of every step), replayed as CUDA graphs; L2 is flushed between
+bench steps.  Prints one JSON line (rank 0).
+
+value      M cell-updates/s over all ranks, inputs resident in HBM, CUDA events
+           on the library's stream around each bench step (max over ranks)
+e2e        the same metric through the C ABI with host buffers: upload of the
+           state, the steps, download of the state, all timed
+roofline   the step kernel: algorithmic bytes (32 B per cell-update in FP32,
+           64 B in FP64) / average launch time, against the measured HBM peak
+cpu_baseline  the FP64 CPU oracle timed on this host on a bounded sample
+N > 1      independent replicas, one per GPU (weak scaling): the workload has
+           no data exchange between cavities.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, n or (nx, ny), phi, Ra, Pr, Ma, precision, inner steps, kind)
+    "cavity512": dict(
+        desc="differentially heated cavity 512x512, tanh stretching phi=2.0 (Eq. 74), "
+             "Ra=1e8, Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions",
+        nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=1000,
+        kind="cavity"),
+    "cavity64": dict(
+        desc="differentially heated cavity 64x64 uniform, Ra=1e3, Pr=0.71, Ma=0.1, FP64",
+        nx=64, ny=64, phi=0.0, Ra=1e3, Pr=0.71, Ma=0.1, precision="fp64", inner=1000,
+        kind="cavity"),
+    "rb1024x512": dict(
+        desc="Rayleigh-Benard 2:1 box 1024x512 uniform, periodic in x, Ra=1e6, Pr=0.71, "
+             "Ma=0.1, FP32 bulk + FP64 reductions, seeded noise 1e-3",
+        nx=1024, ny=512, phi=0.0, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32", inner=500,
+        kind="rb"),
+    "cavity512_fp64": dict(
+        desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
+        nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
+        kind="cavity"),
+}
+DEFAULT_WORKLOAD = "cavity512"
+STEP_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_step.cu",
+                "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh",
+                "paper_2202_13449_gb300/csrc/rtlbfs_kernels.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in STEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(f"{workload}:{precision}")
+        if e and e.get("kernel_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rtlbfs_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def setup_solver(capi, inputs, w):
+    import numpy as np
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
+    nx, ny = w["nx"], w["ny"]
+    if w["kind"] == "cavity":
+        xf = capi.tanh_faces(nx, float(nx), w["phi"])
+        yf = capi.tanh_faces(ny, float(ny), w["phi"])
+        s = capi.Solver(xf, yf, prec)
+        dt = 0.5 * float(min(np.min(np.diff(xf)), np.min(np.diff(yf))))
+        s.set_params(w["Ra"], w["Pr"], w["Ma"], dt)
+        st = inputs.conduction_state(xf, yf)
+    else:  # Rayleigh-Benard: periodic x, hot bottom, cold top; L = H
+        xf = inputs.uniform_faces(nx)
+        yf = inputs.uniform_faces(ny)
+        s = capi.Solver(xf, yf, prec)
+        s.set_bc(capi.WEST, capi.PERIODIC)
+        s.set_bc(capi.EAST, capi.PERIODIC)
+        s.set_bc(capi.SOUTH, capi.WALL_DIRICHLET, 1.0)
+        s.set_bc(capi.NORTH, capi.WALL_DIRICHLET, 0.0)
+        s.set_params_ref(w["Ra"], w["Pr"], w["Ma"], 0.5, float(ny), 1.0, 0.5)
+        st = inputs.rb_state(xf, yf, amp=1e-3, seed=0)
+    s.set_state(*st)
+    return s, st, xf, yf
+
+
+def run_ours(args, w):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    cells = w["nx"] * w["ny"]
+    inner = args.inner or w["inner"]
+    s, st0, xf, yf = setup_solver(capi, inputs, w)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        s.step(inner)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = capi.launch_count()
+    ev = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed iterations (not timed)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(inner)
+        b.record(stream)
+        ev.append((a, b))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    updates = cells * inner * args.steps * ws
+    value = updates / (ms_max * 1e-3) / 1e6
+
+    # e2e through the C ABI with host buffers
+    import numpy as np
+    host = [np.ascontiguousarray(a, dtype=np.float64) for a in st0]
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(*host)
+        s.step(inner)
+        out = s.get_state()
+    torch.cuda.synchronize()
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t_e2e, op=torch.distributed.ReduceOp.MAX)
+    e2e = cells * inner * e2e_steps * ws / float(t_e2e.item()) / 1e6
+    assert np.all(np.isfinite(out[3]))
+    bytes_io = 4 * cells * 8
+
+    rs = 4 if w["precision"] == "fp32" else 8
+    alg_bytes = 8 * rs * cells  # read 4 fields + write 4 fields per cell
+    per_launch_s = ms_max * 1e-3 / (inner * args.steps)
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    res, steps_total = s.residual()
+    line = {
+        "metric": "M cell-updates/s (whole job) and fraction of the HBM roofline",
+        "value": round(value, 2),
+        "unit": "M cell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if w["precision"] == "fp32" else "f64",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "time_steps_per_bench_step": inner, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between bench steps (256 MB write)",
+                   "state_bytes_per_buffer": 4 * rs * cells},
+        "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": profile_traffic(args.workload, w["precision"]),
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "rtlbfs::step_kernel", "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+        "wall_s": round(t_wall, 3),
+        "residual_last_step": res,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def oracle_problem(oracle, inputs, w):
+    import numpy as np
+    nx, ny = w["nx"], w["ny"]
+    if w["kind"] == "cavity":
+        xf = oracle.tanh_faces(nx, float(nx), w["phi"])
+        yf = oracle.tanh_faces(ny, float(ny), w["phi"])
+        nu, chi, bg = oracle.params_from_ra(w["Ra"], w["Pr"], w["Ma"], float(nx))
+        dt = 0.5 * float(min(np.min(np.diff(xf)), np.min(np.diff(yf))))
+        p = oracle.Problem(xf=xf, yf=yf, nu=nu, chi=chi, beta_g=bg, dt=dt)
+        st = inputs.conduction_state(xf, yf)
+    else:
+        xf, yf = inputs.uniform_faces(nx), inputs.uniform_faces(ny)
+        nu, chi, bg = oracle.params_from_ra(w["Ra"], w["Pr"], w["Ma"], float(ny))
+        p = oracle.Problem(xf=xf, yf=yf, nu=nu, chi=chi, beta_g=bg, dt=0.5,
+                           bc_kind=(oracle.PERIODIC, oracle.PERIODIC, oracle.DIRICHLET,
+                                    oracle.DIRICHLET), bc_T=(0, 0, 1, 0))
+        st = inputs.rb_state(xf, yf, amp=1e-3, seed=0)
+    return p, st
+
+
+def cpu_baseline(w, seconds):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample
+    of the same workload (time steps of the same mesh until `seconds`)."""
+    import oracle
+    from paper_2202_13449_gb300 import inputs
+    oracle.build()
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    p, st = oracle_problem(oracle, inputs, w)
+    cells = w["nx"] * w["ny"]
+    st, _, _ = oracle.step(p, st, 1)  # warm
+    n, t0 = 0, time.perf_counter()
+    chunk = 2
+    while time.perf_counter() - t0 < seconds:
+        st, _, _ = oracle.step(p, st, chunk)
+        n += chunk
+    dt = time.perf_counter() - t0
+    return {"value": round(cells * n / dt / 1e6, 3), "unit": "M cell-updates/s", "cores": used,
+            "kind": "oracle",
+            "sample": f"{n} FP64 time steps of the same {w['nx']}x{w['ny']} mesh "
+                      f"({dt:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2202_13449_gb300 import inputs
+    oracle.build()
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    p, st = oracle_problem(oracle, inputs, w)
+    cells = w["nx"] * w["ny"]
+    per_step = max(1, int(args.ref_steps_per_step))
+    for _ in range(args.warmup):
+        st, _, _ = oracle.step(p, st, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _, _ = oracle.step(p, st, per_step)
+    dt = time.perf_counter() - t0
+    value = cells * per_step * args.steps / dt / 1e6
+    line = {
+        "impl": "reference",
+        "metric": "M cell-updates/s (whole job) and fraction of the HBM roofline",
+        "value": round(value, 3), "unit": "M cell-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "time_steps_per_bench_step": per_step,
+                   "note": "reference arm = the FP64 CPU oracle (the paper ships no code)"},
+        "e2e": {"value": round(value, 3), "unit": "M cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": round(value, 3), "unit": "M cell-updates/s", "cores": used,
+                         "kind": "oracle",
+                         "sample": f"{args.steps} x {per_step} FP64 time steps of the "
+                                   f"{w['nx']}x{w['ny']} mesh"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", type=int, default=0, help="time steps per bench step")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -85,6 +85,10 @@ struct Vec4 {
 template <typename R>
 __host__ __device__ __forceinline__ R rconst(double v) { return static_cast<R>(v); }
 
+// 1/x: IEEE in FP64; the hardware approximation (a few ulp) in FP32.
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+
 // -------------------------------------------------------------------------
 // One face in its own frame: normal n (the "x" of a node (a, b)), tangent t.
 // q[] = (drho, u_n, u_t, T - Tbar) of a cell, gn/gt its gradients along n
@@ -198,7 +202,7 @@ __device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& R
         mns_ = rconst<R>(0.0);
         mts_ = rho_s * u_wall_t;
     }
-    const R inv = one / rho_s;
+    const R inv = fast_rcp(rho_s);
     const R uns = mns_ * inv, uts = mts_ * inv;
     const R as_ = (es_ - drs * Tbar) * inv;  // T* - Tbar
 
@@ -241,7 +245,10 @@ struct StoreD {
     static __host__ __device__ __forceinline__ double to_double(S s, int) { return s; }
     static __host__ __device__ __forceinline__ S mirror_odd(S wall2, S s) { return wall2 - s; }
     static __host__ __device__ __forceinline__ S twice(S s) { return 2.0 * s; }
+    static __host__ __device__ __forceinline__ bool representable(double, int) { return true; }
     static __host__ __device__ __forceinline__ bool in_range(R v, int) { return v == v; }
+    static __device__ __forceinline__ R rcp(R x) { return 1.0 / x; }
+    static __device__ __forceinline__ R fsqrt(R x) { return sqrt(x); }
 };
 
 struct StoreQ {
@@ -268,8 +275,13 @@ struct StoreQ {
     {
         return (int)((unsigned)s + (unsigned)__float2int_rn(d * (1.0f / scale_f(k))));
     }
+    static __host__ __device__ __forceinline__ bool representable(double v, int k)
+    {
+        return fabs(v) < (double)limit(k);  // false for NaN too
+    }
     static __host__ __device__ __forceinline__ S from_double(double v, int k)
     {
+        if (!(v == v)) return 0;
         double q = v / scale_d(k);
         q = q > 2147483000.0 ? 2147483000.0 : (q < -2147483000.0 ? -2147483000.0 : q);
         return (int)(q < 0 ? q - 0.5 : q + 0.5);
@@ -285,6 +297,9 @@ struct StoreQ {
     {
         return fabsf(v) < limit(k);
     }
+    // reciprocal and square root at FP32 accuracy (a few ulp), not IEEE rounding
+    static __device__ __forceinline__ R rcp(R x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ R fsqrt(R x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 };
 
 }  // namespace rtlbfs

@@ -434,8 +434,13 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
         CK(cudaMemcpyAsync(d_stage_ + k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice,
                            stream_));
     const CavityDesc& d = h_desc_[slot];
-    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0]));
+    int* d_bad = reinterpret_cast<int*>(d_scalar_ + 7);
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), stream_));
+    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0], d_bad));
     g_launches++;
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
     CavityCtl z;
     std::memset(&z, 0, sizeof(z));
     z.cur = 0;
@@ -444,6 +449,10 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     z.res[0] = z.res[1] = INFINITY;
     CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
     CK(cudaStreamSynchronize(stream_));  // z lives on this stack frame
+    if (h_bad)
+        return fail(RTLBFS_ERR_ARG, "state not representable in the FP32 mode's fixed-point "
+                                    "storage: NaN, |rho-1| >= 0.49, |u|,|v| >= 0.99 or "
+                                    "|T| >= 1.98");
     return RTLBFS_OK;
 }
 

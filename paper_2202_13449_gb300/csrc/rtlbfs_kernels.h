@@ -8,9 +8,22 @@
 
 namespace rtlbfs {
 
-constexpr int kStepThreads = 256;  // threads of a step block
-constexpr int kTileX = 32;         // cells of a tile along x (one warp row)
-constexpr int kTileY = 8;          // cells of a tile along y
+#ifndef RTLBFS_STEP_THREADS
+#define RTLBFS_STEP_THREADS 256
+#endif
+#ifndef RTLBFS_TILE_X
+#define RTLBFS_TILE_X 32
+#endif
+#ifndef RTLBFS_TILE_Y
+#define RTLBFS_TILE_Y 16
+#endif
+#ifndef RTLBFS_MIN_BLOCKS_FP32
+#define RTLBFS_MIN_BLOCKS_FP32 4
+#endif
+constexpr int kStepThreads = RTLBFS_STEP_THREADS;  // threads of a step block
+constexpr int kTileX = RTLBFS_TILE_X;              // cells of a tile along x
+constexpr int kTileY = RTLBFS_TILE_Y;              // cells of a tile along y
+constexpr int kMinBlocksFP32 = RTLBFS_MIN_BLOCKS_FP32;  // resident blocks per SM to aim for
 
 constexpr int kNuWest = 0, kNuEast = 1, kNuSouth = 2, kNuNorth = 3, kNuAvg = 4, kNuHalf = 5;
 
@@ -32,7 +45,7 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
                            long long count, double scale, double* partial, int max_blocks,
                            double* out);
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* const* f);
+                            int pitch, void* const* f, int* bad);
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny,
                              int pitch, void* const* f);
 cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,

@@ -34,7 +34,9 @@ struct TileSmem {
     using R = typename P::R;
     static constexpr int BX = TX + 4, BY = TY + 4;  // tile + 2-cell halo
     static constexpr int GX = TX + 2, GY = TY + 2;  // gradient ring
-    Vec4<S> val[BY][BX];
+    // (rho - 1, u, v, T - T_tile) of the haloed tile; T_tile is one cell's
+    // stored temperature, so the in-tile deviations keep their bits in FP32
+    Vec4<R> val[BY][BX];
     Vec4<R> gx[GY][GX];
     Vec4<R> gy[GY][GX];
     Vec4<R> fx[TY][TX + 1];
@@ -51,37 +53,43 @@ struct TileSmem {
 // cell (si, sj) to read, and the wall side whose mirror rule applies
 // (-1: none).  Returns false for positions no stencil uses (corner ghosts,
 // cells beyond the ghost layer of a wall).
-__device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj, int& si,
-                                             int& sj, int& mside)
+__device__ __forceinline__ bool resolve_cell(int nx, int ny, bool xper, bool yper, int gi, int gj,
+                                             int& si, int& sj, int& mside)
 {
-    const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
     si = gi;
     sj = gj;
     mside = -1;
-    if (gi < 0 || gi >= d.nx) {
+    if (gi < 0 || gi >= nx) {
         if (xper) {
-            si = ((gi % d.nx) + d.nx) % d.nx;
+            si = ((gi % nx) + nx) % nx;
         } else if (gi == -1) {
             si = 0;
             mside = kSideW;
-        } else if (gi == d.nx) {
-            si = d.nx - 1;
+        } else if (gi == nx) {
+            si = nx - 1;
             mside = kSideE;
         } else {
             return false;
         }
     }
-    if (gj < 0 || gj >= d.ny) {
+    if (gj < 0 || gj >= ny) {
         if (yper) {
-            sj = ((gj % d.ny) + d.ny) % d.ny;
-        } else if ((gj == -1 || gj == d.ny) && mside < 0) {
-            sj = gj < 0 ? 0 : d.ny - 1;
+            sj = ((gj % ny) + ny) % ny;
+        } else if ((gj == -1 || gj == ny) && mside < 0) {
+            sj = gj < 0 ? 0 : ny - 1;
             mside = gj < 0 ? kSideS : kSideN;
         } else {
             return false;
         }
     }
     return true;
+}
+
+__device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj, int& si,
+                                             int& sj, int& mside)
+{
+    return resolve_cell(d.nx, d.ny, d.kind[kSideW] == kPeriodic, d.kind[kSideS] == kPeriodic, gi,
+                        gj, si, sj, mside);
 }
 
 // Ghost state across wall `side` in the storage type: rho even, velocity odd
@@ -137,7 +145,8 @@ __device__ __forceinline__ typename P::S comp(const Vec4<typename P::S>& v, int 
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// Eqs. 55-56: Green-Gauss gradient from the four neighbour differences.
+// Eqs. 55-56: Green-Gauss gradient from the four neighbour differences
+// (storage values; exact differences for the fixed-point state).
 template <class P>
 __device__ __forceinline__ void gg_gradient(const Vec4<typename P::S>& p,
                                             const Vec4<typename P::S>& e,
@@ -159,6 +168,23 @@ __device__ __forceinline__ void gg_gradient(const Vec4<typename P::S>& p,
     }
 }
 
+// The same from working values (rho - 1, u, v, T - T_tile) in R.
+template <typename R>
+__device__ __forceinline__ void gg_gradient_r(const Vec4<R>& p, const Vec4<R>& e,
+                                              const Vec4<R>& w, const Vec4<R>& n,
+                                              const Vec4<R>& s, R ixe, R ixw, R iyn, R iys,
+                                              Vec4<R>& gx, Vec4<R>& gy)
+{
+    gx.x = (e.x - p.x) * ixe + (p.x - w.x) * ixw;
+    gx.y = (e.y - p.y) * ixe + (p.y - w.y) * ixw;
+    gx.z = (e.z - p.z) * ixe + (p.z - w.z) * ixw;
+    gx.w = (e.w - p.w) * ixe + (p.w - w.w) * ixw;
+    gy.x = (n.x - p.x) * iyn + (p.x - s.x) * iys;
+    gy.y = (n.y - p.y) * iyn + (p.y - s.y) * iys;
+    gy.z = (n.z - p.z) * iyn + (p.z - s.z) * iys;
+    gy.w = (n.w - p.w) * iyn + (p.w - s.w) * iys;
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v)
 {
@@ -168,33 +194,36 @@ __device__ __forceinline__ R warp_sum(R v)
 }
 
 // Build the two cells of a face in the face frame (normal along x for an
-// x-face, along y for a y-face); T enters as a deviation from Tbar = T_L.
-template <class P>
-__device__ __forceinline__ void face_cells(bool isx, const Vec4<typename P::S>& sl,
-                                           const Vec4<typename P::S>& sr,
-                                           const Vec4<typename P::R>& gxl,
-                                           const Vec4<typename P::R>& gyl,
-                                           const Vec4<typename P::R>& gxr,
-                                           const Vec4<typename P::R>& gyr,
-                                           CellNT<typename P::R>& L, CellNT<typename P::R>& Rr,
-                                           typename P::R& Tbar)
+// x-face, along y for a y-face) from working values (rho - 1, u, v, T - Tz);
+// T enters as a deviation from Tbar = T_L.
+template <typename R>
+__device__ __forceinline__ void face_cells(bool isx, const Vec4<R>& vl, const Vec4<R>& vr,
+                                           R Tz, const Vec4<R>& gxl, const Vec4<R>& gyl,
+                                           const Vec4<R>& gxr, const Vec4<R>& gyr, CellNT<R>& L,
+                                           CellNT<R>& Rr, R& Tbar)
 {
-    using R = typename P::R;
-    Tbar = P::val(sl.w, 3);
-    const R tR = P::diff(sr.w, sl.w, 3);
-    const R dl = P::val(sl.x, 0), ul = P::val(sl.y, 1), vl = P::val(sl.z, 2);
-    const R dr = P::val(sr.x, 0), ur = P::val(sr.y, 1), vr = P::val(sr.z, 2);
+    Tbar = Tz + vl.w;
+    const R tR = vr.w - vl.w;
     if (isx) {
-        L = {{dl, ul, vl, R(0)}, {gxl.x, gxl.y, gxl.z, gxl.w}, {gyl.x, gyl.y, gyl.z, gyl.w}};
-        Rr = {{dr, ur, vr, tR}, {gxr.x, gxr.y, gxr.z, gxr.w}, {gyr.x, gyr.y, gyr.z, gyr.w}};
+        L = {{vl.x, vl.y, vl.z, R(0)}, {gxl.x, gxl.y, gxl.z, gxl.w}, {gyl.x, gyl.y, gyl.z, gyl.w}};
+        Rr = {{vr.x, vr.y, vr.z, tR}, {gxr.x, gxr.y, gxr.z, gxr.w}, {gyr.x, gyr.y, gyr.z, gyr.w}};
     } else {
-        L = {{dl, vl, ul, R(0)}, {gyl.x, gyl.z, gyl.y, gyl.w}, {gxl.x, gxl.z, gxl.y, gxl.w}};
-        Rr = {{dr, vr, ur, tR}, {gyr.x, gyr.z, gyr.y, gyr.w}, {gxr.x, gxr.z, gxr.y, gxr.w}};
+        L = {{vl.x, vl.z, vl.y, R(0)}, {gyl.x, gyl.z, gyl.y, gyl.w}, {gxl.x, gxl.z, gxl.y, gxl.w}};
+        Rr = {{vr.x, vr.z, vr.y, tR}, {gyr.x, gyr.z, gyr.y, gyr.w}, {gxr.x, gxr.z, gxr.y, gxr.w}};
     }
 }
 
+template <class P>
+struct MinBlocks {
+    static constexpr int value = 1;
+};
+template <>
+struct MinBlocks<StoreQ> {
+    static constexpr int value = kMinBlocksFP32;
+};
+
 template <class P, int TX, int TY>
-__global__ void __launch_bounds__(kStepThreads)
+__global__ void __launch_bounds__(kStepThreads, MinBlocks<P>::value)
 step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
 {
@@ -210,44 +239,63 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tile = tiles[t];
         const int slot = tile.x, i0 = tile.y, j0 = tile.z;
-        const CavityDesc& d = descs[slot];
+        const CavityDesc* dp = &descs[slot];
         CavityCtl* ctl = &ctls[slot];
         if (ctl->done) continue;  // uniform across the block
         const int cur = ctl->cur;
+        const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
+        const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
         const S* fin[4];
-        S* fout[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            fin[k] = static_cast<const S*>(d.f[cur][k]);
-            fout[k] = static_cast<S*>(d.f[cur ^ 1][k]);
-        }
-        const int nx = d.nx, ny = d.ny, pitch = d.pitch;
-        const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
+        for (int k = 0; k < 4; ++k) fin[k] = static_cast<const S*>(dp->f[cur][k]);
+        // temperature reference of this tile: its (clamped) centre cell
+        const int ic = min(i0 + TX / 2, nx - 1), jc = min(j0 + TY / 2, ny - 1);
+        const S qTz = fin[3][(size_t)jc * pitch + ic];
+        const R Tz = P::val(qTz, 3);
 
         // ---- 1. lines and the haloed tile -------------------------------
         {
-            const CellLine<R>* xc = static_cast<const CellLine<R>*>(d.xcell);
-            const CellLine<R>* yc = static_cast<const CellLine<R>*>(d.ycell);
-            const FaceLine<R>* xl = static_cast<const FaceLine<R>*>(d.xline);
-            const FaceLine<R>* yl = static_cast<const FaceLine<R>*>(d.yline);
+            const CellLine<R>* xc = static_cast<const CellLine<R>*>(dp->xcell);
+            const CellLine<R>* yc = static_cast<const CellLine<R>*>(dp->ycell);
+            const FaceLine<R>* xl = static_cast<const FaceLine<R>*>(dp->xline);
+            const FaceLine<R>* yl = static_cast<const FaceLine<R>*>(dp->yline);
             for (int k = tid; k < BX; k += kStepThreads) sm.xc[k] = xc[min(i0 + k, nx + 3)];
             for (int k = tid; k < BY; k += kStepThreads) sm.yc[k] = yc[min(j0 + k, ny + 3)];
             for (int k = tid; k < TX + 1; k += kStepThreads) sm.xl[k] = xl[min(i0 + k, nx)];
             for (int k = tid; k < TY + 1; k += kStepThreads) sm.yl[k] = yl[min(j0 + k, ny)];
         }
-        for (int k = tid; k < BX * BY; k += kStepThreads) {
-            const int c = k % BX, r = k / BX;
-            int si, sj, ms;
-            Vec4<S> v = {S(0), S(0), S(0), S(0)};
-            if (resolve_cell(d, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
-                const size_t o = (size_t)sj * pitch + si;
-                v.x = fin[0][o];
-                v.y = fin[1][o];
-                v.z = fin[2][o];
-                v.w = fin[3][o];
-                if (ms >= 0) v = mirror_state<P>(d, ms, v);
+        {
+            constexpr int NB = BX * BY;
+            constexpr int NR = (NB + kStepThreads - 1) / kStepThreads;
+            Vec4<S> v[NR];
+            int ms[NR];
+            bool ok[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {  // issue every load first
+                const int k = tid + q * kStepThreads;
+                const int c = k % BX, r = k / BX;
+                int si = 0, sj = 0;
+                ms[q] = -1;
+                ok[q] = k < NB && resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms[q]);
+                v[q] = {S(0), S(0), S(0), S(0)};
+                if (ok[q]) {
+                    const size_t o = (size_t)sj * pitch + si;
+                    v[q].x = fin[0][o];
+                    v[q].y = fin[1][o];
+                    v[q].z = fin[2][o];
+                    v[q].w = fin[3][o];
+                }
             }
-            sm.val[r][c] = v;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int k = tid + q * kStepThreads;
+                if (k >= NB) continue;
+                Vec4<S> x = v[q];
+                if (ms[q] >= 0) x = mirror_state<P>(*dp, ms[q], x);
+                Vec4<R> y = {R(0), R(0), R(0), R(0)};
+                if (ok[q]) y = {P::val(x.x, 0), P::val(x.y, 1), P::val(x.z, 2), P::diff(x.w, qTz, 3)};
+                sm.val[k / BX][k % BX] = y;
+            }
         }
         __syncthreads();
 
@@ -257,16 +305,16 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             int c = gc + 1, r = gr + 1;  // box position
             int si, sj, ms;
             Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
-            if (resolve_cell(d, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+            if (resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
                 // a wall ghost takes its partner's gradient, mirrored
                 if (ms == kSideW) c += 1;
                 else if (ms == kSideE) c -= 1;
                 else if (ms == kSideS) r += 1;
                 else if (ms == kSideN) r -= 1;
-                gg_gradient<P>(sm.val[r][c], sm.val[r][c + 1], sm.val[r][c - 1], sm.val[r + 1][c],
-                               sm.val[r - 1][c], sm.xc[c].is_next, sm.xc[c - 1].is_next,
-                               sm.yc[r].is_next, sm.yc[r - 1].is_next, gxv, gyv);
-                if (ms >= 0) mirror_grad(d, ms, gxv, gyv);
+                gg_gradient_r(sm.val[r][c], sm.val[r][c + 1], sm.val[r][c - 1], sm.val[r + 1][c],
+                              sm.val[r - 1][c], sm.xc[c].is_next, sm.xc[c - 1].is_next,
+                              sm.yc[r].is_next, sm.yc[r - 1].is_next, gxv, gyv);
+                if (ms >= 0) mirror_grad(*dp, ms, gxv, gyv);
             }
             sm.gx[gr][gc] = gxv;
             sm.gy[gr][gc] = gyv;
@@ -293,14 +341,14 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 const int rc = fc + 2, rr = fr + 2;
                 CellNT<R> L, Rr;
                 R Tbar;
-                face_cells<P>(isx, sm.val[lr][lc], sm.val[rr][rc], sm.gx[lr - 1][lc - 1],
+                face_cells<R>(isx, sm.val[lr][lc], sm.val[rr][rc], Tz, sm.gx[lr - 1][lc - 1],
                               sm.gy[lr - 1][lc - 1], sm.gx[rr - 1][rc - 1], sm.gy[rr - 1][rc - 1],
                               L, Rr, Tbar);
                 const FaceLine<R> fl = isx ? sm.xl[fc] : sm.yl[fr];
                 int wside = -1;
                 if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
                 if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
-                const R uw = wside >= 0 ? rconst<R>(d.bcU[wside]) : R(0);
+                const R uw = wside >= 0 ? rconst<R>(dp->bcU[wside]) : R(0);
                 R F[4];
                 face_flux<R>(L, Rr, Tbar, fl, wside >= 0, uw, F);
                 if (isx) out = {F[0], F[1], F[2], F[3]};
@@ -313,51 +361,57 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
 
         // ---- 4. update (increment form), 5. residual sums ---------------
         R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
-        const R one = rconst<R>(1.0);
-        const R dt = rconst<R>(d.dt), bg = rconst<R>(d.beta_g), Tr = rconst<R>(d.T_ref);
-        const R fxb = rconst<R>(d.fx), fyb = rconst<R>(d.fy);
-        bool bad = false;
-        for (int k = tid; k < TX * TY; k += kStepThreads) {
-            const int tc = k % TX, tr = k / TX;
-            const int gi = i0 + tc, gj = j0 + tr;
-            if (gi >= nx || gj >= ny) continue;
-            const Vec4<S> p = sm.val[tr + 2][tc + 2];
-            const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
-            const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
-            const R ax = sm.xc[tc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
-            const R dr = P::val(p.x, 0), u = P::val(p.y, 1), v = P::val(p.z, 2), T = P::val(p.w, 3);
-            const R rho = one + dr;
-            // Dt/dV sum_k F_k dS_k for mass, momentum, energy
-            const R div0 = ax * (Fe.x - Fw.x) + ay * (Fn.x - Fs.x);
-            const R div1 = ax * (Fe.y - Fw.y) + ay * (Fn.y - Fs.y);
-            const R div2 = ax * (Fe.z - Fw.z) + ay * (Fn.z - Fs.z);
-            const R div3 = ax * (Fe.w - Fw.w) + ay * (Fn.w - Fs.w);
-            // Boussinesq source (Eq. 64, hot fluid rises) and body force
-            const R src_x = rho * fxb;
-            const R src_y = rho * (bg * (T - Tr) + fyb);
-            // rho^{n+1} = rho - div0; q^{n+1} - q = (q div0 - div_q + dt src) / rho^{n+1}
-            const R inv = one / (rho - div0);
-            const R du = (u * div0 - div1 + dt * src_x) * inv;
-            const R dv = (v * div0 - div2 + dt * src_y) * inv;
-            const R dT = (T * div0 - div3) * inv;
-            const R dr1 = dr - div0, u1 = u + du, v1 = v + dv, T1 = T + dT;
-            const size_t o = (size_t)gj * pitch + gi;
-            fout[0][o] = P::add(p.x, -div0, 0);
-            fout[1][o] = P::add(p.y, du, 1);
-            fout[2][o] = P::add(p.z, dv, 2);
-            fout[3][o] = P::add(p.w, dT, 3);
-            bad = bad || !(P::in_range(dr1, 0) && P::in_range(u1, 1) && P::in_range(v1, 2) &&
-                           P::in_range(T1, 3));
-            // |u|^{n+1} - |u|^n without cancellation
-            const R m0 = sqrt(u * u + v * v), m1 = sqrt(u1 * u1 + v1 * v1);
-            const R den = m0 + m1;
-            const R dm = den > R(0) ? (du * (u + u1) + dv * (v + v1)) / den : R(0);
-            s0 += dm * dm;
-            s1 += m1 * m1;
-            s2 += dT * dT;
-            s3 += T1 * T1;
+        {
+            S* fout[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) fout[k] = static_cast<S*>(dp->f[cur ^ 1][k]);
+            const R one = rconst<R>(1.0);
+            const R dt = rconst<R>(dp->dt), bg = rconst<R>(dp->beta_g), Tr = rconst<R>(dp->T_ref);
+            const R fxb = rconst<R>(dp->fx), fyb = rconst<R>(dp->fy);
+            bool bad = false;
+            for (int k = tid; k < TX * TY; k += kStepThreads) {
+                const int tc = k % TX, tr = k / TX;
+                const int gi = i0 + tc, gj = j0 + tr;
+                if (gi >= nx || gj >= ny) continue;
+                const size_t o = (size_t)gj * pitch + gi;
+                const Vec4<S> q = {fin[0][o], fin[1][o], fin[2][o], fin[3][o]};
+                const Vec4<R> p = sm.val[tr + 2][tc + 2];
+                const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
+                const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
+                const R ax = sm.xc[tc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
+                const R dr = p.x, u = p.y, v = p.z, T = Tz + p.w;
+                const R rho = one + dr;
+                // Dt/dV sum_k F_k dS_k for mass, momentum, energy
+                const R div0 = ax * (Fe.x - Fw.x) + ay * (Fn.x - Fs.x);
+                const R div1 = ax * (Fe.y - Fw.y) + ay * (Fn.y - Fs.y);
+                const R div2 = ax * (Fe.z - Fw.z) + ay * (Fn.z - Fs.z);
+                const R div3 = ax * (Fe.w - Fw.w) + ay * (Fn.w - Fs.w);
+                // Boussinesq source (Eq. 64, hot fluid rises) and body force
+                const R src_x = rho * fxb;
+                const R src_y = rho * (bg * (T - Tr) + fyb);
+                // rho^{n+1} = rho - div0; q^{n+1} - q = (q div0 - div_q + dt src) / rho^{n+1}
+                const R inv = P::rcp(rho - div0);
+                const R du = (u * div0 - div1 + dt * src_x) * inv;
+                const R dv = (v * div0 - div2 + dt * src_y) * inv;
+                const R dT = (T * div0 - div3) * inv;
+                const R dr1 = dr - div0, u1 = u + du, v1 = v + dv, T1 = T + dT;
+                fout[0][o] = P::add(q.x, -div0, 0);
+                fout[1][o] = P::add(q.y, du, 1);
+                fout[2][o] = P::add(q.z, dv, 2);
+                fout[3][o] = P::add(q.w, dT, 3);
+                bad = bad || !(P::in_range(dr1, 0) && P::in_range(u1, 1) && P::in_range(v1, 2) &&
+                               P::in_range(T1, 3));
+                // |u|^{n+1} - |u|^n without cancellation
+                const R m0 = P::fsqrt(u * u + v * v), m1 = P::fsqrt(u1 * u1 + v1 * v1);
+                const R den = m0 + m1;
+                const R dm = den > R(0) ? (du * (u + u1) + dv * (v + v1)) * P::rcp(den) : R(0);
+                s0 += dm * dm;
+                s1 += m1 * m1;
+                s2 += dT * dT;
+                s3 += T1 * T1;
+            }
+            if (bad) s0 = R(NAN);
         }
-        if (bad) s0 = R(NAN);
         // warp sums in R, then FP64 across warps and tiles
         s0 = warp_sum(s0);
         s1 = warp_sum(s1);
@@ -377,7 +431,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
             __threadfence();
             const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-            if (prev == (unsigned)d.ntiles - 1u) {
+            if (prev == (unsigned)dp->ntiles - 1u) {
                 // last tile of this cavity in this step: finalize
                 __threadfence();
                 volatile double* acc = ctl->acc;
@@ -461,7 +515,7 @@ __device__ double energy_flux_d(const CavityDesc& d, const typename P::S* const*
     grad_d<P>(d, f, ln.xc, ln.yc, i, j, gxr, gyr);
     CellNT<double> L, Rr;
     double Tbar;
-    face_cells<StoreD>(nd == 0, vl, vr, gxl, gyl, gxr, gyr, L, Rr, Tbar);
+    face_cells<double>(nd == 0, vl, vr, 0.0, gxl, gyl, gxr, gyr, L, Rr, Tbar);
     int wside = -1;
     if (nd == 0 && !xper) wside = i == 0 ? kSideW : (i == d.nx ? kSideE : -1);
     if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
@@ -535,18 +589,22 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 template <class P>
 __global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, int pitch,
                                 typename P::S* f0, typename P::S* f1, typename P::S* f2,
-                                typename P::S* f3)
+                                typename P::S* f3, int* __restrict__ bad)
 {
     const long long n = (long long)nx * ny;
+    bool b = false;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
         const size_t o = (size_t)j * pitch + i;
-        f0[o] = P::from_double(st[k] - 1.0, 0);
-        f1[o] = P::from_double(st[n + k], 1);
-        f2[o] = P::from_double(st[2 * n + k], 2);
-        f3[o] = P::from_double(st[3 * n + k], 3);
+        const double x[4] = {st[k] - 1.0, st[n + k], st[2 * n + k], st[3 * n + k]};
+        for (int q = 0; q < 4; ++q) b = b || !P::representable(x[q], q);
+        f0[o] = P::from_double(x[0], 0);
+        f1[o] = P::from_double(x[1], 1);
+        f2[o] = P::from_double(x[2], 2);
+        f3[o] = P::from_double(x[3], 3);
     }
+    if (b) atomicOr(bad, 1);
 }
 
 template <class P>
@@ -598,15 +656,21 @@ size_t step_smem(int precision)
     return precision == 0 ? step_smem_bytes<StoreD>() : step_smem_bytes<StoreQ>();
 }
 
+template <class P>
+static cudaError_t prepare_kernel()
+{
+    auto fn = step_kernel<P, kTileX, kTileY>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<P>());
+    if (e != cudaSuccess) return e;
+    // all of the unified L1/shared array to shared memory: occupancy is
+    // bounded by the tile buffers, and global loads are streamed once
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 cudaError_t step_prepare(int precision)
 {
-    if (precision == 0)
-        return cudaFuncSetAttribute(step_kernel<StoreD, kTileX, kTileY>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)step_smem_bytes<StoreD>());
-    return cudaFuncSetAttribute(step_kernel<StoreQ, kTileX, kTileY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_smem_bytes<StoreQ>());
+    return precision == 0 ? prepare_kernel<StoreD>() : prepare_kernel<StoreQ>();
 }
 
 cudaError_t step_occupancy(int precision, int* blocks_per_sm)
@@ -649,17 +713,18 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
 }
 
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* const* f)
+                            int pitch, void* const* f, int* bad)
 {
     const long long n = (long long)nx * ny;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
         state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (double*)f[0],
-                                                       (double*)f[1], (double*)f[2], (double*)f[3]);
+                                                       (double*)f[1], (double*)f[2], (double*)f[3],
+                                                       bad);
     else
         state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (int*)f[0], (int*)f[1],
-                                                       (int*)f[2], (int*)f[3]);
+                                                       (int*)f[2], (int*)f[3], bad);
     return cudaGetLastError();
 }
 

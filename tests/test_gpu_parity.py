@@ -5,7 +5,7 @@ velocity scale of the case, T the temperature difference):
   FP64: <= 1e-12 after one step, <= 1e-11 after tens of steps, <= 1e-10 at
         the steady state;
   FP32 (rho - 1 stored): <= 1e-5 on u, v, T and 1e-6 absolute on rho.
-Cases span several 32 x 8 tiles with ragged tails, every boundary kind,
+Cases span several tiles with ragged tails, every boundary kind,
 stretched and irregular meshes, degenerate 1-cell meshes, and the full
 512 x 512 tanh mesh of the Ra = 1e8 cavity.
 """
@@ -214,10 +214,10 @@ def test_nusselt_of_generic_state(orc, precision):
     s.close()
 
 
-def test_divergence_is_reported_not_trapped(orc):
-    """Host-side fault injection: a NaN in the uploaded state makes the step
-    return RTLBFS_ERR_DIVERGED; the handle stays usable."""
-    p, s = cavity_solver(orc, 16, 1e4, capi.FP32)
+def test_nan_state_fp64_reports_divergence(orc):
+    """Host-side fault injection: a NaN in the uploaded FP64 state makes the
+    step return RTLBFS_ERR_DIVERGED; the handle stays usable."""
+    p, s = cavity_solver(orc, 16, 1e4, capi.FP64)
     st = list(inputs.conduction_state(p.xf, p.yf))
     st[3] = st[3].copy()
     st[3][5, 5] = np.nan
@@ -228,6 +228,36 @@ def test_divergence_is_reported_not_trapped(orc):
     s.set_state(*inputs.conduction_state(p.xf, p.yf))
     s.step(10)
     assert np.all(np.isfinite(s.get_state()[3]))
+    s.close()
+
+
+def test_nan_state_fp32_is_rejected_at_upload(orc):
+    """The fixed-point FP32 state cannot hold NaN or out-of-range values: the
+    upload says so instead of storing a wrapped integer."""
+    p, s = cavity_solver(orc, 16, 1e4, capi.FP32)
+    st = list(inputs.conduction_state(p.xf, p.yf))
+    st[3] = st[3].copy()
+    st[3][5, 5] = np.nan
+    with pytest.raises(capi.RTLBFSError) as e:
+        s.set_state(*st)
+    assert e.value.rc == capi.ERR_ARG
+    st[3][5, 5] = 0.5
+    st[1] = st[1].copy()
+    st[1][2, 2] = 1.5  # |u| >= 0.99 is outside the representable range
+    with pytest.raises(capi.RTLBFSError):
+        s.set_state(*st)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_blow_up_is_reported_as_divergence(orc, precision):
+    """An unstable time step: the run stops with RTLBFS_ERR_DIVERGED (NaN in
+    FP64, a field leaving its range in the fixed-point FP32 state)."""
+    p, s = cavity_solver(orc, 16, 1e6, precision)
+    s.set_params(1e6, 0.71, 0.1, 40.0)
+    rc, n, _ = s.run_to_steady(1e-8, 5000)
+    assert rc == capi.ERR_DIVERGED
+    assert n < 5000
     s.close()
 
 
