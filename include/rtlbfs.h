@@ -177,6 +177,15 @@ int rtlbfs_residual(rtlbfs_t h, double* res2, long* steps);
  */
 int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
 
+/*
+ * Execution schedule of the step (results are the same up to FP rounding
+ * order): kernel 0 = warp-marching strips (each warp walks a 28-column strip
+ * up a chunk of chunk_rows rows, rolling its stencil window in registers;
+ * chunk_rows 0 = chosen from the GPU size), kernel 1 = shared-memory tiles.
+ * ERR_ARG on other values.
+ */
+int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
+
 /* Use this CUDA stream (a cudaStream_t, e.g. torch's current stream) for
  * all later work of the handle; NULL restores the handle's own stream. */
 int rtlbfs_set_stream(rtlbfs_t h, void* stream);

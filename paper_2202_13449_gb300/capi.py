@@ -48,6 +48,7 @@ _SIGS = {
     "rtlbfs_residual": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
     "rtlbfs_nusselt": (C.c_int, [_vp, C.c_int, _dp]),
     "rtlbfs_set_stream": (C.c_int, [_vp, _vp]),
+    "rtlbfs_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
     "rtlbfs_sync": (C.c_int, [_vp]),
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
@@ -171,6 +172,11 @@ class Solver:
 
     def set_physics(self, nu, chi, beta_g):
         self._check(lib().rtlbfs_set_physics(self._h, nu, chi, beta_g), "set_physics")
+
+    def set_schedule(self, kernel: int = 0, chunk_rows: int = 0):
+        """kernel 0: warp-marching strips, 1: shared-memory tiles."""
+        self._check(lib().rtlbfs_set_schedule(self._h, int(kernel), int(chunk_rows)),
+                    "set_schedule")
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, an int handle, or None."""

@@ -270,6 +270,14 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu)
     return finish(h, h->eng->nusselt(h->slot, which, nu));
 }
 
+int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    int rc = h->eng->set_kernel(kernel);
+    if (rc == RTLBFS_OK) rc = h->eng->set_chunk_rows(chunk_rows);
+    return finish(h, rc);
+}
+
 int rtlbfs_set_stream(rtlbfs_t h, void* stream)
 {
     if (!cav(h)) return RTLBFS_ERR_ARG;

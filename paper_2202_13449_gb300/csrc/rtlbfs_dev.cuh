@@ -25,14 +25,15 @@ constexpr int kRunning = 0, kConverged = 1, kMaxSteps = 2, kDiverged = 3;
 // the reconstructed lattice), node offsets, transport coefficients.
 template <typename R>
 struct FaceLine {
-    R h;       // lattice spacing dt_f
-    R cL;      // wL - h : normal offset of node a = -1 from the left centre
-    R cR;      // h - wR : normal offset of node a = +1 from the right centre
-    R wL, wR;  // half widths of the two cells (centre-to-face distances)
-    R nu_2h;   // nu / (2 h): viscous term with a central difference over 2h
-    R chi_2h;  // chi / (2 h)
-    R tf15;    // tau_f - 1.5 = nu / (cs2 h) - 1   (Eqs. 9, 58)
-    R tg15;    // tau_g - 1.5 = chi / (cs2 h) - 1  (Eqs. 10, 59)
+    R h;        // lattice spacing dt_f
+    R cL;       // wL - h : normal offset of node a = -1 from the left centre
+    R cR;       // h - wR : normal offset of node a = +1 from the right centre
+    R m_nu_2h;  // -nu / (2 h): viscous term with a central difference over 2h
+    R m_chi_2h; // -chi / (2 h)
+    R m_tf15;   // -(tau_f - 1.5) = 1 - nu / (cs2 h)   (Eqs. 9, 58)
+    R m_tg15;   // -(tau_g - 1.5) = 1 - chi / (cs2 h)  (Eqs. 10, 59)
+    R pad;
+    // wL = cL + h and wR = h - cR are the two centre-to-face distances
 };
 
 // Constants of one line of cells along an axis, ghosts included.
@@ -57,6 +58,12 @@ struct CavityDesc {
     int tiles_x, tiles_y, tile_begin, pad0;
     double bcT[4], bcU[4];        // wall temperature, tangential wall velocity
     double beta_g, T_ref, fx, fy, dt, dT, nu, chi;
+    // FP32 copies (a double -> float conversion runs on the narrow FP64
+    // pipe; the FP32 kernels never convert in their loops)
+    float f_beta_g, f_T_ref, f_fx, f_fy, f_dt, f_bcU[4];
+    // wall mirror constants in the fixed-point storage: 2 u_wall and 2 T_wall
+    // (wrap-around 32-bit values, see StoreQ::twice)
+    int q_u2[4], q_T2[4];
     void* f[2][4];                // two buffers of (drho, u, v, T)
     const void* xline;            // FaceLine<R>[nx+1]
     const void* yline;            // FaceLine<R>[ny+1]
@@ -90,6 +97,58 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 
 // -------------------------------------------------------------------------
+// Value types of the face arithmetic.  float / double: one face.  f2: two
+// faces at once in the packed FP32x2 instructions of sm_100+ (one issue
+// slot for two round-to-nearest FP32 operations); d2: the FP64 pair.
+// -------------------------------------------------------------------------
+struct f2 {
+    float x, y;
+};
+struct d2 {
+    double x, y;
+};
+
+__device__ __forceinline__ f2 mk(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 fl2(f2 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return mk(__fadd2_rn(fl2(a), fl2(b))); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b)
+{
+    return mk(__ffma2_rn(fl2(b), make_float2(-1.0f, -1.0f), fl2(a)));
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return mk(__fmul2_rn(fl2(a), fl2(b))); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return mk(__ffma2_rn(fl2(a), fl2(b), fl2(c))); }
+
+__host__ __device__ __forceinline__ d2 operator+(d2 a, d2 b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ d2 operator-(d2 a, d2 b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ d2 operator*(d2 a, d2 b) { return {a.x * b.x, a.y * b.y}; }
+__device__ __forceinline__ d2 vfma(d2 a, d2 b, d2 c) { return {fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename V>
+struct vtraits;
+template <>
+struct vtraits<float> {
+    static __device__ __forceinline__ float bc(double c) { return (float)c; }
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+};
+template <>
+struct vtraits<double> {
+    static __device__ __forceinline__ double bc(double c) { return c; }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+};
+template <>
+struct vtraits<f2> {
+    static __device__ __forceinline__ f2 bc(double c) { return {(float)c, (float)c}; }
+    static __device__ __forceinline__ f2 rcp(f2 x) { return {__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)}; }
+};
+template <>
+struct vtraits<d2> {
+    static __device__ __forceinline__ d2 bc(double c) { return {c, c}; }
+    static __device__ __forceinline__ d2 rcp(d2 x) { return {1.0 / x.x, 1.0 / x.y}; }
+};
+
+// -------------------------------------------------------------------------
 // One face in its own frame: normal n (the "x" of a node (a, b)), tangent t.
 // q[] = (drho, u_n, u_t, T - Tbar) of a cell, gn/gt its gradients along n
 // and t.  Temperatures enter as deviations from a face reference Tbar so
@@ -102,119 +161,111 @@ struct CellNT {
     R gt[4];
 };
 
-// Eqs. 29, 46-48 and the braces of Eqs. 57-59 for one face.  Output
-// F = (mass, normal momentum, tangential momentum, energy) flux through the
-// face along +n, with the constant c_s^2 dropped from the normal momentum
-// flux (see the file comment).  wall: the face lies on a wall whose
-// tangential velocity is u_wall_t.
+// Eqs. 29, 46-48 and the braces of Eqs. 57-59 for one face (V = float,
+// double) or two faces (V = f2, d2).  Output F = (mass, normal momentum,
+// tangential momentum, energy) flux through the face along +n, with the
+// constant c_s^2 dropped from the normal momentum flux (see the file
+// comment).  keep = 1 on an interior face, 0 on a wall face, whose
+// tangential wall velocity is u_wall (no mass through a wall, (rho u_t)* =
+// rho* u_wall: the products with keep and 1 - keep are exact).
 //
-// Node values.  A cell's reconstruction plane restricted to a column of
-// nodes a = const is linear in b, so the three columns are c_a + b s_a:
-//   a = -1: left plane,  a = +1: right plane,  a = 0: mean of both (Eq. 29).
-// Central differences on the 9 nodes, written without the powers of h that
-// cancel in Eqs. 46-48 (d_x ~ 2h D_x, d_xx ~ h^2 D_xx, d_xy ~ 4h^2 D_xy).
-// The energy rho*T at a node is written Tbar + e with e = tau + drho*T,
-// tau = T - Tbar; every difference of rho*T is a difference of e.
-template <typename R>
-__device__ __forceinline__ void face_flux(const CellNT<R>& L, const CellNT<R>& Rc, R Tbar,
-                                          const FaceLine<R>& fl, bool wall, R u_wall_t,
-                                          R F[4])
+// Node values.  Node (a, b) sits at x_S + (a, b) h (a along the normal).
+// A cell's reconstruction plane restricted to a column a = const is linear
+// in b, so every primitive on column a is c_a + b s_a:
+//   a = -1: the left plane,  a = +1: the right plane,  a = 0: their mean
+// (Eq. 29).  The predictor needs central differences of node products:
+//   d_x f  = f(1,0) - f(-1,0)             (= 2h D_x f)
+//   d_xx f = f(1,0) - 2 f(0,0) + f(-1,0)  (= h^2 D_xx f)
+//   d_y f  = f(0,1) - f(0,-1),  d_yy f = f(0,1) - 2 f(0,0) + f(0,-1)
+//   d_xy f = f(1,1) - f(1,-1) - f(-1,1) + f(-1,-1)  (= 4 h^2 D_xy f)
+// and the products are polynomials in b on each column, so
+//   d_y f = 2 (odd coefficients at a = 0), d_yy f = 2 (b^2 coefficient at a = 0),
+//   d_xy f = 2 (odd(a = +1) - odd(a = -1)):
+// the same numbers as forming the products at the nine nodes, with fewer
+// operations.  The powers of h cancel in Eqs. 46-48.  The energy rho*T at a
+// node is written Tbar + e with e = tau + drho*T, tau = T - Tbar, so every
+// difference of rho*T is a difference of e.
+template <typename V>
+__device__ __forceinline__ void face_flux(const CellNT<V>& L, const CellNT<V>& Rc, V Tbar,
+                                          const FaceLine<V>& fl, V keep, V u_wall, V F[4])
 {
-    const R half = rconst<R>(0.5);
-    const R one = rconst<R>(1.0);
-    const R cs2 = rconst<R>(1.0 / 3.0);
-    const R hh = fl.h * half;
-    R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+    using T = vtraits<V>;
+    const V half = T::bc(0.5), one = T::bc(1.0), two = T::bc(2.0), three = T::bc(3.0);
+    const V m2 = T::bc(-2.0), mhalf = T::bc(-0.5);
+    const V cs2 = T::bc(1.0 / 3.0), mcs2 = T::bc(-1.0 / 3.0);
+    const V hcs2 = T::bc(0.5 / 3.0);  // c_s^2 / 2
+    const V h = fl.h;
+    const V wL = fl.cL + h, mwR = fl.cR - h;  // wL, -wR
+    const V hh = h * half;
+    // column coefficients: A (a = -1), M (a = 0), B (a = +1); S* slopes in b
+    V A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        A[k] = L.q[k] + L.gn[k] * fl.cL;
-        Sa[k] = L.gt[k] * fl.h;
-        B[k] = Rc.q[k] + Rc.gn[k] * fl.cR;
-        Sb[k] = Rc.gt[k] * fl.h;
-        M[k] = half * ((L.q[k] + L.gn[k] * fl.wL) + (Rc.q[k] - Rc.gn[k] * fl.wR));
+        A[k] = vfma(L.gn[k], fl.cL, L.q[k]);
+        Sa[k] = L.gt[k] * h;
+        B[k] = vfma(Rc.gn[k], fl.cR, Rc.q[k]);
+        Sb[k] = Rc.gt[k] * h;
+        M[k] = half * (vfma(L.gn[k], wL, L.q[k]) + vfma(Rc.gn[k], mwR, Rc.q[k]));
         Sm[k] = hh * (L.gt[k] + Rc.gt[k]);
     }
-    // plus nodes: c = (0,0), w = (-1,0), e = (+1,0), s = (0,-1), n = (0,+1);
-    // d* = rho - 1, t* = tangential velocity, a* = T - Tbar
-    const R d0 = M[0], n0 = M[1], t0 = M[2], a0 = M[3];
-    const R dw = A[0], nw = A[1], tw = A[2], aw = A[3];
-    const R de = B[0], ne = B[1], te = B[2], ae = B[3];
-    const R ds = M[0] - Sm[0], ns = M[1] - Sm[1], ts = M[2] - Sm[2], as = M[3] - Sm[3];
-    const R dn = M[0] + Sm[0], nn = M[1] + Sm[1], tn = M[2] + Sm[2], an = M[3] + Sm[3];
-    const R T0 = Tbar + a0, Tw = Tbar + aw, Te = Tbar + ae, Ts = Tbar + as, Tn = Tbar + an;
+    // centres (b = 0) of the three columns: rho u_n, rho u_t, products
+    const V TA = Tbar + A[3], TM = Tbar + M[3], TB = Tbar + B[3];
+    const V mnA = vfma(A[0], A[1], A[1]), mnM = vfma(M[0], M[1], M[1]), mnB = vfma(B[0], B[1], B[1]);
+    const V mtA = vfma(A[0], A[2], A[2]), mtM = vfma(M[0], M[2], M[2]), mtB = vfma(B[0], B[2], B[2]);
+    const V PnnA = mnA * A[1], PnnM = mnM * M[1], PnnB = mnB * B[1];
+    const V PntA = mnA * A[2], PntM = mnM * M[2], PntB = mnB * B[2];
+    const V QnA = mnA * TA, QnM = mnM * TM, QnB = mnB * TB;
+    const V eA = vfma(A[0], TA, A[3]), eM = vfma(M[0], TM, M[3]), eB = vfma(B[0], TB, B[3]);
+    // column a = 0 in b: rho = rM + b sd, u_n = M1 + b sn, u_t = M2 + b st, T = TM + b sT
+    const V rM = one + M[0];
+    const V sd = Sm[0], sn = Sm[1], st = Sm[2], sT = Sm[3];
+    const V mn_l = vfma(rM, sn, sd * M[1]), mn_q = sd * sn;  // rho u_n: linear, quadratic
+    const V mt_l = vfma(rM, st, sd * M[2]), mt_q = sd * st;  // rho u_t
+    const V e_q = sd * sT;                                   // e: quadratic
+    const V Pnt_o = vfma(mnM, st, vfma(mn_l, M[2], mn_q * st));  // rho u_n u_t: odd part
+    const V Ptt_o = vfma(mtM, st, vfma(mt_l, M[2], mt_q * st));  // rho u_t u_t: odd part
+    const V Ptt_q = vfma(mt_l, st, mt_q * M[2]);                 //              quadratic
+    const V Qt_o = vfma(mtM, sT, vfma(mt_l, TM, mt_q * sT));     // rho u_t T: odd part
+    // columns a = -1, +1: odd parts in b (for d_xy)
+    const V rA = one + A[0], rB = one + B[0];
+    const V mnA_o = vfma(rA, Sa[1], Sa[0] * A[1]), mnB_o = vfma(rB, Sb[1], Sb[0] * B[1]);
+    const V mtA_o = vfma(rA, Sa[2], Sa[0] * A[2]), mtB_o = vfma(rB, Sb[2], Sb[0] * B[2]);
+    const V PntA_o = vfma(mnA, Sa[2], vfma(mnA_o, A[2], Sa[0] * Sa[1] * Sa[2]));
+    const V PntB_o = vfma(mnB, Sb[2], vfma(mnB_o, B[2], Sb[0] * Sb[1] * Sb[2]));
+    // differences along the normal (b = 0)
+    const V dx_mn = mnB - mnA, dx_mt = mtB - mtA, dx_e = eB - eA, dx_dr = B[0] - A[0];
+    const V dxx_mn = vfma(m2, mnM, mnB + mnA), dxx_mt = vfma(m2, mtM, mtB + mtA);
+    const V dxx_e = vfma(m2, eM, eB + eA), dxx_dr = vfma(m2, M[0], B[0] + A[0]);
+    const V dxx_Pnn = vfma(m2, PnnM, PnnB + PnnA);
 
-    // node products (only those the predictor and the flux use)
-    const R mn0 = (one + d0) * n0, mt0 = (one + d0) * t0, e0 = a0 + d0 * T0;
-    const R Pnn0 = mn0 * n0, Pnt0 = mn0 * t0, Ptt0 = mt0 * t0, Qn0 = mn0 * T0;
-    const R mnw = (one + dw) * nw, mtw = (one + dw) * tw, ew = aw + dw * Tw;
-    const R Pnnw = mnw * nw, Pntw = mnw * tw, Qnw = mnw * Tw;
-    const R mne = (one + de) * ne, mte = (one + de) * te, ee = ae + de * Te;
-    const R Pnne = mne * ne, Pnte = mne * te, Qne = mne * Te;
-    const R mns = (one + ds) * ns, mts = (one + ds) * ts, es = as + ds * Ts;
-    const R Pnts = mns * ts, Ptts = mts * ts, Qts = mts * Ts;
-    const R mnn = (one + dn) * nn, mtn = (one + dn) * tn, en = an + dn * Tn;
-    const R Pntn = mnn * tn, Pttn = mtn * tn, Qtn = mtn * Tn;
-    // corners (a, b): only rho u_n, rho u_t and rho u_n u_t enter (through d_xy)
-    R mnc[4], mtc[4], Pntc[4];  // order (-1,-1), (-1,+1), (+1,-1), (+1,+1)
-    {
-        const R rc[4] = {one + (A[0] - Sa[0]), one + (A[0] + Sa[0]), one + (B[0] - Sb[0]),
-                         one + (B[0] + Sb[0])};
-        const R nc[4] = {A[1] - Sa[1], A[1] + Sa[1], B[1] - Sb[1], B[1] + Sb[1]};
-        const R tc[4] = {A[2] - Sa[2], A[2] + Sa[2], B[2] - Sb[2], B[2] + Sb[2]};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            mnc[k] = rc[k] * nc[k];
-            mtc[k] = rc[k] * tc[k];
-            Pntc[k] = mnc[k] * tc[k];
-        }
-    }
-    const R two = rconst<R>(2.0);
-    // central differences
-    const R dx_mn = mne - mnw, dx_mt = mte - mtw, dx_e = ee - ew;
-    const R dy_mn = mnn - mns, dy_mt = mtn - mts;
-    const R dx_dr = B[0] - A[0];
-    const R dy_dr = two * Sm[0];
-    const R dxx_dr = (B[0] + A[0]) - two * M[0];
-    const R dxx_Pnn = (Pnne + Pnnw) - two * Pnn0;
-    const R dyy_Ptt = (Pttn + Ptts) - two * Ptt0;
-    const R dxy_Pnt = (Pntc[3] - Pntc[2]) - (Pntc[1] - Pntc[0]);
-    const R dxy_mn = (mnc[3] - mnc[2]) - (mnc[1] - mnc[0]);
-    const R dxy_mt = (mtc[3] - mtc[2]) - (mtc[1] - mtc[0]);
-    const R dxx_mn = (mne + mnw) - two * mn0, dyy_mn = (mnn + mns) - two * mn0;
-    const R dxx_mt = (mte + mtw) - two * mt0, dyy_mt = (mtn + mts) - two * mt0;
-    const R dxx_e = (ee + ew) - two * e0, dyy_e = (en + es) - two * e0;
-    const R quarter = rconst<R>(0.25);
-    const R hcs2 = rconst<R>(0.5 / 3.0);  // c_s^2 / 2
-
-    // Eq. 46: rho* (as drho*)
-    const R drs = M[0] - half * (dx_mn + dy_mt) +
-                  half * (dxx_Pnn + cs2 * dxx_dr + dyy_Ptt) + quarter * dxy_Pnt;
+    // Eq. 46: drho* = rho* - 1
+    const V drs = vfma(half, (dxx_Pnn - dx_mn) + (PntB_o - PntA_o),
+                       vfma(hcs2, dxx_dr, (M[0] - mt_l) + Ptt_q));
     // Eq. 47: (rho u_n)*, (rho u_t)*
-    R mns_ = mn0 - half * ((Pnne - Pnnw) + cs2 * dx_dr + (Pntn - Pnts)) +
-             hcs2 * (rconst<R>(3.0) * dxx_mn + dyy_mn + half * dxy_mt);
-    R mts_ = mt0 - half * ((Pnte - Pntw) + (Pttn - Ptts) + cs2 * dy_dr) +
-             hcs2 * (dxx_mt + rconst<R>(3.0) * dyy_mt + half * dxy_mn);
+    V mns_ = vfma(hcs2, vfma(three, dxx_mn, vfma(two, mn_q, mtB_o - mtA_o)),
+                  vfma(mhalf, vfma(cs2, dx_dr, PnnB - PnnA), mnM - Pnt_o));
+    V mts_ = vfma(hcs2, vfma(T::bc(6.0), mt_q, dxx_mt + (mnB_o - mnA_o)),
+                  vfma(mhalf, PntB - PntA, vfma(mcs2, sd, mtM - Ptt_o)));
     // Eq. 48: (rho T)* - Tbar
-    const R es_ = e0 - half * ((Qne - Qnw) + (Qtn - Qts)) + hcs2 * (dxx_e + dyy_e);
+    const V es_ = vfma(hcs2, vfma(two, e_q, dxx_e), vfma(mhalf, QnB - QnA, eM - Qt_o));
 
-    const R rho_s = one + drs;
-    if (wall) {  // no mass through a wall; the wall's tangential velocity
-        mns_ = rconst<R>(0.0);
-        mts_ = rho_s * u_wall_t;
-    }
-    const R inv = fast_rcp(rho_s);
-    const R uns = mns_ * inv, uts = mts_ * inv;
-    const R as_ = (es_ - drs * Tbar) * inv;  // T* - Tbar
+    const V rho_s = one + drs;
+    // wall faces: no mass through the wall, the wall's tangential velocity
+    mns_ = mns_ * keep;
+    mts_ = vfma(keep, mts_, (one - keep) * (rho_s * u_wall));
+    const V inv = T::rcp(rho_s);
+    const V uns = mns_ * inv, uts = mts_ * inv;
+    const V as_ = (es_ - drs * Tbar) * inv;  // T* - Tbar
 
-    // Eqs. 57-59 braces along the face normal
+    // Eqs. 57-59 braces along the face normal; d_y f = 2 (odd part)
     F[0] = mns_;
-    const R Xnn0 = Pnn0 + cs2 * d0;
-    F[1] = Xnn0 - fl.nu_2h * (rconst<R>(3.0) * dx_mn + dy_mt) -
-           fl.tf15 * ((mns_ * uns + cs2 * drs) - Xnn0);
-    F[2] = Pnt0 - fl.nu_2h * (dx_mt + dy_mn) - fl.tf15 * (mns_ * uts - Pnt0);
+    const V Xnn0 = vfma(cs2, M[0], PnnM);
+    F[1] = vfma(fl.m_nu_2h, vfma(three, dx_mn, two * mt_l),
+                vfma(fl.m_tf15, vfma(mns_, uns, cs2 * drs) - Xnn0, Xnn0));
+    F[2] = vfma(fl.m_nu_2h, vfma(two, mn_l, dx_mt), vfma(fl.m_tf15, vfma(mns_, uts, T::bc(0.0) - PntM), PntM));
     // (rho u_n T)* - (rho u_n T)^n = Tbar (mn* - mn0) + mn* a* - mn0 a0
-    F[3] = Qn0 - fl.chi_2h * dx_e -
-           fl.tg15 * (Tbar * (mns_ - mn0) + (mns_ * as_ - mn0 * a0));
+    F[3] = vfma(fl.m_chi_2h, dx_e,
+                vfma(fl.m_tg15, vfma(Tbar, mns_ - mnM, vfma(mns_, as_, T::bc(0.0) - mnM * M[3])), QnM));
 }
 
 // Parity of quantity k (0 drho, 1 u, 2 v, 3 T) about a wall of side s:
@@ -238,6 +289,7 @@ __host__ __device__ __forceinline__ int wall_parity(int kind, int k)
 struct StoreD {
     using S = double;
     using R = double;
+    using V2 = d2;
     static __host__ __device__ __forceinline__ R val(S s, int) { return s; }
     static __host__ __device__ __forceinline__ R diff(S a, S b, int) { return a - b; }
     static __host__ __device__ __forceinline__ S add(S s, R d, int) { return s + d; }
@@ -249,11 +301,21 @@ struct StoreD {
     static __host__ __device__ __forceinline__ bool in_range(R v, int) { return v == v; }
     static __device__ __forceinline__ R rcp(R x) { return 1.0 / x; }
     static __device__ __forceinline__ R fsqrt(R x) { return sqrt(x); }
+    // constants of a cavity in R, and the wall mirror constants in S
+    static __device__ __forceinline__ R dt(const CavityDesc* d) { return d->dt; }
+    static __device__ __forceinline__ R beta_g(const CavityDesc* d) { return d->beta_g; }
+    static __device__ __forceinline__ R T_ref(const CavityDesc* d) { return d->T_ref; }
+    static __device__ __forceinline__ R fx(const CavityDesc* d) { return d->fx; }
+    static __device__ __forceinline__ R fy(const CavityDesc* d) { return d->fy; }
+    static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->bcU[s]; }
+    static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return 2.0 * d->bcU[s]; }
+    static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return 2.0 * d->bcT[s]; }
 };
 
 struct StoreQ {
     using S = int;
     using R = float;
+    using V2 = f2;
     // scale of quantity k: 2^-32 (rho - 1), 2^-31 (u, v), 2^-30 (T)
     static __host__ __device__ __forceinline__ double scale_d(int k)
     {
@@ -300,6 +362,14 @@ struct StoreQ {
     // reciprocal and square root at FP32 accuracy (a few ulp), not IEEE rounding
     static __device__ __forceinline__ R rcp(R x) { return __fdividef(1.0f, x); }
     static __device__ __forceinline__ R fsqrt(R x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    static __device__ __forceinline__ R dt(const CavityDesc* d) { return d->f_dt; }
+    static __device__ __forceinline__ R beta_g(const CavityDesc* d) { return d->f_beta_g; }
+    static __device__ __forceinline__ R T_ref(const CavityDesc* d) { return d->f_T_ref; }
+    static __device__ __forceinline__ R fx(const CavityDesc* d) { return d->f_fx; }
+    static __device__ __forceinline__ R fy(const CavityDesc* d) { return d->f_fy; }
+    static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->f_bcU[s]; }
+    static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return d->q_u2[s]; }
+    static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return d->q_T2[s]; }
 };
 
 }  // namespace rtlbfs

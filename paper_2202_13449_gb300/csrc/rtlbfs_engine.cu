@@ -51,12 +51,11 @@ void build_lines(const Cavity& c, const std::vector<double>& f, bool periodic, d
         x.h = (R)h;
         x.cL = (R)(0.5 * wl - h);
         x.cR = (R)(h - 0.5 * wr);
-        x.wL = (R)(0.5 * wl);
-        x.wR = (R)(0.5 * wr);
-        x.nu_2h = (R)(nu / (2.0 * h));
-        x.chi_2h = (R)(chi / (2.0 * h));
-        x.tf15 = (R)(3.0 * nu / h - 1.0);
-        x.tg15 = (R)(3.0 * chi / h - 1.0);
+        x.pad = (R)0;
+        x.m_nu_2h = (R)(-nu / (2.0 * h));
+        x.m_chi_2h = (R)(-chi / (2.0 * h));
+        x.m_tf15 = (R)(1.0 - 3.0 * nu / h);
+        x.m_tg15 = (R)(1.0 - 3.0 * chi / h);
         fl[i] = x;
     }
     cl.resize(n + 4);
@@ -125,6 +124,9 @@ int Engine::init()
     CK(step_prepare(precision_));
     CK(step_occupancy(precision_, &occ_));
     if (occ_ < 1) return fail(RTLBFS_ERR_CUDA, "step kernel does not fit on an SM");
+    CK(march_prepare(precision_));
+    CK(march_occupancy(precision_, &occ_march_));
+    if (occ_march_ < 1) return fail(RTLBFS_ERR_CUDA, "march kernel does not fit on an SM");
     CK(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
     stream_ = own_stream_;
     slots_.resize(capacity_);
@@ -321,7 +323,7 @@ int Engine::upload_lines(int slot)
     }
     d.tiles_x = (c.nx + kTileX - 1) / kTileX;
     d.tiles_y = (c.ny + kTileY - 1) / kTileY;
-    d.ntiles = d.tiles_x * d.tiles_y;
+    d.ntiles = c.ntiles;  // work units of this cavity in the current list
     d.tile_begin = c.first_tile;
     d.beta_g = c.beta_g;
     d.T_ref = c.T_ref;
@@ -331,6 +333,16 @@ int Engine::upload_lines(int slot)
     d.dT = c.dT;
     d.nu = c.nu;
     d.chi = c.chi;
+    d.f_beta_g = (float)c.beta_g;
+    d.f_T_ref = (float)c.T_ref;
+    d.f_fx = (float)c.fx;
+    d.f_fy = (float)c.fy;
+    d.f_dt = (float)c.dt;
+    for (int s2 = 0; s2 < 4; ++s2) {
+        d.f_bcU[s2] = (float)c.bcU[s2];
+        d.q_u2[s2] = StoreQ::from_double(2.0 * c.bcU[s2], 1);
+        d.q_T2[s2] = StoreQ::twice(StoreQ::from_double(c.bcT[s2], 3));
+    }
     const size_t plane = rsize_ * (size_t)c.pitch * c.ny;
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 4; ++k)
@@ -345,18 +357,68 @@ int Engine::upload_lines(int slot)
     return RTLBFS_OK;
 }
 
+int Engine::set_kernel(int kind)
+{
+    if (kind != 0 && kind != 1) return fail(RTLBFS_ERR_ARG, "kernel kind must be 0 or 1");
+    if (kind != kernel_) {
+        kernel_ = kind;
+        tiles_dirty_ = true;
+        if (gexec_) {
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+        }
+    }
+    return RTLBFS_OK;
+}
+
+int Engine::set_chunk_rows(int rows)
+{
+    if (rows < 0) return fail(RTLBFS_ERR_ARG, "chunk rows must be >= 0");
+    chunk_rows_ = rows;
+    tiles_dirty_ = true;
+    return RTLBFS_OK;
+}
+
 int Engine::rebuild_tiles()
 {
     std::vector<int4> t;
-    for (int s = 0; s < capacity_; ++s) {
-        Cavity& c = slots_[s];
-        if (!c.active) continue;
-        const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
-        c.first_tile = (int)t.size();
-        c.ntiles = tx * ty;
-        for (int j = 0; j < ty; ++j)
-            for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * kTileY, 0));
-        c.dirty = true;  // tile_begin lives in the descriptor
+    if (kernel_ == 1) {
+        for (int s = 0; s < capacity_; ++s) {
+            Cavity& c = slots_[s];
+            if (!c.active) continue;
+            const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
+            c.first_tile = (int)t.size();
+            c.ntiles = tx * ty;
+            for (int j = 0; j < ty; ++j)
+                for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * kTileY, 0));
+            c.dirty = true;  // the unit count lives in the descriptor
+        }
+    } else {
+        // warp-marching units: strips of kStrip columns, chunks of H rows.
+        // H: long enough to amortise each unit's 2-row prologue, short
+        // enough that there are ~8 warps per SM of units to run.
+        long long strip_rows = 0;
+        for (int s = 0; s < capacity_; ++s)
+            if (slots_[s].active)
+                strip_rows += (long long)((slots_[s].nx + kStrip - 1) / kStrip) * slots_[s].ny;
+        int H = chunk_rows_;
+        if (H <= 0) {
+            const long long target = (long long)sms_ * 8;
+            H = (int)std::max<long long>(8, (strip_rows + target - 1) / std::max<long long>(target, 1));
+        }
+        for (int s = 0; s < capacity_; ++s) {
+            Cavity& c = slots_[s];
+            if (!c.active) continue;
+            const int strips = (c.nx + kStrip - 1) / kStrip;
+            const int h = std::min(H, c.ny);
+            const int chunks = (c.ny + h - 1) / h;
+            c.first_tile = (int)t.size();
+            c.ntiles = strips * chunks;
+            for (int k = 0; k < chunks; ++k)
+                for (int i = 0; i < strips; ++i)
+                    t.push_back(make_int4(s, i * kStrip, k * h, std::min(c.ny, (k + 1) * h)));
+            c.dirty = true;
+        }
     }
     CK(cudaStreamSynchronize(stream_));
     if ((int)t.size() > tile_cap_) {
@@ -387,9 +449,14 @@ int Engine::prepare_launch()
             int rc = upload_lines(s);
             if (rc) return rc;
         }
-    // persistent grid: every SM full, never more blocks than tiles
-    const int full = sms_ * occ_;
-    const int want = std::max(1, std::min(full, std::max(ntiles_, 1)));
+    // persistent grid: every SM full, never more blocks than work units
+    int want;
+    if (kernel_ == 1) {
+        want = std::max(1, std::min(sms_ * occ_, std::max(ntiles_, 1)));
+    } else {
+        const int wpb = kMarchThreads / 32;
+        want = std::max(1, std::min(sms_ * occ_march_, (std::max(ntiles_, 1) + wpb - 1) / wpb));
+    }
     if (want != grid_ && gexec_) {
         cudaGraphExecDestroy(gexec_);
         gexec_ = nullptr;
@@ -528,7 +595,8 @@ int Engine::launch_steps(long long launches)
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
-                    e = launch_step(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
+                    e = kernel_ == 1 ? launch_step(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+                                     : launch_march(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
                 cudaError_t e2 = cudaStreamEndCapture(cs, &g);
                 if (e == cudaSuccess) e = e2;
             }
@@ -545,7 +613,8 @@ int Engine::launch_steps(long long launches)
         }
     }
     for (; left > 0; --left) {
-        CK(launch_step(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
+        CK(kernel_ == 1 ? launch_step(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+                        : launch_march(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
         g_launches++;
     }
     return RTLBFS_OK;

@@ -82,6 +82,11 @@ public:
     int cuda_fail(cudaError_t e, const char* what);
     int active_tiles() const { return ntiles_; }
     int grid() const { return grid_; }
+    // step kernel: 0 = warp-marching strips (default), 1 = shared-memory tiles
+    int set_kernel(int kind);
+    int kernel() const { return kernel_; }
+    // rows per warp-marching work unit (0 = automatic)
+    int set_chunk_rows(int rows);
 
 private:
     int upload_lines(int slot);
@@ -92,6 +97,8 @@ private:
     int capacity_;
     size_t rsize_;
     int sms_ = 0, occ_ = 0, grid_ = 0;
+    int kernel_ = 0, occ_march_ = 0, chunk_rows_ = 0;
+    int launch_one(cudaStream_t s);
     cudaStream_t stream_ = nullptr, own_stream_ = nullptr;
     std::vector<Cavity> slots_;
     std::vector<CavityDesc> h_desc_;

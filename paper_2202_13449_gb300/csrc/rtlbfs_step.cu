@@ -101,19 +101,15 @@ __device__ __forceinline__ Vec4<typename P::S> mirror_state(const CavityDesc& d,
 {
     using S = typename P::S;
     const bool xn = (side == kSideW || side == kSideE);
-    const S zero2 = P::from_double(0.0, 1);
-    const S ut2 = P::from_double(2.0 * d.bcU[side], 1);
+    const S ut2 = P::u2(&d, side);
     if (xn) {
-        v.y = P::mirror_odd(zero2, v.y);
+        v.y = P::mirror_odd(S(0), v.y);
         v.z = P::mirror_odd(ut2, v.z);
     } else {
-        v.z = P::mirror_odd(zero2, v.z);
+        v.z = P::mirror_odd(S(0), v.z);
         v.y = P::mirror_odd(ut2, v.y);
     }
-    if (d.kind[side] == kDirichlet) {
-        const S Tw = P::from_double(d.bcT[side], 3);
-        v.w = P::mirror_odd(P::twice(Tw), v.w);
-    }
+    if (d.kind[side] == kDirichlet) v.w = P::mirror_odd(P::T2(&d, side), v.w);
     return v;
 }
 
@@ -348,9 +344,9 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 int wside = -1;
                 if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
                 if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
-                const R uw = wside >= 0 ? rconst<R>(dp->bcU[wside]) : R(0);
+                const R uw = wside >= 0 ? P::bcU(dp, wside) : R(0);
                 R F[4];
-                face_flux<R>(L, Rr, Tbar, fl, wside >= 0, uw, F);
+                face_flux<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
                 if (isx) out = {F[0], F[1], F[2], F[3]};
                 else out = {F[0], F[2], F[1], F[3]};
             }
@@ -366,8 +362,8 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
 #pragma unroll
             for (int k = 0; k < 4; ++k) fout[k] = static_cast<S*>(dp->f[cur ^ 1][k]);
             const R one = rconst<R>(1.0);
-            const R dt = rconst<R>(dp->dt), bg = rconst<R>(dp->beta_g), Tr = rconst<R>(dp->T_ref);
-            const R fxb = rconst<R>(dp->fx), fyb = rconst<R>(dp->fy);
+            const R dt = P::dt(dp), bg = P::beta_g(dp), Tr = P::T_ref(dp);
+            const R fxb = P::fx(dp), fyb = P::fy(dp);
             bool bad = false;
             for (int k = tid; k < TX * TY; k += kStepThreads) {
                 const int tc = k % TX, tr = k / TX;
@@ -521,7 +517,7 @@ __device__ double energy_flux_d(const CavityDesc& d, const typename P::S* const*
     if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
     const FaceLine<double> fl = nd == 0 ? ln.xl[i] : ln.yl[j];
     double F[4];
-    face_flux<double>(L, Rr, Tbar, fl, wside >= 0, wside >= 0 ? d.bcU[wside] : 0.0, F);
+    face_flux<double>(L, Rr, Tbar, fl, wside >= 0 ? 0.0 : 1.0, wside >= 0 ? d.bcU[wside] : 0.0, F);
     return F[3];
 }
 

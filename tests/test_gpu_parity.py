@@ -61,11 +61,15 @@ def case_mesh(name, nx, ny, mesh):
     return inputs.random_faces(nx, seed), inputs.random_faces(ny, seed + 1)
 
 
-def run_case(orc, name, precision, nsteps):
+KERNELS = [0, 1]  # warp-marching strips, shared-memory tiles
+
+
+def run_case(orc, name, precision, nsteps, kernel=0, chunk_rows=0):
     nx, ny, mesh, kinds, bcT, bcU, kappa, bg = CASES[name]
     xf, yf = case_mesh(name, nx, ny, mesh)
     p, s = make_pair(orc, xf, yf, nu=0.04, chi=0.05, beta_g=bg, dt=0.25, kappa=kappa,
                      kinds=kinds, bcT=bcT, bcU=bcU, precision=precision)
+    s.set_schedule(kernel, chunk_rows)
     st = inputs.perturbed_state(nx, ny, seed=7 + nx * 31 + ny)
     ref, _, rc = orc.step(p, st, nsteps)
     assert rc == 0
@@ -78,10 +82,11 @@ def run_case(orc, name, precision, nsteps):
     return ref, got, res_gpu
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
-def test_single_step_matches_oracle(orc, name, precision):
-    ref, got, _ = run_case(orc, name, precision, 1)
+def test_single_step_matches_oracle(orc, name, precision, kernel):
+    ref, got, _ = run_case(orc, name, precision, 1, kernel)
     tol = TOL[precision]
     if precision == capi.FP64:
         assert rel(got[0], ref[0], 1.0) < tol
@@ -92,10 +97,11 @@ def test_single_step_matches_oracle(orc, name, precision):
     assert rel(got[3], ref[3], 1.0) < tol
 
 
+@pytest.mark.parametrize("kernel,chunk", [(0, 0), (0, 5), (1, 0)])
 @pytest.mark.parametrize("name", ["cavity_irregular_lid", "rb_periodic_x_stretched_y",
                                   "periodic_y_walls_x"])
-def test_thirty_steps_match_oracle_fp64(orc, name):
-    ref, got, res = run_case(orc, name, capi.FP64, 30)
+def test_thirty_steps_match_oracle_fp64(orc, name, kernel, chunk):
+    ref, got, res = run_case(orc, name, capi.FP64, 30, kernel, chunk)
     for q, floor in ((0, 1.0), (1, 1e-2), (2, 1e-2), (3, 1.0)):
         assert rel(got[q], ref[q], floor) < 1e-11, (q, rel(got[q], ref[q], floor))
 
@@ -122,11 +128,13 @@ def config2_pair(orc, precision):
                      (0, 0, 0, 0), precision)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
-def test_full_size_512_tanh_cavity_one_step(orc, precision):
+def test_full_size_512_tanh_cavity_one_step(orc, precision, kernel):
     """The Ra = 1e8, 512 x 512, tanh (phi = 2) cavity: one step from a
     generic state, every cell compared."""
     p, s = config2_pair(orc, precision)
+    s.set_schedule(kernel, 0)
     st = inputs.perturbed_state(512, 512, seed=2024, amp_u=0.05)
     ref, _, rc = orc.step(p, st, 1)
     s.set_state(*st)
@@ -138,11 +146,13 @@ def test_full_size_512_tanh_cavity_one_step(orc, precision):
         assert rel(got[q], ref[q], floor) < tol, (q, rel(got[q], ref[q], floor))
 
 
-def test_mass_conserved_to_round_off_on_gpu(orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mass_conserved_to_round_off_on_gpu(orc, kernel):
     nx, ny = 40, 24
     xf, yf = inputs.random_faces(nx, 5), inputs.random_faces(ny, 6)
     _, s = make_pair(orc, xf, yf, 0.03, 0.04, 2e-3, 0.3, 1.0, (D, D, A, A), (1, 0, 0, 0),
                      (0, 0, 0, 0), capi.FP64)
+    s.set_schedule(kernel, 7)
     st = inputs.perturbed_state(nx, ny, seed=11)
     dV = np.outer(np.diff(yf), np.diff(xf))
     m0 = float(np.sum(st[0] * dV))
@@ -181,10 +191,12 @@ def test_config1_run_to_steady_fp64(orc):
     s.close()
 
 
-def test_config1_fp32_against_fp64_oracle(orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_config1_fp32_against_fp64_oracle(orc, kernel):
     """FP32 bulk with FP64 reductions on the same case: fields within 1e-5 and
     the mean wall Nusselt number within 1e-4 of the FP64 oracle."""
     p, s = cavity_solver(orc, 64, 1e3, capi.FP32)
+    s.set_schedule(kernel, 0)
     st0 = inputs.conduction_state(p.xf, p.yf)
     ref, n_ref, _, rc = orc.run_to_steady(p, st0, 1e-8, 400000)
     assert rc == 0
