@@ -49,6 +49,11 @@ WORKLOADS = {
              "Ma=0.1, FP32 bulk + FP64 reductions, seeded noise 1e-3",
         nx=1024, ny=512, phi=0.0, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32", inner=500,
         kind="rb"),
+    "cavity8192": dict(
+        desc="roofline probe: differentially heated cavity 8192x8192, tanh phi=2.0, Ra=1e8, "
+             "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
+        nx=8192, ny=8192, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=10,
+        kind="cavity"),
     "cavity512_fp64": dict(
         desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
@@ -56,6 +61,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "cavity512"
 STEP_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_step.cu",
+                "paper_2202_13449_gb300/csrc/rtlbfs_march.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh",
                 "paper_2202_13449_gb300/csrc/rtlbfs_kernels.h"]
 
@@ -77,14 +83,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(workload: str, precision: str):
+def profile_traffic(workload: str, precision: str, kernel: str):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get(f"{workload}:{precision}")
+        e = d.get(f"{workload}:{precision}:{kernel}")
         if e and e.get("kernel_hash") == kernel_hash():
             return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -188,6 +194,15 @@ def run_ours(args, w):
     s, st0, xf, yf = setup_solver(capi, inputs, w)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
+    # pick the schedule on a snapshot of the state (restored afterwards),
+    # or take the one given on the command line
+    if args.schedule == "auto":
+        sched = s.autotune(max(16, min(256, 2_000_000 // cells + 16)))
+    else:
+        k = 0 if args.schedule.startswith("march") else 1
+        rows = int(args.schedule.split(":")[1]) if ":" in args.schedule else 0
+        s.set_schedule(k, rows)
+        sched = (k, rows, 0.0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -265,15 +280,19 @@ def run_ours(args, w):
         "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
                    "time_steps_per_bench_step": inner, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between bench steps (256 MB write)",
+                   "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1],
+                                "autotune_ms_per_step": round(sched[2], 5)},
                    "state_bytes_per_buffer": 4 * rs * cells},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": profile_traffic(args.workload, w["precision"]),
+                     "traffic": profile_traffic(args.workload, w["precision"],
+                                                ["march", "tile"][sched[0]]),
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": "rtlbfs::step_kernel", "alg_bytes_per_launch": alg_bytes},
+                     "kernel": ["rtlbfs::march_kernel", "rtlbfs::step_kernel"][sched[0]],
+                     "alg_bytes_per_launch": alg_bytes},
         "clocks": clocks,
         "wall_s": round(t_wall, 3),
         "residual_last_step": res,
@@ -380,6 +399,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--schedule", default="auto",
+                    help="auto (autotuner), tile, or march[:rows per unit]")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -186,6 +186,16 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
  */
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
 
+/*
+ * Autotuner: time every candidate schedule (the tile kernel and the
+ * marching kernel with 8..256 rows per unit) for `steps` steps each on a
+ * device-side snapshot of the current state, restore the state exactly
+ * (fields, step counter, residual) and keep the fastest schedule.  Writes
+ * the choice and its time per step if the pointers are non-null.  Needs
+ * one extra copy of the state in device memory while it runs.
+ */
+int rtlbfs_autotune(rtlbfs_t h, int steps, int* kernel, int* chunk_rows, double* ms_per_step);
+
 /* Use this CUDA stream (a cudaStream_t, e.g. torch's current stream) for
  * all later work of the handle; NULL restores the handle's own stream. */
 int rtlbfs_set_stream(rtlbfs_t h, void* stream);

@@ -49,6 +49,8 @@ _SIGS = {
     "rtlbfs_nusselt": (C.c_int, [_vp, C.c_int, _dp]),
     "rtlbfs_set_stream": (C.c_int, [_vp, _vp]),
     "rtlbfs_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "rtlbfs_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double)]),
     "rtlbfs_sync": (C.c_int, [_vp]),
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
@@ -177,6 +179,14 @@ class Solver:
         """kernel 0: warp-marching strips, 1: shared-memory tiles."""
         self._check(lib().rtlbfs_set_schedule(self._h, int(kernel), int(chunk_rows)),
                     "set_schedule")
+
+    def autotune(self, steps: int = 64):
+        """Pick the fastest schedule on a snapshot of the state (restored);
+        returns (kernel, chunk_rows, ms_per_step)."""
+        k, r, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        self._check(lib().rtlbfs_autotune(self._h, int(steps), C.byref(k), C.byref(r), C.byref(ms)),
+                    "autotune")
+        return int(k.value), int(r.value), float(ms.value)
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, an int handle, or None."""

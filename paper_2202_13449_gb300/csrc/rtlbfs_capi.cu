@@ -278,6 +278,12 @@ int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows)
     return finish(h, rc);
 }
 
+int rtlbfs_autotune(rtlbfs_t h, int steps, int* kernel, int* chunk_rows, double* ms_per_step)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->autotune(steps, kernel, chunk_rows, ms_per_step));
+}
+
 int rtlbfs_set_stream(rtlbfs_t h, void* stream)
 {
     if (!cav(h)) return RTLBFS_ERR_ARG;

@@ -402,9 +402,10 @@ int Engine::rebuild_tiles()
             if (slots_[s].active)
                 strip_rows += (long long)((slots_[s].nx + kStrip - 1) / kStrip) * slots_[s].ny;
         int H = chunk_rows_;
-        if (H <= 0) {
-            const long long target = (long long)sms_ * 8;
-            H = (int)std::max<long long>(8, (strip_rows + target - 1) / std::max<long long>(target, 1));
+        if (H <= 0) {  // ~16 warps of units per SM, at least 16 rows each
+            const long long target = (long long)sms_ * 16;
+            H = (int)std::max<long long>(16, (strip_rows + target - 1) / std::max<long long>(target, 1));
+            H = std::min(H, 64);
         }
         for (int s = 0; s < capacity_; ++s) {
             Cavity& c = slots_[s];
@@ -617,6 +618,93 @@ int Engine::launch_steps(long long launches)
                         : launch_march(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
         g_launches++;
     }
+    return RTLBFS_OK;
+}
+
+int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
+{
+    if (steps < 1) return fail(RTLBFS_ERR_ARG, "autotune needs steps >= 1");
+    CK(cudaStreamSynchronize(stream_));
+    // snapshot every active cavity's fields and the run control
+    std::vector<void*> snap(capacity_, nullptr);
+    std::vector<CavityCtl> ctl_save(capacity_);
+    CK(cudaMemcpy(ctl_save.data(), d_ctl_, sizeof(CavityCtl) * capacity_, cudaMemcpyDeviceToHost));
+    int maxny = 1;
+    for (int s = 0; s < capacity_; ++s) {
+        if (!slots_[s].active) continue;
+        maxny = std::max(maxny, slots_[s].ny);
+        cudaError_t e = cudaMalloc(&snap[s], slots_[s].fields_bytes);
+        if (e != cudaSuccess) {
+            for (void* p : snap) cudaFree(p);
+            return cuda_fail(e, "autotune snapshot");
+        }
+        CK(cudaMemcpyAsync(snap[s], slots_[s].d_fields, slots_[s].fields_bytes,
+                           cudaMemcpyDeviceToDevice, stream_));
+    }
+    struct Cand {
+        int kernel, rows;
+    };
+    std::vector<Cand> cands = {{1, 0}};
+    for (int H : {8, 16, 32, 64, 128, 256}) {
+        if (H > maxny && H != 8) break;
+        cands.push_back({0, H});
+    }
+    const int keep_kernel = kernel_, keep_rows = chunk_rows_;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick = {keep_kernel, keep_rows};
+    int rc = RTLBFS_OK;
+    for (const Cand& c : cands) {
+        if ((rc = set_kernel(c.kernel)) || (rc = set_chunk_rows(c.rows))) break;
+        for (int s = 0; s < capacity_ && !rc; ++s)
+            if (slots_[s].active) rc = arm(s, (long long)steps + 8, -1.0);
+        if (rc || (rc = launch_steps(4))) break;
+        cudaEventRecord(e0, stream_);
+        if ((rc = launch_steps(steps))) break;
+        cudaEventRecord(e1, stream_);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+        // restore the snapshot before the next candidate
+        for (int s = 0; s < capacity_; ++s)
+            if (snap[s])
+                cudaMemcpyAsync(slots_[s].d_fields, snap[s], slots_[s].fields_bytes,
+                                cudaMemcpyDeviceToDevice, stream_);
+        cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityCtl) * capacity_,
+                        cudaMemcpyHostToDevice, stream_);
+        cudaStreamSynchronize(stream_);
+    }
+    // final restore (also after an error)
+    for (int s = 0; s < capacity_; ++s)
+        if (snap[s])
+            cudaMemcpyAsync(slots_[s].d_fields, snap[s], slots_[s].fields_bytes,
+                            cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityCtl) * capacity_, cudaMemcpyHostToDevice,
+                    stream_);
+    cudaStreamSynchronize(stream_);
+    for (void* p : snap) cudaFree(p);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        set_kernel(keep_kernel);
+        set_chunk_rows(keep_rows);
+        return rc;
+    }
+    set_kernel(pick.kernel);
+    set_chunk_rows(pick.rows);
+    if (kernel_out) *kernel_out = pick.kernel;
+    if (rows_out) *rows_out = pick.rows;
+    if (ms_out) *ms_out = best / steps;
     return RTLBFS_OK;
 }
 

@@ -87,6 +87,10 @@ public:
     int kernel() const { return kernel_; }
     // rows per warp-marching work unit (0 = automatic)
     int set_chunk_rows(int rows);
+    int chunk_rows() const { return chunk_rows_; }
+    // time every candidate schedule for `steps` steps on a snapshot of the
+    // current state (restored afterwards) and keep the fastest
+    int autotune(int steps, int* kernel, int* chunk_rows, double* ms_per_step);
 
 private:
     int upload_lines(int slot);

@@ -284,3 +284,24 @@ def test_run_controls(orc):
     s.step(0)
     assert s.residual()[1] == 300
     s.close()
+
+
+def test_autotune_keeps_the_state(orc):
+    """The autotuner times schedules on a snapshot: afterwards the state,
+    step counter and results are those of an untuned run."""
+    p, s = cavity_solver(orc, 96, 1e5, capi.FP64)
+    s.step(7)
+    before = s.get_state()
+    (_, _), steps = s.residual()
+    kernel, rows, ms = s.autotune(16)
+    assert kernel in (0, 1) and ms > 0
+    after = s.get_state()
+    assert s.residual()[1] == steps
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    s.step(5)
+    ref, _, _ = orc.step(p, before, 5)
+    got = s.get_state()
+    for q, floor in ((1, 0.1), (2, 0.1), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < 1e-12
+    s.close()
