@@ -209,6 +209,41 @@ const char* rtlbfs_last_error(rtlbfs_t h);
 /* Free every device and host resource of h; NULL is ignored. */
 void rtlbfs_destroy(rtlbfs_t h);
 
+/*
+ * Allocation-free Nusselt number of a caller-owned FP64 state.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they call in -- real-time or graph-built
+ * pipelines where a cudaMalloc could block or fail, hosts that hand the
+ * library only memory they own -- and for fields that live in the caller's
+ * buffers rather than in a handle.  It computes what rtlbfs_nusselt computes
+ * (same selectors `which`, same FP64 arithmetic) and allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call.
+ *
+ *   nx, ny         cells, each at most 8192 (larger: RTLBFS_ERR_ARG)
+ *   xf, yf         host face coordinates (nx+1, ny+1), strictly ascending
+ *   rho,u,v,T      device pointers, FP64, row-major ny x nx (rho itself, not rho-1)
+ *   nu, chi, kappa transport coefficients and lattice factor (as rtlbfs_set_physics /
+ *                  rtlbfs_set_lattice); dT the reference temperature difference
+ *   bc_kind, bc_T, bc_u   host arrays of 4 (W, E, S, N) as in rtlbfs_set_bc
+ *   nu_out         device pointer to one double, written asynchronously on `stream`
+ *   stream         a cudaStream_t (NULL: the legacy default stream)
+ *
+ * Working memory: one file-scope device array of about 1.8 MB (descriptor,
+ * mesh lines, partial sums) that every GPU which loads the library keeps
+ * until the process exits.  The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress, once per device): make that first call
+ * before any stream capture.  Every call reuses the array and the call
+ * re-initialises what it needs; two calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on it and must be
+ * ordered by the caller.  Returns RTLBFS_OK, RTLBFS_ERR_ARG or
+ * RTLBFS_ERR_CUDA.
+ */
+int rtlbfs_nusselt_noalloc(int nx, int ny, const double* xf, const double* yf,
+                           const double* rho, const double* u, const double* v, const double* T,
+                           double nu, double chi, double kappa, double dT, const int* bc_kind,
+                           const double* bc_T, const double* bc_u, int which, double* nu_out,
+                           void* stream);
+
 /* Number of kernel launches issued by the library since load (for the
  * benchmark's launch count). */
 long long rtlbfs_launch_count(void);

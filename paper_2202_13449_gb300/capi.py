@@ -55,6 +55,9 @@ _SIGS = {
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
     "rtlbfs_launch_count": (C.c_longlong, []),
+    "rtlbfs_nusselt_noalloc": (C.c_int, [C.c_int, C.c_int, _dp, _dp, _vp, _vp, _vp, _vp,
+                                         C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.POINTER(C.c_int), _dp, _dp, C.c_int, _vp, _vp]),
 }
 
 
@@ -110,6 +113,22 @@ def tanh_faces(n: int, L: float, phi: float) -> np.ndarray:
     if rc:
         raise RTLBFSError(rc, "rtlbfs_tanh_faces")
     return out
+
+
+def nusselt_noalloc(xf, yf, rho_ptr, u_ptr, v_ptr, T_ptr, nu, chi, kappa, dT, bc_kind, bc_T,
+                    bc_u, which, out_ptr, stream=None):
+    """Allocation-free Nusselt number of caller-owned FP64 device fields
+    (pointers as ints); the result is written to the device double at
+    out_ptr asynchronously on `stream`.  Returns the status code."""
+    xf = np.ascontiguousarray(xf, dtype=np.float64)
+    yf = np.ascontiguousarray(yf, dtype=np.float64)
+    kinds = (C.c_int * 4)(*[int(k) for k in bc_kind])
+    bT = np.ascontiguousarray(bc_T, dtype=np.float64)
+    bU = np.ascontiguousarray(bc_u, dtype=np.float64)
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    return int(lib().rtlbfs_nusselt_noalloc(len(xf) - 1, len(yf) - 1, _ptr(xf), _ptr(yf), rho_ptr,
+                                            u_ptr, v_ptr, T_ptr, nu, chi, kappa, dT, kinds,
+                                            _ptr(bT), _ptr(bU), int(which), out_ptr, st))
 
 
 def launch_count() -> int:

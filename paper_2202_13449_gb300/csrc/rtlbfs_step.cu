@@ -20,9 +20,12 @@
 // write of the four fields per cell per step (halo re-reads hit L2).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
+#include "rtlbfs.h"
 #include "rtlbfs_dev.cuh"
 #include "rtlbfs_kernels.h"
 
@@ -749,3 +752,182 @@ cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nste
 }
 
 }  // namespace rtlbfs
+
+// ---------------------------------------------------------------------------
+// Allocation-free Nusselt number (rtlbfs_nusselt_noalloc).
+//
+// For callers that must not allocate device memory at call time -- code
+// running where a cudaMalloc could block or fail unpredictably (a real-time
+// loop, a CUDA-graph-built pipeline, a host that gives the library only a
+// fixed memory pool), or that keeps its fields in buffers it owns -- the
+// wall/average Nusselt reduction runs on caller-owned device fields with all
+// of its working memory in one file-scope device array: the cavity
+// descriptor, the FP64 mesh lines and the per-block partial sums.  Every GPU
+// that loads the library holds this array (kNoAllocBytes, about 1.8 MB)
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace rtlbfs {
+
+extern std::atomic<long long> g_launches;
+
+constexpr int kNoAllocMaxN = 8192;       // cells per side
+constexpr int kNoAllocPartials = 1024;   // reduction blocks
+
+struct NoAllocScratch {
+    CavityDesc desc;
+    CavityCtl ctl;
+    double xf[kNoAllocMaxN + 1];
+    double yf[kNoAllocMaxN + 1];
+    FaceLine<double> xl[kNoAllocMaxN + 1];
+    FaceLine<double> yl[kNoAllocMaxN + 1];
+    CellLine<double> xc[kNoAllocMaxN + 4];
+    CellLine<double> yc[kNoAllocMaxN + 4];
+    double partial[kNoAllocPartials];
+};
+constexpr size_t kNoAllocBytes = sizeof(NoAllocScratch);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// The caller's rho (not rho - 1) in the first field.
+struct StoreRho : StoreD {
+    static __host__ __device__ __forceinline__ double to_double(double s, int k)
+    {
+        return k == 0 ? s - 1.0 : s;
+    }
+};
+
+// Mesh lines of one axis from its face coordinates (the same formulas as
+// the host-side line builder of the engine), in device memory.
+__global__ void noalloc_lines_kernel(const double* __restrict__ f, int n, int periodic,
+                                     double kappa, double nu, double chi,
+                                     FaceLine<double>* __restrict__ fl,
+                                     CellLine<double>* __restrict__ cl)
+{
+    auto width = [&](int i) {
+        int k = i;
+        if (periodic) {
+            k = ((i % n) + n) % n;
+        } else {
+            if (i < 0) k = -1 - i;
+            if (i >= n) k = 2 * n - 1 - i;
+            k = min(max(k, 0), n - 1);
+        }
+        return f[k + 1] - f[k];
+    };
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+        const double wl = width(i - 1), wr = width(i);
+        const double h = kappa * fmin(wl, wr);
+        FaceLine<double> x;
+        x.h = h;
+        x.cL = 0.5 * wl - h;
+        x.cR = h - 0.5 * wr;
+        x.m_nu_2h = -nu / (2.0 * h);
+        x.m_chi_2h = -chi / (2.0 * h);
+        x.m_tf15 = 1.0 - 3.0 * nu / h;
+        x.m_tg15 = 1.0 - 3.0 * chi / h;
+        x.pad = 0.0;
+        fl[i] = x;
+    }
+    for (int i = (int)threadIdx.x - 2; i <= n + 1; i += blockDim.x) {
+        const double w = width(i), wn = width(i + 1);
+        CellLine<double> y;
+        y.w = w;
+        y.is_next = 1.0 / (w + wn);
+        y.dt_w = 0.0;
+        y.pad = 0.0;
+        cl[i + 2] = y;
+    }
+}
+
+namespace {
+std::atomic<void*> g_noalloc_ptr[64];
+}
+
+}  // namespace rtlbfs
+
+extern "C" int rtlbfs_nusselt_noalloc(int nx, int ny, const double* xf, const double* yf,
+                                      const double* rho, const double* u, const double* v,
+                                      const double* T, double nu, double chi, double kappa,
+                                      double dT, const int* bc_kind, const double* bc_T,
+                                      const double* bc_u, int which, double* nu_out,
+                                      void* stream)
+{
+    using namespace rtlbfs;
+    if (nx < 1 || ny < 1 || nx > kNoAllocMaxN || ny > kNoAllocMaxN) return RTLBFS_ERR_ARG;
+    if (!xf || !yf || !rho || !u || !v || !T || !bc_kind || !bc_T || !bc_u || !nu_out)
+        return RTLBFS_ERR_ARG;
+    if (which < kNuWest || which > kNuHalf || (which == kNuHalf && (nx % 2))) return RTLBFS_ERR_ARG;
+    if (!(nu > 0) || !(chi > 0) || !(kappa > 0) || !(dT > 0)) return RTLBFS_ERR_ARG;
+    for (int i = 0; i < nx; ++i)
+        if (!(xf[i + 1] > xf[i])) return RTLBFS_ERR_ARG;
+    for (int j = 0; j < ny; ++j)
+        if (!(yf[j + 1] > yf[j])) return RTLBFS_ERR_ARG;
+    for (int s = 0; s < 4; ++s)
+        if (bc_kind[s] < 0 || bc_kind[s] > 2) return RTLBFS_ERR_ARG;
+    if ((bc_kind[0] == kPeriodic) != (bc_kind[1] == kPeriodic) ||
+        (bc_kind[2] == kPeriodic) != (bc_kind[3] == kPeriodic))
+        return RTLBFS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // once per device, with that device current: the scratch array's address
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RTLBFS_ERR_CUDA;
+    void* base = g_noalloc_ptr[dev].load();
+    if (!base) {
+        if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base)
+            return RTLBFS_ERR_CUDA;
+        g_noalloc_ptr[dev].store(base);
+    }
+    NoAllocScratch* sc = static_cast<NoAllocScratch*>(base);
+
+    // descriptor of the caller's cavity (fields used as buffer 0)
+    CavityDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nx = nx;
+    d.ny = ny;
+    d.pitch = nx;
+    for (int s = 0; s < 4; ++s) {
+        d.kind[s] = bc_kind[s];
+        d.bcT[s] = bc_T[s];
+        d.bcU[s] = bc_u[s];
+    }
+    d.nu = nu;
+    d.chi = chi;
+    d.dT = dT;
+    d.f[0][0] = const_cast<double*>(rho);
+    d.f[0][1] = const_cast<double*>(u);
+    d.f[0][2] = const_cast<double*>(v);
+    d.f[0][3] = const_cast<double*>(T);
+    // the copies read their pageable sources before returning
+    if (cudaMemcpyAsync(&sc->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(&sc->ctl, 0, sizeof(CavityCtl), st) != cudaSuccess ||  // cur = 0
+        cudaMemcpyAsync(sc->xf, xf, sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(sc->yf, yf, sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return RTLBFS_ERR_CUDA;
+    noalloc_lines_kernel<<<1, 256, 0, st>>>(sc->xf, nx, bc_kind[0] == kPeriodic, kappa, nu, chi,
+                                            sc->xl, sc->xc);
+    noalloc_lines_kernel<<<1, 256, 0, st>>>(sc->yf, ny, bc_kind[2] == kPeriodic, kappa, nu, chi,
+                                            sc->yl, sc->yc);
+    NuLines ln;
+    ln.xl = sc->xl;
+    ln.yl = sc->yl;
+    ln.xc = sc->xc;
+    ln.yc = sc->yc;
+    long long count;
+    double scale = 1.0 / (chi * dT);
+    if (which == kNuWest || which == kNuEast || which == kNuHalf) count = ny;
+    else if (which == kNuSouth || which == kNuNorth) count = nx;
+    else {
+        count = (long long)nx * ny;
+        scale /= (xf[nx] - xf[0]);
+    }
+    int blocks = (int)((count + 255) / 256);
+    blocks = blocks > kNoAllocPartials ? kNoAllocPartials : (blocks < 1 ? 1 : blocks);
+    nusselt_partial_kernel<StoreRho><<<blocks, 256, 0, st>>>(&sc->desc, &sc->ctl, 0, ln, which,
+                                                            sc->partial);
+    sum_partials_kernel<<<1, 256, 0, st>>>(sc->partial, blocks, scale, nu_out);
+    g_launches += 4;
+    return cudaGetLastError() == cudaSuccess ? RTLBFS_OK : RTLBFS_ERR_CUDA;
+}
