@@ -1,0 +1,148 @@
+/*
+ * rtlbfs_batch.h -- many independent RTLBFS cavities advanced together, and
+ * a continuous-batching request loop on top of them (GB300, sm_103a).
+ *
+ * The method per cavity is the one of rtlbfs.h (arXiv 2202.13449, Section
+ * 3.2: Eqs. 29, 46-48, 55-59, 64).  A batch holds up to max_slots cavities of
+ * any mesh size; one kernel launch advances every active cavity by one step
+ * (one work list of strips or tiles over all of them), each cavity stopping
+ * on its own residual tolerance or step cap (decided on the device after
+ * every step).  The paper solves one cavity at a time; batching and serving
+ * are systems layers around its per-face arithmetic.
+ *
+ * Conventions as in rtlbfs.h: status returns, host arrays copied, device
+ * memory owned by the batch, not thread-safe per batch.
+ */
+#ifndef RTLBFS_BATCH_H
+#define RTLBFS_BATCH_H
+
+#include <stddef.h>
+
+#include "rtlbfs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtlbfs_batch_ctx* rtlbfs_batch_t;
+
+/* per-slot status of rtlbfs_batch_poll */
+#define RTLBFS_SLOT_EMPTY (-1)
+#define RTLBFS_SLOT_RUNNING 0
+#define RTLBFS_SLOT_CONVERGED 1
+#define RTLBFS_SLOT_MAX_STEPS 2
+#define RTLBFS_SLOT_DIVERGED 3
+
+/* Create an empty batch of up to max_slots cavities (precision RTLBFS_FP64
+ * or RTLBFS_FP32).  ERR_ARG, ERR_OOM, ERR_CUDA. */
+int rtlbfs_batch_create(int precision, int max_slots, rtlbfs_batch_t* out);
+
+/* Device bytes one nx x ny cavity of this precision occupies in a batch
+ * (both state buffers and mesh lines); for admission control. */
+size_t rtlbfs_batch_bytes(int precision, int nx, int ny);
+
+/* Free and total device memory of the current device (cudaMemGetInfo). */
+int rtlbfs_batch_free_bytes(size_t* free_bytes, size_t* total_bytes);
+
+/*
+ * Add a cavity with faces xf[0..nx], yf[0..ny] (copied) and parameters as
+ * rtlbfs_set_params (Eq. 63 with V_c = Ma, L = domain width): the defaults
+ * of rtlbfs_create_mesh (differentially heated cavity, conduction initial
+ * state).  *slot receives its slot id.  The slot is idle until armed.
+ * ERR_STATE when no slot is free, ERR_OOM when device memory is short.
+ */
+int rtlbfs_batch_add(rtlbfs_batch_t b, int nx, int ny, const double* xf, const double* yf,
+                     double Ra, double Pr, double Ma, double dt, int* slot);
+
+/* Boundary condition of one side of a slot (as rtlbfs_set_bc). */
+int rtlbfs_batch_set_bc(rtlbfs_batch_t b, int slot, int side, int kind, double T_wall,
+                        double u_wall);
+
+/* State in/out of a slot (ny*nx doubles per field, rho/u/v/T). */
+int rtlbfs_batch_set_state(rtlbfs_batch_t b, int slot, const double* rho, const double* u,
+                           const double* v, const double* T);
+int rtlbfs_batch_get_state(rtlbfs_batch_t b, int slot, double* rho, double* u, double* v,
+                           double* T);
+
+/* Let a slot take up to max_steps more steps, stopping after the first step
+ * with max(R_u, R_T) < tol (tol <= 0: never). */
+int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps);
+
+/* Launch nsteps batched steps (asynchronous; slots that are done skip). */
+int rtlbfs_batch_step(rtlbfs_batch_t b, long nsteps);
+
+/* Per-slot status, steps since the last state upload and last (R_u, R_T)
+ * (arrays of max_slots, 2*max_slots for res2; null pointers skipped).
+ * Synchronises. */
+int rtlbfs_batch_poll(rtlbfs_batch_t b, int* status, long* steps, double* res2);
+
+/* FP64 Nusselt number of a slot (selectors of rtlbfs_nusselt). */
+int rtlbfs_batch_nusselt(rtlbfs_batch_t b, int slot, int which, double* nu);
+
+/* Free a slot and its device memory. */
+int rtlbfs_batch_remove(rtlbfs_batch_t b, int slot);
+
+/* Pick the step schedule for the current set of slots (see rtlbfs_autotune). */
+int rtlbfs_batch_autotune(rtlbfs_batch_t b, int steps, int* kernel, int* chunk_rows,
+                          double* ms_per_step);
+
+/* Stream for all later work of the batch (NULL: its own). */
+int rtlbfs_batch_set_stream(rtlbfs_batch_t b, void* stream);
+
+/* Active cells summed over slots, and kernel launches' work units. */
+int rtlbfs_batch_info(rtlbfs_batch_t b, long long* active_cells, int* active_slots, int* units);
+
+const char* rtlbfs_batch_last_error(rtlbfs_batch_t b);
+void rtlbfs_batch_destroy(rtlbfs_batch_t b);
+
+/* ------------------------------------------------------------------------ */
+/* Continuous-batching request loop                                          */
+/* ------------------------------------------------------------------------ */
+
+/* One request: a square uniform n x n cavity (L = n, unit cells, dt 0.5,
+ * kappa 1) at Rayleigh number Ra and Prandtl number Pr, arriving t_arrive
+ * seconds after the trace starts. */
+typedef struct {
+    double t_arrive;
+    int n;
+    double Ra, Pr;
+} rtlbfs_request;
+
+/* What became of one request (times in seconds from the trace start; -1:
+ * never happened). */
+typedef struct {
+    double t_admit;   /* admitted to a slot (its work starts on the next launch) */
+    double t_finish;  /* converged, capped or diverged, and retired */
+    long steps;
+    int status;       /* RTLBFS_SLOT_CONVERGED / _MAX_STEPS / _DIVERGED, or -1 not finished */
+    double nu_hot, nu_cold;  /* FP64 wall Nusselt numbers (west, east) at the end */
+} rtlbfs_result;
+
+typedef struct {
+    int max_slots;          /* concurrent cavities */
+    double mem_fraction;    /* admit while batch bytes <= this fraction of free memory at start */
+    double tol;             /* steady tolerance of every request */
+    long max_steps;         /* step cap of every request */
+    double Ma;              /* Mach number (V_c) */
+    double time_limit_s;    /* wall-clock cap of the whole trace */
+    int chunk_steps;        /* batched steps between polls */
+    int precision;          /* RTLBFS_FP32 or RTLBFS_FP64 */
+} rtlbfs_serve_opts;
+
+/*
+ * Replay a request trace in real time: requests are admitted (in arrival
+ * order) once they have arrived, a slot is free and the device memory budget
+ * allows; all admitted cavities advance together in batched launches of
+ * chunk_steps steps; after each chunk finished ones are retired (their
+ * Nusselt numbers taken) and their slots and memory reused.  Stops when all
+ * requests are finished or time_limit_s has passed.  out[nreq] receives the
+ * per-request results; *elapsed_s the wall time.  Returns OK or an error.
+ */
+int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* opts,
+                 rtlbfs_result* out, double* elapsed_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTLBFS_BATCH_H */

@@ -24,6 +24,23 @@ WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC = 0, 1, 2
 NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
 
 HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
+HEADERS = [HEADER, os.path.join(_build.ROOT, "include", "rtlbfs_batch.h")]
+SLOT_EMPTY, SLOT_RUNNING, SLOT_CONVERGED, SLOT_MAX_STEPS, SLOT_DIVERGED = -1, 0, 1, 2, 3
+
+
+class Request(C.Structure):
+    _fields_ = [("t_arrive", C.c_double), ("n", C.c_int), ("Ra", C.c_double), ("Pr", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("t_admit", C.c_double), ("t_finish", C.c_double), ("steps", C.c_long),
+                ("status", C.c_int), ("nu_hot", C.c_double), ("nu_cold", C.c_double)]
+
+
+class ServeOpts(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("mem_fraction", C.c_double), ("tol", C.c_double),
+                ("max_steps", C.c_long), ("Ma", C.c_double), ("time_limit_s", C.c_double),
+                ("chunk_steps", C.c_int), ("precision", C.c_int)]
 
 _lib = None
 
@@ -55,6 +72,28 @@ _SIGS = {
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
     "rtlbfs_launch_count": (C.c_longlong, []),
+    "rtlbfs_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_vp)]),
+    "rtlbfs_batch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "rtlbfs_batch_free_bytes": (C.c_int, [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "rtlbfs_batch_add": (C.c_int, [_vp, C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, C.POINTER(C.c_int)]),
+    "rtlbfs_batch_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]),
+    "rtlbfs_batch_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
+    "rtlbfs_batch_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
+    "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
+    "rtlbfs_batch_step": (C.c_int, [_vp, C.c_long]),
+    "rtlbfs_batch_poll": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_long), _dp]),
+    "rtlbfs_batch_nusselt": (C.c_int, [_vp, C.c_int, C.c_int, _dp]),
+    "rtlbfs_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "rtlbfs_batch_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double)]),
+    "rtlbfs_batch_set_stream": (C.c_int, [_vp, _vp]),
+    "rtlbfs_batch_info": (C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int)]),
+    "rtlbfs_batch_last_error": (C.c_char_p, [_vp]),
+    "rtlbfs_batch_destroy": (None, [_vp]),
+    "rtlbfs_serve": (C.c_int, [C.POINTER(Request), C.c_int, C.POINTER(ServeOpts),
+                               C.POINTER(Result), C.POINTER(C.c_double)]),
     "rtlbfs_nusselt_noalloc": (C.c_int, [C.c_int, C.c_int, _dp, _dp, _vp, _vp, _vp, _vp,
                                          C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.POINTER(C.c_int), _dp, _dp, C.c_int, _vp, _vp]),
@@ -88,11 +127,14 @@ def lib(build_if_needed: bool = True):
     return _lib
 
 
-def header_functions(path: str = HEADER):
-    """Names of the functions declared in the public header."""
-    text = open(path).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rtlbfs_[a-z0-9_]+)\s*\(", text)))
+def header_functions(paths=None):
+    """Names of the functions declared in the public headers."""
+    names = set()
+    for path in (paths or HEADERS):
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(rtlbfs_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def _ptr(a: np.ndarray):
@@ -250,3 +292,122 @@ class Solver:
 
     def sync(self):
         self._check(lib().rtlbfs_sync(self._h), "sync")
+
+
+class Batch:
+    """Many cavities advanced together (a batch of ``include/rtlbfs_batch.h``)."""
+
+    def __init__(self, precision: int = FP32, max_slots: int = 64):
+        h = _vp()
+        rc = lib().rtlbfs_batch_create(int(precision), int(max_slots), C.byref(h))
+        if rc:
+            raise RTLBFSError(rc, "rtlbfs_batch_create")
+        self._h = h
+        self.max_slots = max_slots
+        self.precision = precision
+        self.shapes = {}
+
+    def _check(self, rc, what):
+        if rc:
+            msg = lib().rtlbfs_batch_last_error(self._h)
+            raise RTLBFSError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rtlbfs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, xf, yf, Ra, Pr, Ma, dt) -> int:
+        xf = np.ascontiguousarray(xf, dtype=np.float64)
+        yf = np.ascontiguousarray(yf, dtype=np.float64)
+        s = C.c_int(-1)
+        self._check(lib().rtlbfs_batch_add(self._h, len(xf) - 1, len(yf) - 1, _ptr(xf), _ptr(yf),
+                                           Ra, Pr, Ma, dt, C.byref(s)), "batch_add")
+        self.shapes[s.value] = (len(yf) - 1, len(xf) - 1)
+        return int(s.value)
+
+    def set_bc(self, slot, side, kind, T_wall=0.0, u_wall=0.0):
+        self._check(lib().rtlbfs_batch_set_bc(self._h, slot, side, kind, T_wall, u_wall),
+                    "batch_set_bc")
+
+    def set_state(self, slot, rho, u, v, T):
+        ny, nx = self.shapes[slot]
+        arrs = [_f64(a, nx * ny) for a in (rho, u, v, T)]
+        self._check(lib().rtlbfs_batch_set_state(self._h, slot, *[_ptr(a) for a in arrs]),
+                    "batch_set_state")
+
+    def get_state(self, slot):
+        ny, nx = self.shapes[slot]
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        self._check(lib().rtlbfs_batch_get_state(self._h, slot, *[_ptr(a) for a in out]),
+                    "batch_get_state")
+        return tuple(out)
+
+    def arm(self, slot, tol, max_steps):
+        self._check(lib().rtlbfs_batch_arm(self._h, slot, float(tol), int(max_steps)), "batch_arm")
+
+    def step(self, nsteps):
+        self._check(lib().rtlbfs_batch_step(self._h, int(nsteps)), "batch_step")
+
+    def poll(self):
+        st = (C.c_int * self.max_slots)()
+        steps = (C.c_long * self.max_slots)()
+        res = np.empty(2 * self.max_slots)
+        self._check(lib().rtlbfs_batch_poll(self._h, st, steps, _ptr(res)), "batch_poll")
+        return list(st), list(steps), res.reshape(-1, 2)
+
+    def nusselt(self, slot, which):
+        out = np.empty(1)
+        self._check(lib().rtlbfs_batch_nusselt(self._h, slot, int(which), _ptr(out)),
+                    "batch_nusselt")
+        return float(out[0])
+
+    def remove(self, slot):
+        self._check(lib().rtlbfs_batch_remove(self._h, slot), "batch_remove")
+        self.shapes.pop(slot, None)
+
+    def autotune(self, steps=32):
+        k, r, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        self._check(lib().rtlbfs_batch_autotune(self._h, int(steps), C.byref(k), C.byref(r),
+                                                C.byref(ms)), "batch_autotune")
+        return int(k.value), int(r.value), float(ms.value)
+
+    def set_stream(self, stream):
+        ptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self._check(lib().rtlbfs_batch_set_stream(self._h, ptr), "batch_set_stream")
+
+    def info(self):
+        cells, slots, units = C.c_longlong(0), C.c_int(0), C.c_int(0)
+        self._check(lib().rtlbfs_batch_info(self._h, C.byref(cells), C.byref(slots),
+                                            C.byref(units)), "batch_info")
+        return int(cells.value), int(slots.value), int(units.value)
+
+
+def batch_bytes(precision, nx, ny) -> int:
+    return int(lib().rtlbfs_batch_bytes(int(precision), int(nx), int(ny)))
+
+
+def serve(requests, *, max_slots=64, mem_fraction=0.5, tol=1e-8, max_steps=100000, Ma=0.1,
+          time_limit_s=0.0, chunk_steps=256, precision=FP32):
+    """Replay (t_arrive, n, Ra, Pr) requests through the library's request
+    loop; returns (list of result dicts, elapsed seconds)."""
+    n = len(requests)
+    reqs = (Request * max(n, 1))()
+    for k, (t, nn, Ra, Pr) in enumerate(requests):
+        reqs[k].t_arrive, reqs[k].n, reqs[k].Ra, reqs[k].Pr = float(t), int(nn), float(Ra), float(Pr)
+    out = (Result * max(n, 1))()
+    opts = ServeOpts(int(max_slots), float(mem_fraction), float(tol), int(max_steps), float(Ma),
+                     float(time_limit_s), int(chunk_steps), int(precision))
+    el = C.c_double(0)
+    rc = lib().rtlbfs_serve(reqs, n, C.byref(opts), out, C.byref(el))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs_serve")
+    res = [dict(t_admit=r.t_admit, t_finish=r.t_finish, steps=r.steps, status=r.status,
+                nu_hot=r.nu_hot, nu_cold=r.nu_cold) for r in out[:n]]
+    return res, float(el.value)

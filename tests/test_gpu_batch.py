@@ -1,0 +1,146 @@
+"""Batched cavities and the request loop, through the C ABI, against single
+runs and the FP64 oracle.
+
+* a batch of uneven meshes advances each cavity exactly as the oracle does
+  (FP64 <= 1e-12 per step, FP32 <= 1e-5);
+* each cavity's result is the same alone (batch of one) and in a mix of
+  others, within the same tolerances;
+* per-slot run control: tolerance and step caps stop slots independently,
+  slots are reused after removal;
+* the request loop retires requests with the Nusselt numbers a single run
+  of the same request gives.
+"""
+import numpy as np
+import pytest
+
+from paper_2202_13449_gb300 import capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {capi.FP64: 1e-12, capi.FP32: 1e-5}
+
+
+def rel(a, b, floor):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(float(np.max(np.abs(b))), floor))
+
+
+SPECS = [  # (nx, ny, phi, Ra, seed)
+    (37, 21, 1.5, 1e5, 1),
+    (64, 64, 0.0, 1e3, 2),
+    (29, 45, 2.2, 3e4, 3),
+    (96, 33, 1.0, 1e6, 4),
+]
+
+
+def mesh(orc, nx, ny, phi):
+    return orc.tanh_faces(nx, float(nx), phi), orc.tanh_faces(ny, float(nx) * ny / nx, phi)
+
+
+def add(b, orc, spec, state):
+    nx, ny, phi, Ra, _ = spec
+    xf, yf = mesh(orc, nx, ny, phi)
+    dt = 0.5 * float(min(np.min(np.diff(xf)), np.min(np.diff(yf))))
+    s = b.add(xf, yf, Ra, 0.71, 0.1, dt)
+    b.set_state(s, *state)
+    return s, xf, yf, dt
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_batch_matches_oracle_per_cavity(orc, precision):
+    b = capi.Batch(precision, 8)
+    slots = []
+    for spec in SPECS:
+        st = inputs.perturbed_state(spec[0], spec[1], seed=spec[4])
+        s, xf, yf, dt = add(b, orc, spec, st)
+        b.arm(s, 0.0, 12)
+        slots.append((s, xf, yf, dt, st, spec))
+    b.step(12)
+    status, steps, _ = b.poll()
+    for s, xf, yf, dt, st, spec in slots:
+        assert status[s] == capi.SLOT_MAX_STEPS and steps[s] == 12
+        nu, chi, bg = orc.params_from_ra(spec[3], 0.71, 0.1, float(spec[0]))
+        p = orc.Problem(xf=xf, yf=yf, nu=nu, chi=chi, beta_g=bg, dt=dt)
+        ref, _, rc = orc.step(p, st, 12)
+        got = b.get_state(s)
+        for q, floor in ((1, 1e-2), (2, 1e-2), (3, 1.0)):
+            assert rel(got[q], ref[q], floor) < 10 * TOL[precision], (spec, q)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_same_result_alone_and_in_the_mix(orc, precision):
+    """The first cavity stepped alone and stepped together with three others
+    (which changes the work list and the chunking of the marching kernel)."""
+    spec = SPECS[0]
+    st = inputs.perturbed_state(spec[0], spec[1], seed=11)
+    alone = capi.Batch(precision, 1)
+    s0, *_ = add(alone, orc, spec, st)
+    alone.arm(s0, 0.0, 40)
+    alone.step(40)
+    a = alone.get_state(s0)
+    alone.close()
+    mix = capi.Batch(precision, 8)
+    sm = None
+    for k, sp in enumerate(SPECS):
+        stk = st if k == 0 else inputs.perturbed_state(sp[0], sp[1], seed=20 + k)
+        s, *_ = add(mix, orc, sp, stk)
+        mix.arm(s, 0.0, 40)
+        if k == 0:
+            sm = s
+    mix.step(40)
+    m = mix.get_state(sm)
+    mix.close()
+    for q, floor in ((1, 1e-2), (2, 1e-2), (3, 1.0)):
+        assert rel(m[q], a[q], floor) < TOL[precision], q
+
+
+def test_slots_stop_independently_and_are_reused(orc):
+    b = capi.Batch(capi.FP64, 3)
+    ids = []
+    for k, spec in enumerate(SPECS[:3]):
+        st = inputs.conduction_state(*mesh(orc, spec[0], spec[1], spec[2]))
+        s, *_ = add(b, orc, spec, st)
+        ids.append(s)
+    b.arm(ids[0], 0.0, 5)
+    b.arm(ids[1], 0.0, 50)
+    b.arm(ids[2], 1e-30, 30)
+    b.step(60)
+    status, steps, res = b.poll()
+    assert steps[ids[0]] == 5 and steps[ids[1]] == 50 and steps[ids[2]] == 30
+    assert status[ids[0]] == capi.SLOT_MAX_STEPS
+    b.remove(ids[1])
+    status, _, _ = b.poll()
+    assert status[ids[1]] == capi.SLOT_EMPTY
+    spec = SPECS[3]
+    st = inputs.conduction_state(*mesh(orc, spec[0], spec[1], spec[2]))
+    s, *_ = add(b, orc, spec, st)
+    assert s == ids[1]
+    b.arm(s, 0.0, 7)
+    b.step(7)
+    _, steps, _ = b.poll()
+    assert steps[s] == 7 and steps[ids[0]] == 5
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_request_loop_results_equal_single_runs(orc, precision):
+    reqs = [(0.002 * k, n, Ra, Pr) for k, (n, Ra, Pr) in enumerate(
+        [(16, 1e3, 0.71), (24, 3e3, 7.0), (20, 1e4, 0.71), (16, 2e3, 7.0), (32, 1e3, 0.71),
+         (18, 5e3, 0.71)])]
+    tol, cap = 1e-6, 30000
+    res, el = capi.serve(reqs, max_slots=4, tol=tol, max_steps=cap, chunk_steps=64,
+                         precision=precision, time_limit_s=120.0)
+    for (t, n, Ra, Pr), r in zip(reqs, res):
+        assert r["status"] in (capi.SLOT_CONVERGED, capi.SLOT_MAX_STEPS)
+        assert r["t_admit"] >= t and r["t_finish"] >= r["t_admit"]
+        xf = inputs.uniform_faces(n)
+        s = capi.Solver(xf, xf, precision)
+        s.set_params(Ra, Pr, 0.1, 0.5)
+        rc, steps, _ = s.run_to_steady(tol, cap)
+        assert abs(steps - r["steps"]) <= 1, (steps, r["steps"])
+        tol_nu = 1e-10 if precision == capi.FP64 else 1e-4
+        for which, key in ((capi.NU_WEST, "nu_hot"), (capi.NU_EAST, "nu_cold")):
+            want = s.nusselt(which)
+            if steps == r["steps"]:
+                assert abs(r[key] - want) <= tol_nu * abs(want), (n, Ra, key, r[key], want)
+        s.close()
