@@ -54,6 +54,16 @@ WORKLOADS = {
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
         nx=8192, ny=8192, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=10,
         kind="cavity"),
+    "batch1024": dict(
+        desc="1024 independent cavities, sides from {32,48,64,96,128,192,256}, tanh phi in "
+             "[1.0,2.5], Ra log-uniform in [1e3,1e6], Pr=0.71, Ma=0.1, seed 1234; all advanced "
+             "together, FP32 bulk + FP64 reductions",
+        count=1024, seed=1234, precision="fp32", inner=50, kind="batch"),
+    "serve": dict(
+        desc="request trace: 10,000 square uniform cavities, Poisson arrivals at 200/s, side "
+             "log-uniform 64..1024, Ra log-uniform 1e3..1e8, Pr in {0.71, 7.0}, seed 42; "
+             "continuous batching, FP32 bulk + FP64 reductions",
+        count=10000, seed=42, rate=200.0, precision="fp32", kind="serve"),
     "cavity512_fp64": dict(
         desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
@@ -180,7 +190,157 @@ def setup_solver(capi, inputs, w):
     return s, st, xf, yf
 
 
+def run_batch(args, w):
+    """Config-4 style workload: one bench step = `inner` batched time steps of
+    all cavities (one launch per step, graphs), L2 flushed between steps."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    specs = inputs.batch_specs(w["count"], w["seed"])
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
+    b = capi.Batch(prec, len(specs))
+    # a dedicated stream shared by torch (events, L2 flush) and the library;
+    # the legacy default stream (handle 0) would leave the library on its own
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b.set_stream(stream)
+    cells = 0
+    slots = []
+    for sp in specs:
+        xf = capi.tanh_faces(sp.n, float(sp.n), sp.phi)
+        s = b.add(xf, xf, sp.Ra, sp.Pr, 0.1, 0.0)  # dt from the stability rule
+        slots.append(s)
+        cells += sp.n * sp.n
+    inner = args.inner or w["inner"]
+    total = inner * (args.steps + args.warmup + 64) + 1000
+    for s in slots:
+        b.arm(s, 0.0, total)
+    if args.schedule == "auto":
+        sched = b.autotune(16)
+    else:
+        sched = (0 if args.schedule.startswith("march") else 1, 0, 0.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        b.step(inner)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = capi.launch_count()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(inner)
+        e.record(stream)
+        ev.append((a, e))
+    torch.cuda.synchronize()
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(e) for a, e in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    status, steps, res = b.poll()
+    value = cells * inner * args.steps * ws / (ms * 1e-3) / 1e6
+    rs = 4 if prec == capi.FP32 else 8
+    per_launch = ms * 1e-3 / (inner * args.steps)
+    achieved = 8 * rs * cells / per_launch / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "M cell-updates/s (whole job) and fraction of the HBM roofline",
+        "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == capi.FP32 else "f64", "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cavities": len(specs),
+                   "cells": cells, "time_steps_per_bench_step": inner,
+                   "state_bytes_per_buffer": 4 * rs * cells,
+                   "l2": "inputs larger than L2; also flushed between bench steps",
+                   "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1]},
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": ["rtlbfs::march_kernel", "rtlbfs::step_kernel"][sched[0]]},
+        "clocks": clocks,
+        "all_running": all(st == capi.SLOT_RUNNING for st in status[:len(specs)]),
+    }
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, w):
+    """Config-5 style workload: the request loop on a seeded trace, plus the
+    plain per-request FP64 comparator on a sample of the same requests."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    trace = inputs.serving_trace(w["count"], w["seed"], w["rate"])
+    reqs = [(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace]
+    cap, tol = args.max_steps, args.tol
+    res, el = capi.serve(reqs, max_slots=args.slots, tol=tol, max_steps=cap, chunk_steps=128,
+                         precision=capi.FP32, time_limit_s=args.time_limit, mem_fraction=0.5)
+    done = [(q, r) for q, r in zip(reqs, res) if r["status"] >= 0]
+    diverged = sum(1 for _, r in done if r["status"] == capi.SLOT_DIVERGED)
+    lat = np.array([r["t_finish"] - q[0] for q, r in done]) if done else np.array([np.nan])
+    conv = sum(1 for _, r in done if r["status"] == capi.SLOT_CONVERGED)
+    capped = sum(1 for _, r in done if r["status"] == capi.SLOT_MAX_STEPS)
+    # plain per-request FP64 on the first finished requests, alone, one at a time
+    sample = done[:args.fp64_sample]
+    t0 = time.perf_counter()
+    errs = []
+    for q, r in sample:
+        xf = inputs.uniform_faces(q[1])
+        s = capi.Solver(xf, xf, capi.FP64)
+        s.set_params(q[2], q[3], 0.1, 0.0)
+        s.run_to_steady(tol, cap)
+        nu64 = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+        nu32 = 0.5 * (r["nu_hot"] + r["nu_cold"])
+        errs.append(abs(nu32 - nu64) / abs(nu64))
+        s.close()
+    t64 = time.perf_counter() - t0
+    line = {
+        "metric": "batched solves/s and p50/p99 time-to-steady (request loop)",
+        "value": round(len(done) / el, 3) if el > 0 else None, "unit": "solves/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(el * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "requests": len(reqs),
+                   "max_steps_cap": cap, "tol": tol, "time_limit_s": args.time_limit,
+                   "slots": args.slots},
+        "finished": len(done), "converged": conv, "hit_step_cap": capped, "diverged": diverged,
+        "unfinished": len(reqs) - len(done),
+        "time_to_steady_s": {"p50": float(np.nanpercentile(lat, 50)),
+                             "p99": float(np.nanpercentile(lat, 99)),
+                             "note": "arrival to retirement; queue-dominated at this load"},
+        "fp64_per_request": {"requests": len(sample), "solves_per_s": round(len(sample) / t64, 3)
+                             if t64 > 0 else None,
+                             "max_rel_err_mean_wall_nu_fp32_vs_fp64": max(errs) if errs else None},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "batch":
+        return run_batch(args, w)
+    if w.get("kind") == "serve":
+        return run_serve(args, w)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -192,7 +352,10 @@ def run_ours(args, w):
     cells = w["nx"] * w["ny"]
     inner = args.inner or w["inner"]
     s, st0, xf, yf = setup_solver(capi, inputs, w)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream shared by torch (events, L2 flush) and the library;
+    # the legacy default stream (handle 0) would leave the library on its own
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     s.set_stream(stream)
     # pick the schedule on a snapshot of the state (restored afterwards),
     # or take the one given on the command line
@@ -399,6 +562,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--max-steps", type=int, default=2000, help="serve: step cap per request")
+    ap.add_argument("--tol", type=float, default=1e-8, help="serve: steady tolerance")
+    ap.add_argument("--time-limit", type=float, default=60.0, help="serve: wall-clock cap (s)")
+    ap.add_argument("--slots", type=int, default=256, help="serve: concurrent cavities")
+    ap.add_argument("--fp64-sample", type=int, default=20, help="serve: FP64 comparator sample")
     ap.add_argument("--schedule", default="auto",
                     help="auto (autotuner), tile, or march[:rows per unit]")
     args = ap.parse_args()

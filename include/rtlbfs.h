@@ -92,8 +92,11 @@ int rtlbfs_create_mesh(int nx, int ny, const double* xf, const double* yf, int p
 /*
  * Physical parameters (Eq. 63 with V_c = Ma, c = 1): nu = V_c L sqrt(Pr/Ra),
  * chi = nu / Pr, beta_g = V_c^2 / (dT L) with L = xf[nx] - xf[0] and
- * dT = 1; dt is the macroscopic time step Delta t of Eqs. 41-43 / 57-59.
- * ERR_ARG unless all are positive.
+ * dT = 1; dt is the macroscopic time step Delta t of Eqs. 41-43 / 57-59;
+ * dt = 0 selects the explicit-stability rule
+ * dt = min(0.5 w_min, 0.2 w_min^2 / max(nu, chi)) with w_min the smallest
+ * cell width (about half the largest stable step, acoustic and diffusive).
+ * ERR_ARG unless Ra, Pr, Ma > 0 and dt >= 0.
  */
 int rtlbfs_set_params(rtlbfs_t h, double Ra, double Pr, double Ma, double dt);
 
@@ -197,7 +200,9 @@ int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
 int rtlbfs_autotune(rtlbfs_t h, int steps, int* kernel, int* chunk_rows, double* ms_per_step);
 
 /* Use this CUDA stream (a cudaStream_t, e.g. torch's current stream) for
- * all later work of the handle; NULL restores the handle's own stream. */
+ * all later work of the handle; NULL restores the handle's own non-blocking
+ * stream (pass cudaStreamLegacy to order work with the legacy default
+ * stream). */
 int rtlbfs_set_stream(rtlbfs_t h, void* stream);
 
 /* Wait for the handle's stream. */

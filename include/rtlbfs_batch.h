@@ -46,7 +46,8 @@ int rtlbfs_batch_free_bytes(size_t* free_bytes, size_t* total_bytes);
 
 /*
  * Add a cavity with faces xf[0..nx], yf[0..ny] (copied) and parameters as
- * rtlbfs_set_params (Eq. 63 with V_c = Ma, L = domain width): the defaults
+ * rtlbfs_set_params (Eq. 63 with V_c = Ma, L = domain width; dt = 0: the
+ * stability rule of rtlbfs_set_params): the defaults
  * of rtlbfs_create_mesh (differentially heated cavity, conduction initial
  * state).  *slot receives its slot id.  The slot is idle until armed.
  * ERR_STATE when no slot is free, ERR_OOM when device memory is short.
@@ -99,8 +100,8 @@ void rtlbfs_batch_destroy(rtlbfs_batch_t b);
 /* Continuous-batching request loop                                          */
 /* ------------------------------------------------------------------------ */
 
-/* One request: a square uniform n x n cavity (L = n, unit cells, dt 0.5,
- * kappa 1) at Rayleigh number Ra and Prandtl number Pr, arriving t_arrive
+/* One request: a square uniform n x n cavity (L = n, unit cells, dt from
+ * the stability rule of rtlbfs_set_params, kappa 1) at Rayleigh number Ra and Prandtl number Pr, arriving t_arrive
  * seconds after the trace starts. */
 typedef struct {
     double t_arrive;

@@ -86,8 +86,8 @@ int rtlbfs_batch_add(rtlbfs_batch_t b, int nx, int ny, const double* xf, const d
                      double Ra, double Pr, double Ma, double dt, int* slot)
 {
     if (!b || !slot) return RTLBFS_ERR_ARG;
-    if (!(Ra > 0 && Pr > 0 && Ma > 0 && dt > 0)) {
-        b->err = "Ra, Pr, Ma, dt must be > 0";
+    if (!(Ra > 0 && Pr > 0 && Ma > 0) || !(dt >= 0)) {
+        b->err = "Ra, Pr, Ma must be > 0, dt >= 0";
         return RTLBFS_ERR_ARG;
     }
     int s = -1;
@@ -98,7 +98,8 @@ int rtlbfs_batch_add(rtlbfs_batch_t b, int nx, int ny, const double* xf, const d
     c->Ra = Ra;
     c->Pr = Pr;
     c->Ma = Ma;
-    c->dt = dt;
+    c->dt_auto = !(dt > 0);
+    if (dt > 0) c->dt = dt;
     b->eng->touch(s);
     rc = b->eng->set_conduction_state(s);
     if (rc) {
@@ -267,7 +268,7 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
             c->Ra = q.Ra;
             c->Pr = q.Pr;
             c->Ma = opts->Ma;
-            c->dt = 0.5;
+            c->dt_auto = true;
             eng.touch(s);
             if ((rc = eng.set_conduction_state(s))) return rc;
             if ((rc = eng.arm(s, opts->max_steps, opts->tol > 0 ? opts->tol : -1.0))) return rc;

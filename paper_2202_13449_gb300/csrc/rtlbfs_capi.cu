@@ -92,12 +92,13 @@ int rtlbfs_set_params(rtlbfs_t h, double Ra, double Pr, double Ma, double dt)
 {
     Cavity* c = cav(h);
     if (!c) return RTLBFS_ERR_ARG;
-    if (!(Ra > 0 && Pr > 0 && Ma > 0 && dt > 0)) return argfail(h, "Ra, Pr, Ma, dt must be > 0");
+    if (!(Ra > 0 && Pr > 0 && Ma > 0) || !(dt >= 0)) return argfail(h, "Ra, Pr, Ma must be > 0, dt >= 0");
     c->from_ra = true;
     c->Ra = Ra;
     c->Pr = Pr;
     c->Ma = Ma;
-    c->dt = dt;
+    c->dt_auto = !(dt > 0);
+    if (dt > 0) c->dt = dt;
     h->eng->touch(h->slot);
     return RTLBFS_OK;
 }
@@ -107,13 +108,14 @@ int rtlbfs_set_params_ref(rtlbfs_t h, double Ra, double Pr, double Ma, double dt
 {
     Cavity* c = cav(h);
     if (!c) return RTLBFS_ERR_ARG;
-    if (!(Ra > 0 && Pr > 0 && Ma > 0 && dt > 0 && L > 0 && dT > 0))
-        return argfail(h, "Ra, Pr, Ma, dt, L, dT must be > 0");
+    if (!(Ra > 0 && Pr > 0 && Ma > 0 && L > 0 && dT > 0) || !(dt >= 0))
+        return argfail(h, "Ra, Pr, Ma, L, dT must be > 0, dt >= 0");
     c->from_ra = true;
     c->Ra = Ra;
     c->Pr = Pr;
     c->Ma = Ma;
-    c->dt = dt;
+    c->dt_auto = !(dt > 0);
+    if (dt > 0) c->dt = dt;
     c->Lref = L;
     c->dT = dT;
     c->T_ref = T_ref;

@@ -265,6 +265,15 @@ int Engine::resolve_params(Cavity& c)
         c.beta_g = Vc * Vc / (c.dT * L);
     }
     if (!(c.nu > 0 && c.chi > 0)) return fail(RTLBFS_ERR_ARG, "nu and chi must be positive");
+    if (c.dt_auto) {
+        // explicit step limits: acoustic dt <= 0.5 w_min (c = 1), diffusive
+        // dt <= 0.2 w_min^2 / max(nu, chi) -- about half the largest stable
+        // step of the scheme measured on uniform meshes
+        double wmin = 1e300;
+        for (int i = 0; i < c.nx; ++i) wmin = std::min(wmin, c.xf[i + 1] - c.xf[i]);
+        for (int j = 0; j < c.ny; ++j) wmin = std::min(wmin, c.yf[j + 1] - c.yf[j]);
+        c.dt = std::min(0.5 * wmin, 0.2 * wmin * wmin / std::max(c.nu, c.chi));
+    }
     if (!(c.dt > 0) || !(c.kappa > 0)) return fail(RTLBFS_ERR_ARG, "dt and kappa must be positive");
     const bool xp = c.kind[kSideW] == kPeriodic, xp2 = c.kind[kSideE] == kPeriodic;
     const bool yp = c.kind[kSideS] == kPeriodic, yp2 = c.kind[kSideN] == kPeriodic;

@@ -23,6 +23,7 @@ struct Cavity {
     // parameters
     bool from_ra = true;
     double Ra = 1e3, Pr = 0.71, Ma = 0.1, dt = 0.5, kappa = 1.0;
+    bool dt_auto = false;  // dt from the stability rule of resolve_params
     double Lref = 0.0, dT = 1.0, T_ref = 0.5;
     double nu = 0.0, chi = 0.0, beta_g = 0.0, fx = 0.0, fy = 0.0;
     int kind[4] = {kDirichlet, kDirichlet, kAdiabatic, kAdiabatic};

@@ -135,7 +135,7 @@ def test_request_loop_results_equal_single_runs(orc, precision):
         assert r["t_admit"] >= t and r["t_finish"] >= r["t_admit"]
         xf = inputs.uniform_faces(n)
         s = capi.Solver(xf, xf, precision)
-        s.set_params(Ra, Pr, 0.1, 0.5)
+        s.set_params(Ra, Pr, 0.1, 0.0)
         rc, steps, _ = s.run_to_steady(tol, cap)
         assert abs(steps - r["steps"]) <= 1, (steps, r["steps"])
         tol_nu = 1e-10 if precision == capi.FP64 else 1e-4
@@ -144,3 +144,19 @@ def test_request_loop_results_equal_single_runs(orc, precision):
             if steps == r["steps"]:
                 assert abs(r[key] - want) <= tol_nu * abs(want), (n, Ra, key, r[key], want)
         s.close()
+
+
+def test_batch_workload_stays_stable_with_the_automatic_step():
+    """The seeded batch workload (sides 32..256, tanh phi 1..2.5, Ra 1e3..1e6)
+    with dt = 0 (the stability rule): no cavity diverges in 300 steps."""
+    specs = inputs.batch_specs(96, 1234)
+    b = capi.Batch(capi.FP32, len(specs))
+    for sp in specs:
+        xf = capi.tanh_faces(sp.n, float(sp.n), sp.phi)
+        s = b.add(xf, xf, sp.Ra, sp.Pr, 0.1, 0.0)
+        b.arm(s, 0.0, 300)
+    b.step(300)
+    status, steps, _ = b.poll()
+    assert all(st == capi.SLOT_MAX_STEPS for st in status[:len(specs)]), status
+    assert all(k == 300 for k in steps[:len(specs)])
+    b.close()
