@@ -252,7 +252,6 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
         const double t = now();
         if (opts->time_limit_s > 0 && t > opts->time_limit_s) break;
         // admit arrived requests in order while a slot and memory are free
-        bool admitted = false;
         while (next < nreq && reqs[next].t_arrive <= t && active < opts->max_slots) {
             const rtlbfs_request& q = reqs[next];
             const size_t need = Engine::bytes_for(opts->precision, q.n, q.n);
@@ -278,9 +277,7 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
             out[next].t_admit = now();
             ++active;
             ++next;
-            admitted = true;
         }
-        (void)admitted;
         if (active == 0) {
             if (next >= nreq) break;
             const double wait = reqs[next].t_arrive - now();

@@ -64,7 +64,10 @@ struct CavityDesc {
     // wall mirror constants in the fixed-point storage: 2 u_wall and 2 T_wall
     // (wrap-around 32-bit values, see StoreQ::twice)
     int q_u2[4], q_T2[4];
-    void* f[2][4];                // two buffers of (drho, u, v, T)
+    // two state buffers; each is an array of ny*pitch cell records
+    // (rho - 1, u, v, T) -- Vec4<S>, 16 bytes in FP32 mode, 32 in FP64 --
+    // in f[b][0] (f[b][1..3] used only by callers' separate-array layouts)
+    void* f[2][4];
     const void* xline;            // FaceLine<R>[nx+1]
     const void* yline;            // FaceLine<R>[ny+1]
     const void* xcell;            // CellLine<R>[nx+4], index i+2 for cell i in [-2, nx+1]
@@ -84,8 +87,10 @@ struct CavityCtl {
     double acc[4];            // running sums of this step: sum (d|u|)^2, |u|^2, (dT)^2, T^2
 };
 
+// Four values of one cell; 16-byte aligned for 4-byte R, 32 for double, so
+// a cell record moves in one (or two) vector memory instructions.
 template <typename R>
-struct Vec4 {
+struct alignas(4 * sizeof(R)) Vec4 {
     R x, y, z, w;
 };
 
@@ -310,6 +315,15 @@ struct StoreD {
     static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->bcU[s]; }
     static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return 2.0 * d->bcU[s]; }
     static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return 2.0 * d->bcT[s]; }
+    // cell records of buffer b
+    static __device__ __forceinline__ Vec4<S> load4(const CavityDesc* d, int b, size_t o)
+    {
+        return static_cast<const Vec4<S>*>(d->f[b][0])[o];
+    }
+    static __device__ __forceinline__ void store4(const CavityDesc* d, int b, size_t o, Vec4<S> v)
+    {
+        static_cast<Vec4<S>*>(d->f[b][0])[o] = v;
+    }
 };
 
 struct StoreQ {
@@ -370,6 +384,14 @@ struct StoreQ {
     static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->f_bcU[s]; }
     static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return d->q_u2[s]; }
     static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return d->q_T2[s]; }
+    static __device__ __forceinline__ Vec4<S> load4(const CavityDesc* d, int b, size_t o)
+    {
+        return static_cast<const Vec4<S>*>(d->f[b][0])[o];
+    }
+    static __device__ __forceinline__ void store4(const CavityDesc* d, int b, size_t o, Vec4<S> v)
+    {
+        static_cast<Vec4<S>*>(d->f[b][0])[o] = v;
+    }
 };
 
 }  // namespace rtlbfs

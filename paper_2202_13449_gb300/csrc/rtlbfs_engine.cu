@@ -352,10 +352,11 @@ int Engine::upload_lines(int slot)
         d.q_u2[s2] = StoreQ::from_double(2.0 * c.bcU[s2], 1);
         d.q_T2[s2] = StoreQ::twice(StoreQ::from_double(c.bcT[s2], 3));
     }
-    const size_t plane = rsize_ * (size_t)c.pitch * c.ny;
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 4; ++k)
-            d.f[b][k] = static_cast<unsigned char*>(c.d_fields) + (size_t)(4 * b + k) * plane;
+    const size_t rec = 4 * rsize_ * (size_t)c.pitch * c.ny;  // cell records of one buffer
+    for (int b = 0; b < 2; ++b) {
+        d.f[b][0] = static_cast<unsigned char*>(c.d_fields) + (size_t)b * rec;
+        d.f[b][1] = d.f[b][2] = d.f[b][3] = nullptr;
+    }
     unsigned char* L = static_cast<unsigned char*>(c.d_lines);
     d.xline = L + c.off_xl;
     d.yline = L + c.off_yl;
@@ -513,7 +514,7 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     const CavityDesc& d = h_desc_[slot];
     int* d_bad = reinterpret_cast<int*>(d_scalar_ + 7);
     CK(cudaMemsetAsync(d_bad, 0, sizeof(int), stream_));
-    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0], d_bad));
+    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0][0], d_bad));
     g_launches++;
     int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
@@ -553,7 +554,8 @@ int Engine::get_state(int slot, double* rho, double* u, double* v, double* T)
         stage_cap_ = 4 * n;
     }
     const CavityDesc& d = h_desc_[slot];
-    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[ctl.cur & 1]));
+    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch,
+                        d.f[ctl.cur & 1][0]));
     g_launches++;
     double* dst[4] = {rho, u, v, T};
     for (int k = 0; k < 4; ++k)

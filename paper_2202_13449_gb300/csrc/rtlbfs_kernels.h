@@ -62,9 +62,9 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
                            long long count, double scale, double* partial, int max_blocks,
                            double* out);
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* const* f, int* bad);
+                            int pitch, void* cells, int* bad);
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny,
-                             int pitch, void* const* f);
+                             int pitch, const void* cells);
 cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
                        int reset_counter);
 

@@ -150,10 +150,8 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         const int cur = ctl->cur;
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
-        // the four fields of a buffer are consecutive planes of ny*pitch
-        const size_t plane = (size_t)ny * pitch;
-        const S* __restrict__ fin = static_cast<const S*>(dp->f[cur][0]);
-        S* __restrict__ fout = static_cast<S*>(dp->f[cur ^ 1][0]);
+        const Vec4<S>* __restrict__ fin = static_cast<const Vec4<S>*>(dp->f[cur][0]);
+        Vec4<S>* __restrict__ fout = static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]);
         const CellLine<R>* xc = static_cast<const CellLine<R>*>(dp->xcell);
         const CellLine<R>* yc = static_cast<const CellLine<R>*>(dp->ycell);
         const FaceLine<R>* xl = static_cast<const FaceLine<R>*>(dp->xline);
@@ -171,7 +169,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         const bool xghosts = !xper && (c0 == 0 || c0 + 29 >= nx);  // warp-uniform
 
         // temperature reference of this unit
-        const S qTz = fin[3 * plane + (size_t)min(j0, ny - 1) * pitch + min(c0 + 14, nx - 1)];
+        const S qTz = fin[(size_t)min(j0, ny - 1) * pitch + min(c0 + 14, nx - 1)].w;
         const R Tz = P::val(qTz, 3);
 
         // raw row r of this lane's column (ghost rule applied later in conv)
@@ -179,10 +177,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             int rs, yms;
             const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms);
             q = {S(0), S(0), S(0), S(0)};
-            if (colok && rowok && !(xms >= 0 && yms >= 0)) {
-                const S* p = fin + (size_t)rs * pitch + gs;
-                q = {p[0], p[plane], p[2 * plane], p[3 * plane]};
-            }
+            if (colok && rowok && !(xms >= 0 && yms >= 0)) q = fin[(size_t)rs * pitch + gs];
         };
         auto conv = [&](int r, Vec4<S> q) -> Vec4<R> {
             int rs, yms;
@@ -341,10 +336,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             v2 = conv(j + 2, qpre);
             fetch(j + 3, qpre);  // in flight during this row's work
             Vec4<S> qo = {S(0), S(0), S(0), S(0)};
-            if (upd_lane) {  // raw state of the updated cell (an L1 hit)
-                const S* p = fin + (size_t)j * pitch + g;
-                qo = {p[0], p[plane], p[2 * plane], p[3 * plane]};
-            }
+            if (upd_lane) qo = fin[(size_t)j * pitch + g];  // raw state of the updated cell (L1)
             // gradients of row j+1 (a north ghost row mirrors row j)
             grad(j + 1, v0, v1, v2, gx1, gy1);
             if (!yper && j + 1 == ny) {
@@ -383,11 +375,8 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 const R dv = (v * div0 - div2 + dtc * src_y) * inv;
                 const R dT = (T * div0 - div3) * inv;
                 const R dr1 = dr - div0, u1 = u + du, v1n = v + dv, T1 = T + dT;
-                S* o = fout + (size_t)j * pitch + g;
-                o[0] = P::add(qo.x, -div0, 0);
-                o[plane] = P::add(qo.y, du, 1);
-                o[2 * plane] = P::add(qo.z, dv, 2);
-                o[3 * plane] = P::add(qo.w, dT, 3);
+                fout[(size_t)j * pitch + g] = {P::add(qo.x, -div0, 0), P::add(qo.y, du, 1),
+                                               P::add(qo.z, dv, 2), P::add(qo.w, dT, 3)};
                 bad = bad || !(P::in_range(dr1, 0) && P::in_range(u1, 1) && P::in_range(v1n, 2) &&
                                P::in_range(T1, 3));
                 const R m0 = P::fsqrt(u * u + v * v), m1 = P::fsqrt(u1 * u1 + v1n * v1n);

@@ -230,7 +230,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     using S = typename P::S;
     using R = typename P::R;
     constexpr int BX = Sm::BX, BY = Sm::BY, GX = Sm::GX, GY = Sm::GY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
     const int ntiles = *ntiles_ptr;
@@ -244,13 +244,15 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         const int cur = ctl->cur;
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
-        const S* fin[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) fin[k] = static_cast<const S*>(dp->f[cur][k]);
+        const Vec4<S>* __restrict__ fin = static_cast<const Vec4<S>*>(dp->f[cur][0]);
         // temperature reference of this tile: its (clamped) centre cell
         const int ic = min(i0 + TX / 2, nx - 1), jc = min(j0 + TY / 2, ny - 1);
-        const S qTz = fin[3][(size_t)jc * pitch + ic];
+        const S qTz = fin[(size_t)jc * pitch + ic].w;
         const R Tz = P::val(qTz, 3);
+
+        // A tile whose halo lies inside the mesh touches no boundary: no
+        // ghost resolution, no mirror rules, no wall faces (block-uniform).
+        const bool interior = i0 >= 2 && j0 >= 2 && i0 + TX + 2 <= nx && j0 + TY + 2 <= ny;
 
         // ---- 1. lines and the haloed tile -------------------------------
         {
@@ -269,20 +271,27 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             Vec4<S> v[NR];
             int ms[NR];
             bool ok[NR];
+            if (interior) {
+                const Vec4<S>* base = fin + (size_t)(j0 - 2) * pitch + (i0 - 2);
 #pragma unroll
-            for (int q = 0; q < NR; ++q) {  // issue every load first
-                const int k = tid + q * kStepThreads;
-                const int c = k % BX, r = k / BX;
-                int si = 0, sj = 0;
-                ms[q] = -1;
-                ok[q] = k < NB && resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms[q]);
-                v[q] = {S(0), S(0), S(0), S(0)};
-                if (ok[q]) {
-                    const size_t o = (size_t)sj * pitch + si;
-                    v[q].x = fin[0][o];
-                    v[q].y = fin[1][o];
-                    v[q].z = fin[2][o];
-                    v[q].w = fin[3][o];
+                for (int q = 0; q < NR; ++q) {  // issue every load first
+                    const int k = tid + q * kStepThreads;
+                    ms[q] = -1;
+                    ok[q] = k < NB;
+                    v[q] = {S(0), S(0), S(0), S(0)};
+                    if (ok[q]) v[q] = base[(size_t)(k / BX) * pitch + (k % BX)];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const int k = tid + q * kStepThreads;
+                    const int c = k % BX, r = k / BX;
+                    int si = 0, sj = 0;
+                    ms[q] = -1;
+                    ok[q] = k < NB &&
+                            resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms[q]);
+                    v[q] = {S(0), S(0), S(0), S(0)};
+                    if (ok[q]) v[q] = fin[(size_t)sj * pitch + si];
                 }
             }
 #pragma unroll
@@ -302,9 +311,10 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         for (int k = tid; k < GX * GY; k += kStepThreads) {
             const int gc = k % GX, gr = k / GX;
             int c = gc + 1, r = gr + 1;  // box position
-            int si, sj, ms;
+            int si, sj, ms = -1;
             Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
-            if (resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+            if (interior ||
+                resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
                 // a wall ghost takes its partner's gradient, mirrored
                 if (ms == kSideW) c += 1;
                 else if (ms == kSideE) c -= 1;
@@ -333,7 +343,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 fr = (k - NXF) / TX;
             }
             const int gi = i0 + fc, gj = j0 + fr;
-            const bool valid = isx ? (gi <= nx && gj < ny) : (gi < nx && gj <= ny);
+            const bool valid = interior || (isx ? (gi <= nx && gj < ny) : (gi < nx && gj <= ny));
             Vec4<R> out = {R(0), R(0), R(0), R(0)};
             if (valid) {
                 const int lc = isx ? fc + 1 : fc + 2, lr = isx ? fr + 2 : fr + 1;
@@ -345,8 +355,10 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                               L, Rr, Tbar);
                 const FaceLine<R> fl = isx ? sm.xl[fc] : sm.yl[fr];
                 int wside = -1;
-                if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
-                if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
+                if (!interior) {
+                    if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
+                    if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
+                }
                 const R uw = wside >= 0 ? P::bcU(dp, wside) : R(0);
                 R F[4];
                 face_flux<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
@@ -361,9 +373,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         // ---- 4. update (increment form), 5. residual sums ---------------
         R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
         {
-            S* fout[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) fout[k] = static_cast<S*>(dp->f[cur ^ 1][k]);
+            Vec4<S>* __restrict__ fout = static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]);
             const R one = rconst<R>(1.0);
             const R dt = P::dt(dp), bg = P::beta_g(dp), Tr = P::T_ref(dp);
             const R fxb = P::fx(dp), fyb = P::fy(dp);
@@ -373,7 +383,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 const int gi = i0 + tc, gj = j0 + tr;
                 if (gi >= nx || gj >= ny) continue;
                 const size_t o = (size_t)gj * pitch + gi;
-                const Vec4<S> q = {fin[0][o], fin[1][o], fin[2][o], fin[3][o]};
+                const Vec4<S> q = fin[o];
                 const Vec4<R> p = sm.val[tr + 2][tc + 2];
                 const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
                 const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
@@ -394,10 +404,8 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 const R dv = (v * div0 - div2 + dt * src_y) * inv;
                 const R dT = (T * div0 - div3) * inv;
                 const R dr1 = dr - div0, u1 = u + du, v1 = v + dv, T1 = T + dT;
-                fout[0][o] = P::add(q.x, -div0, 0);
-                fout[1][o] = P::add(q.y, du, 1);
-                fout[2][o] = P::add(q.z, dv, 2);
-                fout[3][o] = P::add(q.w, dT, 3);
+                fout[o] = {P::add(q.x, -div0, 0), P::add(q.y, du, 1), P::add(q.z, dv, 2),
+                           P::add(q.w, dT, 3)};
                 bad = bad || !(P::in_range(dr1, 0) && P::in_range(u1, 1) && P::in_range(v1, 2) &&
                                P::in_range(T1, 3));
                 // |u|^{n+1} - |u|^n without cancellation
@@ -460,13 +468,12 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
 // FP64 evaluation straight from global memory (Nusselt reductions).
 // ---------------------------------------------------------------------------
 template <class P>
-__device__ bool load_cell_d(const CavityDesc& d, const typename P::S* const* f, int gi, int gj,
-                            Vec4<double>& v)
+__device__ bool load_cell_d(const CavityDesc& d, int b, int gi, int gj, Vec4<double>& v)
 {
     int si, sj, ms;
     if (!resolve_cell(d, gi, gj, si, sj, ms)) return false;
     const size_t o = (size_t)sj * d.pitch + si;
-    Vec4<typename P::S> x = {f[0][o], f[1][o], f[2][o], f[3][o]};
+    Vec4<typename P::S> x = P::load4(&d, b, o);
     if (ms >= 0) x = mirror_state<P>(d, ms, x);
     v = {P::to_double(x.x, 0), P::to_double(x.y, 1), P::to_double(x.z, 2), P::to_double(x.w, 3)};
     return true;
@@ -475,9 +482,9 @@ __device__ bool load_cell_d(const CavityDesc& d, const typename P::S* const* f, 
 // Green-Gauss gradient (Eqs. 55-56) of cell (gi, gj) in FP64; a wall ghost
 // mirrors its partner's.  xc/yc: FP64 cell lines (index i + 2).
 template <class P>
-__device__ void grad_d(const CavityDesc& d, const typename P::S* const* f,
-                       const CellLine<double>* xc, const CellLine<double>* yc, int gi, int gj,
-                       Vec4<double>& gx, Vec4<double>& gy)
+__device__ void grad_d(const CavityDesc& d, int f, const CellLine<double>* xc,
+                       const CellLine<double>* yc, int gi, int gj, Vec4<double>& gx,
+                       Vec4<double>& gy)
 {
     int si, sj, ms;
     gx = {0, 0, 0, 0};
@@ -502,8 +509,8 @@ __device__ void grad_d(const CavityDesc& d, const typename P::S* const* f,
 // Energy flux (Eq. 59 brace) through x-face (i, j) (nd = 0) or y-face
 // (nd = 1), in FP64.
 template <class P>
-__device__ double energy_flux_d(const CavityDesc& d, const typename P::S* const* f,
-                                const NuLines& ln, int nd, int i, int j)
+__device__ double energy_flux_d(const CavityDesc& d, int f, const NuLines& ln, int nd, int i,
+                                int j)
 {
     const bool xper = d.kind[kSideW] == kPeriodic, yper = d.kind[kSideS] == kPeriodic;
     const int li = nd == 0 ? i - 1 : i, lj = nd == 0 ? j : j - 1;
@@ -530,11 +537,8 @@ __global__ void __launch_bounds__(256)
 nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityCtl* __restrict__ ctls,
                        int slot, NuLines ln, int which, double* __restrict__ partial)
 {
-    using S = typename P::S;
     const CavityDesc& d = descs[slot];
-    const int cur = ctls[slot].cur;
-    const S* f[4] = {static_cast<const S*>(d.f[cur][0]), static_cast<const S*>(d.f[cur][1]),
-                     static_cast<const S*>(d.f[cur][2]), static_cast<const S*>(d.f[cur][3])};
+    const int f = ctls[slot].cur;  // buffer holding the current state
     long long count;
     if (which == kNuWest || which == kNuEast || which == kNuHalf) count = d.ny;
     else if (which == kNuSouth || which == kNuNorth) count = d.nx;
@@ -587,39 +591,34 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 // cells, row-major nx) <-> device storage (rho - 1, u, v, T with row pitch).
 template <class P>
 __global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, int pitch,
-                                typename P::S* f0, typename P::S* f1, typename P::S* f2,
-                                typename P::S* f3, int* __restrict__ bad)
+                                Vec4<typename P::S>* __restrict__ cells, int* __restrict__ bad)
 {
     const long long n = (long long)nx * ny;
     bool b = false;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
-        const size_t o = (size_t)j * pitch + i;
         const double x[4] = {st[k] - 1.0, st[n + k], st[2 * n + k], st[3 * n + k]};
         for (int q = 0; q < 4; ++q) b = b || !P::representable(x[q], q);
-        f0[o] = P::from_double(x[0], 0);
-        f1[o] = P::from_double(x[1], 1);
-        f2[o] = P::from_double(x[2], 2);
-        f3[o] = P::from_double(x[3], 3);
+        cells[(size_t)j * pitch + i] = {P::from_double(x[0], 0), P::from_double(x[1], 1),
+                                        P::from_double(x[2], 2), P::from_double(x[3], 3)};
     }
     if (b) atomicOr(bad, 1);
 }
 
 template <class P>
 __global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pitch,
-                                 const typename P::S* f0, const typename P::S* f1,
-                                 const typename P::S* f2, const typename P::S* f3)
+                                 const Vec4<typename P::S>* __restrict__ cells)
 {
     const long long n = (long long)nx * ny;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
-        const size_t o = (size_t)j * pitch + i;
-        st[k] = 1.0 + P::to_double(f0[o], 0);
-        st[n + k] = P::to_double(f1[o], 1);
-        st[2 * n + k] = P::to_double(f2[o], 2);
-        st[3 * n + k] = P::to_double(f3[o], 3);
+        const Vec4<typename P::S> c = cells[(size_t)j * pitch + i];
+        st[k] = 1.0 + P::to_double(c.x, 0);
+        st[n + k] = P::to_double(c.y, 1);
+        st[2 * n + k] = P::to_double(c.z, 2);
+        st[3 * n + k] = P::to_double(c.w, 3);
     }
 }
 
@@ -712,35 +711,32 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
 }
 
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* const* f, int* bad)
+                            int pitch, void* cells, int* bad)
 {
     const long long n = (long long)nx * ny;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (double*)f[0],
-                                                       (double*)f[1], (double*)f[2], (double*)f[3],
-                                                       bad);
+        state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+                                                       static_cast<Vec4<double>*>(cells), bad);
     else
-        state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (int*)f[0], (int*)f[1],
-                                                       (int*)f[2], (int*)f[3], bad);
+        state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+                                                       static_cast<Vec4<int>*>(cells), bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny, int pitch,
-                             void* const* f)
+                             const void* cells)
 {
     const long long n = (long long)nx * ny;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_out_kernel<StoreD><<<blocks, 256, 0, s>>>(
-            st, nx, ny, pitch, (const double*)f[0], (const double*)f[1], (const double*)f[2],
-            (const double*)f[3]);
+        state_out_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+                                                        static_cast<const Vec4<double>*>(cells));
     else
-        state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, (const int*)f[0],
-                                                        (const int*)f[1], (const int*)f[2],
-                                                        (const int*)f[3]);
+        state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+                                                        static_cast<const Vec4<int>*>(cells));
     return cudaGetLastError();
 }
 
@@ -788,11 +784,16 @@ constexpr size_t kNoAllocBytes = sizeof(NoAllocScratch);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// The caller's rho (not rho - 1) in the first field.
+// The caller's four separate FP64 arrays, rho (not rho - 1) in the first.
 struct StoreRho : StoreD {
     static __host__ __device__ __forceinline__ double to_double(double s, int k)
     {
         return k == 0 ? s - 1.0 : s;
+    }
+    static __device__ __forceinline__ Vec4<double> load4(const CavityDesc* d, int b, size_t o)
+    {
+        return {static_cast<const double*>(d->f[b][0])[o], static_cast<const double*>(d->f[b][1])[o],
+                static_cast<const double*>(d->f[b][2])[o], static_cast<const double*>(d->f[b][3])[o]};
     }
 };
 
