@@ -184,14 +184,16 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
  * Execution schedule of the step (results are the same up to FP rounding
  * order): kernel 0 = warp-marching strips (each warp walks a 28-column strip
  * up a chunk of chunk_rows rows, rolling its stencil window in registers;
- * chunk_rows 0 = chosen from the GPU size), kernel 1 = shared-memory tiles.
+ * chunk_rows 0 = chosen from the GPU size), kernel 1 = shared-memory tiles
+ * of 32 columns by chunk_rows rows (16, 14, 12, 10 or 8 in FP32, 16 in
+ * FP64; 0 = the height whose tile count fills the SMs most evenly).
  * ERR_ARG on other values.
  */
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
 
 /*
- * Autotuner: time every candidate schedule (the tile kernel and the
- * marching kernel with 8..256 rows per unit) for `steps` steps each on a
+ * Autotuner: time every candidate schedule (the tile kernel at each tile
+ * height and the marching kernel with 8..256 rows per unit) for `steps` steps each on a
  * device-side snapshot of the current state, restore the state exactly
  * (fields, step counter, residual) and keep the fastest schedule.  Writes
  * the choice and its time per step if the pointers are non-null.  Needs

@@ -122,8 +122,11 @@ int Engine::init()
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
     CK(step_prepare(precision_));
-    CK(step_occupancy(precision_, &occ_));
-    if (occ_ < 1) return fail(RTLBFS_ERR_CUDA, "step kernel does not fit on an SM");
+    for (int h : kTileHeights) {
+        if (!tile_height_ok(precision_, h)) continue;
+        CK(step_occupancy(precision_, h, &occ_tile_[h]));
+        if (occ_tile_[h] < 1) return fail(RTLBFS_ERR_CUDA, "step kernel does not fit on an SM");
+    }
     CK(march_prepare(precision_));
     CK(march_occupancy(precision_, &occ_march_));
     if (occ_march_ < 1) return fail(RTLBFS_ERR_CUDA, "march kernel does not fit on an SM");
@@ -331,7 +334,7 @@ int Engine::upload_lines(int slot)
         d.bcU[s] = c.bcU[s];
     }
     d.tiles_x = (c.nx + kTileX - 1) / kTileX;
-    d.tiles_y = (c.ny + kTileY - 1) / kTileY;
+    d.tiles_y = (c.ny + tile_h_ - 1) / tile_h_;
     d.ntiles = c.ntiles;  // work units of this cavity in the current list
     d.tile_begin = c.first_tile;
     d.beta_g = c.beta_g;
@@ -384,23 +387,58 @@ int Engine::set_kernel(int kind)
 int Engine::set_chunk_rows(int rows)
 {
     if (rows < 0) return fail(RTLBFS_ERR_ARG, "chunk rows must be >= 0");
+    if (kernel_ == 1 && rows != 0 && !tile_height_ok(precision_, rows))
+        return fail(RTLBFS_ERR_ARG, precision_ == RTLBFS_FP64
+                                        ? "FP64 tile height must be 16 (or 0)"
+                                        : "tile height must be one of 16, 14, 12, 10, 8 (or 0)");
     chunk_rows_ = rows;
     tiles_dirty_ = true;
     return RTLBFS_OK;
+}
+
+// Tile height for the current set of cavities: the tiles of one launch run
+// about ceil(tiles / SMs) deep on the busiest SM, and a tile of height h
+// costs its faces and gradient ring plus a fixed share (loads, barriers,
+// the residual), in face-equivalents: 65 h + 32 + 0.25 * 34 (h + 2) + 300.
+int Engine::pick_tile_height() const
+{
+    if (precision_ == RTLBFS_FP64) return kTileYDefault;
+    int best_h = kTileYDefault;
+    double best = 1e300;
+    for (int h : kTileHeights) {
+        long long tiles = 0;
+        for (int s = 0; s < capacity_; ++s)
+            if (slots_[s].active)
+                tiles += (long long)((slots_[s].nx + kTileX - 1) / kTileX) *
+                         ((slots_[s].ny + h - 1) / h);
+        const double deep = (double)((tiles + sms_ - 1) / std::max(sms_, 1));
+        const double cost = deep * (65.0 * h + 32.0 + 0.25 * 34.0 * (h + 2) + 300.0);
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            best_h = h;
+        }
+    }
+    return best_h;
 }
 
 int Engine::rebuild_tiles()
 {
     std::vector<int4> t;
     if (kernel_ == 1) {
+        const int h = chunk_rows_ > 0 ? chunk_rows_ : pick_tile_height();
+        if (h != tile_h_ && gexec_) {  // the graph baked the other tile kernel
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+        }
+        tile_h_ = h;
         for (int s = 0; s < capacity_; ++s) {
             Cavity& c = slots_[s];
             if (!c.active) continue;
-            const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
+            const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + tile_h_ - 1) / tile_h_;
             c.first_tile = (int)t.size();
             c.ntiles = tx * ty;
             for (int j = 0; j < ty; ++j)
-                for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * kTileY, 0));
+                for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * tile_h_, 0));
             c.dirty = true;  // the unit count lives in the descriptor
         }
     } else {
@@ -463,7 +501,7 @@ int Engine::prepare_launch()
     // persistent grid: every SM full, never more blocks than work units
     int want;
     if (kernel_ == 1) {
-        want = std::max(1, std::min(sms_ * occ_, std::max(ntiles_, 1)));
+        want = std::max(1, std::min(sms_ * occ_tile_[tile_h_], std::max(ntiles_, 1)));
     } else {
         const int wpb = kMarchThreads / 32;
         want = std::max(1, std::min(sms_ * occ_march_, (std::max(ntiles_, 1) + wpb - 1) / wpb));
@@ -607,7 +645,7 @@ int Engine::launch_steps(long long launches)
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
-                    e = kernel_ == 1 ? launch_step(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+                    e = kernel_ == 1 ? launch_step(precision_, tile_h_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
                                      : launch_march(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
                 cudaError_t e2 = cudaStreamEndCapture(cs, &g);
                 if (e == cudaSuccess) e = e2;
@@ -625,7 +663,7 @@ int Engine::launch_steps(long long launches)
         }
     }
     for (; left > 0; --left) {
-        CK(kernel_ == 1 ? launch_step(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+        CK(kernel_ == 1 ? launch_step(precision_, tile_h_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
                         : launch_march(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
         g_launches++;
     }
@@ -655,7 +693,9 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
     struct Cand {
         int kernel, rows;
     };
-    std::vector<Cand> cands = {{1, 0}};
+    std::vector<Cand> cands;
+    for (int h : kTileHeights)
+        if (tile_height_ok(precision_, h)) cands.push_back({1, h});
     for (int H : {8, 16, 32, 64, 128, 256}) {
         if (H > maxny && H != 8) break;
         cands.push_back({0, H});

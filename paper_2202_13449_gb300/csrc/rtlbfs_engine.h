@@ -86,7 +86,8 @@ public:
     // step kernel: 0 = warp-marching strips (default), 1 = shared-memory tiles
     int set_kernel(int kind);
     int kernel() const { return kernel_; }
-    // rows per warp-marching work unit (0 = automatic)
+    // rows per work unit (0 = automatic): chunk rows of a warp-marching
+    // unit, or the tile height of the tile kernel (one of kTileHeights)
     int set_chunk_rows(int rows);
     int chunk_rows() const { return chunk_rows_; }
     // time every candidate schedule for `steps` steps on a snapshot of the
@@ -101,7 +102,10 @@ private:
     int precision_;
     int capacity_;
     size_t rsize_;
-    int sms_ = 0, occ_ = 0, grid_ = 0;
+    int sms_ = 0, grid_ = 0;
+    int occ_tile_[32] = {};  // resident tile blocks per SM, by tile height
+    int tile_h_ = 16;        // tile height of the current tile list
+    int pick_tile_height() const;
     int kernel_ = 0, occ_march_ = 0, chunk_rows_ = 0;
     int launch_one(cudaStream_t s);
     cudaStream_t stream_ = nullptr, own_stream_ = nullptr;

@@ -8,22 +8,21 @@
 
 namespace rtlbfs {
 
-#ifndef RTLBFS_STEP_THREADS
-#define RTLBFS_STEP_THREADS 256
-#endif
-#ifndef RTLBFS_TILE_X
-#define RTLBFS_TILE_X 32
-#endif
-#ifndef RTLBFS_TILE_Y
-#define RTLBFS_TILE_Y 16
-#endif
-#ifndef RTLBFS_MIN_BLOCKS_FP32
-#define RTLBFS_MIN_BLOCKS_FP32 4
-#endif
-constexpr int kStepThreads = RTLBFS_STEP_THREADS;  // threads of a step block
-constexpr int kTileX = RTLBFS_TILE_X;              // cells of a tile along x
-constexpr int kTileY = RTLBFS_TILE_Y;              // cells of a tile along y
-constexpr int kMinBlocksFP32 = RTLBFS_MIN_BLOCKS_FP32;  // resident blocks per SM to aim for
+// Tiles of the shared-memory step kernel: kTileX = 32 columns by one of
+// the compiled heights below, 16 threads per tile row (two cells per thread
+// in the update).  The height is picked per cavity set so that the number of
+// tiles fills the SMs evenly (a 512-row mesh in 16-row tiles leaves a third
+// of the SMs one tile short).  FP64 is compiled for the default height only.
+constexpr int kTileX = 32;
+constexpr int kTileHeights[] = {16, 14, 12, 10, 8};
+constexpr int kTileYDefault = 16;
+inline bool tile_height_ok(int precision, int h)
+{
+    if (precision == 0) return h == kTileYDefault;
+    for (int t : kTileHeights)
+        if (t == h) return true;
+    return false;
+}
 
 #ifndef RTLBFS_PAIR_FACES
 #define RTLBFS_PAIR_FACES 0  // 1: x- and y-face in one packed FP32x2 evaluation
@@ -48,11 +47,12 @@ struct NuLines {
     const CellLine<double>* yc;
 };
 
-size_t step_smem(int precision);
+// tile_h: one of kTileHeights (FP32) or kTileYDefault (FP64)
 cudaError_t step_prepare(int precision);
-cudaError_t step_occupancy(int precision, int* blocks_per_sm);
-cudaError_t launch_step(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
-                        CavityCtl* ctls, const int4* tiles, const int* ntiles);
+cudaError_t step_occupancy(int precision, int tile_h, int* blocks_per_sm);
+cudaError_t launch_step(int precision, int tile_h, int grid, cudaStream_t s,
+                        const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
+                        const int* ntiles);
 cudaError_t march_prepare(int precision);
 cudaError_t march_occupancy(int precision, int* blocks_per_sm);
 cudaError_t launch_march(int precision, int grid, cudaStream_t s, const CavityDesc* descs,

@@ -31,7 +31,7 @@
 
 namespace rtlbfs {
 
-template <class P, int TX, int TY>
+template <class P, int TX, int TY, int NT>
 struct TileSmem {
     using S = typename P::S;
     using R = typename P::R;
@@ -48,7 +48,7 @@ struct TileSmem {
     FaceLine<R> yl[TY + 1];
     CellLine<R> xc[BX];
     CellLine<R> yc[BY];
-    double red[kStepThreads / 32][4];
+    double red[NT / 32][4];
     int last;
 };
 
@@ -212,21 +212,23 @@ __device__ __forceinline__ void face_cells(bool isx, const Vec4<R>& vl, const Ve
     }
 }
 
-template <class P>
+// Resident blocks per SM to compile for: FP32 aims at 64 registers a thread
+// (the tile buffers then bound occupancy); FP64 takes what it needs.
+template <class P, int NT>
 struct MinBlocks {
     static constexpr int value = 1;
 };
-template <>
-struct MinBlocks<StoreQ> {
-    static constexpr int value = kMinBlocksFP32;
+template <int NT>
+struct MinBlocks<StoreQ, NT> {
+    static constexpr int value = 65536 / (NT * 64);
 };
 
-template <class P, int TX, int TY>
-__global__ void __launch_bounds__(kStepThreads, MinBlocks<P>::value)
+template <class P, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<P, NT>::value)
 step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
 {
-    using Sm = TileSmem<P, TX, TY>;
+    using Sm = TileSmem<P, TX, TY, NT>;
     using S = typename P::S;
     using R = typename P::R;
     constexpr int BX = Sm::BX, BY = Sm::BY, GX = Sm::GX, GY = Sm::GY;
@@ -260,14 +262,14 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const CellLine<R>* yc = static_cast<const CellLine<R>*>(dp->ycell);
             const FaceLine<R>* xl = static_cast<const FaceLine<R>*>(dp->xline);
             const FaceLine<R>* yl = static_cast<const FaceLine<R>*>(dp->yline);
-            for (int k = tid; k < BX; k += kStepThreads) sm.xc[k] = xc[min(i0 + k, nx + 3)];
-            for (int k = tid; k < BY; k += kStepThreads) sm.yc[k] = yc[min(j0 + k, ny + 3)];
-            for (int k = tid; k < TX + 1; k += kStepThreads) sm.xl[k] = xl[min(i0 + k, nx)];
-            for (int k = tid; k < TY + 1; k += kStepThreads) sm.yl[k] = yl[min(j0 + k, ny)];
+            for (int k = tid; k < BX; k += NT) sm.xc[k] = xc[min(i0 + k, nx + 3)];
+            for (int k = tid; k < BY; k += NT) sm.yc[k] = yc[min(j0 + k, ny + 3)];
+            for (int k = tid; k < TX + 1; k += NT) sm.xl[k] = xl[min(i0 + k, nx)];
+            for (int k = tid; k < TY + 1; k += NT) sm.yl[k] = yl[min(j0 + k, ny)];
         }
         {
             constexpr int NB = BX * BY;
-            constexpr int NR = (NB + kStepThreads - 1) / kStepThreads;
+            constexpr int NR = (NB + NT - 1) / NT;
             Vec4<S> v[NR];
             int ms[NR];
             bool ok[NR];
@@ -275,7 +277,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 const Vec4<S>* base = fin + (size_t)(j0 - 2) * pitch + (i0 - 2);
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {  // issue every load first
-                    const int k = tid + q * kStepThreads;
+                    const int k = tid + q * NT;
                     ms[q] = -1;
                     ok[q] = k < NB;
                     v[q] = {S(0), S(0), S(0), S(0)};
@@ -284,7 +286,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             } else {
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {
-                    const int k = tid + q * kStepThreads;
+                    const int k = tid + q * NT;
                     const int c = k % BX, r = k / BX;
                     int si = 0, sj = 0;
                     ms[q] = -1;
@@ -296,7 +298,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             }
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
-                const int k = tid + q * kStepThreads;
+                const int k = tid + q * NT;
                 if (k >= NB) continue;
                 Vec4<S> x = v[q];
                 if (ms[q] >= 0) x = mirror_state<P>(*dp, ms[q], x);
@@ -308,7 +310,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         __syncthreads();
 
         // ---- 2. gradients on the tile plus a 1-cell ring ----------------
-        for (int k = tid; k < GX * GY; k += kStepThreads) {
+        for (int k = tid; k < GX * GY; k += NT) {
             const int gc = k % GX, gr = k / GX;
             int c = gc + 1, r = gr + 1;  // box position
             int si, sj, ms = -1;
@@ -332,7 +334,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
 
         // ---- 3. faces ----------------------------------------------------
         constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
-        for (int k = tid; k < NXF + NYF; k += kStepThreads) {
+        for (int k = tid; k < NXF + NYF; k += NT) {
             const bool isx = k < NXF;
             int fc, fr;
             if (isx) {
@@ -378,7 +380,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const R dt = P::dt(dp), bg = P::beta_g(dp), Tr = P::T_ref(dp);
             const R fxb = P::fx(dp), fyb = P::fy(dp);
             bool bad = false;
-            for (int k = tid; k < TX * TY; k += kStepThreads) {
+            for (int k = tid; k < TX * TY; k += NT) {
                 const int tc = k % TX, tr = k / TX;
                 const int gi = i0 + tc, gj = j0 + tr;
                 if (gi >= nx || gj >= ny) continue;
@@ -433,7 +435,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         __syncthreads();
         if (tid == 0) {
             double a[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < kStepThreads / 32; ++w)
+            for (int w = 0; w < NT / 32; ++w)
                 for (int q = 0; q < 4; ++q) a[q] += sm.red[w][q];
             for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
             __threadfence();
@@ -643,55 +645,73 @@ __global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double t
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-template <class P>
-static size_t step_smem_bytes()
-{
-    return sizeof(TileSmem<P, kTileX, kTileY>);
-}
+template <class P, int TY>
+struct TileKernel {
+    static constexpr int NT = 16 * TY;
+    static constexpr size_t smem = sizeof(TileSmem<P, kTileX, TY, NT>);
+    static constexpr auto fn = step_kernel<P, kTileX, TY, NT>;
+    static cudaError_t prepare()
+    {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        // all of the unified L1/shared array to shared memory: occupancy is
+        // bounded by the tile buffers, and global loads are streamed once
+        return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    static cudaError_t occupancy(int* blocks)
+    {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, NT, smem);
+    }
+    static cudaError_t launch(int grid, cudaStream_t s, const CavityDesc* descs, CavityCtl* ctls,
+                              const int4* tiles, const int* ntiles)
+    {
+        fn<<<grid, NT, smem, s>>>(descs, ctls, tiles, ntiles);
+        return cudaGetLastError();
+    }
+};
 
-size_t step_smem(int precision)
+// Call op on the compiled tile kernel of (precision, tile_h).
+template <class Op>
+static cudaError_t with_tile_kernel(int precision, int tile_h, Op op)
 {
-    return precision == 0 ? step_smem_bytes<StoreD>() : step_smem_bytes<StoreQ>();
-}
-
-template <class P>
-static cudaError_t prepare_kernel()
-{
-    auto fn = step_kernel<P, kTileX, kTileY>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step_smem_bytes<P>());
-    if (e != cudaSuccess) return e;
-    // all of the unified L1/shared array to shared memory: occupancy is
-    // bounded by the tile buffers, and global loads are streamed once
-    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (precision == 0) {
+        if (tile_h == 16) return op(TileKernel<StoreD, 16>());
+        return cudaErrorInvalidValue;
+    }
+    switch (tile_h) {
+    case 16: return op(TileKernel<StoreQ, 16>());
+    case 14: return op(TileKernel<StoreQ, 14>());
+    case 12: return op(TileKernel<StoreQ, 12>());
+    case 10: return op(TileKernel<StoreQ, 10>());
+    case 8: return op(TileKernel<StoreQ, 8>());
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t step_prepare(int precision)
 {
-    return precision == 0 ? prepare_kernel<StoreD>() : prepare_kernel<StoreQ>();
+    if (precision == 0) return TileKernel<StoreD, 16>::prepare();
+    for (int h : kTileHeights) {
+        cudaError_t e = with_tile_kernel(precision, h, [](auto k) { return k.prepare(); });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-cudaError_t step_occupancy(int precision, int* blocks_per_sm)
+cudaError_t step_occupancy(int precision, int tile_h, int* blocks_per_sm)
 {
-    if (precision == 0)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            blocks_per_sm, step_kernel<StoreD, kTileX, kTileY>, kStepThreads,
-            step_smem_bytes<StoreD>());
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, step_kernel<StoreQ, kTileX, kTileY>, kStepThreads,
-        step_smem_bytes<StoreQ>());
+    return with_tile_kernel(precision, tile_h,
+                            [&](auto k) { return k.occupancy(blocks_per_sm); });
 }
 
-cudaError_t launch_step(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
-                        CavityCtl* ctls, const int4* tiles, const int* ntiles)
+cudaError_t launch_step(int precision, int tile_h, int grid, cudaStream_t s,
+                        const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
+                        const int* ntiles)
 {
-    if (precision == 0)
-        step_kernel<StoreD, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<StoreD>(), s>>>(
-            descs, ctls, tiles, ntiles);
-    else
-        step_kernel<StoreQ, kTileX, kTileY><<<grid, kStepThreads, step_smem_bytes<StoreQ>(), s>>>(
-            descs, ctls, tiles, ntiles);
-    return cudaGetLastError();
+    return with_tile_kernel(precision, tile_h, [&](auto k) {
+        return k.launch(grid, s, descs, ctls, tiles, ntiles);
+    });
 }
 
 cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
