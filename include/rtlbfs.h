@@ -213,6 +213,17 @@ int rtlbfs_sync(rtlbfs_t h);
 /* Message of the last failure on h (static storage of the handle). */
 const char* rtlbfs_last_error(rtlbfs_t h);
 
+/*
+ * Measurement aid (no counterpart in the paper): floating-point operations
+ * of one cell-update of the step with every face and gradient evaluated
+ * once -- *face_ops per face (the face arithmetic of the kernels run on an
+ * operation-counting type), *cell_ops per cell-update (two faces plus the
+ * gradients, update and residual terms), *sfu_ops reciprocals and square
+ * roots per cell-update.  An add, multiply or fused multiply-add counts 1.
+ * Host-only; needs no GPU.  Null pointers are skipped.  Returns RTLBFS_OK.
+ */
+int rtlbfs_op_counts(double* face_ops, double* cell_ops, double* sfu_ops);
+
 /* Free every device and host resource of h; NULL is ignored. */
 void rtlbfs_destroy(rtlbfs_t h);
 

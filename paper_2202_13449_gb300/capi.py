@@ -72,6 +72,7 @@ _SIGS = {
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
     "rtlbfs_launch_count": (C.c_longlong, []),
+    "rtlbfs_op_counts": (C.c_int, [_dp, _dp, _dp]),
     "rtlbfs_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_vp)]),
     "rtlbfs_batch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     "rtlbfs_batch_free_bytes": (C.c_int, [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
@@ -175,6 +176,16 @@ def nusselt_noalloc(xf, yf, rho_ptr, u_ptr, v_ptr, T_ptr, nu, chi, kappa, dT, bc
 
 def launch_count() -> int:
     return int(lib().rtlbfs_launch_count())
+
+
+def op_counts():
+    """(FP ops per face, FP ops per cell-update, SFU ops per cell-update) of
+    the step, each face and gradient evaluated once (host-only)."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().rtlbfs_op_counts(C.byref(a), C.byref(b), C.byref(c))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs_op_counts")
+    return a.value, b.value, c.value
 
 
 class Solver:

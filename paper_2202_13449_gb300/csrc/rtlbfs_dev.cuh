@@ -191,7 +191,7 @@ struct CellNT {
 // node is written Tbar + e with e = tau + drho*T, tau = T - Tbar, so every
 // difference of rho*T is a difference of e.
 template <typename V>
-__device__ __forceinline__ void face_flux(const CellNT<V>& L, const CellNT<V>& Rc, V Tbar,
+__host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const CellNT<V>& Rc, V Tbar,
                                           const FaceLine<V>& fl, V keep, V u_wall, V F[4])
 {
     using T = vtraits<V>;

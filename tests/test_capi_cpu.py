@@ -40,3 +40,13 @@ def test_host_argument_errors_are_status_codes():
     assert L.rtlbfs_create_mesh(4, 4, xf.ctypes.data_as(dp), bad.ctypes.data_as(dp), 0,
                                 C.byref(h)) != capi.OK
     assert not h.value
+
+
+def test_op_counts_of_the_step():
+    """The ALU work measure: the face arithmetic of the kernels counted on
+    the host (data-independent, so fixed), two faces plus the per-cell
+    terms per cell-update."""
+    face, cell, sfu = capi.op_counts()
+    assert face == int(face) and 150 <= face <= 200
+    assert cell == 2 * face + 95
+    assert sfu == 2 * 1 + 4  # one reciprocal per face; rho^{n+1}, two roots, one reciprocal
