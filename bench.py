@@ -58,10 +58,10 @@ WORKLOADS = {
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
         nx=8192, ny=8192, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=10,
         kind="cavity"),
-    "cavity2048": dict(
-        desc="profiling case: differentially heated cavity 2048x2048, tanh phi=2.0, Ra=1e8, "
-             "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 67 MB per buffer)",
-        nx=2048, ny=2048, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=100,
+    "cavity4096": dict(
+        desc="profiling case: differentially heated cavity 4096x4096, tanh phi=2.0, Ra=1e8, "
+             "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 268 MB per buffer, > L2)",
+        nx=4096, ny=4096, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=20,
         kind="cavity"),
     "batch1024": dict(
         desc="1024 independent cavities, sides from {32,48,64,96,128,192,256}, tanh phi in "
