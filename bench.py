@@ -125,16 +125,20 @@ def rooflines(kernel: str, cells: int, per_launch_s: float, rs: int, traffic, cl
     _, ops_cell, sfu_cell = capi.op_counts()
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    if rs == 4:
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        unit, src = "T FP32 op/s", f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz max SM clock"
+    else:  # the FP64 path runs on GB300's narrow FP64 units
+        alu_peak = 1.25 / 2
+        unit, src = "T FP64 op/s", "nominal FP64 1.25 TFLOP/s = 0.625 T fused multiply-adds/s"
     alu = ops_cell * cells / per_launch_s / 1e12
     alg_bytes = 8 * rs * cells  # read 4 fields + write 4 fields per cell
     hbm = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    alu_line = {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 2),
-                "unit": "T FP32 op/s", "frac": round(alu / alu_peak, 4), "traffic": traffic,
+    alu_line = {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
+                "unit": unit, "frac": round(alu / alu_peak, 4), "traffic": traffic,
                 "kernel": kernel, "ops_per_cell_update": ops_cell,
-                "sfu_ops_per_cell_update": sfu_cell,
-                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz max SM clock",
+                "sfu_ops_per_cell_update": sfu_cell, "peak_source": src,
                 "alg_ops_per_launch": ops_cell * cells}
     hbm_line = {"bound": "hbm", "achieved": round(hbm, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(hbm / peak, 4), "traffic": traffic, "kernel": kernel,
