@@ -80,10 +80,15 @@ Engine::Engine(int precision, int capacity)
 Engine::~Engine()
 {
     if (gexec_) cudaGraphExecDestroy(gexec_);
+    // the caller's stream may be gone by now: wait for the device, free on
+    // the engine's own stream
+    cudaDeviceSynchronize();
     for (auto& c : slots_) {
-        if (c.d_fields) cudaFree(c.d_fields);
-        if (c.d_lines) cudaFree(c.d_lines);
+        if (c.d_fields) cudaFreeAsync(c.d_fields, own_stream_);
+        if (c.d_lines) cudaFreeAsync(c.d_lines, own_stream_);
     }
+    if (own_stream_) cudaStreamSynchronize(own_stream_);
+    if (pool_) cudaMemPoolDestroy(pool_);
     cudaFree(d_desc_);
     cudaFree(d_ctl_);
     cudaFree(d_tiles_);
@@ -132,6 +137,19 @@ int Engine::init()
     if (occ_march_ < 1) return fail(RTLBFS_ERR_CUDA, "march kernel does not fit on an SM");
     CK(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
     stream_ = own_stream_;
+    // cavities come and go (batches, the request loop): their memory comes
+    // from a stream-ordered pool of this engine, which keeps freed blocks
+    // for reuse instead of returning them (no device-wide synchronisation)
+    {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CK(cudaMemPoolCreate(&pool_, &props));
+        uint64_t keep = ~0ull;
+        CK(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     slots_.resize(capacity_);
     h_desc_.resize(capacity_);
     std::memset(h_desc_.data(), 0, sizeof(CavityDesc) * capacity_);
@@ -210,17 +228,17 @@ int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_ou
     c.off_xcd = off; off = align_up(off + sizeof(CellLine<double>) * (nx + 4), 256);
     c.off_ycd = off; off = align_up(off + sizeof(CellLine<double>) * (ny + 4), 256);
     c.lines_bytes = off;
-    cudaError_t e = cudaMalloc(&c.d_fields, c.fields_bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fields)");
-    e = cudaMalloc(&c.d_lines, c.lines_bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(&c.d_fields, c.fields_bytes, pool_, stream_);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(fields)");
+    e = cudaMallocFromPoolAsync(&c.d_lines, c.lines_bytes, pool_, stream_);
     if (e != cudaSuccess) {
-        cudaFree(c.d_fields);
-        return cuda_fail(e, "cudaMalloc(lines)");
+        cudaFreeAsync(c.d_fields, stream_);
+        return cuda_fail(e, "cudaMallocFromPoolAsync(lines)");
     }
     e = cudaMemsetAsync(c.d_fields, 0, c.fields_bytes, stream_);
     if (e != cudaSuccess) {
-        cudaFree(c.d_fields);
-        cudaFree(c.d_lines);
+        cudaFreeAsync(c.d_fields, stream_);
+        cudaFreeAsync(c.d_lines, stream_);
         return cuda_fail(e, "cudaMemset(fields)");
     }
     c.active = true;
@@ -233,8 +251,8 @@ int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_ou
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
+    // from pageable memory: staged before the call returns, ordered on the stream
     CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
-    CK(cudaStreamSynchronize(stream_));
     *slot_out = slot;
     return RTLBFS_OK;
 }
@@ -243,9 +261,9 @@ int Engine::remove(int slot)
 {
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
-    CK(cudaStreamSynchronize(stream_));
-    cudaFree(c->d_fields);
-    cudaFree(c->d_lines);
+    // stream-ordered: released after the work already queued on the stream
+    CK(cudaFreeAsync(c->d_fields, stream_));
+    CK(cudaFreeAsync(c->d_lines, stream_));
     slots_[slot] = Cavity();
     tiles_dirty_ = true;
     return RTLBFS_OK;
@@ -319,9 +337,9 @@ int Engine::upload_lines(int slot)
         put(c.off_xc, cx.data(), cx.size() * sizeof(cx[0]));
         put(c.off_yc, cy.data(), cy.size() * sizeof(cy[0]));
     }
-    // synchronous copy: buf is pageable and about to go out of scope
-    CK(cudaStreamSynchronize(stream_));
-    CK(cudaMemcpy(c.d_lines, buf.data(), c.lines_bytes, cudaMemcpyHostToDevice));
+    // pageable source: staged before the call returns (buf may go out of
+    // scope), copied in stream order after the work already queued
+    CK(cudaMemcpyAsync(c.d_lines, buf.data(), c.lines_bytes, cudaMemcpyHostToDevice, stream_));
 
     CavityDesc& d = h_desc_[slot];
     std::memset(&d, 0, sizeof(d));
@@ -365,7 +383,7 @@ int Engine::upload_lines(int slot)
     d.yline = L + c.off_yl;
     d.xcell = L + c.off_xc;
     d.ycell = L + c.off_yc;
-    CK(cudaMemcpy(&d_desc_[slot], &d, sizeof(d), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(&d_desc_[slot], &d, sizeof(d), cudaMemcpyHostToDevice, stream_));
     c.dirty = false;
     return RTLBFS_OK;
 }
@@ -439,7 +457,6 @@ int Engine::rebuild_tiles()
             c.ntiles = tx * ty;
             for (int j = 0; j < ty; ++j)
                 for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * tile_h_, 0));
-            c.dirty = true;  // the unit count lives in the descriptor
         }
     } else {
         // warp-marching units: strips of kStrip columns, chunks of H rows.
@@ -466,11 +483,21 @@ int Engine::rebuild_tiles()
             for (int k = 0; k < chunks; ++k)
                 for (int i = 0; i < strips; ++i)
                     t.push_back(make_int4(s, i * kStrip, k * h, std::min(c.ny, (k + 1) * h)));
-            c.dirty = true;
         }
     }
-    CK(cudaStreamSynchronize(stream_));
+    // the unit range of every cavity lives in its descriptor
+    for (int s = 0; s < capacity_; ++s) {
+        const Cavity& c = slots_[s];
+        if (!c.active) continue;
+        CavityDesc& d = h_desc_[s];
+        d.ntiles = c.ntiles;
+        d.tile_begin = c.first_tile;
+        d.tiles_x = (c.nx + kTileX - 1) / kTileX;
+        d.tiles_y = (c.ny + tile_h_ - 1) / tile_h_;
+    }
+    desc_dirty_ = true;
     if ((int)t.size() > tile_cap_) {
+        CK(cudaStreamSynchronize(stream_));
         cudaFree(d_tiles_);
         d_tiles_ = nullptr;
         tile_cap_ = std::max<int>((int)t.size(), 2 * tile_cap_);
@@ -480,9 +507,13 @@ int Engine::rebuild_tiles()
             gexec_ = nullptr;
         }
     }
-    if (!t.empty()) CK(cudaMemcpy(d_tiles_, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+    // pageable sources, staged at the call; in stream order after the
+    // launches already queued (which still read the old list)
+    if (!t.empty())
+        CK(cudaMemcpyAsync(d_tiles_, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice,
+                           stream_));
     ntiles_ = (int)t.size();
-    CK(cudaMemcpy(d_ntiles_, &ntiles_, sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(d_ntiles_, &ntiles_, sizeof(int), cudaMemcpyHostToDevice, stream_));
     tiles_dirty_ = false;
     return RTLBFS_OK;
 }
@@ -498,6 +529,11 @@ int Engine::prepare_launch()
             int rc = upload_lines(s);
             if (rc) return rc;
         }
+    if (desc_dirty_) {  // unit ranges of every cavity: one copy
+        CK(cudaMemcpyAsync(d_desc_, h_desc_.data(), sizeof(CavityDesc) * capacity_,
+                           cudaMemcpyHostToDevice, stream_));
+        desc_dirty_ = false;
+    }
     // persistent grid: every SM full, never more blocks than work units
     int want;
     if (kernel_ == 1) {
@@ -607,25 +643,46 @@ int Engine::set_conduction_state(int slot)
 {
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
-    const size_t n = (size_t)c->nx * c->ny;
-    std::vector<double> r(n, 1.0), u(n, 0.0), v(n, 0.0), T(n, c->T_ref);
+    if (c->dirty) {
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
+    // rho = 1, u = v = 0, T linear in x between Dirichlet side walls (else
+    // T_ref): one temperature per column, spread over the rows on the device
+    std::vector<double> Tcol(c->nx, c->T_ref);
     if (c->kind[kSideW] == kDirichlet && c->kind[kSideE] == kDirichlet) {
         const double x0 = c->xf.front(), Lx = c->xf.back() - c->xf.front();
-        for (int j = 0; j < c->ny; ++j)
-            for (int i = 0; i < c->nx; ++i) {
-                const double s = (0.5 * (c->xf[i] + c->xf[i + 1]) - x0) / Lx;
-                T[(size_t)j * c->nx + i] = c->bcT[kSideW] + (c->bcT[kSideE] - c->bcT[kSideW]) * s;
-            }
+        for (int i = 0; i < c->nx; ++i) {
+            const double s = (0.5 * (c->xf[i] + c->xf[i + 1]) - x0) / Lx;
+            Tcol[i] = c->bcT[kSideW] + (c->bcT[kSideE] - c->bcT[kSideW]) * s;
+        }
     }
-    return set_state(slot, r.data(), u.data(), v.data(), T.data());
+    if (stage_cap_ < (size_t)c->nx) {
+        CK(cudaStreamSynchronize(stream_));
+        cudaFree(d_stage_);
+        d_stage_ = nullptr;
+        CK(cudaMalloc(&d_stage_, sizeof(double) * c->nx));
+        stage_cap_ = c->nx;
+    }
+    CK(cudaMemcpyAsync(d_stage_, Tcol.data(), sizeof(double) * c->nx, cudaMemcpyHostToDevice,
+                       stream_));
+    CK(launch_conduction(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch,
+                         h_desc_[slot].f[0][0]));
+    g_launches++;
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.cur = 0;
+    z.done = 1;
+    z.tol = -1.0;
+    z.res[0] = z.res[1] = INFINITY;
+    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
+    return RTLBFS_OK;
 }
 
 int Engine::arm(int slot, long long nsteps, double tol)
 {
     if (!cavity(slot)) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (nsteps < 0) return fail(RTLBFS_ERR_ARG, "negative step count");
-    int rc = prepare_launch();
-    if (rc) return rc;
     CK(launch_arm(stream_, d_ctl_, slot, nsteps, tol, 0));
     g_launches++;
     return RTLBFS_OK;
@@ -781,8 +838,10 @@ int Engine::nusselt(int slot, int which, double* out)
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (which < kNuWest || which > kNuHalf) return fail(RTLBFS_ERR_ARG, "bad Nusselt selector");
     if (which == kNuHalf && (c->nx % 2)) return fail(RTLBFS_ERR_ARG, "Nu_1/2 needs nx even");
-    int rc = prepare_launch();
-    if (rc) return rc;
+    if (c->dirty) {  // the reduction reads this cavity's lines and descriptor
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
     const CavityDesc& d = h_desc_[slot];
     unsigned char* L = static_cast<unsigned char*>(c->d_lines);
     NuLines ln;

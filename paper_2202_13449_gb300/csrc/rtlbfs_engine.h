@@ -117,6 +117,8 @@ private:
     int* d_ntiles_ = nullptr;
     int tile_cap_ = 0, ntiles_ = 0;
     bool tiles_dirty_ = true;
+    bool desc_dirty_ = false;          // unit ranges changed: re-upload all descriptors
+    cudaMemPool_t pool_ = nullptr;     // device memory of the cavities
     double* d_partial_ = nullptr;  // per-block partial sums of the FP64 reductions
     int partial_cap_ = 0;
     double* d_scalar_ = nullptr;

@@ -65,6 +65,9 @@ cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int
                             int pitch, void* cells, int* bad);
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny,
                              int pitch, const void* cells);
+// rho = 1, u = v = 0, T = Tcol[i] in every row (one buffer of cell records)
+cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol, int nx, int ny,
+                              int pitch, void* cells);
 cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
                        int reset_counter);
 

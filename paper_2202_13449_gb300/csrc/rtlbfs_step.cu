@@ -624,6 +624,19 @@ __global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pi
     }
 }
 
+template <class P>
+__global__ void conduction_kernel(const double* __restrict__ Tcol, int nx, int ny, int pitch,
+                                  Vec4<typename P::S>* __restrict__ cells)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = k % nx, j = k / nx;
+        cells[(size_t)j * pitch + i] = {P::from_double(0.0, 0), P::from_double(0.0, 1),
+                                        P::from_double(0.0, 2), P::from_double(Tcol[i], 3)};
+    }
+}
+
 // Arm the run control of one cavity: take `nsteps` more steps (stop early
 // when max(R_u, R_T) < tol, tol < 0: never).
 __global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double tol,
@@ -645,9 +658,34 @@ __global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double t
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
+#ifndef RTLBFS_TILE_THREADS_16
+#define RTLBFS_TILE_THREADS_16 256
+#endif
+#ifndef RTLBFS_TILE_THREADS_14
+#define RTLBFS_TILE_THREADS_14 224
+#endif
+#ifndef RTLBFS_TILE_THREADS_12
+#define RTLBFS_TILE_THREADS_12 192
+#endif
+#ifndef RTLBFS_TILE_THREADS_10
+#define RTLBFS_TILE_THREADS_10 160
+#endif
+#ifndef RTLBFS_TILE_THREADS_8
+#define RTLBFS_TILE_THREADS_8 128
+#endif
+// threads of the block for a tile height
+constexpr int tile_threads(int ty)
+{
+    return ty == 16 ? RTLBFS_TILE_THREADS_16
+         : ty == 14 ? RTLBFS_TILE_THREADS_14
+         : ty == 12 ? RTLBFS_TILE_THREADS_12
+         : ty == 10 ? RTLBFS_TILE_THREADS_10
+                    : RTLBFS_TILE_THREADS_8;
+}
+
 template <class P, int TY>
 struct TileKernel {
-    static constexpr int NT = 16 * TY;
+    static constexpr int NT = tile_threads(TY);
     static constexpr size_t smem = sizeof(TileSmem<P, kTileX, TY, NT>);
     static constexpr auto fn = step_kernel<P, kTileX, TY, NT>;
     static cudaError_t prepare()
@@ -757,6 +795,21 @@ cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, 
     else
         state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
                                                         static_cast<const Vec4<int>*>(cells));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol, int nx, int ny,
+                              int pitch, void* cells)
+{
+    const long long n = (long long)nx * ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (precision == 0)
+        conduction_kernel<StoreD><<<blocks, 256, 0, s>>>(Tcol, nx, ny, pitch,
+                                                         static_cast<Vec4<double>*>(cells));
+    else
+        conduction_kernel<StoreQ><<<blocks, 256, 0, s>>>(Tcol, nx, ny, pitch,
+                                                         static_cast<Vec4<int>*>(cells));
     return cudaGetLastError();
 }
 
