@@ -53,6 +53,12 @@ WORKLOADS = {
              "Ma=0.1, FP32 bulk + FP64 reductions, seeded noise 1e-3",
         nx=1024, ny=512, phi=0.0, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32", inner=500,
         kind="rb"),
+    "rb1024x512_steady": dict(
+        desc="Rayleigh-Benard 2:1 box 1024x512 uniform, periodic in x, Ra=1e6, Pr=0.71, Ma=0.1, "
+             "FP32 bulk + FP64 reductions, seeded noise 1e-3: time to a statistically steady "
+             "Nusselt number",
+        nx=1024, ny=512, phi=0.0, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32", sample_every=2000,
+        window=25, onset=1.5, max_steps=2_000_000, kind="rb_steady"),
     "cavity8192": dict(
         desc="roofline probe: differentially heated cavity 8192x8192, tanh phi=2.0, Ra=1e8, "
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
@@ -73,6 +79,12 @@ WORKLOADS = {
              "log-uniform 64..1024, Ra log-uniform 1e3..1e8, Pr in {0.71, 7.0}, seed 42; "
              "continuous batching, FP32 bulk + FP64 reductions",
         count=10000, seed=42, rate=200.0, precision="fp32", kind="serve"),
+    "cavity512_accuracy": dict(
+        desc="accuracy run of the 512x512 tanh cavity (Ra=1e8, Pr=0.71, Ma=0.1): the FP32 path "
+             "(fixed-point state, FP64 reductions) against the FP64 path at step checkpoints "
+             "1, 10, 100, 1e3, 1e4, 2e5",
+        nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32",
+        checkpoints=[1, 10, 100, 1000, 10000, 200000], kind="accuracy"),
     "cavity512_fp64": dict(
         desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
@@ -436,7 +448,132 @@ def run_serve(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_accuracy(args, w):
+    """FP32 against FP64 (the GPU FP64 path is tied to the oracle, step by
+    step, by the parity tests) on the config-2 cavity at step checkpoints:
+    field errors relative to max(max|FP64|, floor) and the mean wall Nusselt
+    number's relative error."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    xf = capi.tanh_faces(w["nx"], float(w["nx"]), w["phi"])
+    dt = 0.5 * float(np.min(np.diff(xf)))
+    sol = {}
+    for prec in (capi.FP64, capi.FP32):
+        s = capi.Solver(xf, xf, prec)
+        s.set_params(w["Ra"], w["Pr"], w["Ma"], dt)
+        s.set_state(*inputs.conduction_state(xf, xf))
+        sol[prec] = s
+    rows, done, t0 = [], 0, time.perf_counter()
+    worst = 0.0
+    for cp in w["checkpoints"]:
+        for s in sol.values():
+            s.step(cp - done)
+        done = cp
+        a, b = sol[capi.FP32].get_state(), sol[capi.FP64].get_state()
+        nu = {p: 0.5 * (sol[p].nusselt(capi.NU_WEST) + sol[p].nusselt(capi.NU_EAST)) for p in sol}
+        def rel(x, y, floor):
+            return float(np.max(np.abs(x - y)) / max(float(np.max(np.abs(y))), floor))
+        row = {"step": cp, "rel_err_u": rel(a[1], b[1], 0.1), "rel_err_v": rel(a[2], b[2], 0.1),
+               "rel_err_T": rel(a[3], b[3], 1.0), "abs_err_rho": float(np.max(np.abs(a[0] - b[0]))),
+               "mean_wall_nu_fp64": nu[capi.FP64], "mean_wall_nu_fp32": nu[capi.FP32],
+               "rel_err_nu": abs(nu[capi.FP32] - nu[capi.FP64]) / abs(nu[capi.FP64])}
+        worst = max(worst, row["rel_err_u"], row["rel_err_v"], row["rel_err_T"])
+        rows.append(row)
+    el = time.perf_counter() - t0
+    for s in sol.values():
+        s.close()
+    line = {"metric": "FP32 vs FP64 relative field error (max over u, v, T and checkpoints)",
+            "value": worst, "unit": "relative error", "n_gpus": 1, "steps": len(rows),
+            "warmup": 0, "ms_per_step": round(el * 1e3 / max(done, 1), 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (conduction initial state)",
+            "config": {"workload": args.workload, "description": w["desc"],
+                       "cells": w["nx"] * w["ny"], "dt": dt,
+                       "norm": "max|FP32 - FP64| / max(max|FP64|, floor); floors u, v 0.1 "
+                               "(V_c), T 1 (dT)"},
+            "checkpoints": rows,
+            "targets": {"fields": 1e-5, "mean_wall_nu": 1e-4}}
+    print(json.dumps(line), flush=True)
+
+
+def run_rb_steady(args, w):
+    """Config 3's second figure: from the seeded initial state, step until
+    the wall Nusselt numbers are statistically steady and report the steps
+    and device time it took.  Steady: convection has set in (a wall value
+    above `onset`; the perturbation grows from 1e-3, so Nu first sits at its
+    conduction value 1 for many free-fall times), and over the last `window`
+    samples (one every `sample_every` steps) the bottom and top means agree
+    within 5 % and their mean moved less than 2 % against the window before."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    s, _, _, _ = setup_solver(capi, inputs, dict(w, kind="rb"))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s.set_stream(stream)
+    sched = s.autotune(32)  # on a snapshot of the initial state, restored
+    k, W = w["sample_every"], w["window"]
+    # the library's wall Nusselt number is the wall's heat flux / (chi dT);
+    # per unit wall length and across the layer height that is x (H / width)
+    aspect = float(w["ny"]) / float(w["nx"])
+    bottom, top, steps, t_dev = [], [], 0, 0.0
+    steady_at, onset_at = None, None
+    while steps < w["max_steps"]:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(k)
+        b.record(stream)
+        b.synchronize()
+        t_dev += a.elapsed_time(b) * 1e-3
+        steps += k
+        bottom.append(s.nusselt(capi.NU_SOUTH) * aspect)
+        top.append(s.nusselt(capi.NU_NORTH) * aspect)
+        if onset_at is None and max(bottom[-1], top[-1]) > w["onset"]:
+            onset_at = len(bottom)
+        if onset_at is not None and len(bottom) - onset_at >= 2 * W:
+            m_now = 0.5 * (np.mean(bottom[-W:]) + np.mean(top[-W:]))
+            m_prev = 0.5 * (np.mean(bottom[-2 * W:-W]) + np.mean(top[-2 * W:-W]))
+            gap = abs(np.mean(bottom[-W:]) - np.mean(top[-W:])) / abs(m_now)
+            if gap < 0.05 and abs(m_now - m_prev) / abs(m_now) < 0.02:
+                steady_at = steps
+                break
+    cells = w["nx"] * w["ny"]
+    res, _ = s.residual()
+    s.close()
+    m = 0.5 * (np.mean(bottom[-W:]) + np.mean(top[-W:]))
+    line = {"metric": "time to a statistically steady Nusselt number (device time)",
+            "value": round(t_dev, 3) if steady_at else None, "unit": "s",
+            "n_gpus": 1, "steps": steps, "warmup": 0,
+            "ms_per_step": round(t_dev * 1e3 / max(steps, 1), 5), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded noise, seed 0)",
+            "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                       "criterion": f"after the onset of convection (a wall Nu > {w['onset']}), over "
+                                    f"the last {W} samples (every {k} steps) bottom and top mean "
+                                    "Nu within 5 % and the mean moved < 2 % against the previous "
+                                    "window; Nu per unit wall length across the layer height"},
+            "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1]},
+            "steady_at_step": steady_at, "onset_at_step": onset_at * k if onset_at else None,
+            "nusselt_mean": m,
+            "nusselt_bottom_last": bottom[-1], "nusselt_top_last": top[-1],
+            "throughput_M_cell_updates_per_s": round(cells * steps / t_dev / 1e6, 1),
+            "residual_last_step": res,
+            "nu_history_every_k": {"bottom": [round(x, 5) for x in bottom],
+                                   "top": [round(x, 5) for x in top]}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "rb_steady":
+        return run_rb_steady(args, w)
+    if w.get("kind") == "accuracy":
+        return run_accuracy(args, w)
     if w.get("kind") == "batch":
         return run_batch(args, w)
     if w.get("kind") == "serve":
@@ -790,6 +927,11 @@ def main():
         args.warmup = 3
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
+        if w.get("kind") in ("accuracy", "rb_steady"):
+            print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
+                              "time to a steady state of the GPU path; the oracle's rate is the "
+                              "rb1024x512 / cavity512 reference lines"}))
+            return
         run_reference(args, w)
     else:
         run_ours(args, w)

@@ -172,6 +172,31 @@ def test_full_size_512_tanh_cavity_one_step(orc, precision, kernel):
         assert rel(got[q], ref[q], floor) < tol, (q, rel(got[q], ref[q], floor))
 
 
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_config2_checkpoints_match_oracle(orc, precision):
+    """The config-2 run itself (512 x 512 tanh, Ra = 1e8, conduction start)
+    against the oracle at steps 1, 10 and 100, with the schedule the
+    autotuner picks: fields and the mean wall Nusselt number."""
+    p, s = config2_pair(orc, precision)
+    st = inputs.conduction_state(p.xf, p.yf)
+    s.set_state(*st)
+    s.autotune(16)
+    ref, done = st, 0
+    for cp in (1, 10, 100):
+        ref, _, rc = orc.step(p, ref, cp - done)
+        assert rc == 0
+        s.step(cp - done)
+        done = cp
+        got = s.get_state()
+        tol = 1e-11 if precision == capi.FP64 else 1e-5
+        for q, floor in ((1, 0.1), (2, 0.1), (3, 1.0)):
+            assert rel(got[q], ref[q], floor) < tol, (cp, q, rel(got[q], ref[q], floor))
+        nu_ref = 0.5 * (orc.nusselt(p, ref, 0) + orc.nusselt(p, ref, 1))
+        nu_gpu = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+        assert abs(nu_gpu - nu_ref) / abs(nu_ref) < (1e-10 if precision == capi.FP64 else 1e-4)
+    s.close()
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_mass_conserved_to_round_off_on_gpu(orc, kernel):
     nx, ny = 40, 24
