@@ -628,6 +628,9 @@ static void update_cells(const orc_problem* p, work* w, double* rho, double* u, 
     }
     res[0] = su_den > 0.0 ? sqrt(su_num) / sqrt(su_den) : INFINITY;
     res[1] = sT_den > 0.0 ? sqrt(sT_num) / sqrt(sT_den) : INFINITY;
+    /* a state that is no longer a number has no residual: divergence */
+    if (isnan(su_num) || isnan(su_den)) res[0] = NAN;
+    if (isnan(sT_num) || isnan(sT_den)) res[1] = NAN;
 }
 
 /* ------------------------------------------------------------------ */

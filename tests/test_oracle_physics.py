@@ -295,3 +295,32 @@ def test_cavity_ra1e3_against_table1(orc):
     # hot fluid rises: the flow leaves the hot wall along the top
     assert abs(yc[u_c.argmax()] - gold["u_max_y_over_L"]) < 0.02
     assert abs(xc[v_c.argmax()] - gold["v_max_x_over_L"]) < 0.02
+
+
+def test_non_finite_state_is_divergence(orc):
+    """A state that is no longer a number has no residual: the run stops as
+    diverged on that step (the convergence test of Section 3.3, Eq. 65,
+    needs finite sums)."""
+    p = orc.cavity_problem(12, 1e3)
+    st = list(inputs.conduction_state(p.xf, p.yf))
+    st[1] = st[1].copy()
+    st[1][5, 5] = np.nan
+    _, steps, res, rc = orc.run_to_steady(p, st, 1e-9, 100)
+    assert rc == -4 and steps == 1 and np.isnan(res[0])
+    _, _, rc = orc.step(p, st, 3)
+    assert rc == -4
+
+
+def test_small_lattice_spacing_diverges(orc):
+    """Section 3.3 (Fig. 4): the terms scaled by the lattice spacing delta t
+    are the numerical dissipation; with delta t small they are too weak and
+    the heated cavity diverges, with delta t of the cell size it does not
+    (20 x 20 unit cells, Ra = 1e6, Pr = 0.71, V_c = 0.1, Delta t = 0.5)."""
+    out = {}
+    for kappa in (0.1, 0.5, 1.0):
+        p = orc.cavity_problem(20, 1e6)
+        p.kappa = kappa
+        _, steps, _, rc = orc.run_to_steady(p, inputs.conduction_state(p.xf, p.yf), 1e-12, 2000)
+        out[kappa] = (rc, steps)
+    assert out[0.1][0] == -4 and out[0.1][1] < 2000
+    assert out[0.5][0] == -5 and out[1.0][0] == -5
