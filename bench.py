@@ -59,6 +59,20 @@ WORKLOADS = {
              "Nusselt number",
         nx=1024, ny=512, phi=0.0, Ra=1e6, Pr=0.71, Ma=0.1, precision="fp32", sample_every=2000,
         window=25, onset=1.5, max_steps=2_000_000, kind="rb_steady"),
+    "stability_fig4": dict(
+        desc="stability map of Section 3.3, Fig. 4: differentially heated cavity 50x50 unit "
+             "cells, Pr=0.71, V_c=0.1, Delta t=0.5, Ra in 1e3..1e8 x lattice spacing delta t in "
+             "0.1..1.5, to max(R_u, R_T) < 1e-9, divergence or 200k steps, all cases in one batch",
+        grid_n=[50], grid_Ra=[1e3, 1e4, 1e5, 1e6, 1e7, 1e8],
+        grid_kappa=[0.1, 0.15, 0.2, 0.3, 0.5, 0.7, 1.0, 1.5], dt=0.5, tol=1e-9,
+        max_steps=200000, precision="fp32", kind="stability"),
+    "stability_fig5": dict(
+        desc="stability map of Section 3.3, Fig. 5: differentially heated cavity N x N unit "
+             "cells, N in 10..200, delta t = 1, Pr=0.71, V_c=0.1, Delta t=0.5, Ra in 1e3..1e8, "
+             "to max(R_u, R_T) < 1e-9, divergence or 200k steps, all cases in one batch",
+        grid_n=[10, 20, 30, 50, 70, 100, 150, 200], grid_Ra=[1e3, 1e4, 1e5, 1e6, 1e7, 1e8],
+        grid_kappa=[1.0], dt=0.5, tol=1e-9, max_steps=200000, precision="fp32",
+        kind="stability"),
     "cavity8192": dict(
         desc="roofline probe: differentially heated cavity 8192x8192, tanh phi=2.0, Ra=1e8, "
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
@@ -569,7 +583,66 @@ def run_rb_steady(args, w):
     print(json.dumps(line), flush=True)
 
 
+def stability_cases(w):
+    return [(n, Ra, k) for n in w["grid_n"] for Ra in w["grid_Ra"] for k in w["grid_kappa"]]
+
+
+def run_stability(args, w):
+    """Section 3.3's stability maps through rtlbfs_stability_map: every
+    (N, Ra, delta t) case of the grid in one batch, each run until it
+    converges, diverges or hits the step cap."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2202_13449_gb300 import capi
+    capi.lib()
+    cases = stability_cases(w)
+    n, Ra, kappa = (np.array(c) for c in zip(*cases))
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
+    clk = ClockSampler(0)
+    clk.start()
+    l0 = capi.launch_count()
+    status, steps, el = capi.stability_map(n, Ra, kappa, np.full(len(cases), w["dt"]),
+                                           tol=w["tol"], max_steps=w["max_steps"],
+                                           precision=prec, chunk_steps=256)
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    name = {capi.SLOT_CONVERGED: "converged", capi.SLOT_DIVERGED: "diverged",
+            capi.SLOT_MAX_STEPS: "step cap"}
+    updates = float(np.sum(steps * n.astype(np.float64) ** 2))
+    # Fig. 4's trend: at each (N, Ra) the cases that did not diverge form an
+    # upper range of delta t
+    trend = True
+    for nn in w["grid_n"]:
+        for ra in w["grid_Ra"]:
+            row = [status[k] for k, c in enumerate(cases) if c[0] == nn and c[1] == ra]
+            ok = [x != capi.SLOT_DIVERGED for x in row]
+            trend = trend and all(ok[i] <= ok[i + 1] for i in range(len(ok) - 1))
+    line = {"metric": "stability map: M cell-updates/s of the batched cases (wall time of the "
+                      "call)",
+            "value": round(updates / el / 1e6, 2) if el > 0 else None,
+            "unit": "M cell-updates/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": round(el * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": w["precision"].replace("fp", "f"),
+            "data": "synthetic (conduction initial state)",
+            "config": {"workload": args.workload, "description": w["desc"], "cases": len(cases)},
+            "e2e": {"value": round(updates / el / 1e6, 2) if el > 0 else None,
+                    "unit": "M cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0,
+                    "note": "the call is the public API: cases in, outcomes out; states are "
+                            "built on the device"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "wall_s": round(el, 3),
+            "map": [{"N": int(c[0]), "Ra": c[1], "delta_t": c[2], "outcome": name.get(int(st)),
+                     "steps": int(sp)} for c, st, sp in zip(cases, status, steps)],
+            "counts": {v: int(np.sum(status == k)) for k, v in name.items()},
+            "small_delta_t_diverges_trend": trend}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "stability":
+        return run_stability(args, w)
     if w.get("kind") == "rb_steady":
         return run_rb_steady(args, w)
     if w.get("kind") == "accuracy":
@@ -862,7 +935,20 @@ def run_reference(args, w):
         }
         print(json.dumps(line), flush=True)
         return
-    if kind == "batch":
+    if kind == "stability":
+        probs = []
+        for nn, ra, ka in stability_cases(w)[:8]:
+            p = oracle.cavity_problem(nn, ra, dt=w["dt"])
+            p.kappa = ka
+            probs.append((p, inputs.conduction_state(p.xf, p.yf), nn * nn))
+        states = [st for _, st, _ in probs]
+        cells = sum(c for _, _, c in probs)
+
+        def one():
+            for k, (p, _, _) in enumerate(probs):
+                states[k], _, _ = oracle.step(p, states[k], per_step)
+        sample = f"the first 8 cases of the map ({cells} cells), {per_step} FP64 steps each"
+    elif kind == "batch":
         probs = batch_problems(oracle, inputs, w, 16)
         states = [st for _, st, _ in probs]
         cells = sum(c for _, _, c in probs)
@@ -886,9 +972,12 @@ def run_reference(args, w):
         one()
     dt = time.perf_counter() - t0
     value = cells * per_step * args.steps / dt / 1e6
+    metric = ("stability map: M cell-updates/s of the batched cases (wall time of the call)"
+              if kind == "stability" else
+              "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines")
     line = {
         "impl": "reference",
-        "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
+        "metric": metric,
         "value": round(value, 3), "unit": "M cell-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,

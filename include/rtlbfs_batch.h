@@ -59,6 +59,10 @@ int rtlbfs_batch_add(rtlbfs_batch_t b, int nx, int ny, const double* xf, const d
 int rtlbfs_batch_set_bc(rtlbfs_batch_t b, int slot, int side, int kind, double T_wall,
                         double u_wall);
 
+/* Lattice parameter of a slot (as rtlbfs_set_lattice: delta t_f = kappa *
+ * min(w_L, w_R), Eqs. 9-10).  ERR_ARG unless kappa > 0. */
+int rtlbfs_batch_set_lattice(rtlbfs_batch_t b, int slot, double kappa);
+
 /* State in/out of a slot (ny*nx doubles per field, rho/u/v/T). */
 int rtlbfs_batch_set_state(rtlbfs_batch_t b, int slot, const double* rho, const double* u,
                            const double* v, const double* T);
@@ -141,6 +145,30 @@ typedef struct {
  */
 int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* opts,
                  rtlbfs_result* out, double* elapsed_s);
+
+/* ------------------------------------------------------------------------ */
+/* Stability map                                                             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The stability test of Section 3.3 (Figs. 4 and 5) as one batch: case k is
+ * the differentially heated cavity of n[k] x n[k] unit cells (L = n[k]) at
+ * Rayleigh number Ra[k] with lattice parameter kappa[k] (on unit cells the
+ * paper's lattice spacing delta t = kappa[k]) and time step dt[k] (dt null
+ * or dt[k] = 0: the stability rule of rtlbfs_set_params), Prandtl number Pr,
+ * V_c = Ma, from the conduction state.  All cases advance together in
+ * launches of chunk_steps steps until each has converged (max(R_u, R_T) <
+ * tol after a step; tol <= 0: never), diverged (a non-finite residual, or in
+ * FP32 a value leaving the fixed-point range) or taken max_steps steps.
+ * status_out[k] receives RTLBFS_SLOT_CONVERGED, _DIVERGED or _MAX_STEPS and
+ * steps_out[k] the steps taken (the diverging step included); *elapsed_s
+ * the wall time.  Arrays of ncase; device memory is the library's and freed
+ * on return.  ERR_ARG on bad sizes or parameters, ERR_OOM, ERR_CUDA.
+ */
+int rtlbfs_stability_map(int ncase, const int* n, const double* Ra, const double* kappa,
+                         const double* dt, double Pr, double Ma, double tol, long max_steps,
+                         int precision, int chunk_steps, int* status_out, long* steps_out,
+                         double* elapsed_s);
 
 #ifdef __cplusplus
 }

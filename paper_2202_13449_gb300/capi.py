@@ -79,6 +79,7 @@ _SIGS = {
     "rtlbfs_batch_add": (C.c_int, [_vp, C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double,
                                    C.c_double, C.c_double, C.POINTER(C.c_int)]),
     "rtlbfs_batch_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]),
+    "rtlbfs_batch_set_lattice": (C.c_int, [_vp, C.c_int, C.c_double]),
     "rtlbfs_batch_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
     "rtlbfs_batch_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
     "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
@@ -95,6 +96,9 @@ _SIGS = {
     "rtlbfs_batch_destroy": (None, [_vp]),
     "rtlbfs_serve": (C.c_int, [C.POINTER(Request), C.c_int, C.POINTER(ServeOpts),
                                C.POINTER(Result), C.POINTER(C.c_double)]),
+    "rtlbfs_stability_map": (C.c_int, [C.c_int, C.POINTER(C.c_int), _dp, _dp, _dp, C.c_double,
+                                       C.c_double, C.c_double, C.c_long, C.c_int, C.c_int,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_long), _dp]),
     "rtlbfs_nusselt_noalloc": (C.c_int, [C.c_int, C.c_int, _dp, _dp, _vp, _vp, _vp, _vp,
                                          C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.POINTER(C.c_int), _dp, _dp, C.c_int, _vp, _vp]),
@@ -349,6 +353,10 @@ class Batch:
         self._check(lib().rtlbfs_batch_set_bc(self._h, slot, side, kind, T_wall, u_wall),
                     "batch_set_bc")
 
+    def set_lattice(self, slot, kappa):
+        self._check(lib().rtlbfs_batch_set_lattice(self._h, slot, float(kappa)),
+                    "batch_set_lattice")
+
     def set_state(self, slot, rho, u, v, T):
         ny, nx = self.shapes[slot]
         arrs = [_f64(a, nx * ny) for a in (rho, u, v, T)]
@@ -424,3 +432,23 @@ def serve(requests, *, max_slots=64, mem_fraction=0.5, tol=1e-8, max_steps=10000
     res = [dict(t_admit=r.t_admit, t_finish=r.t_finish, steps=r.steps, status=r.status,
                 nu_hot=r.nu_hot, nu_cold=r.nu_cold) for r in out[:n]]
     return res, float(el.value)
+
+
+def stability_map(n, Ra, kappa, dt=None, *, Pr=0.71, Ma=0.1, tol=1e-9, max_steps=200000,
+                  precision=FP32, chunk_steps=256):
+    """Section 3.3's stability test for cases (n[k], Ra[k], kappa[k], dt[k])
+    in one batch; returns (status array, steps array, elapsed seconds)."""
+    m = len(n)
+    nn = (C.c_int * max(m, 1))(*[int(x) for x in n])
+    ra = np.ascontiguousarray(Ra, dtype=np.float64)
+    ka = np.ascontiguousarray(kappa, dtype=np.float64)
+    dd = None if dt is None else np.ascontiguousarray(dt, dtype=np.float64)
+    st = (C.c_int * max(m, 1))()
+    steps = (C.c_long * max(m, 1))()
+    el = C.c_double(0)
+    rc = lib().rtlbfs_stability_map(m, nn, _ptr(ra), _ptr(ka), None if dd is None else _ptr(dd),
+                                    float(Pr), float(Ma), float(tol), int(max_steps),
+                                    int(precision), int(chunk_steps), st, steps, C.byref(el))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs_stability_map")
+    return np.array(st[:m]), np.array(steps[:m]), float(el.value)

@@ -123,6 +123,16 @@ int rtlbfs_batch_set_bc(rtlbfs_batch_t b, int slot, int side, int kind, double T
     return RTLBFS_OK;
 }
 
+int rtlbfs_batch_set_lattice(rtlbfs_batch_t b, int slot, double kappa)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    Cavity* c = b->eng->cavity(slot);
+    if (!c || !(kappa > 0)) return RTLBFS_ERR_ARG;
+    c->kappa = kappa;
+    b->eng->touch(slot);
+    return RTLBFS_OK;
+}
+
 int rtlbfs_batch_set_state(rtlbfs_batch_t b, int slot, const double* rho, const double* u,
                            const double* v, const double* T)
 {
@@ -309,6 +319,68 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
         }
     }
     if (elapsed_s) *elapsed_s = now();
+    return RTLBFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stability map
+// ---------------------------------------------------------------------------
+int rtlbfs_stability_map(int ncase, const int* n, const double* Ra, const double* kappa,
+                         const double* dt, double Pr, double Ma, double tol, long max_steps,
+                         int precision, int chunk_steps, int* status_out, long* steps_out,
+                         double* elapsed_s)
+{
+    if (ncase < 0 || !n || !Ra || !kappa || !status_out || !steps_out || !(Pr > 0) ||
+        !(Ma > 0) || max_steps < 1 || chunk_steps < 1)
+        return RTLBFS_ERR_ARG;
+    for (int k = 0; k < ncase; ++k) {
+        if (n[k] < 1 || !(Ra[k] > 0) || !(kappa[k] > 0) || (dt && !(dt[k] >= 0)))
+            return RTLBFS_ERR_ARG;
+        status_out[k] = -1;
+        steps_out[k] = 0;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    if (ncase == 0) {
+        if (elapsed_s) *elapsed_s = 0.0;
+        return RTLBFS_OK;
+    }
+    Engine eng(precision, ncase);
+    int rc = eng.init();
+    if (rc) return rc;
+    std::vector<double> faces;
+    std::vector<int> slot_of(ncase, -1);
+    for (int k = 0; k < ncase; ++k) {
+        faces.resize(n[k] + 1);
+        for (int i = 0; i <= n[k]; ++i) faces[i] = (double)i;  // unit cells, L = n
+        int s = -1;
+        if ((rc = eng.add(n[k], n[k], faces.data(), faces.data(), &s))) return rc;
+        Cavity* c = eng.cavity(s);
+        c->from_ra = true;
+        c->Ra = Ra[k];
+        c->Pr = Pr;
+        c->Ma = Ma;
+        c->kappa = kappa[k];
+        if (dt && dt[k] > 0) c->dt = dt[k];
+        else c->dt_auto = true;
+        eng.touch(s);
+        if ((rc = eng.set_conduction_state(s))) return rc;
+        if ((rc = eng.arm(s, max_steps, tol > 0 ? tol : -1.0))) return rc;
+        slot_of[k] = s;
+    }
+    std::vector<CavityCtl> ctl;
+    for (;;) {
+        if ((rc = eng.launch_steps(chunk_steps))) return rc;
+        if ((rc = eng.read_ctls(ctl))) return rc;
+        bool all = true;
+        for (int k = 0; k < ncase; ++k) all = all && ctl[slot_of[k]].done;
+        if (all) break;
+    }
+    for (int k = 0; k < ncase; ++k) {
+        status_out[k] = slot_status(ctl[slot_of[k]]);
+        steps_out[k] = (long)ctl[slot_of[k]].steps;
+    }
+    if (elapsed_s)
+        *elapsed_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return RTLBFS_OK;
 }
 
