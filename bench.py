@@ -62,16 +62,24 @@ WORKLOADS = {
     "stability_fig4": dict(
         desc="stability map of Section 3.3, Fig. 4: differentially heated cavity 50x50 unit "
              "cells, Pr=0.71, V_c=0.1, Delta t=0.5, Ra in 1e3..1e8 x lattice spacing delta t in "
-             "0.1..1.5, to max(R_u, R_T) < 1e-9, divergence or 200k steps, all cases in one batch",
+             "0.1..1.5, FP32, to max(R_u, R_T) < 1e-7 (above the FP32 state's residual floor "
+             "of ~1.4e-8), divergence or 200k steps, all cases in one batch",
+        grid_n=[50], grid_Ra=[1e3, 1e4, 1e5, 1e6, 1e7, 1e8],
+        grid_kappa=[0.1, 0.15, 0.2, 0.3, 0.5, 0.7, 1.0, 1.5], dt=0.5, tol=1e-7,
+        max_steps=200000, precision="fp32", kind="stability"),
+    "stability_fig4_fp64": dict(
+        desc="stability map of Section 3.3, Fig. 4 in FP64 with Eq. 65's 1e-9 (as the R12 "
+             "residual): 50x50 unit cells, Pr=0.71, V_c=0.1, Delta t=0.5, Ra in 1e3..1e8 x "
+             "delta t in 0.1..1.5, to convergence, divergence or 400k steps, one batch",
         grid_n=[50], grid_Ra=[1e3, 1e4, 1e5, 1e6, 1e7, 1e8],
         grid_kappa=[0.1, 0.15, 0.2, 0.3, 0.5, 0.7, 1.0, 1.5], dt=0.5, tol=1e-9,
-        max_steps=200000, precision="fp32", kind="stability"),
+        max_steps=400000, precision="fp64", kind="stability"),
     "stability_fig5": dict(
         desc="stability map of Section 3.3, Fig. 5: differentially heated cavity N x N unit "
              "cells, N in 10..200, delta t = 1, Pr=0.71, V_c=0.1, Delta t=0.5, Ra in 1e3..1e8, "
-             "to max(R_u, R_T) < 1e-9, divergence or 200k steps, all cases in one batch",
+             "FP32, to max(R_u, R_T) < 1e-7, divergence or 200k steps, all cases in one batch",
         grid_n=[10, 20, 30, 50, 70, 100, 150, 200], grid_Ra=[1e3, 1e4, 1e5, 1e6, 1e7, 1e8],
-        grid_kappa=[1.0], dt=0.5, tol=1e-9, max_steps=200000, precision="fp32",
+        grid_kappa=[1.0], dt=0.5, tol=1e-7, max_steps=200000, precision="fp32",
         kind="stability"),
     "cavity8192": dict(
         desc="roofline probe: differentially heated cavity 8192x8192, tanh phi=2.0, Ra=1e8, "
@@ -1005,7 +1013,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--max-steps", type=int, default=2000, help="serve: step cap per request")
-    ap.add_argument("--tol", type=float, default=1e-8, help="serve: steady tolerance")
+    ap.add_argument("--tol", type=float, default=1e-7,
+                    help="serve: steady tolerance (above the FP32 residual floor ~1.4e-8)")
     ap.add_argument("--time-limit", type=float, default=60.0, help="serve: wall-clock cap (s)")
     ap.add_argument("--slots", type=int, default=256, help="serve: concurrent cavities")
     ap.add_argument("--fp64-sample", type=int, default=20, help="serve: FP64 comparator sample")
