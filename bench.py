@@ -242,6 +242,33 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_max(x: float, device="cuda") -> float:
+    """Max of x over the ranks of the job (x itself in a one-process job)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_sum(x: float, device="cuda") -> float:
+    """Sum of x over the ranks of the job."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank: int, world: int):
+    """This rank's share of independent work items (round robin)."""
+    return list(items)[rank::world]
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -331,11 +358,7 @@ def run_batch(args, w):
     torch.cuda.synchronize()
     launches = capi.launch_count() - l0
     clocks = clk.stop()
-    ms = sum(a.elapsed_time(e) for a, e in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = job_max(sum(a.elapsed_time(e) for a, e in ev))
     status, steps, res = b.poll()
     all_running = all(st == capi.SLOT_RUNNING for st in status[:len(specs)])
     value = cells * inner * args.steps * ws / (ms * 1e-3) / 1e6
@@ -362,10 +385,7 @@ def run_batch(args, w):
         for s in slots:
             out = b.get_state(s)
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_e2e, op=torch.distributed.ReduceOp.MAX)
-    e2e = cells * inner * e2e_steps * ws / float(t_e2e.item()) / 1e6
+    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     bytes_io = 4 * 8 * cells
     line = {
         "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
@@ -400,16 +420,23 @@ def run_batch(args, w):
 
 def run_serve(args, w):
     """Config-5 style workload: the request loop on a seeded trace, plus the
-    plain per-request FP64 comparator on a sample of the same requests."""
+    plain per-request FP64 comparator on a sample of the same requests.
+    With N ranks each GPU serves every N-th request of the trace (independent
+    cavities: no exchange between GPUs); solves/s is the job's total over the
+    slowest rank's wall time."""
     import numpy as np
     import torch
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2202_13449_gb300 import capi, inputs
     capi.lib()
     trace = inputs.serving_trace(w["count"], w["seed"], w["rate"])
-    reqs = [(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace]
+    reqs = shard([(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace], rank, ws)
     cap, tol = args.max_steps, args.tol
-    clk = ClockSampler(0)
+    clk = ClockSampler(local)
     clk.start()
     l0 = capi.launch_count()
     res, el = capi.serve(reqs, max_slots=args.slots, tol=tol, max_steps=cap, chunk_steps=128,
@@ -417,12 +444,14 @@ def run_serve(args, w):
     launches = capi.launch_count() - l0
     clocks = clk.stop()
     done = [(q, r) for q, r in zip(reqs, res) if r["status"] >= 0]
+    finished_job = int(job_sum(len(done)))
+    el_job = job_max(el)
     diverged = sum(1 for _, r in done if r["status"] == capi.SLOT_DIVERGED)
     lat = np.array([r["t_finish"] - q[0] for q, r in done]) if done else np.array([np.nan])
     conv = sum(1 for _, r in done if r["status"] == capi.SLOT_CONVERGED)
     capped = sum(1 for _, r in done if r["status"] == capi.SLOT_MAX_STEPS)
     # plain per-request FP64 on the first finished requests, alone, one at a time
-    sample = done[:args.fp64_sample]
+    sample = done[:args.fp64_sample] if rank == 0 else []
     t0 = time.perf_counter()
     errs = []
     for q, r in sample:
@@ -440,22 +469,26 @@ def run_serve(args, w):
     updates = sum(q[1] * q[1] * r["steps"] for q, r in done)
     line = {
         "metric": "batched solves/s and p50/p99 time-to-steady (request loop)",
-        "value": round(len(done) / el, 3) if el > 0 else None, "unit": "solves/s",
-        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(el * 1e3, 1),
+        "value": round(finished_job / el_job, 3) if el_job > 0 else None, "unit": "solves/s",
+        "n_gpus": ws, "steps": 1, "warmup": 0, "ms_per_step": round(el_job * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; no dataset)",
-        "config": {"workload": args.workload, "description": w["desc"], "requests": len(reqs),
+        "config": {"workload": args.workload, "description": w["desc"],
+                   "requests": w["count"], "requests_this_rank": len(reqs),
                    "max_steps_cap": cap, "tol": tol, "time_limit_s": args.time_limit,
-                   "slots": args.slots},
-        "finished": len(done), "converged": conv, "hit_step_cap": capped, "diverged": diverged,
+                   "slots": args.slots, "parallelism": f"trace sharded over {ws} GPU(s)"},
+        "finished": finished_job, "converged": conv, "hit_step_cap": capped, "diverged": diverged,
         "unfinished": len(reqs) - len(done),
+        "counts_scope": "finished: the whole job; converged/capped/diverged/unfinished and the "
+                        "latency percentiles: rank 0's share of the trace",
         "time_to_steady_s": {"p50": float(np.nanpercentile(lat, 50)),
                              "p99": float(np.nanpercentile(lat, 99)),
                              "note": "arrival to retirement; queue-dominated at this load"},
         "fp64_per_request": {"requests": len(sample), "solves_per_s": round(len(sample) / t64, 3)
                              if t64 > 0 else None,
                              "max_rel_err_mean_wall_nu_fp32_vs_fp64": max(errs) if errs else None},
-        "e2e": {"value": round(len(done) / el, 3) if el > 0 else None, "unit": "solves/s",
+        "e2e": {"value": round(finished_job / el_job, 3) if el_job > 0 else None,
+                "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * len(done),
                 "note": "the request loop is the public call: requests from the host, "
                         "conduction states and faces uploaded per admission, Nusselt numbers "
@@ -464,10 +497,13 @@ def run_serve(args, w):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         steps_by_req = [r["steps"] if r["status"] >= 0 else cap for r in res]
         line["cpu_baseline"] = cpu_baseline_serve(w, reqs, steps_by_req, args.cpu_seconds)
-    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_accuracy(args, w):
@@ -713,11 +749,7 @@ def run_ours(args, w):
     t_wall = time.perf_counter() - t_wall
     launches = capi.launch_count() - l0
     clocks = clk.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = job_max(sum(a.elapsed_time(b) for a, b in ev))
     updates = cells * inner * args.steps * ws
     value = updates / (ms_max * 1e-3) / 1e6
 
@@ -732,10 +764,7 @@ def run_ours(args, w):
         s.step(inner)
         out = s.get_state()
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_e2e, op=torch.distributed.ReduceOp.MAX)
-    e2e = cells * inner * e2e_steps * ws / float(t_e2e.item()) / 1e6
+    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     assert np.all(np.isfinite(out[3]))
     bytes_io = 4 * cells * 8
 
