@@ -185,8 +185,9 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
  * order): kernel 0 = warp-marching strips (each warp walks a 28-column strip
  * up a chunk of chunk_rows rows, rolling its stencil window in registers;
  * chunk_rows 0 = chosen from the GPU size), kernel 1 = shared-memory tiles
- * of 32 columns by chunk_rows rows (16, 14, 12, 10 or 8 in FP32, 16 in
- * FP64; 0 = the height whose tile count fills the SMs most evenly).
+ * of 32 columns by chunk_rows rows (16, 14, 12, 10, 8, 4 or 2 in FP32; 16,
+ * 8, 4 or 2 in FP64; 0 = the height whose tile count fills the SMs most
+ * evenly).
  * ERR_ARG on other values.
  */
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);

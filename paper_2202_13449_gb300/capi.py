@@ -253,8 +253,8 @@ class Solver:
 
     def set_schedule(self, kernel: int = 0, chunk_rows: int = 0):
         """kernel 0: warp-marching strips (chunk_rows rows per unit), 1:
-        shared-memory tiles (chunk_rows = tile height: 16, 14, 12, 10 or 8 in
-        FP32, 16 in FP64); chunk_rows 0 picks automatically."""
+        shared-memory tiles (chunk_rows = tile height: 16, 14, 12, 10, 8, 4 or
+        2 in FP32; 16, 8, 4 or 2 in FP64); chunk_rows 0 picks automatically."""
         self._check(lib().rtlbfs_set_schedule(self._h, int(kernel), int(chunk_rows)),
                     "set_schedule")
 

@@ -407,8 +407,8 @@ int Engine::set_chunk_rows(int rows)
     if (rows < 0) return fail(RTLBFS_ERR_ARG, "chunk rows must be >= 0");
     if (kernel_ == 1 && rows != 0 && !tile_height_ok(precision_, rows))
         return fail(RTLBFS_ERR_ARG, precision_ == RTLBFS_FP64
-                                        ? "FP64 tile height must be 16 (or 0)"
-                                        : "tile height must be one of 16, 14, 12, 10, 8 (or 0)");
+                                        ? "FP64 tile height must be one of 16, 8, 4, 2 (or 0)"
+                                        : "tile height must be one of 16, 14, 12, 10, 8, 4, 2 (or 0)");
     chunk_rows_ = rows;
     tiles_dirty_ = true;
     return RTLBFS_OK;
@@ -420,10 +420,10 @@ int Engine::set_chunk_rows(int rows)
 // the residual), in face-equivalents: 65 h + 32 + 0.25 * 34 (h + 2) + 300.
 int Engine::pick_tile_height() const
 {
-    if (precision_ == RTLBFS_FP64) return kTileYDefault;
     int best_h = kTileYDefault;
     double best = 1e300;
     for (int h : kTileHeights) {
+        if (!tile_height_ok(precision_, h)) continue;
         long long tiles = 0;
         for (int s = 0; s < capacity_; ++s)
             if (slots_[s].active)

@@ -12,21 +12,18 @@ namespace rtlbfs {
 // the compiled heights below, 16 threads per tile row (two cells per thread
 // in the update).  The height is picked per cavity set so that the number of
 // tiles fills the SMs evenly (a 512-row mesh in 16-row tiles leaves a third
-// of the SMs one tile short).  FP64 is compiled for the default height only.
+// of the SMs one tile short); the low heights spread small meshes over many
+// SMs, which matters most in FP64, where an SM does 2 FMAs per clock.
 constexpr int kTileX = 32;
-constexpr int kTileHeights[] = {16, 14, 12, 10, 8};
+constexpr int kTileHeights[] = {16, 14, 12, 10, 8, 4, 2};
 constexpr int kTileYDefault = 16;
 inline bool tile_height_ok(int precision, int h)
 {
-    if (precision == 0) return h == kTileYDefault;
+    if (precision == 0) return h == 16 || h == 8 || h == 4 || h == 2;
     for (int t : kTileHeights)
         if (t == h) return true;
     return false;
 }
-
-#ifndef RTLBFS_PAIR_FACES
-#define RTLBFS_PAIR_FACES 0  // 1: x- and y-face in one packed FP32x2 evaluation
-#endif
 #ifndef RTLBFS_MARCH_THREADS
 #define RTLBFS_MARCH_THREADS 128
 #endif
@@ -47,7 +44,7 @@ struct NuLines {
     const CellLine<double>* yc;
 };
 
-// tile_h: one of kTileHeights (FP32) or kTileYDefault (FP64)
+// tile_h: a height tile_height_ok accepts for the precision
 cudaError_t step_prepare(int precision);
 cudaError_t step_occupancy(int precision, int tile_h, int* blocks_per_sm);
 cudaError_t launch_step(int precision, int tile_h, int grid, cudaStream_t s,

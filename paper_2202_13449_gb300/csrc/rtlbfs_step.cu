@@ -658,34 +658,21 @@ __global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double t
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-#ifndef RTLBFS_TILE_THREADS_16
-#define RTLBFS_TILE_THREADS_16 256
-#endif
-#ifndef RTLBFS_TILE_THREADS_14
-#define RTLBFS_TILE_THREADS_14 224
-#endif
-#ifndef RTLBFS_TILE_THREADS_12
-#define RTLBFS_TILE_THREADS_12 192
-#endif
-#ifndef RTLBFS_TILE_THREADS_10
-#define RTLBFS_TILE_THREADS_10 160
-#endif
-#ifndef RTLBFS_TILE_THREADS_8
-#define RTLBFS_TILE_THREADS_8 128
-#endif
-// threads of the block for a tile height
-constexpr int tile_threads(int ty)
-{
-    return ty == 16 ? RTLBFS_TILE_THREADS_16
-         : ty == 14 ? RTLBFS_TILE_THREADS_14
-         : ty == 12 ? RTLBFS_TILE_THREADS_12
-         : ty == 10 ? RTLBFS_TILE_THREADS_10
-                    : RTLBFS_TILE_THREADS_8;
-}
+// Threads of a tile block: two cells per thread in the update; one cell per
+// thread for the small FP64 tiles, whose point is to spread the narrow FP64
+// units' work over as many SM sub-partitions as possible.
+template <class P, int TY>
+struct TileThreads {
+    static constexpr int value = 16 * TY;
+};
+template <int TY>
+struct TileThreads<StoreD, TY> {
+    static constexpr int value = TY <= 8 ? 32 * TY : 16 * TY;
+};
 
 template <class P, int TY>
 struct TileKernel {
-    static constexpr int NT = tile_threads(TY);
+    static constexpr int NT = TileThreads<P, TY>::value;
     static constexpr size_t smem = sizeof(TileSmem<P, kTileX, TY, NT>);
     static constexpr auto fn = step_kernel<P, kTileX, TY, NT>;
     static cudaError_t prepare()
@@ -714,8 +701,13 @@ template <class Op>
 static cudaError_t with_tile_kernel(int precision, int tile_h, Op op)
 {
     if (precision == 0) {
-        if (tile_h == 16) return op(TileKernel<StoreD, 16>());
-        return cudaErrorInvalidValue;
+        switch (tile_h) {
+        case 16: return op(TileKernel<StoreD, 16>());
+        case 8: return op(TileKernel<StoreD, 8>());
+        case 4: return op(TileKernel<StoreD, 4>());
+        case 2: return op(TileKernel<StoreD, 2>());
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (tile_h) {
     case 16: return op(TileKernel<StoreQ, 16>());
@@ -723,14 +715,16 @@ static cudaError_t with_tile_kernel(int precision, int tile_h, Op op)
     case 12: return op(TileKernel<StoreQ, 12>());
     case 10: return op(TileKernel<StoreQ, 10>());
     case 8: return op(TileKernel<StoreQ, 8>());
+    case 4: return op(TileKernel<StoreQ, 4>());
+    case 2: return op(TileKernel<StoreQ, 2>());
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t step_prepare(int precision)
 {
-    if (precision == 0) return TileKernel<StoreD, 16>::prepare();
     for (int h : kTileHeights) {
+        if (!tile_height_ok(precision, h)) continue;
         cudaError_t e = with_tile_kernel(precision, h, [](auto k) { return k.prepare(); });
         if (e != cudaSuccess) return e;
     }

@@ -97,7 +97,8 @@ def test_single_step_matches_oracle(orc, name, precision, kernel):
     assert rel(got[3], ref[3], 1.0) < tol
 
 
-TILE_HEIGHTS = [16, 14, 12, 10, 8]  # compiled tile heights of the FP32 tile kernel
+TILE_HEIGHTS = [16, 14, 12, 10, 8, 4, 2]  # compiled tile heights of the FP32 tile kernel
+TILE_HEIGHTS_FP64 = [16, 8, 4, 2]
 
 
 @pytest.mark.parametrize("tile_h", TILE_HEIGHTS)
@@ -110,6 +111,15 @@ def test_every_tile_height_matches_oracle_fp32(orc, name, tile_h):
     assert np.max(np.abs(got[0] - ref[0])) < 1e-6
     for q, floor in ((1, 1e-2), (2, 1e-2), (3, 1.0)):
         assert rel(got[q], ref[q], floor) < 1e-5, (q, rel(got[q], ref[q], floor))
+
+
+@pytest.mark.parametrize("tile_h", TILE_HEIGHTS_FP64)
+@pytest.mark.parametrize("name", ["cavity_irregular_lid", "rb_periodic_x_stretched_y",
+                                  "periodic_y_walls_x", "tiny_1x5"])
+def test_every_fp64_tile_height_matches_oracle(orc, name, tile_h):
+    ref, got, _ = run_case(orc, name, capi.FP64, 3, 1, tile_h)
+    for q, floor in ((0, 1.0), (1, 1e-2), (2, 1e-2), (3, 1.0)):
+        assert rel(got[q], ref[q], floor) < 1e-12, (q, rel(got[q], ref[q], floor))
 
 
 def test_tile_height_is_validated():
