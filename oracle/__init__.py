@@ -12,7 +12,8 @@ Functions mirror the C entry points (see the header comment of
 * ``tanh_faces`` -- Eq. 74 mesh faces
 * ``params_from_ra`` -- Eq. 63 / Eqs. 9-10 transport coefficients
 * ``Problem`` -- mesh, physics and boundary conditions
-* ``step`` / ``run_to_steady`` -- explicit RTLBFS steps (Eqs. 55-59, 64)
+* ``step`` / ``run_to_steady`` -- explicit RTLBFS steps (Eqs. 55-59, 64), or
+  TLBFS steps (Section 2.2, Eqs. 29-43) with ``Problem.scheme = TLBFS``
 * ``gradients`` / ``face`` / ``fluxes`` / ``nusselt`` -- intermediate results
 """
 from __future__ import annotations
@@ -31,6 +32,7 @@ _OUT = os.path.join(_HERE, "_build", "librtlbfs_oracle.so")
 W, E, S, N = 0, 1, 2, 3
 DIRICHLET, ADIABATIC, PERIODIC = 0, 1, 2
 NU_W, NU_E, NU_S, NU_N, NU_A, NU_HALF = 0, 1, 2, 3, 4, 5
+RTLBFS, TLBFS = 0, 1  # face stage of Problem.scheme
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +59,7 @@ class _Problem(C.Structure):
         ("dt", C.c_double), ("kappa", C.c_double),
         ("fx", C.c_double), ("fy", C.c_double),
         ("bc_kind", C.c_int * 4), ("bc_T", C.c_double * 4), ("bc_u", C.c_double * 4),
+        ("scheme", C.c_int),
     ]
 
 
@@ -146,6 +149,7 @@ class Problem:
     bc_kind: tuple = (DIRICHLET, DIRICHLET, ADIABATIC, ADIABATIC)
     bc_T: tuple = (1.0, 0.0, 0.0, 0.0)
     bc_u: tuple = (0.0, 0.0, 0.0, 0.0)
+    scheme: int = 0  # 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2)
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -169,6 +173,7 @@ class Problem:
         p.bc_kind[:] = list(self.bc_kind)
         p.bc_T[:] = list(self.bc_T)
         p.bc_u[:] = list(self.bc_u)
+        p.scheme = int(self.scheme)
         return p
 
 

@@ -50,7 +50,16 @@
  *       printed in Eq. 64 would make it sink); body force (fx, fy) is an
  *       acceleration, source rho*(fx, fy)
  *   R12 residual: R_u = ||(|u|^{n+1} - |u|^n)||_2 / |||u|^{n+1}||_2,
- *       R_T likewise, plain sums over cells; a zero denominator gives inf
+ *       R_T likewise, plain sums over cells; a zero denominator gives inf,
+ *       a sum that is not a number gives NaN (divergence)
+ *
+ * Second face stage, scheme = 1: the original TLBFS of Section 2.2 that
+ * RTLBFS approximates -- steps 5-6 replaced by (a) D2Q9 equilibria (Eqs.
+ * 3-4, c_p = 1) at the nodes x_S - e_i dt_f, whose values are the step-4
+ * nodes (a, b) = -e_i; (b) the predicted variables as their moments, Eqs.
+ * 30-32, with the wall rule R8; (c) the fluxes of Eqs. 38-40 from the
+ * equilibria of the predicted variables and the non-equilibrium parts of
+ * Eqs. 33-34.  The update (Eqs. 41-43) is step 7 with the same source.
  *   Nu  wall and mid-plane Nusselt numbers are the discrete energy flux of
  *       step 6 summed over a face column, / (chi dT); Nu_a follows Eq. 69
  *       with cell values and Green-Gauss dT/dx.
@@ -81,6 +90,7 @@ typedef struct {
     int bc_kind[4];   /* per side W,E,S,N */
     double bc_T[4];   /* wall temperature (Dirichlet) */
     double bc_u[4];   /* tangential wall velocity */
+    int scheme;       /* 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2) */
 } orc_problem;
 
 /* ------------------------------------------------------------------ */
@@ -172,7 +182,8 @@ static int work_alloc(work* w, int nx, int ny)
 
 static int check_problem(const orc_problem* p)
 {
-    if (!p || p->nx < 1 || p->ny < 1 || !p->xf || !p->yf) return -1;
+    if (!p || (p->scheme != 0 && p->scheme != 1)) return -1;
+    if (p->nx < 1 || p->ny < 1 || !p->xf || !p->yf) return -1;
     for (int i = 0; i < p->nx; ++i)
         if (!(p->xf[i + 1] > p->xf[i])) return -1;
     for (int j = 0; j < p->ny; ++j)
@@ -508,12 +519,94 @@ static void face_from_nodes(const orc_problem* p, int nd, double h, int wall_sid
 #undef C0
 }
 
+/* D2Q9 (Eqs. 5-6): discrete velocities in the order printed, weights. */
+static const int E9[9][2] = {{0, 0}, {1, 0},  {0, 1},   {-1, 0}, {0, -1},
+                             {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+static const double W9[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+/* Eq. 3 */
+static double f_equilibrium(int i, double r, double u, double v)
+{
+    double eu = E9[i][0] * u + E9[i][1] * v;
+    return W9[i] * r * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - (u * u + v * v) / (2.0 * CS2));
+}
+
+/* Eq. 4 with c_p = 1 */
+static double g_equilibrium(int i, double r, double u, double v, double T)
+{
+    double eu = E9[i][0] * u + E9[i][1] * v;
+    return W9[i] * r * T * (1.0 + eu / CS2);
+}
+
+/*
+ * TLBFS steps (a)-(c) of Section 2.2 for a face with normal along axis nd,
+ * from the node primitives o->node (step 4).
+ */
+static void face_tlbfs_from_nodes(const orc_problem* p, int nd, double h, int wall_side,
+                                  orc_face_out* o)
+{
+    o->h = h;
+    o->tau_f = p->nu / (CS2 * h) + 0.5;  /* Eq. 9 */
+    o->tau_g = p->chi / (CS2 * h) + 0.5; /* Eq. 10 */
+
+    /* (a) equilibria at x_S - e_i dt: node (a, b) = -e_i (R5) */
+    double fn[9], gn[9];
+    for (int i = 0; i < 9; ++i) {
+        int a = -E9[i][0] + 1, b = -E9[i][1] + 1;
+        double r = o->node[Q_RHO][a][b], u = o->node[Q_U][a][b];
+        double v = o->node[Q_V][a][b], T = o->node[Q_T][a][b];
+        fn[i] = f_equilibrium(i, r, u, v);
+        gn[i] = g_equilibrium(i, r, u, v, T);
+    }
+
+    /* (b) predicted variables, Eqs. 30-32 */
+    double rho_s = 0.0, m_s[2] = {0.0, 0.0}, E_s = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        rho_s += fn[i];
+        m_s[0] += E9[i][0] * fn[i];
+        m_s[1] += E9[i][1] * fn[i];
+        E_s += gn[i];
+    }
+    if (wall_side >= 0) { /* R8 */
+        int td = 1 - nd;
+        m_s[nd] = 0.0;
+        m_s[td] = rho_s * p->bc_u[wall_side];
+        if (p->bc_kind[wall_side] == BC_DIRICHLET) E_s = rho_s * p->bc_T[wall_side];
+    }
+    o->pred[0] = rho_s;
+    o->pred[1] = m_s[0];
+    o->pred[2] = m_s[1];
+    o->pred[3] = E_s;
+    double us = m_s[0] / rho_s, vs = m_s[1] / rho_s, Ts = E_s / rho_s;
+
+    /* (c) fluxes, Eqs. 38-40 (beta = nd), with the non-equilibrium parts of
+     * Eqs. 33-34: f^(1) = -tau (f_eq(x_S, t+dt) - f_eq(x_S - e dt, t)) */
+    double P = 0.0, Pi[2] = {0.0, 0.0}, Q = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        double fs = f_equilibrium(i, rho_s, us, vs);
+        double gs = g_equilibrium(i, rho_s, us, vs, Ts);
+        double en = E9[i][nd];
+        P += en * fs;
+        for (int al = 0; al < 2; ++al)
+            Pi[al] += E9[i][al] * en * (fs + (0.5 - o->tau_f) * (fs - fn[i]));
+        Q += en * (gs + (0.5 - o->tau_g) * (gs - gn[i]));
+    }
+    o->flux[0] = P;
+    o->flux[1] = Pi[0];
+    o->flux[2] = Pi[1];
+    o->flux[3] = Q;
+}
+
 /* One face from its two cells: steps 4-6. */
 static void face_compute(const orc_problem* p, int nd, const cell_view* L, const cell_view* R,
                          double h, int wall_side, orc_face_out* o)
 {
     face_nodes(nd, L, R, h, o->node);
-    face_from_nodes(p, nd, h, wall_side, o);
+    if (p->scheme == 1)
+        face_tlbfs_from_nodes(p, nd, h, wall_side, o);
+    else
+        face_from_nodes(p, nd, h, wall_side, o);
 }
 
 /* Build the L/R views of x-face (i, j) (between cells i-1 and i) or of
@@ -768,7 +861,10 @@ int orc_face_from_nodes(const orc_problem* p, int nd, const double* nodes, doubl
         wall_side > 3)
         return -1;
     memcpy(o->node, nodes, sizeof(o->node));
-    face_from_nodes(p, nd, h, wall_side, o);
+    if (p->scheme == 1)
+        face_tlbfs_from_nodes(p, nd, h, wall_side, o);
+    else
+        face_from_nodes(p, nd, h, wall_side, o);
     return 0;
 }
 
