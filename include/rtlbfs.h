@@ -180,6 +180,23 @@ int rtlbfs_residual(rtlbfs_t h, double* res2, long* steps);
  */
 int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
 
+/* Face stages (rtlbfs_set_scheme). */
+#define RTLBFS_SCHEME_RTLBFS 0
+#define RTLBFS_SCHEME_TLBFS 1
+
+/*
+ * Face stage of the step.  RTLBFS_SCHEME_RTLBFS (the default): the
+ * reconstructed solver of Section 3.2 (Eqs. 46-48, 57-59).
+ * RTLBFS_SCHEME_TLBFS: the original TLBFS of Section 2.2 that RTLBFS
+ * approximates -- D2Q9 equilibria (Eqs. 3-4) at the nodes x_S - e_i dt_f
+ * (Eq. 29 values), predicted variables as their moments (Eqs. 30-32) and
+ * fluxes from the equilibria and non-equilibrium parts (Eqs. 33-40); same
+ * update, source, boundary and run-control rules.  TLBFS runs on the tile
+ * kernel at height 16 (it sets that schedule).  The Nusselt numbers use
+ * the energy flux of the chosen stage.  ERR_ARG on another value.
+ */
+int rtlbfs_set_scheme(rtlbfs_t h, int scheme);
+
 /*
  * Execution schedule of the step (results are the same up to FP rounding
  * order): kernel 0 = warp-marching strips (each warp walks a 28-column strip
@@ -188,7 +205,8 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu);
  * of 32 columns by chunk_rows rows (16, 14, 12, 10, 8, 4 or 2 in FP32; 16,
  * 8, 4 or 2 in FP64; 0 = the height whose tile count fills the SMs most
  * evenly).
- * ERR_ARG on other values.
+ * ERR_ARG on other values, and on anything but the tile kernel at height
+ * 16 (or 0) under the TLBFS face stage.
  */
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
 
@@ -224,6 +242,10 @@ const char* rtlbfs_last_error(rtlbfs_t h);
  * Host-only; needs no GPU.  Null pointers are skipped.  Returns RTLBFS_OK.
  */
 int rtlbfs_op_counts(double* face_ops, double* cell_ops, double* sfu_ops);
+
+/* The same for a face stage: RTLBFS_SCHEME_RTLBFS or RTLBFS_SCHEME_TLBFS.
+ * ERR_ARG on another scheme. */
+int rtlbfs_op_counts_scheme(int scheme, double* face_ops, double* cell_ops, double* sfu_ops);
 
 /* Free every device and host resource of h; NULL is ignored. */
 void rtlbfs_destroy(rtlbfs_t h);

@@ -19,6 +19,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
 FP64, FP32 = 0, 1
+RTLBFS, TLBFS = 0, 1  # face stages (set_scheme)
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC = 0, 1, 2
 NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
@@ -73,6 +74,8 @@ _SIGS = {
     "rtlbfs_destroy": (None, [_vp]),
     "rtlbfs_launch_count": (C.c_longlong, []),
     "rtlbfs_op_counts": (C.c_int, [_dp, _dp, _dp]),
+    "rtlbfs_op_counts_scheme": (C.c_int, [C.c_int, _dp, _dp, _dp]),
+    "rtlbfs_set_scheme": (C.c_int, [_vp, C.c_int]),
     "rtlbfs_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_vp)]),
     "rtlbfs_batch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     "rtlbfs_batch_free_bytes": (C.c_int, [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
@@ -182,11 +185,12 @@ def launch_count() -> int:
     return int(lib().rtlbfs_launch_count())
 
 
-def op_counts():
+def op_counts(scheme: int = 0):
     """(FP ops per face, FP ops per cell-update, SFU ops per cell-update) of
-    the step, each face and gradient evaluated once (host-only)."""
+    the step with face stage `scheme` (RTLBFS or TLBFS), each face and
+    gradient evaluated once (host-only)."""
     a, b, c = C.c_double(), C.c_double(), C.c_double()
-    rc = lib().rtlbfs_op_counts(C.byref(a), C.byref(b), C.byref(c))
+    rc = lib().rtlbfs_op_counts_scheme(int(scheme), C.byref(a), C.byref(b), C.byref(c))
     if rc:
         raise RTLBFSError(rc, "rtlbfs_op_counts")
     return a.value, b.value, c.value
@@ -250,6 +254,10 @@ class Solver:
 
     def set_physics(self, nu, chi, beta_g):
         self._check(lib().rtlbfs_set_physics(self._h, nu, chi, beta_g), "set_physics")
+
+    def set_scheme(self, scheme: int):
+        """Face stage: RTLBFS (0, Section 3.2) or TLBFS (1, Section 2.2)."""
+        self._check(lib().rtlbfs_set_scheme(self._h, int(scheme)), "set_scheme")
 
     def set_schedule(self, kernel: int = 0, chunk_rows: int = 0):
         """kernel 0: warp-marching strips (chunk_rows rows per unit), 1:

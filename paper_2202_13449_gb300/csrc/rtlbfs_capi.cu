@@ -272,6 +272,12 @@ int rtlbfs_nusselt(rtlbfs_t h, int which, double* nu)
     return finish(h, h->eng->nusselt(h->slot, which, nu));
 }
 
+int rtlbfs_set_scheme(rtlbfs_t h, int scheme)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->set_scheme(scheme));
+}
+
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows)
 {
     if (!cav(h)) return RTLBFS_ERR_ARG;

@@ -55,7 +55,8 @@ struct CellLine {
 struct CavityDesc {
     int nx, ny, pitch, ntiles;    // cells, row stride (elements), tiles of this cavity
     int kind[4];                  // boundary kind per side W,E,S,N
-    int tiles_x, tiles_y, tile_begin, pad0;
+    int tiles_x, tiles_y, tile_begin;
+    int scheme;  // face stage: 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2)
     double bcT[4], bcU[4];        // wall temperature, tangential wall velocity
     double beta_g, T_ref, fx, fy, dt, dT, nu, chi;
     // FP32 copies (a double -> float conversion runs on the narrow FP64
@@ -271,6 +272,104 @@ __host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const Cel
     // (rho u_n T)* - (rho u_n T)^n = Tbar (mn* - mn0) + mn* a* - mn0 a0
     F[3] = vfma(fl.m_chi_2h, dx_e,
                 vfma(fl.m_tg15, vfma(Tbar, mns_ - mnM, vfma(mns_, as_, T::bc(0.0) - mnM * M[3])), QnM));
+}
+
+// The original TLBFS face stage (Section 2.2), from the same inputs as
+// face_flux and in the same frame: (a) D2Q9 equilibria (Eqs. 3-4, c_p = 1)
+// at the nodes x_S - e_i h, i.e. node (a, b) = -e_i of the column form
+// above (Eq. 29); (b) the predicted variables as their moments (Eqs. 30-32),
+// then the wall rule; (c) the fluxes of Eqs. 38-40 from the equilibria of
+// the predicted variables and the non-equilibrium parts of Eqs. 33-34.
+// Equilibria are carried as deviations f_i - w_i and g_i - w_i Tbar: the
+// constants cancel in every moment used except the pressure c_s^2, which is
+// dropped from the normal momentum flux as in face_flux.  The Dirichlet
+// override of (rho T)* is omitted: it enters no flux (u*_n = 0 there).
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux_tlbfs(const CellNT<V>& L, const CellNT<V>& Rc,
+                                                        V Tbar, const FaceLine<V>& fl, V keep,
+                                                        V u_wall, V F[4])
+{
+    using T = vtraits<V>;
+    const V half = T::bc(0.5), one = T::bc(1.0), three = T::bc(3.0);
+    const V c45 = T::bc(4.5), c15 = T::bc(1.5);
+    // D2Q9 in the face frame (n, t); weights of Eq. 6
+    constexpr int en[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int et[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const V w0 = T::bc(4.0 / 9.0), w1 = T::bc(1.0 / 9.0), w2 = T::bc(1.0 / 36.0);
+    const V h = fl.h;
+    const V wL = fl.cL + h, mwR = fl.cR - h;
+    const V hh = h * half;
+    // columns a = -1 (left plane), 0 (mean), +1 (right plane): value + b slope
+    V C[3][4], Sl[3][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        C[0][k] = vfma(L.gn[k], fl.cL, L.q[k]);
+        Sl[0][k] = L.gt[k] * h;
+        C[2][k] = vfma(Rc.gn[k], fl.cR, Rc.q[k]);
+        Sl[2][k] = Rc.gt[k] * h;
+        C[1][k] = half * (vfma(L.gn[k], wL, L.q[k]) + vfma(Rc.gn[k], mwR, Rc.q[k]));
+        Sl[1][k] = hh * (L.gt[k] + Rc.gt[k]);
+    }
+    // (a), (b): equilibria at the nodes and their moments
+    V df[9], dg[9];
+    V drs = T::bc(0.0), mn = T::bc(0.0), mt = T::bc(0.0), es = T::bc(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int a = 1 - en[i], b = -et[i];  // column index, offset along t
+        V q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            q[k] = b == 0 ? C[a][k] : (b > 0 ? C[a][k] + Sl[a][k] : C[a][k] - Sl[a][k]);
+        const V w = i == 0 ? w0 : (i < 5 ? w1 : w2);
+        V eu = T::bc(0.0);
+        if (en[i] > 0) eu = eu + q[1];
+        if (en[i] < 0) eu = eu - q[1];
+        if (et[i] > 0) eu = eu + q[2];
+        if (et[i] < 0) eu = eu - q[2];
+        const V usq = vfma(q[1], q[1], q[2] * q[2]);
+        const V rho = one + q[0];
+        // f_i - w_i = w_i (drho + rho (3 eu + 4.5 eu^2 - 1.5 u^2))
+        df[i] = w * vfma(rho, vfma(eu, vfma(c45, eu, three), T::bc(0.0) - c15 * usq), q[0]);
+        // rho T - Tbar = tau + drho T at the node; g_i - w_i Tbar
+        const V e_node = vfma(q[0], Tbar + q[3], q[3]);
+        dg[i] = w * vfma(three * eu, Tbar + e_node, e_node);
+        drs = drs + df[i];
+        if (en[i] > 0) mn = mn + df[i];
+        if (en[i] < 0) mn = mn - df[i];
+        if (et[i] > 0) mt = mt + df[i];
+        if (et[i] < 0) mt = mt - df[i];
+        es = es + dg[i];
+    }
+    const V rho_s = one + drs;
+    mn = mn * keep;
+    mt = vfma(keep, mt, (one - keep) * (rho_s * u_wall));
+    const V inv = T::rcp(rho_s);
+    const V uns = mn * inv, uts = mt * inv;
+    const V usq_s = vfma(uns, uns, uts * uts);
+    // (c) fluxes along +n with the non-equilibrium parts; 1/2 - tau_f =
+    // -3 nu / h = 6 (-nu / 2h), likewise for tau_g (Eqs. 9-10)
+    const V six = T::bc(6.0);
+    const V cf = six * fl.m_nu_2h, cg = six * fl.m_chi_2h;
+    V Fnn = T::bc(0.0), Fnt = T::bc(0.0), Q = T::bc(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (en[i] == 0) continue;  // no flux along n
+        const V w = i < 5 ? w1 : w2;
+        V eu = en[i] > 0 ? uns : T::bc(0.0) - uns;
+        if (et[i] > 0) eu = eu + uts;
+        if (et[i] < 0) eu = eu - uts;
+        const V dfs = w * vfma(rho_s, vfma(eu, vfma(c45, eu, three), T::bc(0.0) - c15 * usq_s), drs);
+        const V dgs = w * vfma(three * eu, Tbar + es, es);
+        const V pf = vfma(cf, dfs - df[i], dfs);  // f* + (1/2 - tau_f)(f* - f_node)
+        const V pg = vfma(cg, dgs - dg[i], dgs);
+        Fnn = Fnn + pf;  // e_n^2 = 1
+        if (et[i] != 0) Fnt = (en[i] * et[i] > 0) ? Fnt + pf : Fnt - pf;
+        Q = en[i] > 0 ? Q + pg : Q - pg;
+    }
+    F[0] = mn;
+    F[1] = Fnn;
+    F[2] = Fnt;
+    F[3] = Q;
 }
 
 // Parity of quantity k (0 drho, 1 u, 2 v, 3 T) about a wall of side s:

@@ -129,9 +129,11 @@ int Engine::init()
     CK(step_prepare(precision_));
     for (int h : kTileHeights) {
         if (!tile_height_ok(precision_, h)) continue;
-        CK(step_occupancy(precision_, h, &occ_tile_[h]));
+        CK(step_occupancy(precision_, h, kSchemeRTLBFS, &occ_tile_[h]));
         if (occ_tile_[h] < 1) return fail(RTLBFS_ERR_CUDA, "step kernel does not fit on an SM");
     }
+    CK(step_occupancy(precision_, kTileYDefault, kSchemeTLBFS, &occ_tlbfs_));
+    if (occ_tlbfs_ < 1) return fail(RTLBFS_ERR_CUDA, "TLBFS step kernel does not fit on an SM");
     CK(march_prepare(precision_));
     CK(march_occupancy(precision_, &occ_march_));
     if (occ_march_ < 1) return fail(RTLBFS_ERR_CUDA, "march kernel does not fit on an SM");
@@ -353,6 +355,7 @@ int Engine::upload_lines(int slot)
     }
     d.tiles_x = (c.nx + kTileX - 1) / kTileX;
     d.tiles_y = (c.ny + tile_h_ - 1) / tile_h_;
+    d.scheme = scheme_;
     d.ntiles = c.ntiles;  // work units of this cavity in the current list
     d.tile_begin = c.first_tile;
     d.beta_g = c.beta_g;
@@ -388,9 +391,32 @@ int Engine::upload_lines(int slot)
     return RTLBFS_OK;
 }
 
+int Engine::set_scheme(int scheme)
+{
+    if (scheme != kSchemeRTLBFS && scheme != kSchemeTLBFS)
+        return fail(RTLBFS_ERR_ARG, "scheme must be RTLBFS (0) or TLBFS (1)");
+    if (scheme != scheme_) {
+        scheme_ = scheme;
+        if (gexec_) {
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+        }
+        tiles_dirty_ = true;
+        for (auto& c : slots_)
+            if (c.active) c.dirty = true;  // the scheme lives in the descriptor
+    }
+    if (scheme_ == kSchemeTLBFS) {  // tile kernel, default height
+        kernel_ = 1;
+        chunk_rows_ = kTileYDefault;
+    }
+    return RTLBFS_OK;
+}
+
 int Engine::set_kernel(int kind)
 {
     if (kind != 0 && kind != 1) return fail(RTLBFS_ERR_ARG, "kernel kind must be 0 or 1");
+    if (scheme_ == kSchemeTLBFS && kind != 1)
+        return fail(RTLBFS_ERR_ARG, "the TLBFS face stage runs on the tile kernel (1)");
     if (kind != kernel_) {
         kernel_ = kind;
         tiles_dirty_ = true;
@@ -405,6 +431,8 @@ int Engine::set_kernel(int kind)
 int Engine::set_chunk_rows(int rows)
 {
     if (rows < 0) return fail(RTLBFS_ERR_ARG, "chunk rows must be >= 0");
+    if (scheme_ == kSchemeTLBFS && kernel_ == 1 && rows != 0 && rows != kTileYDefault)
+        return fail(RTLBFS_ERR_ARG, "the TLBFS tile kernel has height 16 (or 0)");
     if (kernel_ == 1 && rows != 0 && !tile_height_ok(precision_, rows))
         return fail(RTLBFS_ERR_ARG, precision_ == RTLBFS_FP64
                                         ? "FP64 tile height must be one of 16, 8, 4, 2 (or 0)"
@@ -420,6 +448,7 @@ int Engine::set_chunk_rows(int rows)
 // the residual), in face-equivalents: 65 h + 32 + 0.25 * 34 (h + 2) + 300.
 int Engine::pick_tile_height() const
 {
+    if (scheme_ == kSchemeTLBFS) return kTileYDefault;
     int best_h = kTileYDefault;
     double best = 1e300;
     for (int h : kTileHeights) {
@@ -537,7 +566,8 @@ int Engine::prepare_launch()
     // persistent grid: every SM full, never more blocks than work units
     int want;
     if (kernel_ == 1) {
-        want = std::max(1, std::min(sms_ * occ_tile_[tile_h_], std::max(ntiles_, 1)));
+        const int occ = scheme_ == kSchemeTLBFS ? occ_tlbfs_ : occ_tile_[tile_h_];
+        want = std::max(1, std::min(sms_ * occ, std::max(ntiles_, 1)));
     } else {
         const int wpb = kMarchThreads / 32;
         want = std::max(1, std::min(sms_ * occ_march_, (std::max(ntiles_, 1) + wpb - 1) / wpb));
@@ -702,7 +732,7 @@ int Engine::launch_steps(long long launches)
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
-                    e = kernel_ == 1 ? launch_step(precision_, tile_h_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+                    e = kernel_ == 1 ? launch_step(precision_, tile_h_, scheme_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
                                      : launch_march(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
                 cudaError_t e2 = cudaStreamEndCapture(cs, &g);
                 if (e == cudaSuccess) e = e2;
@@ -720,7 +750,7 @@ int Engine::launch_steps(long long launches)
         }
     }
     for (; left > 0; --left) {
-        CK(kernel_ == 1 ? launch_step(precision_, tile_h_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
+        CK(kernel_ == 1 ? launch_step(precision_, tile_h_, scheme_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
                         : launch_march(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
         g_launches++;
     }
@@ -752,8 +782,10 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
     };
     std::vector<Cand> cands;
     for (int h : kTileHeights)
-        if (tile_height_ok(precision_, h)) cands.push_back({1, h});
+        if (tile_height_ok(precision_, h) && (scheme_ == kSchemeRTLBFS || h == kTileYDefault))
+            cands.push_back({1, h});
     for (int H : {8, 16, 32, 64, 128, 256}) {
+        if (scheme_ == kSchemeTLBFS) break;
         if (H > maxny && H != 8) break;
         cands.push_back({0, H});
     }

@@ -90,6 +90,10 @@ public:
     // unit, or the tile height of the tile kernel (one of kTileHeights)
     int set_chunk_rows(int rows);
     int chunk_rows() const { return chunk_rows_; }
+    // face stage of every cavity: kSchemeRTLBFS or kSchemeTLBFS (the latter
+    // runs on the tile kernel at the default height)
+    int set_scheme(int scheme);
+    int scheme() const { return scheme_; }
     // time every candidate schedule for `steps` steps on a snapshot of the
     // current state (restored afterwards) and keep the fastest
     int autotune(int steps, int* kernel, int* chunk_rows, double* ms_per_step);
@@ -104,6 +108,8 @@ private:
     size_t rsize_;
     int sms_ = 0, grid_ = 0;
     int occ_tile_[32] = {};  // resident tile blocks per SM, by tile height
+    int occ_tlbfs_ = 0;      // the same for the TLBFS tile kernel
+    int scheme_ = 0;
     int tile_h_ = 16;        // tile height of the current tile list
     int pick_tile_height() const;
     int kernel_ = 0, occ_march_ = 0, chunk_rows_ = 0;

@@ -44,10 +44,12 @@ struct NuLines {
     const CellLine<double>* yc;
 };
 
-// tile_h: a height tile_height_ok accepts for the precision
+// tile_h: a height tile_height_ok accepts for the precision; scheme: the
+// face stage, 0 RTLBFS, 1 TLBFS (tile height kTileYDefault only)
+constexpr int kSchemeRTLBFS = 0, kSchemeTLBFS = 1;
 cudaError_t step_prepare(int precision);
-cudaError_t step_occupancy(int precision, int tile_h, int* blocks_per_sm);
-cudaError_t launch_step(int precision, int tile_h, int grid, cudaStream_t s,
+cudaError_t step_occupancy(int precision, int tile_h, int scheme, int* blocks_per_sm);
+cudaError_t launch_step(int precision, int tile_h, int scheme, int grid, cudaStream_t s,
                         const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
                         const int* ntiles);
 cudaError_t march_prepare(int precision);

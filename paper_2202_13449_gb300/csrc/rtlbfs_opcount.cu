@@ -31,13 +31,13 @@ struct Cnt {
 
 Cnt operator+(Cnt a, Cnt b)
 {
-    ++g_tally.ops;
-    return {a.v + b.v, false};
+    if (!a.zero && !b.zero) ++g_tally.ops;  // adding the literal 0 is no operation
+    return {a.v + b.v, a.zero && b.zero};
 }
 Cnt operator-(Cnt a, Cnt b)
 {
-    if (!a.zero) ++g_tally.ops;
-    return {a.v - b.v, false};
+    if (!a.zero && !b.zero) ++g_tally.ops;
+    return {a.v - b.v, a.zero && b.zero};
 }
 Cnt operator*(Cnt a, Cnt b)
 {
@@ -64,9 +64,9 @@ struct vtraits<Cnt> {
 
 namespace {
 
-// One face of generic values: every operation of face_flux is data-
-// independent (no branches), so any inputs give the count.
-Tally count_face()
+// One face of generic values: every operation of the face templates is
+// data-independent (no branches on values), so any inputs give the count.
+Tally count_face(int scheme)
 {
     g_tally = Tally();
     CellNT<Cnt> L, R;
@@ -88,16 +88,21 @@ Tally count_face()
     fl.m_tg15 = {-0.1, false};
     fl.pad = {0.0, true};
     Cnt F[4];
-    face_flux<Cnt>(L, R, Cnt{0.5, false}, fl, Cnt{1.0, false}, Cnt{0.0, false}, F);
+    if (scheme == 1)
+        face_flux_tlbfs<Cnt>(L, R, Cnt{0.5, false}, fl, Cnt{1.0, false}, Cnt{0.0, false}, F);
+    else
+        face_flux<Cnt>(L, R, Cnt{0.5, false}, fl, Cnt{1.0, false}, Cnt{0.0, false}, F);
     return g_tally;
 }
 
 }  // namespace
 }  // namespace rtlbfs
 
-extern "C" int rtlbfs_op_counts(double* face_ops, double* cell_ops, double* sfu_ops)
+extern "C" int rtlbfs_op_counts_scheme(int scheme, double* face_ops, double* cell_ops,
+                                       double* sfu_ops)
 {
-    const rtlbfs::Tally f = rtlbfs::count_face();
+    if (scheme != 0 && scheme != 1) return RTLBFS_ERR_ARG;
+    const rtlbfs::Tally f = rtlbfs::count_face(scheme);
     // Per cell, besides its two faces (the west and south faces it owns):
     //   working values from the stored state         4  (scale of each field)
     //   face frames: Tbar and the right cell's T      4  (2 per face)
@@ -117,4 +122,9 @@ extern "C" int rtlbfs_op_counts(double* face_ops, double* cell_ops, double* sfu_
     if (cell_ops) *cell_ops = 2.0 * (double)f.ops + other;
     if (sfu_ops) *sfu_ops = 2.0 * (double)f.sfu + other_sfu;
     return RTLBFS_OK;
+}
+
+extern "C" int rtlbfs_op_counts(double* face_ops, double* cell_ops, double* sfu_ops)
+{
+    return rtlbfs_op_counts_scheme(0, face_ops, cell_ops, sfu_ops);
 }

@@ -223,7 +223,7 @@ struct MinBlocks<StoreQ, NT> {
     static constexpr int value = 65536 / (NT * 64);
 };
 
-template <class P, int TX, int TY, int NT>
+template <class P, int TX, int TY, int NT, int SCHEME>
 __global__ void __launch_bounds__(NT, MinBlocks<P, NT>::value)
 step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
@@ -363,7 +363,10 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                 }
                 const R uw = wside >= 0 ? P::bcU(dp, wside) : R(0);
                 R F[4];
-                face_flux<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
+                if constexpr (SCHEME == 1)
+                    face_flux_tlbfs<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
+                else
+                    face_flux<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
                 if (isx) out = {F[0], F[1], F[2], F[3]};
                 else out = {F[0], F[2], F[1], F[3]};
             }
@@ -529,7 +532,9 @@ __device__ double energy_flux_d(const CavityDesc& d, int f, const NuLines& ln, i
     if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
     const FaceLine<double> fl = nd == 0 ? ln.xl[i] : ln.yl[j];
     double F[4];
-    face_flux<double>(L, Rr, Tbar, fl, wside >= 0 ? 0.0 : 1.0, wside >= 0 ? d.bcU[wside] : 0.0, F);
+    const double keep = wside >= 0 ? 0.0 : 1.0, uw = wside >= 0 ? d.bcU[wside] : 0.0;
+    if (d.scheme == 1) face_flux_tlbfs<double>(L, Rr, Tbar, fl, keep, uw, F);
+    else face_flux<double>(L, Rr, Tbar, fl, keep, uw, F);
     return F[3];
 }
 
@@ -670,11 +675,11 @@ struct TileThreads<StoreD, TY> {
     static constexpr int value = TY <= 8 ? 32 * TY : 16 * TY;
 };
 
-template <class P, int TY>
+template <class P, int TY, int SCHEME = 0>
 struct TileKernel {
     static constexpr int NT = TileThreads<P, TY>::value;
     static constexpr size_t smem = sizeof(TileSmem<P, kTileX, TY, NT>);
-    static constexpr auto fn = step_kernel<P, kTileX, TY, NT>;
+    static constexpr auto fn = step_kernel<P, kTileX, TY, NT, SCHEME>;
     static cudaError_t prepare()
     {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -696,10 +701,17 @@ struct TileKernel {
     }
 };
 
-// Call op on the compiled tile kernel of (precision, tile_h).
+// Call op on the compiled tile kernel of (precision, tile_h, scheme); the
+// TLBFS face stage is compiled for the default tile height.
 template <class Op>
-static cudaError_t with_tile_kernel(int precision, int tile_h, Op op)
+static cudaError_t with_tile_kernel(int precision, int tile_h, int scheme, Op op)
 {
+    if (scheme == 1) {
+        if (tile_h != kTileYDefault) return cudaErrorInvalidValue;
+        if (precision == 0) return op(TileKernel<StoreD, kTileYDefault, 1>());
+        return op(TileKernel<StoreQ, kTileYDefault, 1>());
+    }
+    if (scheme != 0) return cudaErrorInvalidValue;
     if (precision == 0) {
         switch (tile_h) {
         case 16: return op(TileKernel<StoreD, 16>());
@@ -725,23 +737,23 @@ cudaError_t step_prepare(int precision)
 {
     for (int h : kTileHeights) {
         if (!tile_height_ok(precision, h)) continue;
-        cudaError_t e = with_tile_kernel(precision, h, [](auto k) { return k.prepare(); });
+        cudaError_t e = with_tile_kernel(precision, h, 0, [](auto k) { return k.prepare(); });
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return with_tile_kernel(precision, kTileYDefault, 1, [](auto k) { return k.prepare(); });
 }
 
-cudaError_t step_occupancy(int precision, int tile_h, int* blocks_per_sm)
+cudaError_t step_occupancy(int precision, int tile_h, int scheme, int* blocks_per_sm)
 {
-    return with_tile_kernel(precision, tile_h,
+    return with_tile_kernel(precision, tile_h, scheme,
                             [&](auto k) { return k.occupancy(blocks_per_sm); });
 }
 
-cudaError_t launch_step(int precision, int tile_h, int grid, cudaStream_t s,
+cudaError_t launch_step(int precision, int tile_h, int scheme, int grid, cudaStream_t s,
                         const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
                         const int* ntiles)
 {
-    return with_tile_kernel(precision, tile_h, [&](auto k) {
+    return with_tile_kernel(precision, tile_h, scheme, [&](auto k) {
         return k.launch(grid, s, descs, ctls, tiles, ntiles);
     });
 }

@@ -50,3 +50,12 @@ def test_op_counts_of_the_step():
     assert face == int(face) and 150 <= face <= 200
     assert cell == 2 * face + 95
     assert sfu == 2 * 1 + 4  # one reciprocal per face; rho^{n+1}, two roots, one reciprocal
+
+
+def test_op_counts_of_the_tlbfs_stage():
+    face_r, cell_r, _ = capi.op_counts(capi.RTLBFS)
+    face_t, cell_t, sfu_t = capi.op_counts(capi.TLBFS)
+    assert cell_t == 2 * face_t + 95 and sfu_t == 6
+    assert face_t > 1.5 * face_r  # nine equilibria and their moments per face
+    with pytest.raises(capi.RTLBFSError):
+        capi.op_counts(2)
