@@ -107,6 +107,16 @@ WORKLOADS = {
              "1, 10, 100, 1e3, 1e4, 2e5",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32",
         checkpoints=[1, 10, 100, 1000, 10000, 200000], kind="accuracy"),
+    "cavity512_tlbfs": dict(
+        desc="the 512x512 tanh cavity of config 2 (Ra=1e8, Pr=0.71, Ma=0.1, FP32 bulk + FP64 "
+             "reductions) with the original TLBFS face stage of Section 2.2 instead of RTLBFS",
+        nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=1000,
+        scheme=1, kind="cavity"),
+    "schemes_ra1e3": dict(
+        desc="RTLBFS against TLBFS (Sections 3.2 and 2.2) on the 64x64 uniform cavity at "
+             "Ra=1e3, Pr=0.71, Ma=0.1, FP64, run to max(R_u, R_T) < 1e-9: Table 1's quantities "
+             "and the time to the steady state for each face stage",
+        n=64, Ra=1e3, Pr=0.71, Ma=0.1, tol=1e-9, max_steps=400000, kind="schemes"),
     "cavity512_fp64": dict(
         desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
@@ -151,12 +161,13 @@ def profile_traffic(workload: str, precision: str, kernel: str):
     return None
 
 
-def rooflines(kernel: str, cells: int, per_launch_s: float, rs: int, traffic, clocks):
+def rooflines(kernel: str, cells: int, per_launch_s: float, rs: int, traffic, clocks,
+              scheme: int = 0):
     """(ALU roofline, HBM roofline) of the step kernel for launches of
-    `cells` cell-updates taking per_launch_s each."""
+    `cells` cell-updates taking per_launch_s each (face stage `scheme`)."""
     import torch
     from paper_2202_13449_gb300 import capi
-    _, ops_cell, sfu_cell = capi.op_counts()
+    _, ops_cell, sfu_cell = capi.op_counts(scheme)
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     if rs == 4:
@@ -297,6 +308,8 @@ def setup_solver(capi, inputs, w):
         s.set_bc(capi.NORTH, capi.WALL_DIRICHLET, 0.0)
         s.set_params_ref(w["Ra"], w["Pr"], w["Ma"], 0.5, float(ny), 1.0, 0.5)
         st = inputs.rb_state(xf, yf, amp=1e-3, seed=0)
+    if w.get("scheme", 0):
+        s.set_scheme(w["scheme"])
     s.set_state(*st)
     return s, st, xf, yf
 
@@ -684,7 +697,64 @@ def run_stability(args, w):
     print(json.dumps(line), flush=True)
 
 
+# Table 1 of the paper at Ra = 1e3: the RTLBFS ("Present") and TLBFS [24] rows
+TABLE1_RA1E3 = {
+    "rtlbfs": {"u_max": 3.644, "y_u": 0.814, "v_max": 3.698, "x_v": 0.180, "Nu_a": 1.118},
+    "tlbfs": {"u_max": 3.640, "y_u": 0.815, "v_max": 3.708, "x_v": 0.180, "Nu_a": 1.115},
+}
+
+
+def run_schemes(args, w):
+    """Both face stages to the steady state of the Ra = 1e3 cavity on the
+    GPU in FP64: Table 1's quantities and the device time each needs."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    n = w["n"]
+    xf = inputs.uniform_faces(n)
+    out = {}
+    for name, scheme in (("rtlbfs", capi.RTLBFS), ("tlbfs", capi.TLBFS)):
+        s = capi.Solver(xf, xf, capi.FP64)
+        s.set_params(w["Ra"], w["Pr"], w["Ma"], 0.5)
+        s.set_scheme(scheme)
+        s.set_state(*inputs.conduction_state(xf, xf))
+        s.autotune(16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, steps, res = s.run_to_steady(w["tol"], w["max_steps"])
+        el = time.perf_counter() - t0
+        st = s.get_state()
+        nu_a = s.nusselt(capi.NU_AVG)
+        nu_w = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+        s.close()
+        nu, chi = 0.1 * n * np.sqrt(w["Pr"] / w["Ra"]), 0.1 * n * np.sqrt(w["Pr"] / w["Ra"]) / w["Pr"]
+        u_c = 0.5 * (st[1][:, n // 2 - 1] + st[1][:, n // 2])
+        v_c = 0.5 * (st[2][n // 2 - 1, :] + st[2][n // 2, :])
+        yc = (np.arange(n) + 0.5) / n
+        out[name] = {"converged": rc == 0, "steps": int(steps), "wall_s": round(el, 3),
+                     "ms_per_step": round(el * 1e3 / max(steps, 1), 4),
+                     "u_max": float(u_c.max() * n / chi), "y_u": float(yc[u_c.argmax()]),
+                     "v_max": float(v_c.max() * n / chi), "x_v": float(yc[v_c.argmax()]),
+                     "Nu_a": float(nu_a), "Nu_wall_mean": float(nu_w),
+                     "paper_table1": TABLE1_RA1E3[name]}
+    ratio = out["tlbfs"]["ms_per_step"] / out["rtlbfs"]["ms_per_step"]
+    line = {"metric": "time per step of TLBFS over RTLBFS (FP64, 64x64, to the steady state)",
+            "value": round(ratio, 3), "unit": "ratio", "n_gpus": 1, "steps": 2, "warmup": 0,
+            "ms_per_step": out["rtlbfs"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (conduction initial state)",
+            "config": {"workload": args.workload, "description": w["desc"]},
+            "schemes": out,
+            "note": "the paper's Table 6 compares the two solvers' cost in 3D; here the face "
+                    "stages share mesh, update and reductions"}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "schemes":
+        return run_schemes(args, w)
     if w.get("kind") == "stability":
         return run_stability(args, w)
     if w.get("kind") == "rb_steady":
@@ -772,7 +842,7 @@ def run_ours(args, w):
     per_launch_s = ms_max * 1e-3 / (inner * args.steps)
     kname = ["rtlbfs::march_kernel", "rtlbfs::step_kernel"][sched[0]]
     traffic = profile_traffic(args.workload, w["precision"], ["march", "tile"][sched[0]])
-    alu, hbm = rooflines(kname, cells, per_launch_s, rs, traffic, clocks)
+    alu, hbm = rooflines(kname, cells, per_launch_s, rs, traffic, clocks, w.get("scheme", 0))
     res, steps_total = s.residual()
     line = {
         "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
@@ -1054,7 +1124,7 @@ def main():
         args.warmup = 3
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if w.get("kind") in ("accuracy", "rb_steady"):
+        if w.get("kind") in ("accuracy", "rb_steady", "schemes"):
             print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
                               "time to a steady state of the GPU path; the oracle's rate is the "
                               "rb1024x512 / cavity512 reference lines"}))
