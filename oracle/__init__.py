@@ -1,9 +1,11 @@
-"""FP64 CPU oracle of 2D RTLBFS (arXiv 2202.13449, Section 3.2).
+"""FP64 CPU oracle of RTLBFS (arXiv 2202.13449, Section 3.2): 2D here, 3D
+(D3Q19, Section 4.4) in ``oracle.d3``.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The product package
 never imports this module, and the C source here shares no code with the
-CUDA path.  ``build()`` compiles ``rtlbfs_oracle.c`` with gcc into
+CUDA path.  ``build()`` compiles ``rtlbfs_oracle.c`` and
+``rtlbfs3d_oracle.c`` with gcc into
 ``oracle/_build/``; everything else is ctypes marshalling.
 
 Functions mirror the C entry points (see the header comment of
@@ -26,7 +28,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rtlbfs_oracle.c")
+_SRCS = [os.path.join(_HERE, "rtlbfs_oracle.c"), os.path.join(_HERE, "rtlbfs3d_oracle.c")]
 _OUT = os.path.join(_HERE, "_build", "librtlbfs_oracle.so")
 
 W, E, S, N = 0, 1, 2, 3
@@ -36,15 +38,16 @@ RTLBFS, TLBFS = 0, 1  # face stage of Problem.scheme
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, OpenMP, no fast-math, no FMA
-    contraction so x86 and Arm give the same bits)."""
+    """Compile the oracle shared library from the 2D and 3D sources (gcc,
+    OpenMP, no fast-math, no FMA contraction so x86 and Arm give the same
+    bits)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if (not force and os.path.exists(_OUT)
-            and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_OUT) >= os.path.getmtime(src) for src in _SRCS)):
         return _OUT
     tmp = _OUT + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _OUT)
     return _OUT

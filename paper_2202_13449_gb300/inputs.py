@@ -18,6 +18,10 @@ Workload recipes (the paper uses no dataset; all inputs are generated):
 * ``serving_trace`` -- request stream: Poisson arrivals, square meshes with
   side log-uniform in [64, 1024], Ra log-uniform in [1e3, 1e8], Pr in
   {0.71, 7.0}.
+* ``conduction_state3`` / ``perturbed_state3`` -- the 3D counterparts
+  (rho, u, v, w, T), arrays of shape (nz, ny, nx): the cubic cavity's
+  initial state of Section 4.4 (T linear between the isothermal x walls) and
+  a generic seeded state for parity checks.
 """
 from __future__ import annotations
 
@@ -124,3 +128,28 @@ def serving_trace(count: int = 10000, seed: int = 42, rate: float = 200.0,
     Ra = 10.0 ** g.uniform(log_ra[0], log_ra[1], size=count)
     Pr = np.where(g.uniform(size=count) < 0.5, prs[0], prs[1])
     return [Request(float(t[k]), int(n[k]), float(Ra[k]), float(Pr[k])) for k in range(count)]
+
+
+def conduction_state3(xf, yf, zf, T_west: float = 0.0, T_east: float = 1.0):
+    """(rho, u, v, w, T), each nz x ny x nx: rest, unit density, T linear in x
+    (cold -x wall, hot +x wall by default, as in the cubic cavity)."""
+    xf = np.asarray(xf, dtype=np.float64)
+    nx, ny, nz = len(xf) - 1, len(yf) - 1, len(zf) - 1
+    s = (_centres(xf) - xf[0]) / (xf[-1] - xf[0])
+    T = np.broadcast_to(T_west + (T_east - T_west) * s, (nz, ny, nx)).copy()
+    z = np.zeros((nz, ny, nx))
+    return (np.ones((nz, ny, nx)), z, z.copy(), z.copy(), T)
+
+
+def perturbed_state3(nx: int, ny: int, nz: int, seed: int, amp_rho: float = 1e-3,
+                     amp_u: float = 1e-2, amp_T: float = 0.1, T_mean: float = 0.5):
+    """3D generic state: rho = 1 + U(-amp_rho, amp_rho), u, v, w =
+    U(-amp_u, amp_u), T = T_mean + U(-amp_T, amp_T), shape (nz, ny, nx)."""
+    g = rng(seed)
+    sh = (nz, ny, nx)
+    rho = 1.0 + g.uniform(-amp_rho, amp_rho, size=sh)
+    u = g.uniform(-amp_u, amp_u, size=sh)
+    v = g.uniform(-amp_u, amp_u, size=sh)
+    w = g.uniform(-amp_u, amp_u, size=sh)
+    T = T_mean + g.uniform(-amp_T, amp_T, size=sh)
+    return (rho, u, v, w, T)

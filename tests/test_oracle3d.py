@@ -1,0 +1,450 @@
+"""Pins of the 3D FP64 oracle (D3Q19 RTLBFS; Sections 2.1, 3.2 and 4.4)
+against what the paper and the mathematics fix independently of the
+oracle's own formulas.
+
+* Eqs. 5-7 (R5's reading of the printed D3Q19 matrix): the velocity set
+  with the weights of Eq. 6 has the moments that Eq. 7 needs (isotropy to
+  fourth order); the set the oracle uses is that set.
+* Eqs. 55-56: exact for linear fields on an irregular hexahedral mesh.
+* Eq. 29: each of the 19 nodes takes the plane of the cell it lies in.
+* Eqs. 46-48: for constant rho and linear u, v, w, T the D3Q19 equilibria
+  are quadratic in space, so the predictor equals the moment sums of
+  Eqs. 30-32 computed from Eqs. 3-6 -- a different formula for the same
+  quantity -- and the fluxes equal Eqs. 38-40 with the first-order Taylor
+  step of Eq. 50; on smooth data the two stay O(h^3) and O(h^2) close,
+  which catches a wrong second-order coefficient, in particular in the
+  cross-derivative terms that only three dimensions have.
+* Reduction to 2D: a state invariant along a periodic axis with no velocity
+  along it evolves as the (separately pinned) 2D oracle does in the other
+  two axes, for each choice of the invariant axis.
+* Walls, conservation, the conduction fixed point, symmetries under axis
+  permutation and reflection, and Table 5 at Ra = 1e3 as physical sanity.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from helpers import CS2, E_D3Q19, W_D3Q19, centres, f_eq3, g_eq3
+from paper_2202_13449_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def d3(orc):
+    from oracle import d3 as mod
+    return mod
+
+
+# ---------------------------------------------------------------- Eqs. 5-7
+def test_d3q19_reading_gives_an_isotropic_lattice(d3):
+    E = E_D3Q19
+    assert len({tuple(e) for e in E.T}) == 19
+    assert {tuple(e) for e in d3.lattice()} == {tuple(e) for e in E.T.astype(int)}
+    d = np.eye(3)
+    assert W_D3Q19.sum() == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(E @ W_D3Q19, 0.0, atol=1e-16)
+    np.testing.assert_allclose((W_D3Q19 * E) @ E.T, CS2 * d, atol=1e-16)
+    m3 = np.einsum("i,ai,bi,ci->abc", W_D3Q19, E, E, E)
+    np.testing.assert_allclose(m3, 0.0, atol=1e-16)
+    m4 = np.einsum("i,ai,bi,ci,di->abcd", W_D3Q19, E, E, E, E)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    np.testing.assert_allclose(m4, iso, atol=1e-16)
+
+
+# ---------------------------------------------------------------- linear fields
+LIN = np.array([
+    # c0, cx, cy, cz  for rho, u, v, w, T
+    [1.0, 0.0, 0.0, 0.0],
+    [0.012, 0.0011, -0.0007, 0.0005],
+    [-0.008, 0.0004, 0.0009, -0.0006],
+    [0.005, -0.0008, 0.0003, 0.0010],
+    [0.45, 0.013, -0.009, 0.007],
+])
+
+
+def _lin_at(pos, coef=LIN):
+    return [c[0] + c[1] * pos[0] + c[2] * pos[1] + c[3] * pos[2] for c in coef]
+
+
+def _grid(p):
+    xc, yc, zc = centres(p.xf), centres(p.yf), centres(p.zf)
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    return X, Y, Z
+
+
+def lin_problem(d3, kappa=1.0, nu=0.02, chi=0.03, coef=LIN):
+    xf, yf, zf = inputs.random_faces(8, 11), inputs.random_faces(9, 12), inputs.random_faces(8, 13)
+    p = d3.Problem3(xf=xf, yf=yf, zf=zf, nu=nu, chi=chi, kappa=kappa)
+    X, Y, Z = _grid(p)
+    st = tuple(c[0] + c[1] * X + c[2] * Y + c[3] * Z for c in coef)
+    return p, st
+
+
+def test_gradients_exact_for_linear_fields(d3):
+    p, st = lin_problem(d3)
+    g = d3.gradients(p, st)
+    inner = (slice(1, -1),) * 3
+    for q in range(5):
+        for d in range(3):
+            np.testing.assert_allclose(g[q, d][inner], LIN[q, 1 + d], rtol=0, atol=2e-15)
+
+
+def _face_geometry(p, nd, c, kappa):
+    f = (p.xf, p.yf, p.zf)
+    xS = np.array([centres(f[a])[c[a]] if a != nd else f[a][c[a]] for a in range(3)])
+    fa = f[nd]
+    h = kappa * min(fa[c[nd]] - fa[c[nd] - 1], fa[c[nd] + 1] - fa[c[nd]])
+    return xS, h
+
+
+FACES = [(0, (4, 3, 4), 1.0), (1, (3, 4, 4), 1.0), (2, (4, 4, 3), 1.0), (0, (3, 5, 3), 0.55),
+         (1, (5, 3, 4), 0.3), (2, (3, 4, 5), 0.7)]
+
+
+@pytest.mark.parametrize("nd,c,kappa", FACES)
+def test_nodes_take_the_plane_of_the_cell_they_lie_in(d3, nd, c, kappa):
+    xf, yf, zf = inputs.random_faces(8, 21), inputs.random_faces(9, 22), inputs.random_faces(8, 23)
+    p = d3.Problem3(xf=xf, yf=yf, zf=zf, nu=0.02, chi=0.03, kappa=kappa)
+    st = inputs.perturbed_state3(8, 9, 8, seed=24)
+    g = d3.gradients(p, st)
+    o = d3.face(p, st, nd, *c)
+    nodes = o.nodes()
+    xS, h = _face_geometry(p, nd, c, kappa)
+    assert o.h == pytest.approx(h, rel=1e-15)
+    cl = list(c)
+    cl[nd] -= 1
+    ctr = [centres(f) for f in (p.xf, p.yf, p.zf)]
+
+    def plane(cell, q, pos):
+        i, j, k = cell
+        x0 = np.array([ctr[0][i], ctr[1][j], ctr[2][k]])
+        return st[q][k, j, i] + sum(g[q, d][k, j, i] * (pos[d] - x0[d]) for d in range(3))
+
+    for i in range(19):
+        pos = xS + h * E_D3Q19[:, i]
+        for q in range(5):
+            s = E_D3Q19[nd, i]
+            if s < 0:
+                want = plane(cl, q, pos)
+            elif s > 0:
+                want = plane(c, q, pos)
+            else:
+                want = 0.5 * (plane(cl, q, pos) + plane(c, q, pos))
+            assert nodes[q, i] == pytest.approx(want, rel=0, abs=1e-14)
+
+
+def _moments(fields_at, xS, h):
+    """Eqs. 30-32 with D3Q19: rho*, (rho u_a)*, (rho T)* from the equilibria
+    at x_S - e_i h."""
+    out = np.zeros(5)
+    for i in range(19):
+        e = E_D3Q19[:, i]
+        r, u, v, w, T = fields_at(xS - e * h)
+        fi = f_eq3(r, u, v, w)[i]
+        gi = g_eq3(r, u, v, w, T)[i]
+        out += np.array([fi, e[0] * fi, e[1] * fi, e[2] * fi, gi])
+    return out
+
+
+@pytest.mark.parametrize("nd,c,kappa", FACES)
+def test_predictor_equals_d3q19_moment_sums(d3, nd, c, kappa):
+    p, st = lin_problem(d3, kappa=kappa)
+    o = d3.face(p, st, nd, *c)
+    xS, h = _face_geometry(p, nd, c, kappa)
+    np.testing.assert_allclose(np.array(o.pred[:]), _moments(_lin_at, xS, h), rtol=0, atol=2e-15)
+
+
+def _distribution_flux(fields_at, dfield, xS, h, nd, nu, chi, pred):
+    """Eqs. 38-40 with the D3Q19 equilibria of the prediction `pred` and the
+    non-equilibrium parts f* - f_eq(x_S) + h e.grad f_eq (the first-order
+    Taylor step of Eq. 50); dfield(k) returns h e_k.grad of (f_eq, g_eq)."""
+    rs = pred[0]
+    us, vs, ws, Ts = pred[1] / rs, pred[2] / rs, pred[3] / rs, pred[4] / rs
+    fs, gs = f_eq3(rs, us, vs, ws), g_eq3(rs, us, vs, ws, Ts)
+    r0, u0, v0, w0, T0 = fields_at(xS)
+    f0, g0 = f_eq3(r0, u0, v0, w0), g_eq3(r0, u0, v0, w0, T0)
+    dfe = np.empty(19)
+    dge = np.empty(19)
+    for k in range(19):
+        dfe[k], dge[k] = dfield(k)
+    tf = nu / (CS2 * h) + 0.5  # Eq. 9
+    tg = chi / (CS2 * h) + 0.5  # Eq. 10
+    b = nd
+    P = np.sum(E_D3Q19[b] * fs)
+    Pi = [np.sum(E_D3Q19[a] * E_D3Q19[b] * (fs + (0.5 - tf) * (fs - f0 + dfe))) for a in range(3)]
+    Q = np.sum(E_D3Q19[b] * (gs + (0.5 - tg) * (gs - g0 + dge)))
+    return np.array([P, Pi[0], Pi[1], Pi[2], Q])
+
+
+@pytest.mark.parametrize("nd,c,kappa", FACES)
+def test_flux_equals_distribution_form(d3, nd, c, kappa):
+    nu, chi = 0.04, 0.05
+    p, st = lin_problem(d3, kappa=kappa, nu=nu, chi=chi)
+    o = d3.face(p, st, nd, *c)
+    xS, h = _face_geometry(p, nd, c, kappa)
+    pred = _moments(_lin_at, xS, h)
+
+    def dfield(k):
+        # exact half-difference for quadratic equilibria
+        e = E_D3Q19[:, k]
+        fp, fm = _lin_at(xS + e * h), _lin_at(xS - e * h)
+        return (0.5 * (f_eq3(*fp[:4])[k] - f_eq3(*fm[:4])[k]),
+                0.5 * (g_eq3(*fp)[k] - g_eq3(*fm)[k]))
+
+    want = _distribution_flux(_lin_at, dfield, xS, h, nd, nu, chi, pred)
+    assert o.tau_f == pytest.approx(nu / (CS2 * h) + 0.5, rel=1e-15)
+    np.testing.assert_allclose(np.array(o.flux[:]), want, rtol=0, atol=5e-15)
+
+
+# ---------------------------------------------------------------- smooth fields
+def smooth_fields(x, y, z):
+    rho = 1.0 + 0.01 * np.sin(0.7 * x - 0.4 * y + 0.3 * z + 0.2)
+    u = 0.03 * np.cos(0.5 * x + 0.9 * y - 0.2 * z)
+    v = -0.02 * np.sin(0.8 * x - 0.3 * y + 0.6 * z + 0.4)
+    w = 0.025 * np.cos(0.4 * x + 0.5 * y + 0.7 * z - 0.3)
+    T = 0.5 + 0.2 * np.cos(0.8 * x + 0.3 * y - 0.6 * z - 0.5)
+    return [rho, u, v, w, T]
+
+
+XS = np.array([0.37, -0.21, 0.13])
+
+
+def sampled_nodes(h):
+    nodes = np.empty((5, 19))
+    for i in range(19):
+        f = smooth_fields(*(XS + h * E_D3Q19[:, i]))
+        for q in range(5):
+            nodes[q, i] = f[q]
+    return nodes
+
+
+@pytest.mark.parametrize("nd", [0, 1, 2])
+def test_predictor_is_third_order_close_to_moment_sums(d3, nd):
+    """Eqs. 46-48 are the second-order Taylor form of Eqs. 30-32: O(h^3)
+    apart on smooth data; a wrong second-order coefficient leaves O(h^2)."""
+    p = d3.Problem3(xf=np.arange(3.0), yf=np.arange(3.0), zf=np.arange(3.0), nu=0.02, chi=0.03)
+    hs = [0.2, 0.1, 0.05]
+    d = []
+    for h in hs:
+        o = d3.face_from_nodes(p, nd, sampled_nodes(h), h)
+        d.append(np.abs(np.array(o.pred[:]) - _moments(lambda x: smooth_fields(*x), XS, h)))
+    d = np.array(d)
+    orders = np.log2(d[:-1] / d[1:])
+    assert np.all(orders > 2.7), orders
+
+
+@pytest.mark.parametrize("nd", [0, 1, 2])
+def test_flux_is_second_order_close_to_distribution_form(d3, nd):
+    """Eqs. 57-59 against Eqs. 38-40 with the exact gradient (complex step)
+    and the prediction of Eqs. 30-32: O(h^2) apart at fixed nu, chi; a
+    dropped viscous term leaves O(1), a wrong dissipation coefficient O(h)."""
+    nu, chi = 0.02, 0.03
+    p = d3.Problem3(xf=np.arange(3.0), yf=np.arange(3.0), zf=np.arange(3.0), nu=nu, chi=chi)
+    hs = [0.01, 0.005, 0.0025]
+    d = []
+    for h in hs:
+        o = d3.face_from_nodes(p, nd, sampled_nodes(h), h)
+        pred = _moments(lambda x: smooth_fields(*x), XS, h)
+        eps = 1e-20
+
+        def dfield(k):
+            z = XS + 1j * eps * E_D3Q19[:, k]
+            fz = smooth_fields(*z)
+            return h * f_eq3(*fz[:4])[k].imag / eps, h * g_eq3(*fz)[k].imag / eps
+
+        want = _distribution_flux(lambda x: smooth_fields(*x), dfield, XS, h, nd, nu, chi, pred)
+        d.append(np.abs(np.array(o.flux[:]) - want))
+    d = np.array(d)
+    orders = np.log2(d[:-1] / d[1:])
+    assert np.all(orders > 1.8), (d, orders)
+
+
+# ---------------------------------------------------------------- reduction to 2D
+def _embed(a2, A, B, P, nP):
+    """3D array (nz, ny, nx) whose axis A carries the 2D x index, axis B the
+    2D y index, constant along axis P."""
+    arr = np.repeat(a2.T[:, :, None], nP, axis=2)  # axes (A, B, P)
+    xyz = np.transpose(arr, np.argsort([A, B, P]))  # axes (x, y, z)
+    return np.ascontiguousarray(xyz.transpose(2, 1, 0))
+
+
+@pytest.mark.parametrize("A,B,P", [(0, 2, 1), (1, 2, 0), (0, 1, 2)])
+def test_invariant_direction_reduces_to_the_2d_oracle(orc, d3, A, B, P):
+    D, Ad, Pe = orc.DIRICHLET, orc.ADIABATIC, orc.PERIODIC
+    nx2, ny2, nP = 9, 7, 3
+    f2x, f2y = inputs.random_faces(nx2, 5), inputs.random_faces(ny2, 6)
+    kinds2 = (D, Ad, Ad, D)
+    bcT2 = (0.9, 0.1, 0.3, 0.6)
+    bcu2 = (0.01, 0.0, 0.0, 0.02)  # tangential wall velocities W, E, S, N
+    p2 = orc.Problem(xf=f2x, yf=f2y, nu=0.03, chi=0.04, beta_g=2e-3, kappa=0.9, dt=0.2,
+                     bc_kind=kinds2, bc_T=bcT2, bc_u=bcu2, fx=1e-4, fy=-2e-4)
+    faces = [None] * 3
+    faces[A], faces[B], faces[P] = f2x, f2y, np.arange(nP + 1.0)
+    kinds, bcT = [Pe] * 6, [0.0] * 6
+    bcu = [[0.0] * 3 for _ in range(6)]
+    for s2, (ax, hi) in enumerate(((A, 0), (A, 1), (B, 0), (B, 1))):
+        s3 = 2 * ax + hi
+        kinds[s3], bcT[s3] = kinds2[s2], bcT2[s2]
+        bcu[s3][B if ax == A else A] = bcu2[s2]
+    force = [0.0] * 3
+    force[A], force[B] = 1e-4, -2e-4
+    p3 = d3.Problem3(xf=faces[0], yf=faces[1], zf=faces[2], nu=0.03, chi=0.04, beta_g=2e-3,
+                     kappa=0.9, dt=0.2, g_axis=B, force=tuple(force), bc_kind=tuple(kinds),
+                     bc_T=tuple(bcT), bc_u=tuple(tuple(b) for b in bcu))
+    rho2, u2, v2, T2 = inputs.perturbed_state(nx2, ny2, seed=7)
+    vel = [None] * 3
+    vel[A], vel[B], vel[P] = u2, v2, np.zeros_like(u2)
+    st3 = [_embed(a, A, B, P, nP) for a in (rho2, vel[0], vel[1], vel[2], T2)]
+    s2, r2, rc2 = orc.step(p2, (rho2, u2, v2, T2), 5)
+    s3, r3, rc3 = d3.step(p3, st3, 5)
+    assert rc2 == 0 and rc3 == 0
+    want_vel = [None] * 3
+    want_vel[A], want_vel[B], want_vel[P] = s2[1], s2[2], np.zeros_like(s2[1])
+    want = [s2[0], want_vel[0], want_vel[1], want_vel[2], s2[3]]
+    for q in range(5):
+        np.testing.assert_allclose(s3[q], _embed(want[q], A, B, P, nP), rtol=0, atol=2e-15)
+    assert r3 == pytest.approx(r2, rel=1e-12)
+
+
+# ---------------------------------------------------------------- walls, conservation
+def _cavity(d3, kinds, seed=31, n=(6, 7, 5), beta_g=1e-3):
+    xf, yf, zf = (inputs.random_faces(n[a], seed + a) for a in range(3))
+    p = d3.Problem3(xf=xf, yf=yf, zf=zf, nu=0.03, chi=0.04, beta_g=beta_g, kappa=0.9, dt=0.2,
+                    bc_kind=kinds, bc_T=(0.9, 0.1, 0.3, 0.6, 0.2, 0.7),
+                    bc_u=((0, 0.01, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0.02, -0.01, 0)))
+    st = inputs.perturbed_state3(*n, seed=seed + 5)
+    return p, st
+
+
+def test_wall_faces_carry_no_mass_and_adiabatic_walls_no_energy(orc, d3):
+    D, A = orc.DIRICHLET, orc.ADIABATIC
+    p, st = _cavity(d3, (D, D, A, A, A, A))
+    fx, fy, fz = d3.fluxes(p, st)
+    for f, sl in ((fx, (Ellipsis, 0)), (fx, (Ellipsis, -1)), (fy, (slice(None), 0)),
+                  (fy, (slice(None), -1)), (fz, (0,)), (fz, (-1,))):
+        mass = f[0][sl] if f is not fy else f[0][:, sl[1], :]
+        assert np.all(mass == 0.0)
+    assert np.all(fy[4][:, 0, :] == 0.0) and np.all(fy[4][:, -1, :] == 0.0)
+    assert np.all(fz[4][0] == 0.0) and np.all(fz[4][-1] == 0.0)
+    assert np.all(fx[4][..., 0] != 0.0)
+
+
+def test_mass_conserved_and_energy_with_adiabatic_walls(orc, d3):
+    D, A = orc.DIRICHLET, orc.ADIABATIC
+    for kinds, energy in (((D, D, A, A, A, D), False), ((A,) * 6, True)):
+        p, st = _cavity(d3, kinds, beta_g=2e-3)
+        dV = np.einsum("k,j,i->kji", np.diff(p.zf), np.diff(p.yf), np.diff(p.xf))
+        m0, e0 = np.sum(st[0] * dV), np.sum(st[0] * st[4] * dV)
+        s, _, rc = d3.step(p, st, 40)
+        assert rc == 0
+        assert np.sum(s[0] * dV) == pytest.approx(m0, rel=1e-14)
+        if energy:
+            assert np.sum(s[0] * s[4] * dV) == pytest.approx(e0, rel=1e-14)
+
+
+def test_conduction_profile_is_a_fixed_point(d3):
+    n = 8
+    p = d3.cubic_cavity(n, 1e4, phi=1.5)
+    p.beta_g = 0.0
+    st = inputs.conduction_state3(p.xf, p.yf, p.zf)
+    s, _, rc = d3.step(p, st, 20)
+    assert rc == 0
+    for q in range(5):
+        np.testing.assert_allclose(s[q], st[q], rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- symmetries
+def test_cyclic_axis_permutation_without_gravity(orc, d3):
+    """x -> y -> z -> x relabelling (no gravity, mixed walls, irregular
+    mesh) commutes with the step: catches face-orientation slips."""
+    D, A, Pe = orc.DIRICHLET, orc.ADIABATIC, orc.PERIODIC
+    p, st = _cavity(d3, (D, A, Pe, Pe, A, D), beta_g=0.0)
+    s, _, rc = d3.step(p, st, 3)
+    assert rc == 0
+    # new axis 0 <- old axis 2, 1 <- 0, 2 <- 1 (old x becomes new y)
+    perm = [2, 0, 1]
+    f_old = (p.xf, p.yf, p.zf)
+    kinds, bcT, bcu = [0] * 6, [0.0] * 6, [None] * 6
+    for new in range(3):
+        old = perm[new]
+        for hi in range(2):
+            kinds[2 * new + hi] = p.bc_kind[2 * old + hi]
+            bcT[2 * new + hi] = p.bc_T[2 * old + hi]
+            ow = p.bc_u[2 * old + hi]
+            bcu[2 * new + hi] = tuple(ow[perm[c]] for c in range(3))
+    q = d3.Problem3(xf=f_old[perm[0]], yf=f_old[perm[1]], zf=f_old[perm[2]], nu=p.nu, chi=p.chi,
+                    beta_g=0.0, kappa=p.kappa, dt=p.dt, bc_kind=tuple(kinds), bc_T=tuple(bcT),
+                    bc_u=tuple(bcu))
+
+    def relabel(a):
+        # a[k, j, i] with (x, y, z) -> new array over (x', y', z') = (z, x, y)
+        xyz = a.transpose(2, 1, 0)
+        return np.ascontiguousarray(np.transpose(xyz, perm).transpose(2, 1, 0))
+
+    vel = (st[1], st[2], st[3])
+    st2 = (relabel(st[0]), relabel(vel[perm[0]]), relabel(vel[perm[1]]), relabel(vel[perm[2]]),
+           relabel(st[4]))
+    s2, _, rc = d3.step(q, st2, 3)
+    assert rc == 0
+    sv = (s[1], s[2], s[3])
+    want = (relabel(s[0]), relabel(sv[perm[0]]), relabel(sv[perm[1]]), relabel(sv[perm[2]]),
+            relabel(s[4]))
+    for k in range(5):
+        np.testing.assert_allclose(s2[k], want[k], rtol=0, atol=1e-15)
+
+
+def test_x_reflection_with_gravity(orc, d3):
+    D, A = orc.DIRICHLET, orc.ADIABATIC
+    p, st = _cavity(d3, (D, D, A, A, A, A), beta_g=3e-3)
+    p.bc_u = ((0, 0, 0),) * 6
+    s, _, rc = d3.step(p, st, 4)
+    assert rc == 0
+    L = p.xf[-1]
+    q = d3.Problem3(xf=(L - p.xf)[::-1].copy(), yf=p.yf, zf=p.zf, nu=p.nu, chi=p.chi,
+                    beta_g=p.beta_g, kappa=p.kappa, dt=p.dt, bc_kind=p.bc_kind,
+                    bc_T=(p.bc_T[1], p.bc_T[0]) + tuple(p.bc_T[2:]), bc_u=p.bc_u)
+
+    def fl(a):
+        return np.ascontiguousarray(a[..., ::-1])
+
+    st2 = (fl(st[0]), -fl(st[1]), fl(st[2]), fl(st[3]), fl(st[4]))
+    s2, _, rc = d3.step(q, st2, 4)
+    assert rc == 0
+    want = (fl(s[0]), -fl(s[1]), fl(s[2]), fl(s[3]), fl(s[4]))
+    for k in range(5):
+        np.testing.assert_allclose(s2[k], want[k], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- Table 5
+@pytest.mark.slow
+def test_cubic_cavity_ra1e3_against_table5(d3):
+    gold = json.load(open(os.path.join(HERE, "golden", "table5_cubic_cavity.json")))
+    n = 16
+    p = d3.cubic_cavity(n, gold["Ra"], Pr=gold["Pr"], Ma=gold["Vc"])
+    st0 = inputs.conduction_state3(p.xf, p.yf, p.zf)
+    st, steps, res, rc = d3.run_to_steady(p, st0, 1e-7, 100000)
+    assert rc == 0
+    # heat enters at the hot +x wall and leaves at the cold -x wall: flux along -x
+    nu_hot, nu_cold = -d3.nusselt(p, st, 1), -d3.nusselt(p, st, 0)
+    # the steady energy balance: the same heat through every x-plane, up to
+    # the storage term left at a residual of 1e-7 (a few 1e-5 here)
+    assert nu_cold == pytest.approx(nu_hot, rel=1e-4)
+    assert -d3.nusselt(p, st, d3.MID_PLANE_X) == pytest.approx(nu_hot, rel=1e-4)
+    assert nu_hot == pytest.approx(gold["Nu_o"], rel=0.015)
+    assert -d3.nusselt(p, st, 1, mid=True) == pytest.approx(gold["Nu_m"], rel=0.015)
+    # u along the vertical line x = y = L/2, w along x at y = z = L/2
+    h = n // 2
+    u_line = 0.25 * (st[1][:, h - 1, h - 1] + st[1][:, h - 1, h] + st[1][:, h, h - 1]
+                     + st[1][:, h, h])
+    w_line = 0.25 * (st[3][h - 1, h - 1, :] + st[3][h - 1, h, :] + st[3][h, h - 1, :]
+                     + st[3][h, h, :])
+    c = centres(p.xf) / n
+    Vc = gold["Vc"]
+    assert u_line.max() / Vc == pytest.approx(gold["u_max_over_Vc"], rel=0.06)
+    assert w_line.max() / Vc == pytest.approx(gold["w_max_over_Vc"], rel=0.04)
+    assert abs(c[u_line.argmax()] - gold["u_max_z_over_L"]) < 1.2 / n
+    assert abs(c[w_line.argmax()] - gold["w_max_x_over_L"]) < 1.2 / n
