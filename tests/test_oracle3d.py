@@ -346,6 +346,22 @@ def test_mass_conserved_and_energy_with_adiabatic_walls(orc, d3):
             assert np.sum(s[0] * s[4] * dV) == pytest.approx(e0, rel=1e-14)
 
 
+def test_periodic_faces_are_shared_and_conserve(orc, d3):
+    """A periodic side's first and last faces are one face: equal fluxes, and
+    mass and rho T conserved with periodic x, z and adiabatic y walls."""
+    A, Pe = orc.ADIABATIC, orc.PERIODIC
+    p, st = _cavity(d3, (Pe, Pe, A, A, Pe, Pe), beta_g=2e-3)
+    fx, fy, fz = d3.fluxes(p, st)
+    np.testing.assert_array_equal(fx[..., 0], fx[..., -1])
+    np.testing.assert_array_equal(fz[:, 0], fz[:, -1])
+    dV = np.einsum("k,j,i->kji", np.diff(p.zf), np.diff(p.yf), np.diff(p.xf))
+    m0, e0 = np.sum(st[0] * dV), np.sum(st[0] * st[4] * dV)
+    s, _, rc = d3.step(p, st, 40)
+    assert rc == 0
+    assert np.sum(s[0] * dV) == pytest.approx(m0, rel=1e-14)
+    assert np.sum(s[0] * s[4] * dV) == pytest.approx(e0, rel=1e-14)
+
+
 def test_conduction_profile_is_a_fixed_point(d3):
     n = 8
     p = d3.cubic_cavity(n, 1e4, phi=1.5)
