@@ -117,21 +117,41 @@ WORKLOADS = {
              "Ra=1e3, Pr=0.71, Ma=0.1, FP64, run to max(R_u, R_T) < 1e-9: Table 1's quantities "
              "and the time to the steady state for each face stage",
         n=64, Ra=1e3, Pr=0.71, Ma=0.1, tol=1e-9, max_steps=400000, kind="schemes"),
+    "cubic80": dict(
+        desc="3D cubic cavity of Section 4.4 / Table 6: 80x80x80 cells, tanh stretching "
+             "phi=1.8 (Eq. 74) on all axes, Ra=1e6, Pr=0.71, V_c=0.1, cold -x / hot +x walls, "
+             "adiabatic others, gravity along -z; D3Q19 lattice, lattice spacing kappa=0.5 times the "
+             "smaller normal width; FP32 bulk + FP64 reductions",
+        n=80, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp32", inner=500,
+        kind="cubic"),
+    "cubic80_fp64": dict(
+        desc="3D cubic cavity of Section 4.4 / Table 6: 80x80x80 cells, tanh phi=1.8, Ra=1e6, "
+             "Pr=0.71, V_c=0.1, D3Q19 lattice, FP64",
+        n=80, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp64", inner=50,
+        kind="cubic"),
+    "cubic256": dict(
+        desc="3D profiling case: cubic cavity 256x256x256, tanh phi=1.8, Ra=1e6, Pr=0.71, "
+             "V_c=0.1, FP32 bulk + FP64 reductions (state 336 MB per buffer, > L2)",
+        n=256, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp32", inner=20,
+        kind="cubic"),
     "cavity512_fp64": dict(
         desc="differentially heated cavity 512x512, tanh phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, FP64",
         nx=512, ny=512, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp64", inner=100,
         kind="cavity"),
 }
 DEFAULT_WORKLOAD = "cavity512"
+STEP3_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs3d.cu",
+                 "paper_2202_13449_gb300/csrc/rtlbfs3d_dev.cuh",
+                 "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh"]
 STEP_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_step.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_march.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh",
                 "paper_2202_13449_gb300/csrc/rtlbfs_kernels.h"]
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for p in STEP_SOURCES:
+    for p in sources or STEP_SOURCES:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -146,7 +166,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(workload: str, precision: str, kernel: str):
+def profile_traffic(workload: str, precision: str, kernel: str, sources=None):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
@@ -154,7 +174,7 @@ def profile_traffic(workload: str, precision: str, kernel: str):
         with open(path) as f:
             d = json.load(f)
         e = d.get(f"{workload}:{precision}:{kernel}")
-        if e and e.get("kernel_hash") == kernel_hash():
+        if e and e.get("kernel_hash") == kernel_hash(sources):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -752,7 +772,191 @@ def run_schemes(args, w):
     print(json.dumps(line), flush=True)
 
 
+def cubic_setup(capi, inputs, w):
+    """The 3D cubic cavity of a workload: solver, initial state, faces."""
+    n = w["n"]
+    f = capi.tanh_faces(n, float(n), w["phi"])
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
+    s = capi.Solver3(f, f, f, prec)
+    dt = 0.5 * float(min(f[1:] - f[:-1]))
+    s.set_params(w["Ra"], w["Pr"], w["Ma"], dt)
+    s.set_lattice(w.get("kappa", 1.0))
+    st = inputs.conduction_state3(f, f, f)
+    s.set_state(*st)
+    return s, st, f, dt
+
+
+def run_cubic(args, w):
+    """3D workload: one bench step = `inner` time steps of the cubic cavity
+    (one launch per step, graphs), L2 flushed between bench steps."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    n = w["n"]
+    cells = n ** 3
+    inner = args.inner or w["inner"]
+    s, st0, f, dt = cubic_setup(capi, inputs, w)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s.set_stream(stream)
+    if args.schedule == "auto":
+        tile, tune_ms = s.autotune(max(8, min(64, 20_000_000 // cells + 8)))
+    else:
+        tile = int(args.schedule.split(":")[1]) if ":" in args.schedule else 0
+        s.set_schedule(tile, 0)
+        tune_ms = 0.0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        s.step(inner)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = capi.launch_count()
+    ev = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(inner)
+        b.record(stream)
+        ev.append((a, b))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    ms_max = job_max(sum(a.elapsed_time(b) for a, b in ev))
+    value = cells * inner * args.steps * ws / (ms_max * 1e-3) / 1e6
+
+    host = pinned(st0)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(*host)
+        s.step(inner)
+        out = s.get_state()
+    torch.cuda.synchronize()
+    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
+    assert np.all(np.isfinite(out[4]))
+    bytes_io = 5 * cells * 8
+
+    per_launch_s = ms_max * 1e-3 / (inner * args.steps)
+    rs = 4 if w["precision"] == "fp32" else 8
+    _, ops_cell, sfu_cell = capi.op_counts3()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    if rs == 4:
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        unit, src = "T FP32 op/s", f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz max SM clock"
+    else:
+        alu_peak = 1.25 / 2
+        unit, src = "T FP64 op/s", "nominal FP64 1.25 TFLOP/s = 0.625 T fused multiply-adds/s"
+    traffic = profile_traffic(args.workload, w["precision"], "step3", STEP3_SOURCES)
+    alu = ops_cell * cells / per_launch_s / 1e12
+    alg_bytes = 10 * rs * cells  # read 5 fields + write 5 fields per cell
+    hbm = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    # Table 6 context: device time for t* = V_c t / L = 1 on this mesh
+    steps_t1 = int(np.ceil(float(n) / (w["Ma"] * dt)))
+    res, steps_total = s.residual()
+    line = {
+        "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
+        "value": round(value, 2),
+        "unit": "M cell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if rs == 4 else "f64",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "time_steps_per_bench_step": inner, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between bench steps (256 MB write)",
+                   "schedule": {"kernel": "step3", "tile": ["32x4", "16x8", "32x8"][tile],
+                                "autotune_ms_per_step": round(tune_ms, 5)},
+                   "dt": dt, "e2e_host_buffers": "pinned",
+                   "state_bytes_per_buffer": 5 * rs * cells},
+        "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
+                     "unit": unit, "frac": round(alu / alu_peak, 4), "traffic": traffic,
+                     "kernel": "rtlbfs3::step3_kernel", "ops_per_cell_update": ops_cell,
+                     "sfu_ops_per_cell_update": sfu_cell, "peak_source": src,
+                     "alg_ops_per_launch": ops_cell * cells},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(hbm, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(hbm / peak, 4), "traffic": traffic,
+                         "kernel": "rtlbfs3::step3_kernel",
+                         "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes},
+        "table6_context": {"steps_for_t_star_1": steps_t1,
+                           "device_s_for_t_star_1": round(steps_t1 * per_launch_s, 3),
+                           "paper_rtlbfs_s": 58864.12, "paper_tlbfs_s": 60585.58,
+                           "paper_hardware": "serial CPU program, machine unspecified"}
+        if n == 80 else None,
+        "clocks": clocks,
+        "wall_s": round(t_wall, 3),
+        "residual_last_step": res,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_cubic(w, args.cpu_seconds)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def oracle_cubic(w):
+    import oracle
+    from oracle import d3
+    from paper_2202_13449_gb300 import inputs
+    oracle.build()
+    n = w["n"]
+    f = oracle.tanh_faces(n, float(n), w["phi"])
+    p = d3.cubic_cavity(n, w["Ra"], Pr=w["Pr"], Ma=w["Ma"], phi=w["phi"], kappa=w.get("kappa", 1.0))
+    st = inputs.conduction_state3(f, f, f)
+    return oracle, d3, p, st
+
+
+def cpu_baseline_cubic(w, seconds):
+    """The 3D FP64 oracle as it stands on this host's cores: time steps of the
+    same mesh until `seconds` (at least one)."""
+    oracle, d3, p, st = oracle_cubic(w)
+    used = oracle.set_threads(os.cpu_count() or 1)
+    cells = w["n"] ** 3
+    n, t0 = 0, time.perf_counter()
+    while n == 0 or time.perf_counter() - t0 < seconds:
+        st, _, _ = d3.step(p, st, 1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(cells * n / dt / 1e6, 3), "unit": "M cell-updates/s", "cores": used,
+            "kind": "oracle",
+            "sample": f"{n} FP64 time steps of the same {w['n']}^3 mesh ({dt:.1f} s, OpenMP "
+                      f"over z-planes)"}
+
+
 def run_ours(args, w):
+    if w.get("kind") == "cubic":
+        return run_cubic(args, w)
     if w.get("kind") == "schemes":
         return run_schemes(args, w)
     if w.get("kind") == "stability":
@@ -1064,6 +1268,14 @@ def run_reference(args, w):
             for k, (p, _, _) in enumerate(probs):
                 states[k], _, _ = oracle.step(p, states[k], per_step)
         sample = f"the first 16 cavities of the batch ({cells} cells), {per_step} FP64 steps each"
+    elif kind == "cubic":
+        _, d3, p, st0 = oracle_cubic(w)
+        cells = w["n"] ** 3
+        box = [st0]
+
+        def one():
+            box[0], _, _ = d3.step(p, box[0], per_step)
+        sample = f"{per_step} FP64 time steps of the {w['n']}^3 mesh"
     else:
         p, st0 = oracle_problem(oracle, inputs, w)
         cells = w["nx"] * w["ny"]

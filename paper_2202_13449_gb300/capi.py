@@ -25,7 +25,8 @@ WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC = 0, 1, 2
 NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
 
 HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
-HEADERS = [HEADER, os.path.join(_build.ROOT, "include", "rtlbfs_batch.h")]
+HEADERS = [HEADER, os.path.join(_build.ROOT, "include", "rtlbfs_batch.h"),
+           os.path.join(_build.ROOT, "include", "rtlbfs3d.h")]
 SLOT_EMPTY, SLOT_RUNNING, SLOT_CONVERGED, SLOT_MAX_STEPS, SLOT_DIVERGED = -1, 0, 1, 2, 3
 
 
@@ -105,6 +106,29 @@ _SIGS = {
     "rtlbfs_nusselt_noalloc": (C.c_int, [C.c_int, C.c_int, _dp, _dp, _vp, _vp, _vp, _vp,
                                          C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.POINTER(C.c_int), _dp, _dp, C.c_int, _vp, _vp]),
+    # 3D (include/rtlbfs3d.h)
+    "rtlbfs3d_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int,
+                                  C.POINTER(_vp)]),
+    "rtlbfs3d_set_params": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs3d_set_physics": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs3d_set_lattice": (C.c_int, [_vp, C.c_double]),
+    "rtlbfs3d_set_gravity_axis": (C.c_int, [_vp, C.c_int]),
+    "rtlbfs3d_set_body_force": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs3d_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _dp]),
+    "rtlbfs3d_set_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
+    "rtlbfs3d_get_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
+    "rtlbfs3d_step": (C.c_int, [_vp, C.c_long]),
+    "rtlbfs3d_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_long, C.c_double,
+                                         C.POINTER(C.c_long), _dp]),
+    "rtlbfs3d_residual": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
+    "rtlbfs3d_nusselt": (C.c_int, [_vp, C.c_int, C.c_int, _dp]),
+    "rtlbfs3d_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "rtlbfs3d_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
+    "rtlbfs3d_set_stream": (C.c_int, [_vp, _vp]),
+    "rtlbfs3d_sync": (C.c_int, [_vp]),
+    "rtlbfs3d_last_error": (C.c_char_p, [_vp]),
+    "rtlbfs3d_op_counts": (C.c_int, [_dp, _dp, _dp]),
+    "rtlbfs3d_destroy": (None, [_vp]),
 }
 
 
@@ -141,7 +165,7 @@ def header_functions(paths=None):
     for path in (paths or HEADERS):
         text = open(path).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(rtlbfs_[a-z0-9_]+)\s*\(", text))
+        names |= set(re.findall(r"\b(rtlbfs(?:3d)?_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
 
@@ -460,3 +484,139 @@ def stability_map(n, Ra, kappa, dt=None, *, Pr=0.71, Ma=0.1, tol=1e-9, max_steps
     if rc:
         raise RTLBFSError(rc, "rtlbfs_stability_map")
     return np.array(st[:m]), np.array(steps[:m]), float(el.value)
+
+
+# ---------------------------------------------------------------------------
+# 3D (include/rtlbfs3d.h)
+# ---------------------------------------------------------------------------
+XM, XP, YM, YP, ZM, ZP, MID_X = 0, 1, 2, 3, 4, 5, 6
+
+
+def op_counts3():
+    """(FP ops per face, FP ops per cell-update, SFU ops per cell-update) of
+    the 3D step, each face and gradient evaluated once (host-only)."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().rtlbfs3d_op_counts(C.byref(a), C.byref(b), C.byref(c))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs3d_op_counts")
+    return a.value, b.value, c.value
+
+
+class Solver3:
+    """One 3D mesh on the GPU (a handle of ``include/rtlbfs3d.h``); the state
+    is five arrays (rho, u, v, w, T) of shape (nz, ny, nx)."""
+
+    def __init__(self, xf, yf, zf, precision: int = FP64):
+        L = lib()
+        self.f = [np.ascontiguousarray(a, dtype=np.float64) for a in (xf, yf, zf)]
+        self.nx, self.ny, self.nz = (len(a) - 1 for a in self.f)
+        self.precision = precision
+        h = _vp()
+        rc = L.rtlbfs3d_create(self.nx, self.ny, self.nz, *[_ptr(a) for a in self.f],
+                               int(precision), C.byref(h))
+        if rc:
+            raise RTLBFSError(rc, "rtlbfs3d_create")
+        self._h = h
+
+    def _check(self, rc: int, what: str):
+        if rc:
+            msg = lib().rtlbfs3d_last_error(self._h)
+            raise RTLBFSError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rtlbfs3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def set_params(self, Ra, Pr, Ma, dt):
+        self._check(lib().rtlbfs3d_set_params(self._h, Ra, Pr, Ma, dt), "set_params")
+
+    def set_physics(self, nu, chi, beta_g):
+        self._check(lib().rtlbfs3d_set_physics(self._h, nu, chi, beta_g), "set_physics")
+
+    def set_lattice(self, kappa):
+        self._check(lib().rtlbfs3d_set_lattice(self._h, kappa), "set_lattice")
+
+    def set_gravity_axis(self, axis):
+        self._check(lib().rtlbfs3d_set_gravity_axis(self._h, int(axis)), "set_gravity_axis")
+
+    def set_body_force(self, fx, fy, fz):
+        self._check(lib().rtlbfs3d_set_body_force(self._h, fx, fy, fz), "set_body_force")
+
+    def set_bc(self, side, kind, T_wall=0.0, u_wall=(0.0, 0.0, 0.0)):
+        uw = np.ascontiguousarray(u_wall, dtype=np.float64)
+        self._check(lib().rtlbfs3d_set_bc(self._h, int(side), int(kind), float(T_wall), _ptr(uw)),
+                    "set_bc")
+
+    def set_schedule(self, tile: int = 0, kchunk: int = 0):
+        """tile 0: 32 x 4, 1: 16 x 8, 2: 32 x 8 columns per block; kchunk
+        z-planes per work unit (0: automatic)."""
+        self._check(lib().rtlbfs3d_set_schedule(self._h, int(tile), int(kchunk)), "set_schedule")
+
+    def autotune(self, steps: int = 32):
+        t, ms = C.c_int(0), C.c_double(0)
+        self._check(lib().rtlbfs3d_autotune(self._h, int(steps), C.byref(t), C.byref(ms)),
+                    "autotune")
+        return int(t.value), float(ms.value)
+
+    def set_stream(self, stream):
+        ptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self._check(lib().rtlbfs3d_set_stream(self._h, ptr), "set_stream")
+
+    def sync(self):
+        self._check(lib().rtlbfs3d_sync(self._h), "sync")
+
+    def set_state(self, rho, u, v, w, T):
+        n = self.nx * self.ny * self.nz
+        arrs = [_f64(a, n) for a in (rho, u, v, w, T)]
+        self._check(lib().rtlbfs3d_set_state(self._h, *[_ptr(a) for a in arrs]), "set_state")
+
+    def get_state(self):
+        out = [np.empty(self.shape) for _ in range(5)]
+        self._check(lib().rtlbfs3d_get_state(self._h, *[_ptr(a) for a in out]), "get_state")
+        return tuple(out)
+
+    def step(self, n: int):
+        self._check(lib().rtlbfs3d_step(self._h, int(n)), "step")
+
+    def step_rc(self, n: int) -> int:
+        """step() returning the status code instead of raising."""
+        return int(lib().rtlbfs3d_step(self._h, int(n)))
+
+    def run_to_steady(self, tol: float, max_steps: int, timeout_s: float = 0.0):
+        """Returns (rc, steps_taken, (R_u, R_T)); rc 0 = converged."""
+        steps = C.c_long(0)
+        res = np.full(2, np.nan)
+        rc = lib().rtlbfs3d_run_to_steady(self._h, float(tol), int(max_steps), float(timeout_s),
+                                          C.byref(steps), _ptr(res))
+        if rc not in (OK, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_DIVERGED):
+            self._check(rc, "run_to_steady")
+        return int(rc), int(steps.value), (float(res[0]), float(res[1]))
+
+    def residual(self):
+        res = np.full(2, np.nan)
+        steps = C.c_long(0)
+        self._check(lib().rtlbfs3d_residual(self._h, _ptr(res), C.byref(steps)), "residual")
+        return (float(res[0]), float(res[1])), int(steps.value)
+
+    def nusselt(self, side: int, mid: bool = False) -> float:
+        out = C.c_double(0)
+        self._check(lib().rtlbfs3d_nusselt(self._h, int(side), int(bool(mid)), C.byref(out)),
+                    "nusselt")
+        return float(out.value)
