@@ -13,7 +13,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import DIRICHLET, ADIABATIC, PERIODIC, lib as _lib2d, params_from_ra, tanh_faces  # noqa: F401
+from . import (DIRICHLET, ADIABATIC, PERIODIC, RTLBFS, TLBFS, lib as _lib2d,  # noqa: F401
+               params_from_ra, tanh_faces)
 
 NQ = 5
 MID_PLANE_X = 6  # side value of nusselt(): the x-normal face plane at nx/2
@@ -29,6 +30,7 @@ class _Problem3(C.Structure):
         ("force", C.c_double * 3),
         ("g_axis", C.c_int),
         ("bc_kind", C.c_int * 6), ("bc_T", C.c_double * 6), ("bc_u", C.c_double * 18),
+        ("scheme", C.c_int),
     ]
 
 
@@ -99,6 +101,7 @@ class Problem3:
     bc_kind: tuple = (DIRICHLET, DIRICHLET, ADIABATIC, ADIABATIC, ADIABATIC, ADIABATIC)
     bc_T: tuple = (0.0, 1.0, 0.0, 0.0, 0.0, 0.0)
     bc_u: tuple = ((0.0, 0.0, 0.0),) * 6
+    scheme: int = 0  # 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2)
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -120,6 +123,7 @@ class Problem3:
         p.bc_kind[:] = list(self.bc_kind)
         p.bc_T[:] = list(self.bc_T)
         p.bc_u[:] = [float(x) for uw in self.bc_u for x in uw]
+        p.scheme = int(self.scheme)
         return p
 
 

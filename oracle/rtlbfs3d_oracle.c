@@ -54,6 +54,11 @@
  *   R12 residual: R_u = || |u|^{n+1} - |u|^n ||_2 / || |u|^{n+1} ||_2 with
  *       |u| = sqrt(u^2 + v^2 + w^2), R_T likewise; zero denominator -> inf,
  *       a sum that is not a number -> NaN (divergence)
+ * Second face stage, scheme = 1: the original TLBFS of Section 2.2 that
+ * RTLBFS approximates -- steps 5-6 replaced by (a) D3Q19 equilibria (Eqs.
+ * 3-4, c_p = 1) at the nodes x_S - e_i h, i.e. node -e_i of step 4; (b) the
+ * predicted variables as their moments, Eqs. 30-32, with the wall rule R8;
+ * (c) the fluxes of Eqs. 38-40 with the non-equilibrium parts of Eqs. 33-34.
  *   Nu  a wall's Nusselt number is the energy flux of step 6 summed over
  *       the wall's faces with their areas, times the domain length normal
  *       to the wall, / (chi dT wall area): Eq. 76 with the conductive flux
@@ -87,6 +92,7 @@ typedef struct {
     int bc_kind[6];
     double bc_T[6];
     double bc_u[6][3]; /* wall velocity; its normal component is ignored */
+    int scheme;        /* 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2) */
 } orc3_problem;
 
 /* D3Q19 (Eqs. 5-6 with the reading R5). */
@@ -176,6 +182,7 @@ static int check_problem(const orc3_problem* p)
     for (int s = 0; s < 6; ++s)
         if (p->bc_kind[s] < 0 || p->bc_kind[s] > 2) return -1;
     if (p->g_axis < 0 || p->g_axis > 2) return -1;
+    if (p->scheme != 0 && p->scheme != 1) return -1;
     if (!(p->kappa > 0.0) || !(p->nu > 0.0) || !(p->chi > 0.0)) return -1;
     return 0;
 }
@@ -510,6 +517,83 @@ static void face_from_nodes(const orc3_problem* p, int nd, double h, int wall_si
 #undef C0
 }
 
+/* D3Q19 weights of Eq. 6 in the order of E19 */
+static double w19(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+/* Eq. 3 */
+static double f_equilibrium3(int i, double r, const double u[3])
+{
+    double eu = E19[i][0] * u[0] + E19[i][1] * u[1] + E19[i][2] * u[2];
+    double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return w19(i) * r * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - usq / (2.0 * CS2));
+}
+
+/* Eq. 4 with c_p = 1 */
+static double g_equilibrium3(int i, double r, const double u[3], double T)
+{
+    double eu = E19[i][0] * u[0] + E19[i][1] * u[1] + E19[i][2] * u[2];
+    return w19(i) * r * T * (1.0 + eu / CS2);
+}
+
+/*
+ * TLBFS steps (a)-(c) of Section 2.2 with D3Q19, for a face with normal
+ * axis nd, from the node primitives o->node (step 4): (a) equilibria at
+ * x_S - e_i dt, which is node -e_i of the lattice (R5); (b) the predicted
+ * variables as their moments, Eqs. 30-32, then the wall rule R8; (c) the
+ * fluxes of Eqs. 38-40 with the non-equilibrium parts of Eqs. 33-34.
+ */
+static void face_tlbfs_from_nodes(const orc3_problem* p, int nd, double h, int wall_side,
+                                  orc3_face_out* o)
+{
+    o->h = h;
+    o->tau_f = p->nu / (CS2 * h) + 0.5;  /* Eq. 9 */
+    o->tau_g = p->chi / (CS2 * h) + 0.5; /* Eq. 10 */
+    double fn[19], gn[19];
+    for (int i = 0; i < 19; ++i) {
+        int j = node_of(-E19[i][0], -E19[i][1], -E19[i][2]);
+        double r = o->node[Q_RHO][j], T = o->node[Q_T][j];
+        double u[3] = {o->node[Q_U][j], o->node[Q_V][j], o->node[Q_W][j]};
+        fn[i] = f_equilibrium3(i, r, u);
+        gn[i] = g_equilibrium3(i, r, u, T);
+    }
+    double rho_s = 0.0, m_s[3] = {0.0, 0.0, 0.0}, E_s = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        rho_s += fn[i];
+        for (int a = 0; a < 3; ++a) m_s[a] += E19[i][a] * fn[i];
+        E_s += gn[i];
+    }
+    if (wall_side >= 0) { /* R8 */
+        for (int a = 0; a < 3; ++a) m_s[a] = a == nd ? 0.0 : rho_s * p->bc_u[wall_side][a];
+        if (p->bc_kind[wall_side] == BC_DIRICHLET) E_s = rho_s * p->bc_T[wall_side];
+    }
+    o->pred[0] = rho_s;
+    for (int a = 0; a < 3; ++a) o->pred[1 + a] = m_s[a];
+    o->pred[4] = E_s;
+    double us[3] = {m_s[0] / rho_s, m_s[1] / rho_s, m_s[2] / rho_s};
+    double Ts = E_s / rho_s;
+    double P = 0.0, Pi[3] = {0.0, 0.0, 0.0}, Q = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        double fs = f_equilibrium3(i, rho_s, us);
+        double gs = g_equilibrium3(i, rho_s, us, Ts);
+        double en = E19[i][nd];
+        P += en * fs;
+        for (int a = 0; a < 3; ++a) Pi[a] += E19[i][a] * en * (fs + (0.5 - o->tau_f) * (fs - fn[i]));
+        Q += en * (gs + (0.5 - o->tau_g) * (gs - gn[i]));
+    }
+    o->flux[0] = P;
+    for (int a = 0; a < 3; ++a) o->flux[1 + a] = Pi[a];
+    o->flux[4] = Q;
+}
+
+/* Steps 5-6 of the selected face stage */
+static void face_stage(const orc3_problem* p, int nd, double h, int wall_side, orc3_face_out* o)
+{
+    if (p->scheme == 1)
+        face_tlbfs_from_nodes(p, nd, h, wall_side, o);
+    else
+        face_from_nodes(p, nd, h, wall_side, o);
+}
+
 /* One face normal to axis nd at face position (i, j, k): the face between
  * cell (i, j, k) - e_nd and cell (i, j, k). */
 static void face_at(const orc3_problem* p, const work* w, int nd, int i, int j, int k,
@@ -531,7 +615,7 @@ static void face_at(const orc3_problem* p, const work* w, int nd, int i, int j, 
         if (c[nd] == p->n[nd]) wall = 2 * nd + 1;
     }
     face_nodes(nd, &L, &R, h, o->node);
-    face_from_nodes(p, nd, h, wall, o);
+    face_stage(p, nd, h, wall, o);
 }
 
 static void all_face_fluxes(const orc3_problem* p, work* w)
@@ -763,7 +847,7 @@ int orc3_face_from_nodes(const orc3_problem* p, int nd, const double* nodes, dou
     if (!p || !nodes || !o || nd < 0 || nd > 2 || !(h > 0.0) || wall_side < -1 || wall_side > 5)
         return -1;
     memcpy(o->node, nodes, sizeof(o->node));
-    face_from_nodes(p, nd, h, wall_side, o);
+    face_stage(p, nd, h, wall_side, o);
     return 0;
 }
 
