@@ -129,6 +129,12 @@ WORKLOADS = {
              "Pr=0.71, V_c=0.1, D3Q19 lattice, FP64",
         n=80, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp64", inner=50,
         kind="cubic"),
+    "table6": dict(
+        desc="Table 6 of Section 4.4 on this GPU: the cost of a time step and of t* = V_c t / L "
+             "= 1 for the RTLBFS and TLBFS face stages on the paper's mesh (80x80x80, tanh "
+             "phi=1.8, Ra=1e6, Pr=0.71, V_c=0.1, lattice spacing kappa=0.5), FP64 and FP32",
+        n=80, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp64", inner=100,
+        kind="table6"),
     "cubic256": dict(
         desc="3D profiling case: cubic cavity 256x256x256, tanh phi=1.8, Ra=1e6, Pr=0.71, "
              "V_c=0.1, FP32 bulk + FP64 reductions (state 336 MB per buffer, > L2)",
@@ -954,7 +960,74 @@ def cpu_baseline_cubic(w, seconds):
                       f"over z-planes)"}
 
 
+def run_table6(args, w):
+    """Per-step device time of both face stages on the Table 6 mesh, each
+    precision; the line's value is the RTLBFS / TLBFS cost ratio in FP64 (the
+    paper's 97.16 % was for serial CPU programs)."""
+    import numpy as np
+    import torch
+    from paper_2202_13449_gb300 import capi, inputs
+    torch.cuda.set_device(0)
+    capi.lib()
+    n = w["n"]
+    cells = n ** 3
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {}
+    launches0 = capi.launch_count()
+    clk = ClockSampler(0)
+    clk.start()
+    for prec_name, prec, inner in (("fp64", capi.FP64, max(20, args.inner or 50)),
+                                   ("fp32", capi.FP32, max(100, (args.inner or 50) * 10))):
+        for scheme, sname in ((0, "rtlbfs"), (1, "tlbfs")):
+            ww = dict(w, precision=prec_name)
+            s, st0, f, dt = cubic_setup(capi, inputs, ww)
+            s.set_scheme(scheme)
+            s.set_stream(stream)
+            tile, _ = s.autotune(8)
+            for _ in range(args.warmup):
+                s.step(inner)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.step(inner)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b) / inner)
+            per = statistics.median(ms)
+            steps_t1 = int(np.ceil(float(n) / (w["Ma"] * dt)))
+            out[f"{sname}_{prec_name}"] = {
+                "ms_per_step": round(per, 5), "M_cell_updates_per_s": round(cells / per / 1e3, 2),
+                "t_cost_s_for_t_star_1": round(per * steps_t1 / 1e3, 3),
+                "tile": ["32x4", "16x8", "32x8"][tile],
+                "ops_per_cell_update": capi.op_counts3(scheme)[1]}
+            s.close()
+    clocks = clk.stop()
+    ratio64 = out["rtlbfs_fp64"]["ms_per_step"] / out["tlbfs_fp64"]["ms_per_step"]
+    ratio32 = out["rtlbfs_fp32"]["ms_per_step"] / out["tlbfs_fp32"]["ms_per_step"]
+    line = {
+        "metric": "RTLBFS / TLBFS cost ratio per time step (Table 6's t_cost ratio), FP64",
+        "value": round(ratio64, 4), "unit": "ratio", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "l2": "state in L2 (20 MB FP64); median of per-bench-step timings"},
+        "fp32_ratio": round(ratio32, 4),
+        "stages": out,
+        "paper": {"rtlbfs_s": 58864.12, "tlbfs_s": 60585.58, "ratio": 0.9716,
+                  "hardware": "serial CPU programs, machine unspecified"},
+        "gpu_launches": int(capi.launch_count() - launches0),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "table6":
+        return run_table6(args, w)
     if w.get("kind") == "cubic":
         return run_cubic(args, w)
     if w.get("kind") == "schemes":
@@ -1336,7 +1409,7 @@ def main():
         args.warmup = 3
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if w.get("kind") in ("accuracy", "rb_steady", "schemes"):
+        if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6"):
             print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
                               "time to a steady state of the GPU path; the oracle's rate is the "
                               "rb1024x512 / cavity512 reference lines"}))

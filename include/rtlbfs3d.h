@@ -139,6 +139,16 @@ int rtlbfs3d_residual(rtlbfs3d_t h, double* res2, long* steps);
 int rtlbfs3d_nusselt(rtlbfs3d_t h, int side, int mid, double* nu);
 
 /*
+ * Face stage of every face: 0 = RTLBFS (Section 3.2, the default), 1 = the
+ * original TLBFS of Section 2.2 with D3Q19 -- equilibria (Eqs. 3-4) at the
+ * nodes x_S - e_i delta t (Eq. 29 values), the predicted variables as their
+ * moments (Eqs. 30-32) and the fluxes of Eqs. 38-40 with the
+ * non-equilibrium parts of Eqs. 33-34.  The update, boundary conditions,
+ * residual and Nusselt sums use the chosen stage.  ERR_ARG otherwise.
+ */
+int rtlbfs3d_set_scheme(rtlbfs3d_t h, int scheme);
+
+/*
  * Work decomposition of the step kernel: tile 0 = 32 x 4 cells, 1 = 16 x 8,
  * 2 = 32 x 8 in x-y (one thread per column, marching up z); kchunk = planes
  * per work unit (0 = automatic: enough units to fill every SM).
@@ -164,6 +174,10 @@ const char* rtlbfs3d_last_error(rtlbfs3d_t h);
  * square roots apart (*sfu_ops).  Host only; pointers may be null.
  */
 int rtlbfs3d_op_counts(double* face_ops, double* cell_ops, double* sfu_ops);
+
+/* The same count for face stage `scheme` (0 RTLBFS, 1 TLBFS); ERR_ARG
+ * for any other scheme. */
+int rtlbfs3d_op_counts_scheme(int scheme, double* face_ops, double* cell_ops, double* sfu_ops);
 
 void rtlbfs3d_destroy(rtlbfs3d_t h);
 

@@ -128,6 +128,8 @@ _SIGS = {
     "rtlbfs3d_sync": (C.c_int, [_vp]),
     "rtlbfs3d_last_error": (C.c_char_p, [_vp]),
     "rtlbfs3d_op_counts": (C.c_int, [_dp, _dp, _dp]),
+    "rtlbfs3d_op_counts_scheme": (C.c_int, [C.c_int, _dp, _dp, _dp]),
+    "rtlbfs3d_set_scheme": (C.c_int, [_vp, C.c_int]),
     "rtlbfs3d_destroy": (None, [_vp]),
 }
 
@@ -492,11 +494,12 @@ def stability_map(n, Ra, kappa, dt=None, *, Pr=0.71, Ma=0.1, tol=1e-9, max_steps
 XM, XP, YM, YP, ZM, ZP, MID_X = 0, 1, 2, 3, 4, 5, 6
 
 
-def op_counts3():
+def op_counts3(scheme: int = 0):
     """(FP ops per face, FP ops per cell-update, SFU ops per cell-update) of
-    the 3D step, each face and gradient evaluated once (host-only)."""
+    the 3D step with face stage `scheme` (RTLBFS or TLBFS), each face and
+    gradient evaluated once (host-only)."""
     a, b, c = C.c_double(), C.c_double(), C.c_double()
-    rc = lib().rtlbfs3d_op_counts(C.byref(a), C.byref(b), C.byref(c))
+    rc = lib().rtlbfs3d_op_counts_scheme(int(scheme), C.byref(a), C.byref(b), C.byref(c))
     if rc:
         raise RTLBFSError(rc, "rtlbfs3d_op_counts")
     return a.value, b.value, c.value
@@ -563,6 +566,10 @@ class Solver3:
         uw = np.ascontiguousarray(u_wall, dtype=np.float64)
         self._check(lib().rtlbfs3d_set_bc(self._h, int(side), int(kind), float(T_wall), _ptr(uw)),
                     "set_bc")
+
+    def set_scheme(self, scheme: int):
+        """Face stage: RTLBFS (0, Section 3.2) or TLBFS (1, Section 2.2)."""
+        self._check(lib().rtlbfs3d_set_scheme(self._h, int(scheme)), "set_scheme")
 
     def set_schedule(self, tile: int = 0, kchunk: int = 0):
         """tile 0: 32 x 4, 1: 16 x 8, 2: 32 x 8 columns per block; kchunk

@@ -228,10 +228,10 @@ __device__ __forceinline__ void take3(const Sm& sm, int vs, int gs, int r, int c
     }
 }
 
-// One face between cells L and R (frame of axis ax): fluxes in global
-// components.  Tz is the unit's temperature reference; the face reference
+// One face between cells L and R (frame of axis ax) with face stage SCH
+// (0 RTLBFS, 1 TLBFS): fluxes in global components.  Tz is the unit's temperature reference; the face reference
 // is the left cell's temperature.
-template <class P, typename R>
+template <class P, typename R, int SCH>
 __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, CellNT3<R>& Rc,
                                       R tauR, const FaceLine<R>& fl, R Tz, int ax, int wside,
                                       R out[5])
@@ -243,7 +243,10 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
     const R uw1 = wside >= 0 ? Cst<P>::uw(d, wside, a1) : R(0);
     const R uw2 = wside >= 0 ? Cst<P>::uw(d, wside, a2) : R(0);
     R F[5];
-    face_flux3<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
+    if (SCH == 1)
+        face_flux3_tlbfs<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
+    else
+        face_flux3<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
     out[0] = F[0];
     out[1 + ax] = F[1];
     out[1 + a1] = F[2];
@@ -251,7 +254,7 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
     out[4] = F[4];
 }
 
-template <class P, int TX, int TY>
+template <class P, int TX, int TY, int SCH>
 __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__ dp,
                                                        Ctl3* __restrict__ ctl)
 {
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
         take3<R>(sm, mod3(kk), mod2(kk), ty + 2, tx + 2, 2, L, tl);
         take3<R>(sm, mod3(kk + 1), mod2(kk + 1), ty + 2, tx + 2, 2, Rr, tr);
         const int ws = zper ? -1 : (kk + 1 == 0 ? 4 : (kk + 1 == nz ? 5 : -1));
-        face3<P, R>(d, L, tl, Rr, tr, zl[kk + 1], Tz, 2, ws, out);
+        face3<P, R, SCH>(d, L, tl, Rr, tr, zl[kk + 1], Tz, 2, ws, out);
     };
 
     // ---- prologue: planes k0-2 .. k0+1, gradients of k0-1 and k0, the
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
             take3<R>(sm, vs, gs, fj + 2, fi + 2, 0, Rr, tr);
             const int ws = xper ? -1 : (gx == 0 ? 0 : (gx == nx ? 1 : -1));
             R F[5];
-            face3<P, R>(d, L, tl, Rr, tr, get_line(sm.xl, fi), Tz, 0, ws, F);
+            face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.xl, fi), Tz, 0, ws, F);
 #pragma unroll
             for (int q = 0; q < 5; ++q) sm.fx[q][fj][fi] = F[q];
         }
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
             take3<R>(sm, vs, gs, fj + 2, fi + 2, 1, Rr, tr);
             const int ws = yper ? -1 : (gy == 0 ? 2 : (gy == ny ? 3 : -1));
             R F[5];
-            face3<P, R>(d, L, tl, Rr, tr, get_line(sm.yl, fj), Tz, 1, ws, F);
+            face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.yl, fj), Tz, 1, ws, F);
 #pragma unroll
             for (int q = 0; q < 5; ++q) sm.fy[q][fj][fi] = F[q];
         }
@@ -634,7 +637,7 @@ __device__ void cell_at(const Desc3& d, const typename P::S* tin,
 // Sum over the faces normal to axis `ax` at face index `pos` with the
 // tangential index of axis b1 restricted to [t1lo, t1hi): flux F_E times
 // face area (times wgt), into *acc.
-template <class P>
+template <class P, int SCH>
 __global__ void nusselt3_kernel(const Desc3* __restrict__ dp, int cur, int ax, int pos, int t1lo,
                                 int t1hi, int wside, double wgt, double* acc)
 {
@@ -682,7 +685,10 @@ __global__ void nusselt3_kernel(const Desc3* __restrict__ dp, int cur, int ax, i
         const double uw1 = wside >= 0 ? d.bcU[wside][b1] : 0.0;
         const double uw2 = wside >= 0 ? d.bcU[wside][b2] : 0.0;
         double F[5];
-        face_flux3<double>(L, Rr, Tbar, fl[pos], keep, uw1, uw2, F);
+        if (SCH == 1)
+            face_flux3_tlbfs<double>(L, Rr, Tbar, fl[pos], keep, uw1, uw2, F);
+        else
+            face_flux3<double>(L, Rr, Tbar, fl[pos], keep, uw1, uw2, F);
         s += F[4] * c1[t1 + 2].w * c2[t2 + 2].w;
     }
     s *= wgt;
@@ -744,21 +750,34 @@ void build_lines(const std::vector<double>& f, bool periodic, double kappa, doub
 }
 
 template <class P, int TX, int TY>
-cudaError_t launch_step(int units, cudaStream_t s, const Desc3* d, Ctl3* c)
+cudaError_t launch_step(int units, int scheme, cudaStream_t s, const Desc3* d, Ctl3* c)
 {
     const size_t sm = sizeof(Smem3<P, TX, TY>);
-    step3_kernel<P, TX, TY><<<units, TX * TY, sm, s>>>(d, c);
+    if (scheme == 1)
+        step3_kernel<P, TX, TY, 1><<<units, TX * TY, sm, s>>>(d, c);
+    else
+        step3_kernel<P, TX, TY, 0><<<units, TX * TY, sm, s>>>(d, c);
     return cudaGetLastError();
 }
 
+// shared-memory opt-in and resident blocks per SM of both face stages
+// (occ[0]: RTLBFS, occ[1]: TLBFS)
 template <class P, int TX, int TY>
-cudaError_t prepare_kernel(int* occ)
+cudaError_t prepare_kernel(int occ[2])
 {
     const size_t sm = sizeof(Smem3<P, TX, TY>);
-    cudaError_t e = cudaFuncSetAttribute(step3_kernel<P, TX, TY>,
+    cudaError_t e = cudaFuncSetAttribute(step3_kernel<P, TX, TY, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3_kernel<P, TX, TY>, TX * TY, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step3_kernel<P, TX, TY, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], step3_kernel<P, TX, TY, 0>,
+                                                          TX * TY, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], step3_kernel<P, TX, TY, 1>,
+                                                          TX * TY, sm);
+    return e;
 }
 
 }  // namespace rtlbfs3
@@ -778,7 +797,8 @@ struct rtlbfs3d_ctx {
     double bcT[6] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0};
     double bcU[6][3] = {};
     int tile = 0, kchunk_req = 0;
-    int sms = 0, occ[3] = {0, 0, 0};
+    int scheme = 0;  // face stage: 0 RTLBFS (Section 3.2), 1 TLBFS (Section 2.2)
+    int sms = 0, occ[3][2] = {};
     // device memory
     void* d_state = nullptr;  // 2 x (Vec4<S>[cells] + S[cells])
     void* d_lines = nullptr;
@@ -795,7 +815,7 @@ struct rtlbfs3d_ctx {
     bool dirty = true;
     cudaStream_t stream = nullptr, own = nullptr, cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int gunits = 0, gtile = -1;
+    int gunits = 0, gtile = -1, gscheme = -1;
     std::string err;
 
     int fail(int code, const std::string& m)
@@ -856,7 +876,8 @@ void decompose(rtlbfs3d_ctx* h, Desc3& d)
     d.tiles_y = (h->n[1] + TY - 1) / TY;
     int kc = h->kchunk_req;
     if (kc <= 0) {
-        const long long slots = (long long)std::max(1, h->sms) * std::max(1, h->occ[h->tile]);
+        const long long slots =
+            (long long)std::max(1, h->sms) * std::max(1, h->occ[h->tile][h->scheme]);
         const long long per_plane = (long long)d.tiles_x * d.tiles_y;
         long long chunks = std::max(1LL, (slots + per_plane - 1) / per_plane);
         kc = (int)std::max(4LL, (h->n[2] + chunks - 1) / chunks);
@@ -955,17 +976,18 @@ cudaError_t launch_one(rtlbfs3d_ctx* h, cudaStream_t s)
 {
     const int units = h->desc.units;
     rtlbfs::g_launches++;
+    const int sc = h->scheme;
     if (h->precision == RTLBFS_FP64) {
         switch (h->tile) {
-        case 0: return launch_step<StoreD, 32, 4>(units, s, h->d_desc, h->d_ctl);
-        case 1: return launch_step<StoreD, 16, 8>(units, s, h->d_desc, h->d_ctl);
-        default: return launch_step<StoreD, 32, 8>(units, s, h->d_desc, h->d_ctl);
+        case 0: return launch_step<StoreD, 32, 4>(units, sc, s, h->d_desc, h->d_ctl);
+        case 1: return launch_step<StoreD, 16, 8>(units, sc, s, h->d_desc, h->d_ctl);
+        default: return launch_step<StoreD, 32, 8>(units, sc, s, h->d_desc, h->d_ctl);
         }
     }
     switch (h->tile) {
-    case 0: return launch_step<StoreQ, 32, 4>(units, s, h->d_desc, h->d_ctl);
-    case 1: return launch_step<StoreQ, 16, 8>(units, s, h->d_desc, h->d_ctl);
-    default: return launch_step<StoreQ, 32, 8>(units, s, h->d_desc, h->d_ctl);
+    case 0: return launch_step<StoreQ, 32, 4>(units, sc, s, h->d_desc, h->d_ctl);
+    case 1: return launch_step<StoreQ, 16, 8>(units, sc, s, h->d_desc, h->d_ctl);
+    default: return launch_step<StoreQ, 32, 8>(units, sc, s, h->d_desc, h->d_ctl);
     }
 }
 
@@ -988,7 +1010,8 @@ int arm(rtlbfs3d_ctx* h, long long nsteps, double tol)
 
 int ensure_graph(rtlbfs3d_ctx* h)
 {
-    if (h->gexec && h->gunits == h->desc.units && h->gtile == h->tile) return RTLBFS_OK;
+    if (h->gexec && h->gunits == h->desc.units && h->gtile == h->tile && h->gscheme == h->scheme)
+        return RTLBFS_OK;
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
@@ -1006,6 +1029,7 @@ int ensure_graph(rtlbfs3d_ctx* h)
     if (ie != cudaSuccess) return h->cuda_fail(ie, "cudaGraphInstantiate");
     h->gunits = h->desc.units;
     h->gtile = h->tile;
+    h->gscheme = h->scheme;
     return RTLBFS_OK;
 }
 
@@ -1073,13 +1097,13 @@ int rtlbfs3d_create(int nx, int ny, int nz, const double* xf, const double* yf, 
         return bail(RTLBFS_ERR_CUDA);
     cudaError_t e;
     if (precision == RTLBFS_FP64) {
-        e = prepare_kernel<StoreD, 32, 4>(&h->occ[0]);
-        if (e == cudaSuccess) e = prepare_kernel<StoreD, 16, 8>(&h->occ[1]);
-        if (e == cudaSuccess) e = prepare_kernel<StoreD, 32, 8>(&h->occ[2]);
+        e = prepare_kernel<StoreD, 32, 4>(h->occ[0]);
+        if (e == cudaSuccess) e = prepare_kernel<StoreD, 16, 8>(h->occ[1]);
+        if (e == cudaSuccess) e = prepare_kernel<StoreD, 32, 8>(h->occ[2]);
     } else {
-        e = prepare_kernel<StoreQ, 32, 4>(&h->occ[0]);
-        if (e == cudaSuccess) e = prepare_kernel<StoreQ, 16, 8>(&h->occ[1]);
-        if (e == cudaSuccess) e = prepare_kernel<StoreQ, 32, 8>(&h->occ[2]);
+        e = prepare_kernel<StoreQ, 32, 4>(h->occ[0]);
+        if (e == cudaSuccess) e = prepare_kernel<StoreQ, 16, 8>(h->occ[1]);
+        if (e == cudaSuccess) e = prepare_kernel<StoreQ, 32, 8>(h->occ[2]);
     }
     if (e != cudaSuccess) return bail(RTLBFS_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1374,12 +1398,22 @@ int rtlbfs3d_nusselt(rtlbfs3d_t h, int side, int mid, double* nu)
         const int block = 128;
         const int grid = (int)std::min<long long>((nf + block - 1) / block, 4LL * std::max(1, h->sms));
         rtlbfs::g_launches++;
-        if (h->precision == RTLBFS_FP64)
-            nusselt3_kernel<StoreD><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo, hi,
-                                                                   wside, wgt, h->d_acc);
-        else
-            nusselt3_kernel<StoreQ><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo, hi,
-                                                                   wside, wgt, h->d_acc);
+        const bool tl = h->scheme == 1;
+        if (h->precision == RTLBFS_FP64) {
+            if (tl)
+                nusselt3_kernel<StoreD, 1><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo,
+                                                                          hi, wside, wgt, h->d_acc);
+            else
+                nusselt3_kernel<StoreD, 0><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo,
+                                                                          hi, wside, wgt, h->d_acc);
+        } else {
+            if (tl)
+                nusselt3_kernel<StoreQ, 1><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo,
+                                                                          hi, wside, wgt, h->d_acc);
+            else
+                nusselt3_kernel<StoreQ, 0><<<grid, block, 0, h->stream>>>(h->d_desc, cur, ax, pos, lo,
+                                                                          hi, wside, wgt, h->d_acc);
+        }
         return cudaGetLastError();
     };
     cudaError_t e;
@@ -1403,6 +1437,15 @@ int rtlbfs3d_nusselt(rtlbfs3d_t h, int side, int mid, double* nu)
     CK3(cudaMemcpyAsync(h->h_acc, h->d_acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK3(cudaStreamSynchronize(h->stream));
     *nu = *h->h_acc;
+    return RTLBFS_OK;
+}
+
+int rtlbfs3d_set_scheme(rtlbfs3d_t h, int scheme)
+{
+    if (bad_handle(h)) return RTLBFS_ERR_ARG;
+    if (scheme != 0 && scheme != 1) return h->fail(RTLBFS_ERR_ARG, "scheme must be 0 or 1");
+    h->scheme = scheme;
+    h->dirty = true;
     return RTLBFS_OK;
 }
 
@@ -1571,6 +1614,13 @@ struct vtraits<rtlbfs3::Cnt3> {
 
 extern "C" int rtlbfs3d_op_counts(double* face_ops, double* cell_ops, double* sfu_ops)
 {
+    return rtlbfs3d_op_counts_scheme(0, face_ops, cell_ops, sfu_ops);
+}
+
+extern "C" int rtlbfs3d_op_counts_scheme(int scheme, double* face_ops, double* cell_ops,
+                                         double* sfu_ops)
+{
+    if (scheme != 0 && scheme != 1) return RTLBFS_ERR_ARG;
     using rtlbfs3::Cnt3;
     rtlbfs3::g_tally3 = rtlbfs3::Tally3();
     rtlbfs3::CellNT3<Cnt3> L, R;
@@ -1594,8 +1644,12 @@ extern "C" int rtlbfs3d_op_counts(double* face_ops, double* cell_ops, double* sf
     fl.m_tg15 = {-0.1, false};
     fl.pad = {0.0, true};
     Cnt3 F[5];
-    rtlbfs3::face_flux3<Cnt3>(L, R, Cnt3{0.5, false}, fl, Cnt3{1.0, false}, Cnt3{0.0, false},
-                              Cnt3{0.0, false}, F);
+    if (scheme == 1)
+        rtlbfs3::face_flux3_tlbfs<Cnt3>(L, R, Cnt3{0.5, false}, fl, Cnt3{1.0, false},
+                                        Cnt3{0.0, false}, Cnt3{0.0, false}, F);
+    else
+        rtlbfs3::face_flux3<Cnt3>(L, R, Cnt3{0.5, false}, fl, Cnt3{1.0, false}, Cnt3{0.0, false},
+                                  Cnt3{0.0, false}, F);
     const rtlbfs3::Tally3 f = rtlbfs3::g_tally3;
     // Per cell, besides its three faces (the -x, -y, -z faces it owns):
     //   working values from the stored state                 5

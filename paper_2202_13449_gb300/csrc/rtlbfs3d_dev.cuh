@@ -238,4 +238,119 @@ __host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const C
     }
 }
 
+// The original TLBFS face stage (Section 2.2) with D3Q19, from the same
+// inputs and in the same frame as face_flux3: (a) equilibria (Eqs. 3-4,
+// c_p = 1) at the nodes x_S - e_i h, i.e. node -e_i of the column form
+// (Eq. 29); (b) the predicted variables as their moments (Eqs. 30-32), then
+// the wall rule; (c) the fluxes of Eqs. 38-40 from the equilibria of the
+// predicted variables and the non-equilibrium parts of Eqs. 33-34.
+// Equilibria are carried as deviations f_i - w_i and g_i - w_i Tbar; the
+// constants cancel in every moment used except the pressure c_s^2 of the
+// normal momentum flux, which is dropped as in face_flux3.
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux3_tlbfs(const CellNT3<V>& L, const CellNT3<V>& Rc,
+                                                         V Tbar, const FaceLine<V>& fl, V keep,
+                                                         V uw1, V uw2, V F[5])
+{
+    using T = vtraits<V>;
+    const V zero = T::bc(0.0), half = T::bc(0.5), one = T::bc(1.0), three = T::bc(3.0);
+    const V c45 = T::bc(4.5), mc15 = T::bc(-1.5), six = T::bc(6.0);
+    // D3Q19 (Eq. 5) in the face frame: the set is the same in every frame
+    constexpr int en[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    constexpr int e1[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+    constexpr int e2[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+    const V w0 = T::bc(1.0 / 3.0), w1 = T::bc(1.0 / 18.0), w2 = T::bc(1.0 / 36.0);
+    const V h = fl.h;
+    const V wL = fl.cL + h, mwR = fl.cR - h;
+    const V hh = h * half;
+    // columns a = -1 (left plane), 0 (mean), +1 (right plane): value + slopes in t1, t2
+    V C[3][5], S1[3][5], S2[3][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        C[0][k] = vfma(L.gn[k], fl.cL, L.q[k]);
+        S1[0][k] = L.g1[k] * h;
+        S2[0][k] = L.g2[k] * h;
+        C[2][k] = vfma(Rc.gn[k], fl.cR, Rc.q[k]);
+        S1[2][k] = Rc.g1[k] * h;
+        S2[2][k] = Rc.g2[k] * h;
+        C[1][k] = half * (vfma(L.gn[k], wL, L.q[k]) + vfma(Rc.gn[k], mwR, Rc.q[k]));
+        S1[1][k] = hh * (L.g1[k] + Rc.g1[k]);
+        S2[1][k] = hh * (L.g2[k] + Rc.g2[k]);
+    }
+    // (a), (b): equilibria at the nodes -e_i and their moments
+    V df[19], dg[19];
+    V drs = zero, mn = zero, m1 = zero, m2 = zero, es = zero;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int a = 1 - en[i], b = -e1[i], c = -e2[i];  // column, offsets along t1, t2
+        V q[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            V x = C[a][k];
+            if (b > 0) x = x + S1[a][k];
+            if (b < 0) x = x - S1[a][k];
+            if (c > 0) x = x + S2[a][k];
+            if (c < 0) x = x - S2[a][k];
+            q[k] = x;
+        }
+        const V w = i == 0 ? w0 : (i < 7 ? w1 : w2);
+        V eu = zero;
+        if (en[i] > 0) eu = eu + q[1];
+        if (en[i] < 0) eu = eu - q[1];
+        if (e1[i] > 0) eu = eu + q[2];
+        if (e1[i] < 0) eu = eu - q[2];
+        if (e2[i] > 0) eu = eu + q[3];
+        if (e2[i] < 0) eu = eu - q[3];
+        const V usq = vfma(q[1], q[1], vfma(q[2], q[2], q[3] * q[3]));
+        const V rho = one + q[0];
+        // f_i - w_i = w_i (drho + rho (3 eu + 4.5 eu^2 - 1.5 u^2))
+        df[i] = w * vfma(rho, vfma(eu, vfma(c45, eu, three), mc15 * usq), q[0]);
+        // rho T - Tbar at the node, and g_i - w_i Tbar
+        const V e_node = vfma(q[0], Tbar + q[4], q[4]);
+        dg[i] = w * vfma(three * eu, Tbar + e_node, e_node);
+        drs = drs + df[i];
+        if (en[i] > 0) mn = mn + df[i];
+        if (en[i] < 0) mn = mn - df[i];
+        if (e1[i] > 0) m1 = m1 + df[i];
+        if (e1[i] < 0) m1 = m1 - df[i];
+        if (e2[i] > 0) m2 = m2 + df[i];
+        if (e2[i] < 0) m2 = m2 - df[i];
+        es = es + dg[i];
+    }
+    const V rho_s = one + drs;
+    mn = mn * keep;
+    const V wallr = (one - keep) * rho_s;
+    m1 = vfma(keep, m1, wallr * uw1);
+    m2 = vfma(keep, m2, wallr * uw2);
+    const V inv = T::rcp(rho_s);
+    const V un = mn * inv, u1 = m1 * inv, u2 = m2 * inv;
+    const V usq_s = vfma(un, un, vfma(u1, u1, u2 * u2));
+    // (c) fluxes along +n; 1/2 - tau = -3 nu / h = 6 (-nu / 2h) (Eqs. 9-10)
+    const V cf = six * fl.m_nu_2h, cg = six * fl.m_chi_2h;
+    V Fnn = zero, Fn1 = zero, Fn2 = zero, Q = zero;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (en[i] == 0) continue;  // no flux along n
+        const V w = i < 7 ? w1 : w2;
+        V eu = en[i] > 0 ? un : zero - un;
+        if (e1[i] > 0) eu = eu + u1;
+        if (e1[i] < 0) eu = eu - u1;
+        if (e2[i] > 0) eu = eu + u2;
+        if (e2[i] < 0) eu = eu - u2;
+        const V dfs = w * vfma(rho_s, vfma(eu, vfma(c45, eu, three), mc15 * usq_s), drs);
+        const V dgs = w * vfma(three * eu, Tbar + es, es);
+        const V pf = vfma(cf, dfs - df[i], dfs);  // f* + (1/2 - tau_f)(f* - f_node)
+        const V pg = vfma(cg, dgs - dg[i], dgs);
+        Fnn = Fnn + pf;  // e_n^2 = 1
+        if (e1[i] != 0) Fn1 = (en[i] * e1[i] > 0) ? Fn1 + pf : Fn1 - pf;
+        if (e2[i] != 0) Fn2 = (en[i] * e2[i] > 0) ? Fn2 + pf : Fn2 - pf;
+        Q = en[i] > 0 ? Q + pg : Q - pg;
+    }
+    F[0] = mn;
+    F[1] = Fnn;
+    F[2] = Fn1;
+    F[3] = Fn2;
+    F[4] = Q;
+}
+
 }  // namespace rtlbfs3

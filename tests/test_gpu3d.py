@@ -86,10 +86,12 @@ def compare(got, ref, tol, precision):
         assert e < tol, (q, e)
 
 
-def run_case(d3, name, precision, nsteps, tile=0, kchunk=0):
+def run_case(d3, name, precision, nsteps, tile=0, kchunk=0, scheme=0):
     nx, ny, nz, mesh, kinds, bcT, g_axis, kappa = CASES[name]
     faces = case_mesh(d3, name, (nx, ny, nz), mesh)
     p, s = make_pair(d3, faces, kinds, bcT, g_axis, kappa, precision)
+    p.scheme = scheme
+    s.set_scheme(scheme)
     s.set_schedule(tile, kchunk)
     st = inputs.perturbed_state3(nx, ny, nz, seed=11 + nx * 31 + ny * 7 + nz)
     ref, res_ref, rc = d3.step(p, st, nsteps)
@@ -123,6 +125,40 @@ def test_thirty_steps_fp64(d3, name):
 def test_steps_fp32(d3, name, tile):
     got, ref, _, _ = run_case(d3, name, capi.FP32, 3, tile=tile, kchunk=4)
     compare(got, ref, 1e-5, capi.FP32)
+
+
+@pytest.mark.parametrize("name", ["cavity_irregular", "mixed_walls_moving", "periodic_x",
+                                  "periodic_z", "tiny_1x5x2"])
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_tlbfs_one_step_fp64(d3, name, tile):
+    """The TLBFS face stage (Section 2.2, D3Q19) against the oracle's."""
+    got, ref, rg, rr = run_case(d3, name, capi.FP64, 1, tile=tile, kchunk=3, scheme=1)
+    compare(got, ref, 1e-12, capi.FP64)
+    np.testing.assert_allclose(rg, rr, rtol=1e-9)
+
+
+@pytest.mark.parametrize("name", ["cavity_irregular", "periodic_y", "all_periodic"])
+def test_tlbfs_steps(d3, name):
+    got, ref, _, _ = run_case(d3, name, capi.FP64, 20, tile=1, scheme=1)
+    compare(got, ref, 1e-11, capi.FP64)
+    got, ref, _, _ = run_case(d3, name, capi.FP32, 3, tile=1, scheme=1)
+    compare(got, ref, 1e-5, capi.FP32)
+
+
+def test_tlbfs_nusselt_fp64(d3):
+    name = "mixed_walls_moving"
+    nx, ny, nz, mesh, kinds, bcT, g_axis, kappa = CASES[name]
+    faces = case_mesh(d3, name, (nx, ny, nz), mesh)
+    p, s = make_pair(d3, faces, kinds, bcT, g_axis, kappa, capi.FP64)
+    p.scheme = 1
+    s.set_scheme(1)
+    st = inputs.perturbed_state3(nx, ny, nz, seed=15)
+    s.set_state(*st)
+    for side in range(6):
+        for mid in (False, True):
+            assert s.nusselt(side, mid) == pytest.approx(d3.nusselt(p, st, side, mid), rel=1e-12,
+                                                         abs=1e-13), (side, mid)
+    s.close()
 
 
 @pytest.mark.parametrize("kchunk", [1, 2, 5, 0])
