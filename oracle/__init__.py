@@ -1,11 +1,12 @@
 """FP64 CPU oracle of RTLBFS (arXiv 2202.13449, Section 3.2): 2D here, 3D
-(D3Q19, Section 4.4) in ``oracle.d3``.
+(D3Q19, Section 4.4) in ``oracle.d3``, 2D curvilinear meshes (Section 4.3)
+in ``oracle.curv``.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The product package
 never imports this module, and the C source here shares no code with the
-CUDA path.  ``build()`` compiles ``rtlbfs_oracle.c`` and
-``rtlbfs3d_oracle.c`` with gcc into
+CUDA path.  ``build()`` compiles ``rtlbfs_oracle.c``, ``rtlbfs3d_oracle.c``
+and ``rtlbfs_curv_oracle.c`` with gcc into
 ``oracle/_build/``; everything else is ctypes marshalling.
 
 Functions mirror the C entry points (see the header comment of
@@ -28,7 +29,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "rtlbfs_oracle.c"), os.path.join(_HERE, "rtlbfs3d_oracle.c")]
+_SRCS = [os.path.join(_HERE, "rtlbfs_oracle.c"), os.path.join(_HERE, "rtlbfs3d_oracle.c"),
+         os.path.join(_HERE, "rtlbfs_curv_oracle.c")]
 _OUT = os.path.join(_HERE, "_build", "librtlbfs_oracle.so")
 
 W, E, S, N = 0, 1, 2, 3
