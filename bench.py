@@ -135,6 +135,11 @@ WORKLOADS = {
              "phi=1.8, Ra=1e6, Pr=0.71, V_c=0.1, lattice spacing kappa=0.5), FP64 and FP32",
         n=80, phi=1.8, Ra=1e6, Pr=0.71, Ma=0.1, kappa=0.5, precision="fp64", inner=100,
         kind="table6"),
+    "cylinder450x300": dict(
+        desc="mixed convection from a heated circular cylinder (Section 4.3): body-fitted O-mesh "
+             "of 450 (around) x 300 (radial) cells, far field at 52.5 D, first spacing 0.003 D, "
+             "D = 1; Re = 20, Gr = 100, Pr = 0.7, u_inf = 0.1 c_s; FP32 bulk + FP64 reductions",
+        ni=450, nj=300, Re=20.0, Gr=100.0, Pr=0.7, precision="fp32", inner=200, kind="curv"),
     "cubic256": dict(
         desc="3D profiling case: cubic cavity 256x256x256, tanh phi=1.8, Ra=1e6, Pr=0.71, "
              "V_c=0.1, FP32 bulk + FP64 reductions (state 336 MB per buffer, > L2)",
@@ -149,6 +154,8 @@ DEFAULT_WORKLOAD = "cavity512"
 STEP3_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs3d.cu",
                  "paper_2202_13449_gb300/csrc/rtlbfs3d_dev.cuh",
                  "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh"]
+CURV_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_curv.cu",
+                "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh"]
 STEP_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_step.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_march.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh",
@@ -1025,7 +1032,143 @@ def run_table6(args, w):
     print(json.dumps(line), flush=True)
 
 
+def curv_setup(capi, inputs, w):
+    """The Section 4.3 cylinder: solver and free-stream initial state."""
+    import numpy as np
+    X, Y = inputs.cylinder_o_mesh(w["ni"], w["nj"])
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
+    uinf = 0.1 / np.sqrt(3.0)
+    nu = uinf * 1.0 / w["Re"]
+    chi = nu / w["Pr"]
+    beta_g = w["Gr"] * nu * nu  # Gr = beta g dT D^3 / nu^2 with D = dT = 1
+    r = np.hypot(X, Y)
+    wmin = float(np.min(np.diff(r, axis=0)))
+    # half the smallest width, capped by the explicit diffusive limit there
+    dt = min(0.5 * wmin, 0.2 * wmin * wmin / max(nu, chi))
+    s = capi.SolverC(X, Y, True, prec)
+    s.set_physics(nu, chi, beta_g, dt)
+    s.set_lattice(w.get("kappa", 1.0))
+    s.set_gravity(0.0, 1.0, 0.0)
+    s.set_bc(2, capi.WALL_DIRICHLET, 1.0)
+    s.set_bc(3, capi.FARFIELD)
+    s.set_farfield(1.0, uinf, 0.0, 0.0)
+    nj, ni = X.shape[0] - 1, X.shape[1] - 1
+    st = (np.ones((nj, ni)), np.full((nj, ni), uinf), np.zeros((nj, ni)), np.zeros((nj, ni)))
+    s.set_state(*st)
+    return s, st, (X, Y), dict(nu=nu, chi=chi, beta_g=beta_g, dt=dt, uinf=uinf)
+
+
+def run_curv(args, w):
+    """Curvilinear workload: one bench step = `inner` time steps of the cylinder
+    O-mesh (one launch per step, graphs), L2 flushed between bench steps."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2202_13449_gb300 import capi, inputs
+    capi.lib()
+    cells = w["ni"] * w["nj"]
+    inner = args.inner or w["inner"]
+    s, st0, XY, phys = curv_setup(capi, inputs, w)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        s.step(inner)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = capi.launch_count()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(inner)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    value = cells * inner * args.steps / (ms * 1e-3) / 1e6
+    host = pinned(st0)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        s.set_state(*host)
+        s.step(inner)
+        out = s.get_state()
+    torch.cuda.synchronize()
+    e2e = cells * inner * e2e_steps / (time.perf_counter() - t0) / 1e6
+    assert np.all(np.isfinite(out[3]))
+    heat, perim = s.wall_heat(2)
+    nu_cyl = heat * 1.0 / (phys["chi"] * 1.0 * perim)  # Eq. 73 with D = dT = 1
+    per_launch = ms * 1e-3 / (inner * args.steps)
+    rs = 4 if w["precision"] == "fp32" else 8
+    _, ops_cell, sfu_cell = capi.op_counts_curv()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    alu = ops_cell * cells / per_launch / 1e12
+    alg_bytes = 8 * rs * cells
+    peak, peak_kind = peaks()
+    res, steps_total = s.residual()
+    traffic = profile_traffic(args.workload, w["precision"], "curv", CURV_SOURCES)
+    line = {
+        "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
+        "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "time_steps_per_bench_step": inner, "dt": phys["dt"], "nu": phys["nu"],
+                   "l2": "flushed between bench steps (256 MB write)"},
+        "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
+                "h2d_bytes_per_step": 4 * cells * 8, "d2h_bytes_per_step": 4 * cells * 8},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
+                     "unit": "T FP32 op/s", "frac": round(alu / alu_peak, 4), "traffic": traffic,
+                     "kernel": "rtlbfsc::curv_step_kernel", "ops_per_cell_update": ops_cell,
+                     "sfu_ops_per_cell_update": sfu_cell,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / per_launch / 1e9, 1),
+                         "peak": peak, "unit": "GB/s",
+                         "frac": round(alg_bytes / per_launch / 1e9 / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes},
+        "nusselt_cylinder_after_run": round(nu_cyl, 4),
+        "clocks": clocks,
+        "residual_last_step": res,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import curv as cv
+        import oracle
+        oracle.build()
+        used = oracle.set_threads(os.cpu_count() or 1)
+        X, Y = XY
+        p = cv.ProblemC(X=X, Y=Y, nu=phys["nu"], chi=phys["chi"], beta_g=phys["beta_g"],
+                        dt=phys["dt"], gdir=(0.0, 1.0), T_ref=0.0,
+                        bc_kind=(cv.PERIODIC, cv.PERIODIC, cv.DIRICHLET, cv.FARFIELD),
+                        bc_T=(0.0, 0.0, 1.0, 0.0), inf=(1.0, phys["uinf"], 0.0, 0.0))
+        st = st0
+        n, t0 = 0, time.perf_counter()
+        while n == 0 or time.perf_counter() - t0 < args.cpu_seconds:
+            st, _, _ = cv.step(p, st, 2)
+            n += 2
+        dtc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(cells * n / dtc / 1e6, 3), "unit": "M cell-updates/s",
+                                "cores": used, "kind": "oracle",
+                                "sample": f"{n} FP64 time steps of the same O-mesh ({dtc:.1f} s)"}
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, w):
+    if w.get("kind") == "curv":
+        return run_curv(args, w)
     if w.get("kind") == "table6":
         return run_table6(args, w)
     if w.get("kind") == "cubic":

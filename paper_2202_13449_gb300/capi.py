@@ -26,7 +26,8 @@ NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
 
 HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
 HEADERS = [HEADER, os.path.join(_build.ROOT, "include", "rtlbfs_batch.h"),
-           os.path.join(_build.ROOT, "include", "rtlbfs3d.h")]
+           os.path.join(_build.ROOT, "include", "rtlbfs3d.h"),
+           os.path.join(_build.ROOT, "include", "rtlbfs_curv.h")]
 SLOT_EMPTY, SLOT_RUNNING, SLOT_CONVERGED, SLOT_MAX_STEPS, SLOT_DIVERGED = -1, 0, 1, 2, 3
 
 
@@ -131,6 +132,27 @@ _SIGS = {
     "rtlbfs3d_op_counts_scheme": (C.c_int, [C.c_int, _dp, _dp, _dp]),
     "rtlbfs3d_set_scheme": (C.c_int, [_vp, C.c_int]),
     "rtlbfs3d_destroy": (None, [_vp]),
+    # curvilinear 2D (include/rtlbfs_curv.h)
+    "rtlbfsc_create": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "rtlbfsc_set_physics": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "rtlbfsc_set_lattice": (C.c_int, [_vp, C.c_double]),
+    "rtlbfsc_set_gravity": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "rtlbfsc_set_body_force": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "rtlbfsc_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
+    "rtlbfsc_set_farfield": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "rtlbfsc_set_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "rtlbfsc_get_state": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "rtlbfsc_step": (C.c_int, [_vp, C.c_long]),
+    "rtlbfsc_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_long, C.c_double,
+                                        C.POINTER(C.c_long), _dp]),
+    "rtlbfsc_residual": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
+    "rtlbfsc_wall_heat": (C.c_int, [_vp, C.c_int, _dp, _dp]),
+    "rtlbfsc_set_schedule": (C.c_int, [_vp, C.c_int]),
+    "rtlbfsc_set_stream": (C.c_int, [_vp, _vp]),
+    "rtlbfsc_sync": (C.c_int, [_vp]),
+    "rtlbfsc_last_error": (C.c_char_p, [_vp]),
+    "rtlbfsc_op_counts": (C.c_int, [_dp, _dp, _dp]),
+    "rtlbfsc_destroy": (None, [_vp]),
 }
 
 
@@ -167,7 +189,7 @@ def header_functions(paths=None):
     for path in (paths or HEADERS):
         text = open(path).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(rtlbfs(?:3d)?_[a-z0-9_]+)\s*\(", text))
+        names |= set(re.findall(r"\b(rtlbfs(?:3d|c)?_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
 
@@ -627,3 +649,114 @@ class Solver3:
         self._check(lib().rtlbfs3d_nusselt(self._h, int(side), int(bool(mid)), C.byref(out)),
                     "nusselt")
         return float(out.value)
+
+
+# ---------------------------------------------------------------------------
+# Curvilinear 2D (include/rtlbfs_curv.h)
+# ---------------------------------------------------------------------------
+FARFIELD = 3
+
+
+def op_counts_curv():
+    """(FP ops per face, per cell-update, SFU ops per cell-update) of the
+    curvilinear step (host-only)."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().rtlbfsc_op_counts(C.byref(a), C.byref(b), C.byref(c))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfsc_op_counts")
+    return a.value, b.value, c.value
+
+
+class SolverC:
+    """One body-fitted 2D mesh on the GPU (a handle of include/rtlbfs_curv.h);
+    vertices X, Y of shape (nj+1, ni+1), fields of shape (nj, ni)."""
+
+    def __init__(self, X, Y, periodic_i: bool, precision: int = FP64):
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.Y = np.ascontiguousarray(Y, dtype=np.float64)
+        self.nj, self.ni = self.X.shape[0] - 1, self.X.shape[1] - 1
+        h = _vp()
+        rc = lib().rtlbfsc_create(self.ni, self.nj, _ptr(self.X), _ptr(self.Y),
+                                  int(bool(periodic_i)), int(precision), C.byref(h))
+        if rc:
+            raise RTLBFSError(rc, "rtlbfsc_create")
+        self._h = h
+
+    def _check(self, rc: int, what: str):
+        if rc:
+            msg = lib().rtlbfsc_last_error(self._h)
+            raise RTLBFSError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rtlbfsc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_physics(self, nu, chi, beta_g, dt):
+        self._check(lib().rtlbfsc_set_physics(self._h, nu, chi, beta_g, dt), "set_physics")
+
+    def set_lattice(self, kappa):
+        self._check(lib().rtlbfsc_set_lattice(self._h, kappa), "set_lattice")
+
+    def set_gravity(self, gx, gy, T_ref=0.5):
+        self._check(lib().rtlbfsc_set_gravity(self._h, gx, gy, T_ref), "set_gravity")
+
+    def set_body_force(self, fx, fy):
+        self._check(lib().rtlbfsc_set_body_force(self._h, fx, fy), "set_body_force")
+
+    def set_bc(self, side, kind, T_wall=0.0, ux=0.0, uy=0.0):
+        self._check(lib().rtlbfsc_set_bc(self._h, int(side), int(kind), float(T_wall), float(ux),
+                                         float(uy)), "set_bc")
+
+    def set_farfield(self, rho, u, v, T):
+        self._check(lib().rtlbfsc_set_farfield(self._h, rho, u, v, T), "set_farfield")
+
+    def set_schedule(self, tile_rows: int = 0):
+        self._check(lib().rtlbfsc_set_schedule(self._h, int(tile_rows)), "set_schedule")
+
+    def set_stream(self, stream):
+        ptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self._check(lib().rtlbfsc_set_stream(self._h, ptr), "set_stream")
+
+    def set_state(self, rho, u, v, T):
+        n = self.ni * self.nj
+        arrs = [_f64(a, n) for a in (rho, u, v, T)]
+        self._check(lib().rtlbfsc_set_state(self._h, *[_ptr(a) for a in arrs]), "set_state")
+
+    def get_state(self):
+        out = [np.empty((self.nj, self.ni)) for _ in range(4)]
+        self._check(lib().rtlbfsc_get_state(self._h, *[_ptr(a) for a in out]), "get_state")
+        return tuple(out)
+
+    def step(self, n: int):
+        self._check(lib().rtlbfsc_step(self._h, int(n)), "step")
+
+    def step_rc(self, n: int) -> int:
+        return int(lib().rtlbfsc_step(self._h, int(n)))
+
+    def run_to_steady(self, tol: float, max_steps: int, timeout_s: float = 0.0):
+        steps = C.c_long(0)
+        res = np.full(2, np.nan)
+        rc = lib().rtlbfsc_run_to_steady(self._h, float(tol), int(max_steps), float(timeout_s),
+                                         C.byref(steps), _ptr(res))
+        if rc not in (OK, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_DIVERGED):
+            self._check(rc, "run_to_steady")
+        return int(rc), int(steps.value), (float(res[0]), float(res[1]))
+
+    def residual(self):
+        res = np.full(2, np.nan)
+        steps = C.c_long(0)
+        self._check(lib().rtlbfsc_residual(self._h, _ptr(res), C.byref(steps)), "residual")
+        return (float(res[0]), float(res[1])), int(steps.value)
+
+    def wall_heat(self, side: int):
+        q, per = C.c_double(0), C.c_double(0)
+        self._check(lib().rtlbfsc_wall_heat(self._h, int(side), C.byref(q), C.byref(per)),
+                    "wall_heat")
+        return float(q.value), float(per.value)

@@ -64,10 +64,8 @@ struct Desc3 {
     int tiles_x, tiles_y, chunks, kchunk, units;
     double beta_g, T_ref, dt, force[3];
     float f_beta_g, f_T_ref, f_dt, f_force[3];
-    double bcU[6][3];
-    float f_bcU[6][3];
-    double d_u2[6][3], d_T2[6];  // FP64 storage: twice the wall values (mirror constants)
-    int q_u2[6][3], q_T2[6];     // fixed-point storage: the same, wrap-around
+    double bcU[6][3], bcT[6];
+    float f_bcU[6][3], f_bcT[6];
     void* rec[2];                // Vec4<S>[cells]: (rho - 1, u, v, w)
     void* tem[2];                // S[cells]: T
     const void* fline[3];        // FaceLine<R>[n[a] + 1]
@@ -97,8 +95,7 @@ struct Cst<StoreD> {
     static __device__ __forceinline__ double dt(const Desc3& d) { return d.dt; }
     static __device__ __forceinline__ double force(const Desc3& d, int a) { return d.force[a]; }
     static __device__ __forceinline__ double uw(const Desc3& d, int s, int c) { return d.bcU[s][c]; }
-    static __device__ __forceinline__ double u2(const Desc3& d, int s, int c) { return d.d_u2[s][c]; }
-    static __device__ __forceinline__ double T2(const Desc3& d, int s) { return d.d_T2[s]; }
+    static __device__ __forceinline__ double Tw(const Desc3& d, int s) { return d.bcT[s]; }
 };
 template <>
 struct Cst<StoreQ> {
@@ -107,8 +104,7 @@ struct Cst<StoreQ> {
     static __device__ __forceinline__ float dt(const Desc3& d) { return d.f_dt; }
     static __device__ __forceinline__ float force(const Desc3& d, int a) { return d.f_force[a]; }
     static __device__ __forceinline__ float uw(const Desc3& d, int s, int c) { return d.f_bcU[s][c]; }
-    static __device__ __forceinline__ int u2(const Desc3& d, int s, int c) { return d.q_u2[s][c]; }
-    static __device__ __forceinline__ int T2(const Desc3& d, int s) { return d.q_T2[s]; }
+    static __device__ __forceinline__ float Tw(const Desc3& d, int s) { return d.f_bcT[s]; }
 };
 
 // Source index of coordinate c on an axis of n cells: wrap when periodic;
@@ -137,15 +133,19 @@ __host__ __device__ __forceinline__ bool resolve_1d(int c, int n, bool per, int 
     return false;
 }
 
-// Ghost state across wall `side` in the storage type: rho even, velocity
-// odd about the wall velocity (its normal part is 0), T odd about T_wall
-// on a Dirichlet wall and even on an adiabatic one.
-template <class P>
-__device__ __forceinline__ void mirror_state3(const Desc3& d, int side, typename P::S q[5])
+// Ghost values across wall `side` from the partner's working values o =
+// (rho - 1, u, v, w, T - Tref): rho even, velocity odd about the wall
+// velocity (its normal part is 0), T odd about T_wall on a Dirichlet wall and
+// even on an adiabatic one.  Formed in the arithmetic type relative to Tref:
+// 2 T_wall - T_P can leave the fixed-point range of a stored temperature (a
+// hot wall next to cold fluid) while its deviation from a temperature inside
+// the unit does not.
+template <class P, typename R>
+__device__ __forceinline__ void mirror_values3(const Desc3& d, int side, R Tref, R o[5])
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) q[1 + c] = P::mirror_odd(Cst<P>::u2(d, side, c), q[1 + c]);
-    if (d.kind[side] == kDirichlet) q[4] = P::mirror_odd(Cst<P>::T2(d, side), q[4]);
+    for (int c = 0; c < 3; ++c) o[1 + c] = R(2) * Cst<P>::uw(d, side, c) - o[1 + c];
+    if (d.kind[side] == kDirichlet) o[4] = R(2) * (Cst<P>::Tw(d, side) - Tref) - o[4];
 }
 
 // Sign of gradient component (q, dir) of a ghost across a wall normal to
@@ -321,14 +321,13 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
             if (zok && xok && yok && nm <= 1) {
                 const size_t off = ((size_t)ks * ny + js) * nx + is;
                 const Vec4<S> a = rin[off];
-                S q[5] = {a.x, a.y, a.z, a.w, tin[off]};
+                o[0] = P::val(a.x, 0);
+                o[1] = P::val(a.y, 1);
+                o[2] = P::val(a.z, 1);
+                o[3] = P::val(a.w, 1);
+                o[4] = P::diff(tin[off], qTz, 3);
                 const int ms = xs >= 0 ? xs : (ys >= 0 ? ys : zs);
-                if (ms >= 0) mirror_state3<P>(d, ms, q);
-                o[0] = P::val(q[0], 0);
-                o[1] = P::val(q[1], 1);
-                o[2] = P::val(q[2], 1);
-                o[3] = P::val(q[3], 1);
-                o[4] = P::diff(q[4], qTz, 3);
+                if (ms >= 0) mirror_values3<P, R>(d, ms, Tz, o);
             }
 #pragma unroll
             for (int q = 0; q < 5; ++q) sm.v[vs][q][r][c] = o[q];
@@ -600,9 +599,9 @@ __device__ void cell_at(const Desc3& d, const typename P::S* tin,
         }
         const size_t off = ((size_t)s[2] * d.n[1] + s[1]) * d.n[0] + s[0];
         const Vec4<S> r = rin[off];
-        S qq[5] = {r.x, r.y, r.z, r.w, tin[off]};
-        if (side >= 0) mirror_state3<P>(d, side, qq);
+        const S qq[5] = {r.x, r.y, r.z, r.w, tin[off]};
         for (int k = 0; k < 5; ++k) o[k] = P::to_double(qq[k], kind_of(k));
+        if (side >= 0) mirror_values3<StoreD, double>(d, side, 0.0, o);  // FP64, T absolute
     };
     double qc[5];
     fetch(p, qc);
@@ -622,12 +621,9 @@ __device__ void cell_at(const Desc3& d, const typename P::S* tin,
         for (int k = 0; k < 5; ++k) q[k] = qc[k];
         return;
     }
-    // a wall ghost: the mirrored state of its partner and mirrored gradient
-    const size_t off = ((size_t)p[2] * d.n[1] + p[1]) * d.n[0] + p[0];
-    const Vec4<S> r = rin[off];
-    S qq[5] = {r.x, r.y, r.z, r.w, tin[off]};
-    mirror_state3<P>(d, ms, qq);
-    for (int k = 0; k < 5; ++k) q[k] = P::to_double(qq[k], kind_of(k));
+    // a wall ghost: the mirrored values of its partner and mirrored gradient
+    for (int k = 0; k < 5; ++k) q[k] = qc[k];
+    mirror_values3<StoreD, double>(d, ms, 0.0, q);
     const int kind = d.kind[ms], ax = ms / 2;
     for (int k = 0; k < 5; ++k)
         for (int a = 0; a < 3; ++a)
@@ -943,11 +939,9 @@ int upload(rtlbfs3d_ctx* h)
             const double uw = (c == s / 2) ? 0.0 : h->bcU[s][c];
             d.bcU[s][c] = uw;
             d.f_bcU[s][c] = (float)uw;
-            d.d_u2[s][c] = 2.0 * uw;
-            d.q_u2[s][c] = StoreQ::twice(StoreQ::from_double(uw, 1));
         }
-        d.d_T2[s] = 2.0 * h->bcT[s];
-        d.q_T2[s] = StoreQ::twice(StoreQ::from_double(h->bcT[s], 3));
+        d.bcT[s] = h->bcT[s];
+        d.f_bcT[s] = (float)h->bcT[s];
     }
     d.g_axis = h->g_axis;
     d.beta_g = h->beta_g;

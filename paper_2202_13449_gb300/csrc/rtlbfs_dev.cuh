@@ -61,10 +61,7 @@ struct CavityDesc {
     double beta_g, T_ref, fx, fy, dt, dT, nu, chi;
     // FP32 copies (a double -> float conversion runs on the narrow FP64
     // pipe; the FP32 kernels never convert in their loops)
-    float f_beta_g, f_T_ref, f_fx, f_fy, f_dt, f_bcU[4];
-    // wall mirror constants in the fixed-point storage: 2 u_wall and 2 T_wall
-    // (wrap-around 32-bit values, see StoreQ::twice)
-    int q_u2[4], q_T2[4];
+    float f_beta_g, f_T_ref, f_fx, f_fy, f_dt, f_bcU[4], f_bcT[4];
     // two state buffers; each is an array of ny*pitch cell records
     // (rho - 1, u, v, T) -- Vec4<S>, 16 bytes in FP32 mode, 32 in FP64 --
     // in f[b][0] (f[b][1..3] used only by callers' separate-array layouts)
@@ -400,7 +397,6 @@ struct StoreD {
     static __host__ __device__ __forceinline__ S from_double(double v, int) { return v; }
     static __host__ __device__ __forceinline__ double to_double(S s, int) { return s; }
     static __host__ __device__ __forceinline__ S mirror_odd(S wall2, S s) { return wall2 - s; }
-    static __host__ __device__ __forceinline__ S twice(S s) { return 2.0 * s; }
     static __host__ __device__ __forceinline__ bool representable(double, int) { return true; }
     static __host__ __device__ __forceinline__ bool in_range(R v, int) { return v == v; }
     static __device__ __forceinline__ R rcp(R x) { return 1.0 / x; }
@@ -412,8 +408,7 @@ struct StoreD {
     static __device__ __forceinline__ R fx(const CavityDesc* d) { return d->fx; }
     static __device__ __forceinline__ R fy(const CavityDesc* d) { return d->fy; }
     static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->bcU[s]; }
-    static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return 2.0 * d->bcU[s]; }
-    static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return 2.0 * d->bcT[s]; }
+    static __device__ __forceinline__ R Tw(const CavityDesc* d, int s) { return d->bcT[s]; }
     // cell records of buffer b
     static __device__ __forceinline__ Vec4<S> load4(const CavityDesc* d, int b, size_t o)
     {
@@ -466,8 +461,6 @@ struct StoreQ {
     {
         return (int)((unsigned)wall2 - (unsigned)s);
     }
-    // 2 s with wrap-around: exact for the mirror 2 s - x whenever that fits
-    static __host__ __device__ __forceinline__ S twice(S s) { return (int)(2u * (unsigned)s); }
     static __host__ __device__ __forceinline__ bool in_range(R v, int k)
     {
         return fabsf(v) < limit(k);
@@ -481,8 +474,7 @@ struct StoreQ {
     static __device__ __forceinline__ R fx(const CavityDesc* d) { return d->f_fx; }
     static __device__ __forceinline__ R fy(const CavityDesc* d) { return d->f_fy; }
     static __device__ __forceinline__ R bcU(const CavityDesc* d, int s) { return d->f_bcU[s]; }
-    static __device__ __forceinline__ S u2(const CavityDesc* d, int s) { return d->q_u2[s]; }
-    static __device__ __forceinline__ S T2(const CavityDesc* d, int s) { return d->q_T2[s]; }
+    static __device__ __forceinline__ R Tw(const CavityDesc* d, int s) { return d->f_bcT[s]; }
     static __device__ __forceinline__ Vec4<S> load4(const CavityDesc* d, int b, size_t o)
     {
         return static_cast<const Vec4<S>*>(d->f[b][0])[o];

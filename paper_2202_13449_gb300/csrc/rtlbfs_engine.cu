@@ -373,8 +373,7 @@ int Engine::upload_lines(int slot)
     d.f_dt = (float)c.dt;
     for (int s2 = 0; s2 < 4; ++s2) {
         d.f_bcU[s2] = (float)c.bcU[s2];
-        d.q_u2[s2] = StoreQ::from_double(2.0 * c.bcU[s2], 1);
-        d.q_T2[s2] = StoreQ::twice(StoreQ::from_double(c.bcT[s2], 3));
+        d.f_bcT[s2] = (float)c.bcT[s2];
     }
     const size_t rec = 4 * rsize_ * (size_t)c.pitch * c.ny;  // cell records of one buffer
     for (int b = 0; b < 2; ++b) {

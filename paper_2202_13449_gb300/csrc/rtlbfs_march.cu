@@ -52,22 +52,29 @@ __device__ __forceinline__ bool resolve_1d(int c, int n, bool per, int side_lo, 
     return false;
 }
 
+// Ghost values across wall `side` from the partner's working values (rho - 1,
+// u, v, T - Tref), formed in the arithmetic type: rho even, velocity odd
+// about the wall velocity (normal component about 0), T odd about T_wall on
+// a Dirichlet wall, even on an adiabatic one.  The mirror temperature
+// 2 T_wall - T_P can leave the fixed-point range of a stored value; its
+// deviation from the unit's reference does not.
 template <class P>
-__device__ __forceinline__ Vec4<typename P::S> mirror_state_m(const CavityDesc* d, int side,
-                                                              Vec4<typename P::S> v)
+__device__ __forceinline__ Vec4<typename P::R> mirror_values_m(const CavityDesc* d, int side,
+                                                               Vec4<typename P::R> y,
+                                                               typename P::R Tref)
 {
-    using S = typename P::S;
+    using R = typename P::R;
     const bool xn = (side == kSideW || side == kSideE);
-    const S ut2 = P::u2(d, side);
+    const R ut2 = R(2) * P::bcU(d, side);
     if (xn) {
-        v.y = P::mirror_odd(S(0), v.y);
-        v.z = P::mirror_odd(ut2, v.z);
+        y.y = -y.y;
+        y.z = ut2 - y.z;
     } else {
-        v.z = P::mirror_odd(S(0), v.z);
-        v.y = P::mirror_odd(ut2, v.y);
+        y.z = -y.z;
+        y.y = ut2 - y.y;
     }
-    if (d->kind[side] == kDirichlet) v.w = P::mirror_odd(P::T2(d, side), v.w);
-    return v;
+    if (d->kind[side] == kDirichlet) y.w = R(2) * (P::Tw(d, side) - Tref) - y.w;
+    return y;
 }
 
 template <typename R>
@@ -183,9 +190,10 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             int rs, yms;
             const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms);
             if (!(colok && rowok && !(xms >= 0 && yms >= 0))) return {R(0), R(0), R(0), R(0)};
-            if (xms >= 0) q = mirror_state_m<P>(dp, xms, q);
-            if (yms >= 0) q = mirror_state_m<P>(dp, yms, q);
-            return {P::val(q.x, 0), P::val(q.y, 1), P::val(q.z, 2), P::diff(q.w, qTz, 3)};
+            Vec4<R> y = {P::val(q.x, 0), P::val(q.y, 1), P::val(q.z, 2), P::diff(q.w, qTz, 3)};
+            if (xms >= 0) y = mirror_values_m<P>(dp, xms, y, Tz);
+            if (yms >= 0) y = mirror_values_m<P>(dp, yms, y, Tz);
+            return y;
         };
         // Green-Gauss gradient of row r from its value v, the rows below (vs)
         // and above (vn); x-neighbours by shuffles.  Wall ghost lanes mirror

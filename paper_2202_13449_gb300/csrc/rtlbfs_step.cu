@@ -95,25 +95,30 @@ __device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj
                         gj, si, sj, mside);
 }
 
-// Ghost state across wall `side` in the storage type: rho even, velocity odd
-// about the wall velocity (normal component about 0), T odd about T_wall on
-// a Dirichlet wall and even on an adiabatic one.
+// Ghost values across wall `side` from the partner's working values y =
+// (rho - 1, u, v, T - Tref): rho even, velocity odd about the wall velocity
+// (normal component about 0), T odd about T_wall on a Dirichlet wall and
+// even on an adiabatic one.  Formed in the arithmetic type relative to
+// Tref: 2 T_wall - T_P can leave the fixed-point range of a stored
+// temperature (a hot wall next to cold fluid) while its deviation from a
+// temperature inside the tile does not.
 template <class P>
-__device__ __forceinline__ Vec4<typename P::S> mirror_state(const CavityDesc& d, int side,
-                                                            Vec4<typename P::S> v)
+__device__ __forceinline__ Vec4<typename P::R> mirror_values(const CavityDesc& d, int side,
+                                                             Vec4<typename P::R> y,
+                                                             typename P::R Tref)
 {
-    using S = typename P::S;
+    using R = typename P::R;
     const bool xn = (side == kSideW || side == kSideE);
-    const S ut2 = P::u2(&d, side);
+    const R ut2 = R(2) * P::bcU(&d, side);
     if (xn) {
-        v.y = P::mirror_odd(S(0), v.y);
-        v.z = P::mirror_odd(ut2, v.z);
+        y.y = -y.y;
+        y.z = ut2 - y.z;
     } else {
-        v.z = P::mirror_odd(S(0), v.z);
-        v.y = P::mirror_odd(ut2, v.y);
+        y.z = -y.z;
+        y.y = ut2 - y.y;
     }
-    if (d.kind[side] == kDirichlet) v.w = P::mirror_odd(P::T2(&d, side), v.w);
-    return v;
+    if (d.kind[side] == kDirichlet) y.w = R(2) * (P::Tw(&d, side) - Tref) - y.w;
+    return y;
 }
 
 // Ghost gradient across wall `side`: even quantities negate the normal
@@ -300,10 +305,12 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
             for (int q = 0; q < NR; ++q) {
                 const int k = tid + q * NT;
                 if (k >= NB) continue;
-                Vec4<S> x = v[q];
-                if (ms[q] >= 0) x = mirror_state<P>(*dp, ms[q], x);
+                const Vec4<S> x = v[q];
                 Vec4<R> y = {R(0), R(0), R(0), R(0)};
-                if (ok[q]) y = {P::val(x.x, 0), P::val(x.y, 1), P::val(x.z, 2), P::diff(x.w, qTz, 3)};
+                if (ok[q]) {
+                    y = {P::val(x.x, 0), P::val(x.y, 1), P::val(x.z, 2), P::diff(x.w, qTz, 3)};
+                    if (ms[q] >= 0) y = mirror_values<P>(*dp, ms[q], y, Tz);
+                }
                 sm.val[k / BX][k % BX] = y;
             }
         }
@@ -478,9 +485,9 @@ __device__ bool load_cell_d(const CavityDesc& d, int b, int gi, int gj, Vec4<dou
     int si, sj, ms;
     if (!resolve_cell(d, gi, gj, si, sj, ms)) return false;
     const size_t o = (size_t)sj * d.pitch + si;
-    Vec4<typename P::S> x = P::load4(&d, b, o);
-    if (ms >= 0) x = mirror_state<P>(d, ms, x);
+    const Vec4<typename P::S> x = P::load4(&d, b, o);
     v = {P::to_double(x.x, 0), P::to_double(x.y, 1), P::to_double(x.z, 2), P::to_double(x.w, 3)};
+    if (ms >= 0) v = mirror_values<StoreD>(d, ms, v, 0.0);  // FP64, T absolute
     return true;
 }
 

@@ -18,6 +18,10 @@ Workload recipes (the paper uses no dataset; all inputs are generated):
 * ``serving_trace`` -- request stream: Poisson arrivals, square meshes with
   side log-uniform in [64, 1024], Ra log-uniform in [1e3, 1e8], Pr in
   {0.71, 7.0}.
+* ``cylinder_o_mesh`` -- the body-fitted O-mesh of Section 4.3 (vertices
+  only): a circle of diameter D, far field at a given radius, first radial
+  spacing fixed, geometric growth outward, theta numbered clockwise so the
+  mesh is right-handed.
 * ``conduction_state3`` / ``perturbed_state3`` -- the 3D counterparts
   (rho, u, v, w, T), arrays of shape (nz, ny, nx): the cubic cavity's
   initial state of Section 4.4 (T linear between the isothermal x walls) and
@@ -153,3 +157,27 @@ def perturbed_state3(nx: int, ny: int, nz: int, seed: int, amp_rho: float = 1e-3
     w = g.uniform(-amp_u, amp_u, size=sh)
     T = T_mean + g.uniform(-amp_T, amp_T, size=sh)
     return (rho, u, v, w, T)
+
+
+def cylinder_o_mesh(ni: int, nj: int, D: float = 1.0, r_far: float = 52.5, first: float = 0.003):
+    """Vertices (X, Y), shape (nj+1, ni+1), of an O-mesh around a circle of
+    diameter D: radii from D/2 to r_far * D with the first spacing
+    first * D and a constant growth ratio (solved by bisection); theta
+    decreasing with i so i, j are right-handed; column ni repeats column 0."""
+    r0, r1, d0 = 0.5 * D, r_far * D, first * D
+    lo, hi = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        total = d0 * (q ** nj - 1.0) / (q - 1.0)
+        if total > r1 - r0:
+            hi = q
+        else:
+            lo = q
+    q = 0.5 * (lo + hi)
+    r = r0 + d0 * (q ** np.arange(nj + 1) - 1.0) / (q - 1.0)
+    r[-1] = r1
+    th = -2.0 * np.pi * np.arange(ni + 1) / ni
+    X = np.outer(r, np.cos(th))
+    Y = np.outer(r, np.sin(th))
+    X[:, -1], Y[:, -1] = X[:, 0], Y[:, 0]
+    return X, Y

@@ -328,3 +328,20 @@ def test_table5_ra1e6_on_the_paper_mesh():
     assert abs(c[iu] - gold["u_max_z_over_L"]) < w_cells[iu]
     assert abs(c[iw] - gold["w_max_x_over_L"]) < w_cells[iw]
     s.close()
+
+
+def test_fp32_hot_wall_next_to_cold_fluid(d3):
+    """The hot wall (T = 1) next to fluid near T = 0: the mirror temperature
+    is beyond a stored FP32 value's range; the kernel forms it relative to a
+    temperature inside the unit, so the step still matches the oracle."""
+    n = (20, 9, 11)
+    faces = [inputs.random_faces(m, 31 + a) for a, m in enumerate(n)]
+    p, s = make_pair(d3, faces, (D, D, A, A, A, D), (0.0, 1.0, 0, 0, 0, 1.0), 2, 1.0, capi.FP32)
+    rho, u, v, w, T = inputs.perturbed_state3(*n, seed=8)
+    st = (rho, u, v, w, T - 0.5)
+    ref, _, rc = d3.step(p, st, 3)
+    assert rc == 0
+    s.set_state(*st)
+    s.step(3)
+    compare(s.get_state(), ref, 1e-5, capi.FP32)
+    s.close()

@@ -1,0 +1,163 @@
+"""Curvilinear CUDA path (include/rtlbfs_curv.h) against the curvilinear FP64
+oracle, element by element, through the C ABI: FP64 <= 1e-12 after one
+step and <= 1e-11 after 20, FP32 <= 1e-5 on u, v, T (1e-6 on rho); wall heat
+sums <= 1e-12.  Meshes: a bent (non-orthogonal) cavity with moving walls and
+oblique gravity, O-meshes of an annulus (walls, periodic seam) and of a
+cylinder in a free stream (wall inside, far field outside), and a 1-cell
+wide strip; both tile heights.
+"""
+import numpy as np
+import pytest
+
+from paper_2202_13449_gb300 import capi, inputs
+from test_oracle_curv import o_mesh, rect_vertices  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+D, A, P, F = capi.WALL_DIRICHLET, capi.WALL_ADIABATIC, capi.PERIODIC, capi.FARFIELD
+
+
+@pytest.fixture(scope="module")
+def cv(orc):
+    from oracle import curv as mod
+    return mod
+
+
+def bent(nx, ny, seed):
+    X, Y = rect_vertices(inputs.random_faces(nx, seed), inputs.random_faces(ny, seed + 1))
+    X = X + 0.15 * np.sin(0.4 * Y)
+    Y = Y + 0.1 * np.cos(0.3 * X)
+    return X, Y
+
+
+def case(cv, name):
+    # transport coefficients and time step scaled to each mesh's cells (so
+    # the explicit step is stable and tau < 1.5): unit cells for the bent
+    # cavity and the strip, ~0.1 on the annulus, 0.02 at the cylinder wall
+    base = dict(nu=0.03, chi=0.04, beta_g=2e-3, dt=0.05, kappa=0.9, force=(1e-4, -2e-4))
+    if name == "annulus":
+        base.update(nu=0.003, chi=0.004, dt=0.02)
+    if name == "cylinder":
+        base.update(nu=0.002, chi=0.003, dt=0.006)
+    if name == "bent_cavity":
+        X, Y = bent(37, 19, 91)
+        g = np.array([0.3, 0.95]) / np.hypot(0.3, 0.95)  # a unit vector, as the library uses
+        return cv.ProblemC(X=X, Y=Y, gdir=tuple(g), bc_kind=(D, A, A, D), bc_T=(0.9, 0.1, 0.3, 0.6),
+                           bc_u=((0.0, 0.01), (0.0, 0.0), (0.0, 0.0), (0.02, -0.005)), **base), False
+    if name == "annulus":
+        X, Y = o_mesh(70, 18, 1.0, 3.0)
+        return cv.ProblemC(X=X, Y=Y, gdir=(0.0, 1.0), bc_kind=(P, P, D, D), bc_T=(0, 0, 1.0, 0.0),
+                           **base), True
+    if name == "cylinder":
+        X, Y = o_mesh(48, 21, 0.5, 8.0, stretch=1.4)
+        return cv.ProblemC(X=X, Y=Y, gdir=(0.0, 1.0), bc_kind=(P, P, D, F), bc_T=(0, 0, 1.0, 0.0),
+                           inf=(1.0, 0.0577, 0.0, 0.0), **base), True
+    if name == "strip_1xN":
+        X, Y = bent(1, 7, 95)
+        return cv.ProblemC(X=X, Y=Y, gdir=(0.0, 1.0), bc_kind=(D, A, D, A), bc_T=(1.0, 0, 0.2, 0),
+                           **base), False
+    raise KeyError(name)
+
+
+def solver(p, periodic, precision, tile_rows=0):
+    s = capi.SolverC(p.X, p.Y, periodic, precision)
+    s.set_physics(p.nu, p.chi, p.beta_g, p.dt)
+    s.set_lattice(p.kappa)
+    s.set_gravity(*p.gdir, p.T_ref)
+    s.set_body_force(*p.force)
+    s.set_farfield(*p.inf)
+    for side in range(4):
+        if periodic and side < 2:
+            continue
+        s.set_bc(side, p.bc_kind[side], p.bc_T[side], *p.bc_u[side])
+    s.set_schedule(tile_rows)
+    return s
+
+
+def rel(a, b, floor):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), floor))
+
+
+def compare(got, ref, tol, precision):
+    for q, floor in ((0, 1.0), (1, 1e-2), (2, 1e-2), (3, 1.0)):
+        if q == 0 and precision == capi.FP32:
+            assert np.max(np.abs(got[0] - ref[0])) < 1e-6
+            continue
+        e = rel(got[q], ref[q], floor)
+        assert e < tol, (q, e)
+
+
+def state_for(p, name):
+    nj, ni = p.shape
+    st = list(inputs.perturbed_state(ni, nj, seed=sum(map(ord, name))))
+    if name == "cylinder":
+        # a free stream of cold fluid against the hot wall: the wall's mirror
+        # temperature 2 T_w - T_P is near 2, the edge of a stored FP32 value
+        st[1] = st[1] + 0.0577
+        st[3] = st[3] - 0.45
+    return tuple(st)
+
+
+NAMES = ["bent_cavity", "annulus", "cylinder", "strip_1xN"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("tile_rows", [8, 16])
+def test_one_step_fp64(cv, name, tile_rows):
+    p, per = case(cv, name)
+    st = state_for(p, name)
+    ref, rr, rc = cv.step(p, st, 1)
+    assert rc == 0
+    s = solver(p, per, capi.FP64, tile_rows)
+    s.set_state(*st)
+    s.step(1)
+    compare(s.get_state(), ref, 1e-12, capi.FP64)
+    rg, steps = s.residual()
+    assert steps == 1
+    np.testing.assert_allclose(rg, rr, rtol=1e-9)
+    s.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_twenty_steps_fp64_and_three_fp32(cv, name):
+    p, per = case(cv, name)
+    st = state_for(p, name)
+    ref, _, rc = cv.step(p, st, 20)
+    assert rc == 0
+    s = solver(p, per, capi.FP64)
+    s.set_state(*st)
+    s.step(20)
+    compare(s.get_state(), ref, 1e-11, capi.FP64)
+    s.close()
+    ref, _, rc = cv.step(p, st, 3)
+    s = solver(p, per, capi.FP32)
+    s.set_state(*st)
+    s.step(3)
+    compare(s.get_state(), ref, 1e-5, capi.FP32)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["annulus", "cylinder"])
+def test_wall_heat_fp64(cv, name):
+    p, per = case(cv, name)
+    st = state_for(p, name)
+    s = solver(p, per, capi.FP64)
+    s.set_state(*st)
+    for side in (2, 3):
+        q, perim = s.wall_heat(side)
+        qr, pr = cv.heat(p, st, side)
+        assert q == pytest.approx(qr, rel=1e-12, abs=1e-15)
+        assert perim == pytest.approx(pr, rel=1e-13)
+    s.close()
+
+
+def test_mass_conserved_on_the_annulus(cv):
+    p, per = case(cv, "annulus")
+    st = state_for(p, "annulus")
+    _, geo = cv.gradients(p, st)
+    s = solver(p, per, capi.FP64)
+    s.set_state(*st)
+    s.step(300)
+    got = s.get_state()
+    s.close()
+    m0, m1 = np.sum(st[0] * geo[2]), np.sum(got[0] * geo[2])
+    assert abs(m1 - m0) / m0 < 1e-13
