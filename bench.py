@@ -138,8 +138,15 @@ WORKLOADS = {
     "cylinder450x300": dict(
         desc="mixed convection from a heated circular cylinder (Section 4.3): body-fitted O-mesh "
              "of 450 (around) x 300 (radial) cells, far field at 52.5 D, first spacing 0.003 D, "
-             "D = 1; Re = 20, Gr = 100, Pr = 0.7, u_inf = 0.1 c_s; FP32 bulk + FP64 reductions",
+             "D = 1; Re = 20, Gr = 100, Pr = 0.7, u_inf = 0.1 c_s along +x, buoyancy along the "
+             "free stream; FP32 bulk + FP64 reductions",
         ni=450, nj=300, Re=20.0, Gr=100.0, Pr=0.7, precision="fp32", inner=200, kind="curv"),
+    "table4": dict(
+        desc="Table 4 of Section 4.3 on this GPU: mean Nusselt number (Eq. 73) and separation "
+             "angle on the heated cylinder at Re = 20, Pr = 0.7, Gr = 0, 100, 800, 1600, each run "
+             "from the free stream to a steady state on the 450 x 300 O-mesh, FP32",
+        ni=450, nj=300, Re=20.0, Pr=0.7, Grs=(0.0, 100.0, 800.0, 1600.0), precision="fp32",
+        tol=1e-8, max_steps=5000000, kind="table4"),
     "cubic256": dict(
         desc="3D profiling case: cubic cavity 256x256x256, tanh phi=1.8, Ra=1e6, Pr=0.71, "
              "V_c=0.1, FP32 bulk + FP64 reductions (state 336 MB per buffer, > L2)",
@@ -1032,6 +1039,65 @@ def run_table6(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_table4(args, w):
+    """Table 4 on the GPU: each Gr case from the free stream to a steady state
+    (max(R_u, R_T) < tol, checked on the device every step), then Eq. 73's
+    mean Nusselt number and the separation angles from the state.  The
+    line's value is the largest relative deviation of Nu from the paper's
+    RTLBFS column."""
+    import torch
+    from paper_2202_13449_gb300 import capi, inputs, post
+    torch.cuda.set_device(0)
+    capi.lib()
+    with open(os.path.join(ROOT, "tests", "golden", "table4_cylinder.json")) as f:
+        gold = {c["Gr"]: c for c in json.load(f)["cases"]}
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    launches0 = capi.launch_count()
+    clk = ClockSampler(0)
+    clk.start()
+    rows, worst, total_ms, total_steps = [], 0.0, 0.0, 0
+    for Gr in w["Grs"]:
+        s, st0, XY, phys = curv_setup(capi, inputs, dict(w, Gr=Gr))
+        s.set_stream(stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc, steps, res = s.run_to_steady(w["tol"], w["max_steps"], timeout_s=600.0)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        heat, perim = s.wall_heat(2)
+        nu_cyl = heat / (phys["chi"] * perim)  # Eq. 73 with D = dT = 1
+        rho, u, v, T = s.get_state()
+        th = post.separation_angle(XY[0], XY[1], u, v)
+        g = gold[Gr]
+        dev = abs(nu_cyl - g["Nu"]) / g["Nu"]
+        worst = max(worst, dev)
+        total_ms += ms
+        total_steps += steps
+        rows.append({"Gr": Gr, "status": rc, "steps": steps, "residual": res,
+                     "Nu": round(nu_cyl, 4), "Nu_paper": g["Nu"], "Nu_rel_dev": round(dev, 4),
+                     "theta_s_deg": [round(t, 2) for t in th], "theta_s_paper": g["theta_s_deg"],
+                     "device_s": round(ms / 1e3, 2)})
+        s.close()
+    clocks = clk.stop()
+    cells = w["ni"] * w["nj"]
+    line = {
+        "metric": "max relative deviation of the mean cylinder Nusselt number from Table 4",
+        "value": round(worst, 4), "unit": "ratio", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
+                   "tol": w["tol"], "dt": phys["dt"]},
+        "cases": rows,
+        "throughput_M_cell_updates_per_s": round(cells * total_steps / (total_ms * 1e-3) / 1e6, 1),
+        "gpu_launches": int(capi.launch_count() - launches0),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def curv_setup(capi, inputs, w):
     """The Section 4.3 cylinder: solver and free-stream initial state."""
     import numpy as np
@@ -1048,7 +1114,7 @@ def curv_setup(capi, inputs, w):
     s = capi.SolverC(X, Y, True, prec)
     s.set_physics(nu, chi, beta_g, dt)
     s.set_lattice(w.get("kappa", 1.0))
-    s.set_gravity(0.0, 1.0, 0.0)
+    s.set_gravity(1.0, 0.0, 0.0)  # buoyancy along the free stream (aiding flow)
     s.set_bc(2, capi.WALL_DIRICHLET, 1.0)
     s.set_bc(3, capi.FARFIELD)
     s.set_farfield(1.0, uinf, 0.0, 0.0)
@@ -1150,7 +1216,7 @@ def run_curv(args, w):
         used = oracle.set_threads(os.cpu_count() or 1)
         X, Y = XY
         p = cv.ProblemC(X=X, Y=Y, nu=phys["nu"], chi=phys["chi"], beta_g=phys["beta_g"],
-                        dt=phys["dt"], gdir=(0.0, 1.0), T_ref=0.0,
+                        dt=phys["dt"], gdir=(1.0, 0.0), T_ref=0.0,
                         bc_kind=(cv.PERIODIC, cv.PERIODIC, cv.DIRICHLET, cv.FARFIELD),
                         bc_T=(0.0, 0.0, 1.0, 0.0), inf=(1.0, phys["uinf"], 0.0, 0.0))
         st = st0
@@ -1171,6 +1237,8 @@ def run_ours(args, w):
         return run_curv(args, w)
     if w.get("kind") == "table6":
         return run_table6(args, w)
+    if w.get("kind") == "table4":
+        return run_table4(args, w)
     if w.get("kind") == "cubic":
         return run_cubic(args, w)
     if w.get("kind") == "schemes":
@@ -1552,7 +1620,7 @@ def main():
         args.warmup = 3
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6"):
+        if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6", "table4"):
             print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
                               "time to a steady state of the GPU path; the oracle's rate is the "
                               "rb1024x512 / cavity512 reference lines"}))

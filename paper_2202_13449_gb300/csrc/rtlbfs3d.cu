@@ -42,6 +42,8 @@ extern std::atomic<long long> g_launches;
 namespace rtlbfs3 {
 
 using rtlbfs::CellLine;
+using rtlbfs::chain_sync;
+using rtlbfs::launch_chained;
 using rtlbfs::kAdiabatic;
 using rtlbfs::kConverged;
 using rtlbfs::kDiverged;
@@ -265,6 +267,7 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm& sm = *reinterpret_cast<Sm*>(smraw);
 
+    chain_sync();
     if (ctl->done) return;  // uniform: written by the previous launch
     const Desc3& d = *dp;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -749,11 +752,8 @@ template <class P, int TX, int TY>
 cudaError_t launch_step(int units, int scheme, cudaStream_t s, const Desc3* d, Ctl3* c)
 {
     const size_t sm = sizeof(Smem3<P, TX, TY>);
-    if (scheme == 1)
-        step3_kernel<P, TX, TY, 1><<<units, TX * TY, sm, s>>>(d, c);
-    else
-        step3_kernel<P, TX, TY, 0><<<units, TX * TY, sm, s>>>(d, c);
-    return cudaGetLastError();
+    if (scheme == 1) return launch_chained(step3_kernel<P, TX, TY, 1>, units, TX * TY, sm, s, d, c);
+    return launch_chained(step3_kernel<P, TX, TY, 0>, units, TX * TY, sm, s, d, c);
 }
 
 // shared-memory opt-in and resident blocks per SM of both face stages

@@ -9,10 +9,44 @@
 // closed rectilinear cell sum to zero).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cmath>
 #include <cstdint>
 
 namespace rtlbfs {
+
+// Chained time steps.  A step kernel launched with programmatic stream
+// serialisation (launch_chained) may become resident while the previous
+// step's grid drains; its blocks wait here, before they read anything that
+// grid wrote (run control, state), and then allow the next step's grid to
+// launch.  In a launch without the attribute both instructions return at
+// once.
+__device__ __forceinline__ void chain_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch kernel fn on stream s with programmatic stream serialisation: it
+// may start before the preceding kernel on s has finished, and must call
+// chain_sync() before it touches that kernel's output.
+template <typename... K, typename... A>
+cudaError_t launch_chained(void (*fn)(K...), unsigned grid, unsigned block, size_t smem,
+                           cudaStream_t s, A... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<K>(args)...);
+}
 
 constexpr int kSideW = 0, kSideE = 1, kSideS = 2, kSideN = 3;
 constexpr int kDirichlet = 0, kAdiabatic = 1, kPeriodic = 2;

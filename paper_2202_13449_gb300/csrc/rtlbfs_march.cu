@@ -146,6 +146,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     using V2 = typename P::V2;
     const int lane = threadIdx.x & 31;
     const int wpb = kMarchThreads / 32;
+    chain_sync();
     const int nunits = *nunits_ptr;
 
     for (int ui = blockIdx.x * wpb + (threadIdx.x >> 5); ui < nunits; ui += gridDim.x * wpb) {
@@ -458,10 +459,10 @@ cudaError_t launch_march(int precision, int grid, cudaStream_t s, const CavityDe
                          CavityCtl* ctls, const int4* units, const int* nunits)
 {
     if (precision == 0)
-        march_kernel<StoreD><<<grid, kMarchThreads, 0, s>>>(descs, ctls, units, nunits);
-    else
-        march_kernel<StoreQ><<<grid, kMarchThreads, 0, s>>>(descs, ctls, units, nunits);
-    return cudaGetLastError();
+        return launch_chained(march_kernel<StoreD>, grid, kMarchThreads, 0, s, descs, ctls, units,
+                              nunits);
+    return launch_chained(march_kernel<StoreQ>, grid, kMarchThreads, 0, s, descs, ctls, units,
+                          nunits);
 }
 
 }  // namespace rtlbfs

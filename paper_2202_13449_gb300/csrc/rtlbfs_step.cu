@@ -240,6 +240,7 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     extern __shared__ __align__(32) unsigned char smem_raw[];
     Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
+    chain_sync();
     const int ntiles = *ntiles_ptr;
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -703,8 +704,7 @@ struct TileKernel {
     static cudaError_t launch(int grid, cudaStream_t s, const CavityDesc* descs, CavityCtl* ctls,
                               const int4* tiles, const int* ntiles)
     {
-        fn<<<grid, NT, smem, s>>>(descs, ctls, tiles, ntiles);
-        return cudaGetLastError();
+        return launch_chained(fn, grid, NT, smem, s, descs, ctls, tiles, ntiles);
     }
 };
 

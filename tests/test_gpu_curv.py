@@ -161,3 +161,45 @@ def test_mass_conserved_on_the_annulus(cv):
     s.close()
     m0, m1 = np.sum(st[0] * geo[2]), np.sum(got[0] * geo[2])
     assert abs(m1 - m0) / m0 < 1e-13
+
+
+@pytest.mark.slow
+def test_table4_gr100_on_the_paper_mesh():
+    """Physics of the curvilinear GPU path at the paper's own setting
+    (Section 4.3, Table 4, Gr = 100): the 450 x 300 O-mesh from 0.003 D to
+    52.5 D, Re = 20, Pr = 0.7, u_inf = 0.1 c_s with buoyancy along the free
+    stream, FP32 from the free stream to a 1e-8 residual (about 2.2e6 steps).
+    The oracle cannot run this to a steady state, so the check is against
+    the printed values: Eq. 73's mean Nusselt number within 1 % and the
+    separation angle within 1.2 degrees (1.5 wall cells of 0.8 degrees)."""
+    import json
+    import math
+    import os
+    from paper_2202_13449_gb300 import post
+    gold = {c["Gr"]: c for c in json.load(open(os.path.join(
+        os.path.dirname(__file__), "golden", "table4_cylinder.json")))["cases"]}[100.0]
+    X, Y = inputs.cylinder_o_mesh(450, 300)
+    uinf = 0.1 / math.sqrt(3.0)
+    nu = uinf / 20.0
+    chi = nu / 0.7
+    wmin = float(np.min(np.diff(np.hypot(X, Y), axis=0)))
+    dt = 0.2 * wmin * wmin / chi
+    s = capi.SolverC(X, Y, True, capi.FP32)
+    s.set_physics(nu, chi, 100.0 * nu * nu, dt)
+    s.set_gravity(1.0, 0.0, 0.0)
+    s.set_bc(2, capi.WALL_DIRICHLET, 1.0)
+    s.set_bc(3, capi.FARFIELD)
+    s.set_farfield(1.0, uinf, 0.0, 0.0)
+    nj, ni = 300, 450
+    s.set_state(np.ones((nj, ni)), np.full((nj, ni), uinf), np.zeros((nj, ni)),
+                np.zeros((nj, ni)))
+    rc, steps, res = s.run_to_steady(1e-8, 4000000, timeout_s=400.0)
+    assert rc == capi.OK, (rc, steps, res)
+    heat, perim = s.wall_heat(2)
+    nu_cyl = heat / (chi * perim)
+    assert nu_cyl == pytest.approx(gold["Nu"], rel=0.01)
+    _, u, v, _ = s.get_state()
+    up, lo = post.separation_angle(X, Y, u, v)
+    assert up == pytest.approx(lo, abs=1e-3)  # the aiding flow is symmetric
+    assert abs(up - gold["theta_s_deg"]) < 1.2
+    s.close()
