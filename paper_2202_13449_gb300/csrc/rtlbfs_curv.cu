@@ -4,16 +4,20 @@
 // 4.3), its FP64 wall-heat sums and the rtlbfsc_* C ABI.
 //
 // Geometry is precomputed on the host in FP64 (cell centres, areas, ghost
-// centres mirrored across wall faces) and stored per face: the face vector,
-// its unit normal and length, the Eq. 56 weight, the lattice spacing with
-// the normal offsets of the two centres, their tangential offsets and the
-// transport coefficients of Eqs. 9-10.
+// centres mirrored across wall faces).  The step kernel reads two records:
+// per face, its unit normal and length, the tangential offsets of the two
+// centres, the lattice spacing with their normal offsets and the transport
+// coefficients of Eqs. 9-10 (FaceRec); per cell, the four Green-Gauss
+// coefficients w_f S_f / A of Eqs. 55-56 (CellGrad).
 //
-// Step kernel.  Work unit: a TX x TY tile of cells.  In shared memory:
+// Step kernel.  Work unit: a TX x TY tile of cells.  Before it waits for the
+// previous step's grid, a block starts asynchronous copies of the tile's
+// geometry into shared memory (it never changes between steps); then:
 //   1. the tile plus a 2-cell ring of (rho - 1, u, v, T - Tz), ghosts
 //      materialised (wall mirror, free stream, periodic seam);
-//   2. Green-Gauss gradients (Eqs. 55-56) on the tile plus a 1-cell ring; a
-//      wall ghost takes its partner's gradient reflected in the face normal;
+//   2. Green-Gauss gradients (Eqs. 55-56) on the tile plus a 1-cell ring,
+//      written over the cell's staged coefficients; a wall ghost takes its
+//      partner's gradient reflected in the face normal;
 //   3. every face of the tile: the cells' values and gradients rotated into
 //      the face frame (n, t), the tangential offsets of the centres folded
 //      into the values, then the rectilinear face template face_flux (Eq. 29
@@ -42,6 +46,8 @@ extern std::atomic<long long> g_launches;
 namespace rtlbfsc {
 
 using rtlbfs::CellNT;
+using rtlbfs::chain_sync;
+using rtlbfs::launch_chained;
 using rtlbfs::FaceLine;
 using rtlbfs::face_flux;
 using rtlbfs::kConverged;
@@ -55,16 +61,66 @@ using rtlbfs::vfma;
 
 constexpr int kDir = 0, kAdia = 1, kPer = 2, kFar = 3;
 
-// Geometry of one face (16 values).
+// Geometry of one face (16 values, host side and the FP64 wall sums).
 template <typename R>
-struct FaceGeo {
+struct __align__(16) FaceGeo {
     R Sx, Sy;   // face vector: length times the unit normal, from the low- to the high-index cell
     R wR;       // Eq. 56: phi_S = phi_L + wR (phi_R - phi_L)
+    R pad;
     R nx, ny;   // unit normal
-    R len;      // face length
     R tL, tR;   // tangential offsets (x_L - x_S).t, (x_R - x_S).t, t = (-n_y, n_x)
-    R h, cL, cR, m_nu_2h, m_chi_2h, m_tf15, m_tg15, pad;  // FaceLine fields
+    R h, cL, cR, m_nu_2h, m_chi_2h, m_tf15, m_tg15;  // FaceLine fields
+    R len;      // face length
 };
+
+// What the face stage of the step kernel reads of a face (12 values).
+template <typename R>
+struct __align__(16) FaceRec {
+    R nx, ny, tL, tR;
+    R h, cL, cR, m_nu_2h;
+    R m_chi_2h, m_tf15, m_tg15, len;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ FaceRec<R> face_rec(const FaceGeo<double>& a)
+{
+    FaceRec<R> b;
+    b.nx = (R)a.nx;
+    b.ny = (R)a.ny;
+    b.tL = (R)a.tL;
+    b.tR = (R)a.tR;
+    b.h = (R)a.h;
+    b.cL = (R)a.cL;
+    b.cR = (R)a.cR;
+    b.m_nu_2h = (R)a.m_nu_2h;
+    b.m_chi_2h = (R)a.m_chi_2h;
+    b.m_tf15 = (R)a.m_tf15;
+    b.m_tg15 = (R)a.m_tg15;
+    b.len = (R)a.len;
+    return b;
+}
+
+// Green-Gauss coefficients of a cell (Eqs. 55-56 with the weights and the
+// area folded in): grad phi = sum_f c_f (phi_f - phi_P) over the east, west,
+// north and south neighbours, c_f = +-w_f S_f / A.
+template <typename R>
+struct __align__(16) CellGrad {
+    R c[8];  // (x, y) of east, west, north, south
+};
+
+// A 16-byte aligned record by 16-byte vector loads (the unused groups are
+// not loaded).
+template <typename T>
+__device__ __forceinline__ T ld_vec(const T* p)
+{
+    static_assert(sizeof(T) % 16 == 0 && alignof(T) >= 16, "16-byte records");
+    T v;
+    const uint4* src = reinterpret_cast<const uint4*>(p);
+    uint4* dst = reinterpret_cast<uint4*>(&v);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T) / 16); ++k) dst[k] = src[k];
+    return v;
+}
 
 struct DescC {
     int ni, nj, per, tiles_x, tiles_y, units;
@@ -76,9 +132,9 @@ struct DescC {
     double d_inf[4];  // free stream (rho - 1, u, v, T)
     float f_inf[4];
     void* rec[2];                          // Vec4<S>[cells]
-    const void* gi;                        // FaceGeo<R>[nj][ni+1]
-    const void* gj;                        // FaceGeo<R>[nj+1][ni]
-    const void* ia;                        // R[cells]: 1 / area
+    const void* fri;                       // FaceRec<R>[nj][ni+1]
+    const void* frj;                       // FaceRec<R>[nj+1][ni]
+    const void* cg;                        // CellGrad<R>[cells]
     const void* dta;                       // R[cells]: dt / area
     const void* gi_d;                      // FP64 copies for the wall sums
     const void* gj_d;
@@ -193,7 +249,7 @@ __host__ __device__ __forceinline__ void mirror_grad_c(int kind, R nx, R ny, R g
 // Returns the fluxes times the face length in x, y components.
 template <typename R>
 __host__ __device__ __forceinline__ void face_c(const R vL[4], const R gL[8], const R vR[4],
-                                                const R gR[8], const FaceGeo<R>& fg, R keep,
+                                                const R gR[8], const FaceRec<R>& fg, R keep,
                                                 R uwx, R uwy, R Tz, R out[4])
 {
     const R nx = fg.nx, ny = fg.ny, tx = -ny, ty = nx;
@@ -239,14 +295,34 @@ __host__ __device__ __forceinline__ void face_c(const R vL[4], const R gL[8], co
     out[3] = F[3] * fg.len;
 }
 
+// Asynchronous global -> shared copies (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_n(void* sdst, const void* gsrc, float*)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_n(void* sdst, const void* gsrc, double*)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class P, int TX, int TY>
 struct SmemC {
     using R = typename P::R;
     static constexpr int BX = TX + 4, BY = TY + 4, GX = TX + 2, GY = TY + 2, NT = TX * TY;
+    FaceRec<R> fi[TY][TX + 1];  // face records; each face's flux is written over its own
+    FaceRec<R> fj[TY + 1][TX];
+    CellGrad<R> g[GY][GX];      // coefficients, overwritten by the gradients
     R v[4][BY][BX];
-    R g[8][GY][GX];
-    R fi[4][TY][TX + 1];
-    R fj[4][TY + 1][TX];
+    R dta[TY][TX];
     double red[NT / 32][4];
 };
 
@@ -258,21 +334,55 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
     using R = typename P::R;
     using Sm = SmemC<P, TX, TY>;
     constexpr int BX = Sm::BX, BY = Sm::BY, GX = Sm::GX, GY = Sm::GY, NT = Sm::NT;
+    constexpr int FC = sizeof(FaceRec<R>) / 16, GC = sizeof(CellGrad<R>) / 16;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm& sm = *reinterpret_cast<Sm*>(smraw);
-    if (ctl->done) return;  // uniform: written by the previous launch
     const DescC& d = *dp;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int ni = d.ni, nj = d.nj;
     const bool per = d.per != 0;
     const int i0 = (blockIdx.x % d.tiles_x) * TX, j0 = (blockIdx.x / d.tiles_x) * TY;
+    const FaceRec<R>* fI = static_cast<const FaceRec<R>*>(d.fri);
+    const FaceRec<R>* fJ = static_cast<const FaceRec<R>*>(d.frj);
+    const CellGrad<R>* cG = static_cast<const CellGrad<R>*>(d.cg);
+    const R* dta = static_cast<const R*>(d.dta);
+
+    // 0. the tile's geometry (constant across steps) into shared memory
+    for (int t = tid; t < TY * (TX + 1) * FC; t += NT) {
+        const int f = t / FC, k = t % FC, fj = f / (TX + 1), fi = f % (TX + 1);
+        const int gx = i0 + fi, gy = j0 + fj;
+        if (gx <= ni && gy < nj)
+            cp_async16(reinterpret_cast<unsigned char*>(&sm.fi[fj][fi]) + 16 * k,
+                       reinterpret_cast<const unsigned char*>(&fI[(size_t)gy * (ni + 1) + gx]) + 16 * k);
+    }
+    for (int t = tid; t < (TY + 1) * TX * FC; t += NT) {
+        const int f = t / FC, k = t % FC, fj = f / TX, fi = f % TX;
+        const int gx = i0 + fi, gy = j0 + fj;
+        if (gx < ni && gy <= nj)
+            cp_async16(reinterpret_cast<unsigned char*>(&sm.fj[fj][fi]) + 16 * k,
+                       reinterpret_cast<const unsigned char*>(&fJ[(size_t)gy * ni + gx]) + 16 * k);
+    }
+    for (int t = tid; t < GY * GX * GC; t += NT) {
+        const int e = t / GC, k = t % GC, r = e / GX, c = e % GX;
+        int is, xs, js, ys;
+        const bool iok = resolve_c(i0 - 1 + c, ni, per, 0, 1, is, xs);
+        const bool jok = resolve_c(j0 - 1 + r, nj, false, 2, 3, js, ys);
+        if (iok && jok && xs < 0 && ys < 0)
+            cp_async16(reinterpret_cast<unsigned char*>(&sm.g[r][c]) + 16 * k,
+                       reinterpret_cast<const unsigned char*>(&cG[(size_t)js * ni + is]) + 16 * k);
+    }
+    if (i0 + tx < ni && j0 + ty < nj)
+        cp_async_n(&sm.dta[ty][tx], &dta[(size_t)(j0 + ty) * ni + i0 + tx], (R*)nullptr);
+    cp_async_commit();
+
+    chain_sync();
+    if (ctl->done) {  // uniform: written by the previous launch
+        cp_async_wait_all();
+        return;
+    }
     const int cur = ctl->cur;
     const Vec4<S>* __restrict__ rin = static_cast<const Vec4<S>*>(d.rec[cur]);
     Vec4<S>* __restrict__ rout = static_cast<Vec4<S>*>(d.rec[cur ^ 1]);
-    const FaceGeo<R>* gI = static_cast<const FaceGeo<R>*>(d.gi);
-    const FaceGeo<R>* gJ = static_cast<const FaceGeo<R>*>(d.gj);
-    const R* ia = static_cast<const R*>(d.ia);
-    const R* dta = static_cast<const R*>(d.dta);
     const S qTz = rin[(size_t)min(j0 + TY / 2, nj - 1) * ni + min(i0 + TX / 2, ni - 1)].w;
     const R Tz = P::val(qTz, 3);
 
@@ -295,6 +405,7 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
 #pragma unroll
         for (int q = 0; q < 4; ++q) sm.v[q][r][c] = o[q];
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // 2. gradients on the tile and a 1-cell ring
@@ -303,46 +414,45 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
         int is, xs, js, ys;
         const bool iok = resolve_c(i0 - 2 + c, ni, per, 0, 1, is, xs);
         const bool jok = resolve_c(j0 - 2 + r, nj, false, 2, 3, js, ys);
-        R g[8];
+        CellGrad<R> g;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) g[e] = R(0);
+        for (int e = 0; e < 8; ++e) g.c[e] = R(0);
         const int side = xs >= 0 ? xs : ys;
         if (iok && jok && !(xs >= 0 && ys >= 0) && !(side >= 0 && d.kind[side] == kFar)) {
-            // the cell itself, or the partner a wall ghost mirrors
+            // the cell itself, or the partner (is, js) a wall ghost mirrors,
+            // whose coefficients a ghost reads from global memory
             int pr = r, pc = c;
             if (xs >= 0) pc = xs == 0 ? c + 1 : c - 1;
             if (ys >= 0) pr = ys == 2 ? r + 1 : r - 1;
-            // faces of the cell (is, js): west, east (i-faces), south, north (j-faces)
-            const FaceGeo<R>& fw = gI[(size_t)js * (ni + 1) + is];
-            const FaceGeo<R>& fe = gI[(size_t)js * (ni + 1) + is + 1];
-            const FaceGeo<R>& fs = gJ[(size_t)js * ni + is];
-            const FaceGeo<R>& fn = gJ[(size_t)(js + 1) * ni + is];
-            const R iA = ia[(size_t)js * ni + is];
-            const R we = fe.wR, ww = R(1) - fw.wR, wn = fn.wR, ws = R(1) - fs.wR;
+            const CellGrad<R> k = side >= 0 ? ld_vec(&cG[(size_t)js * ni + is]) : sm.g[r - 1][c - 1];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const R vc = sm.v[q][pr][pc];
-                const R de = (sm.v[q][pr][pc + 1] - vc) * we, dw = (sm.v[q][pr][pc - 1] - vc) * ww;
-                const R dn = (sm.v[q][pr + 1][pc] - vc) * wn, ds = (sm.v[q][pr - 1][pc] - vc) * ws;
-                g[2 * q] = iA * ((de * fe.Sx - dw * fw.Sx) + (dn * fn.Sx - ds * fs.Sx));
-                g[2 * q + 1] = iA * ((de * fe.Sy - dw * fw.Sy) + (dn * fn.Sy - ds * fs.Sy));
+                const R de = sm.v[q][pr][pc + 1] - vc, dw = sm.v[q][pr][pc - 1] - vc;
+                const R dn = sm.v[q][pr + 1][pc] - vc, ds = sm.v[q][pr - 1][pc] - vc;
+                g.c[2 * q] = vfma(k.c[0], de, vfma(k.c[2], dw, vfma(k.c[4], dn, k.c[6] * ds)));
+                g.c[2 * q + 1] = vfma(k.c[1], de, vfma(k.c[3], dw, vfma(k.c[5], dn, k.c[7] * ds)));
             }
             if (side >= 0) {
-                const FaceGeo<R>& fb = side == 0 ? fw : (side == 1 ? fe : (side == 2 ? fs : fn));
-                mirror_grad_c<R>(d.kind[side], fb.nx, fb.ny, g);
+                // the boundary face of the partner
+                const FaceRec<R> fb = ld_vec(side == 0   ? &fI[(size_t)js * (ni + 1)]
+                                             : side == 1 ? &fI[(size_t)js * (ni + 1) + ni]
+                                             : side == 2 ? &fJ[is]
+                                                         : &fJ[(size_t)nj * ni + is]);
+                mirror_grad_c<R>(d.kind[side], fb.nx, fb.ny, g.c);
             }
         }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) sm.g[e][r - 1][c - 1] = g[e];
+        sm.g[r - 1][c - 1] = g;
     }
     __syncthreads();
 
-    // 3. faces of the tile
+    // 3. faces of the tile; each face's flux replaces its record
     auto cell = [&](int r, int c, R v[4], R g[8]) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = sm.v[q][r][c];
+        const CellGrad<R> k = sm.g[r - 1][c - 1];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) g[e] = sm.g[e][r - 1][c - 1];
+        for (int e = 0; e < 8; ++e) g[e] = k.c[e];
     };
     for (int t = tid; t < TY * (TX + 1); t += NT) {
         const int fj = t / (TX + 1), fi = t % (TX + 1);
@@ -353,11 +463,14 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
         cell(fj + 2, fi + 2, vR, gR);
         const int ws = per ? -1 : (gx == 0 ? 0 : (gx == ni ? 1 : -1));
         const bool wall = ws >= 0 && d.kind[ws] != kFar;
+        const FaceRec<R> fr = sm.fi[fj][fi];
         R F[4];
-        face_c<R>(vL, gL, vR, gR, gI[(size_t)gy * (ni + 1) + gx], wall ? R(0) : R(1),
-                  wall ? CstC<P>::uw(d, ws, 0) : R(0), wall ? CstC<P>::uw(d, ws, 1) : R(0), Tz, F);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sm.fi[q][fj][fi] = F[q];
+        face_c<R>(vL, gL, vR, gR, fr, wall ? R(0) : R(1), wall ? CstC<P>::uw(d, ws, 0) : R(0),
+                  wall ? CstC<P>::uw(d, ws, 1) : R(0), Tz, F);
+        sm.fi[fj][fi].nx = F[0];
+        sm.fi[fj][fi].ny = F[1];
+        sm.fi[fj][fi].tL = F[2];
+        sm.fi[fj][fi].tR = F[3];
     }
     for (int t = tid; t < (TY + 1) * TX; t += NT) {
         const int fj = t / TX, fi = t % TX;
@@ -368,11 +481,14 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
         cell(fj + 2, fi + 2, vR, gR);
         const int ws = gy == 0 ? 2 : (gy == nj ? 3 : -1);
         const bool wall = ws >= 0 && d.kind[ws] != kFar;
+        const FaceRec<R> fr = sm.fj[fj][fi];
         R F[4];
-        face_c<R>(vL, gL, vR, gR, gJ[(size_t)gy * ni + gx], wall ? R(0) : R(1),
-                  wall ? CstC<P>::uw(d, ws, 0) : R(0), wall ? CstC<P>::uw(d, ws, 1) : R(0), Tz, F);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sm.fj[q][fj][fi] = F[q];
+        face_c<R>(vL, gL, vR, gR, fr, wall ? R(0) : R(1), wall ? CstC<P>::uw(d, ws, 0) : R(0),
+                  wall ? CstC<P>::uw(d, ws, 1) : R(0), Tz, F);
+        sm.fj[fj][fi].nx = F[0];
+        sm.fj[fj][fi].ny = F[1];
+        sm.fj[fj][fi].tL = F[2];
+        sm.fj[fj][fi].tR = F[3];
     }
     __syncthreads();
 
@@ -382,12 +498,14 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
     const int gi = i0 + tx, gj = j0 + ty;
     if (gi < ni && gj < nj) {
         const size_t off = (size_t)gj * ni + gi;
-        const R a = dta[off];
+        const R a = sm.dta[ty][tx];
+        const FaceRec<R>&fw = sm.fi[ty][tx], &fe = sm.fi[ty][tx + 1];
+        const FaceRec<R>&fs = sm.fj[ty][tx], &fn = sm.fj[ty + 1][tx];
         R div[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            div[q] = a * ((sm.fi[q][ty][tx + 1] - sm.fi[q][ty][tx]) +
-                          (sm.fj[q][ty + 1][tx] - sm.fj[q][ty][tx]));
+        div[0] = a * ((fe.nx - fw.nx) + (fn.nx - fs.nx));
+        div[1] = a * ((fe.ny - fw.ny) + (fn.ny - fs.ny));
+        div[2] = a * ((fe.tL - fw.tL) + (fn.tL - fs.tL));
+        div[3] = a * ((fe.tR - fw.tR) + (fn.tR - fs.tR));
         const R one = R(1);
         const R dr = sm.v[0][ty + 2][tx + 2], u = sm.v[1][ty + 2][tx + 2];
         const R v = sm.v[2][ty + 2][tx + 2], T = Tz + sm.v[3][ty + 2][tx + 2];
@@ -536,7 +654,7 @@ __global__ void curv_heat_kernel(const DescC* __restrict__ dp, int cur, int jfac
         vL[3] = 0.0;
         vR[3] -= TL;
         double F[4];
-        face_c<double>(vL, gL, vR, gR, gJ[(size_t)jface * d.ni + i], wall ? 0.0 : 1.0,
+        face_c<double>(vL, gL, vR, gR, face_rec<double>(gJ[(size_t)jface * d.ni + i]), wall ? 0.0 : 1.0,
                        wall ? d.bcU[side][0] : 0.0, wall ? d.bcU[side][1] : 0.0, TL, F);
         s += F[3];  // already times the face length
     }
@@ -554,16 +672,20 @@ template <class P, int TY>
 cudaError_t launch_c(int units, cudaStream_t s, const DescC* d, CtlC* c)
 {
     const size_t sm = sizeof(SmemC<P, kTileX, TY>);
-    curv_step_kernel<P, kTileX, TY><<<units, kTileX * TY, sm, s>>>(d, c);
-    return cudaGetLastError();
+    return launch_chained(curv_step_kernel<P, kTileX, TY>, units, kTileX * TY, sm, s, d, c);
 }
 
 template <class P, int TY>
 cudaError_t prepare_c()
 {
     const size_t sm = sizeof(SmemC<P, kTileX, TY>);
+    cudaError_t e = cudaFuncSetAttribute(curv_step_kernel<P, kTileX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    // the staged geometry makes shared memory the resource that bounds
+    // resident blocks: all of the unified L1/shared array to shared memory
     return cudaFuncSetAttribute(curv_step_kernel<P, kTileX, TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 }  // namespace rtlbfsc
@@ -712,63 +834,63 @@ FaceGeo<double> face_geo(const rtlbfsc_ctx* h, const HostGeo& g, int kind, doubl
     return f;
 }
 
-template <typename R>
-FaceGeo<R> cast_geo(const FaceGeo<double>& a)
+size_t align256(std::vector<unsigned char>& buf)
 {
-    FaceGeo<R> b;
-    b.Sx = (R)a.Sx;
-    b.Sy = (R)a.Sy;
-    b.wR = (R)a.wR;
-    b.nx = (R)a.nx;
-    b.ny = (R)a.ny;
-    b.len = (R)a.len;
-    b.tL = (R)a.tL;
-    b.tR = (R)a.tR;
-    b.h = (R)a.h;
-    b.cL = (R)a.cL;
-    b.cR = (R)a.cR;
-    b.m_nu_2h = (R)a.m_nu_2h;
-    b.m_chi_2h = (R)a.m_chi_2h;
-    b.m_tf15 = (R)a.m_tf15;
-    b.m_tg15 = (R)a.m_tg15;
-    b.pad = (R)0;
-    return b;
+    const size_t o = (buf.size() + 255) / 256 * 256;
+    buf.resize(o);
+    return o;
 }
 
-template <typename R>
-void append_geo(std::vector<unsigned char>& buf, size_t& off_i, size_t& off_j, size_t& off_ia,
-                size_t& off_dta, const std::vector<FaceGeo<double>>& fi,
-                const std::vector<FaceGeo<double>>& fj, const std::vector<double>& ia, double dt)
+template <typename T>
+size_t append_array(std::vector<unsigned char>& buf, const std::vector<T>& a)
 {
-    auto align = [&]() {
-        size_t o = (buf.size() + 255) / 256 * 256;
-        buf.resize(o);
-        return o;
-    };
-    off_i = align();
-    buf.resize(off_i + fi.size() * sizeof(FaceGeo<R>));
-    for (size_t k = 0; k < fi.size(); ++k) {
-        FaceGeo<R> x = cast_geo<R>(fi[k]);
-        std::memcpy(buf.data() + off_i + k * sizeof(x), &x, sizeof(x));
-    }
-    off_j = align();
-    buf.resize(off_j + fj.size() * sizeof(FaceGeo<R>));
-    for (size_t k = 0; k < fj.size(); ++k) {
-        FaceGeo<R> x = cast_geo<R>(fj[k]);
-        std::memcpy(buf.data() + off_j + k * sizeof(x), &x, sizeof(x));
-    }
-    off_ia = align();
-    buf.resize(off_ia + ia.size() * sizeof(R));
-    for (size_t k = 0; k < ia.size(); ++k) {
-        R x = (R)ia[k];
-        std::memcpy(buf.data() + off_ia + k * sizeof(R), &x, sizeof(R));
-    }
-    off_dta = align();
-    buf.resize(off_dta + ia.size() * sizeof(R));
-    for (size_t k = 0; k < ia.size(); ++k) {
-        R x = (R)(dt * ia[k]);
-        std::memcpy(buf.data() + off_dta + k * sizeof(R), &x, sizeof(R));
-    }
+    const size_t o = align256(buf);
+    buf.resize(o + a.size() * sizeof(T));
+    if (!a.empty()) std::memcpy(buf.data() + o, a.data(), a.size() * sizeof(T));
+    return o;
+}
+
+// The FP64 face geometry and inverse areas of the wall-heat sums.
+void append_heat_geo(std::vector<unsigned char>& buf, size_t& off_i, size_t& off_j, size_t& off_ia,
+                     const std::vector<FaceGeo<double>>& fi, const std::vector<FaceGeo<double>>& fj,
+                     const std::vector<double>& ia)
+{
+    off_i = append_array(buf, fi);
+    off_j = append_array(buf, fj);
+    off_ia = append_array(buf, ia);
+}
+
+// The step kernel's arrays in precision R: face records, the cells'
+// Green-Gauss coefficients (formed in FP64) and dt / area.
+template <typename R>
+void append_step_geo(std::vector<unsigned char>& buf, size_t& off_i, size_t& off_j, size_t& off_cg,
+                     size_t& off_dta, int ni, int nj, const std::vector<FaceGeo<double>>& fi,
+                     const std::vector<FaceGeo<double>>& fj, const std::vector<double>& ia, double dt)
+{
+    std::vector<FaceRec<R>> ri(fi.size()), rj(fj.size());
+    for (size_t k = 0; k < fi.size(); ++k) ri[k] = face_rec<R>(fi[k]);
+    for (size_t k = 0; k < fj.size(); ++k) rj[k] = face_rec<R>(fj[k]);
+    std::vector<CellGrad<R>> cg((size_t)ni * nj);
+    std::vector<R> dta((size_t)ni * nj);
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            const size_t c = (size_t)j * ni + i;
+            const FaceGeo<double>& fw = fi[(size_t)j * (ni + 1) + i];
+            const FaceGeo<double>& fe = fi[(size_t)j * (ni + 1) + i + 1];
+            const FaceGeo<double>& fs = fj[(size_t)j * ni + i];
+            const FaceGeo<double>& fn = fj[(size_t)(j + 1) * ni + i];
+            const double a = ia[c];
+            const double we = a * fe.wR, ww = -a * (1.0 - fw.wR);
+            const double wn = a * fn.wR, ws = -a * (1.0 - fs.wR);
+            const double k[8] = {we * fe.Sx, we * fe.Sy, ww * fw.Sx, ww * fw.Sy,
+                                 wn * fn.Sx, wn * fn.Sy, ws * fs.Sx, ws * fs.Sy};
+            for (int e = 0; e < 8; ++e) cg[c].c[e] = (R)k[e];
+            dta[c] = (R)(dt * a);
+        }
+    off_i = append_array(buf, ri);
+    off_j = append_array(buf, rj);
+    off_cg = append_array(buf, cg);
+    off_dta = append_array(buf, dta);
 }
 
 int tile_rows_of(const rtlbfsc_ctx* h)
@@ -798,16 +920,12 @@ int upload(rtlbfsc_ctx* h)
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) ia[(size_t)j * ni + i] = 1.0 / g.area[g.id(i, j)];
     std::vector<unsigned char> buf;
-    size_t oi_d, oj_d, oia_d, odta_d, oi, oj, oia, odta;
-    append_geo<double>(buf, oi_d, oj_d, oia_d, odta_d, fi, fj, ia, h->dt);
-    if (h->precision == RTLBFS_FP64) {
-        oi = oi_d;
-        oj = oj_d;
-        oia = oia_d;
-        odta = odta_d;
-    } else {
-        append_geo<float>(buf, oi, oj, oia, odta, fi, fj, ia, h->dt);
-    }
+    size_t oi_d, oj_d, oia_d, oi, oj, ocg, odta;
+    append_heat_geo(buf, oi_d, oj_d, oia_d, fi, fj, ia);
+    if (h->precision == RTLBFS_FP64)
+        append_step_geo<double>(buf, oi, oj, ocg, odta, ni, nj, fi, fj, ia, h->dt);
+    else
+        append_step_geo<float>(buf, oi, oj, ocg, odta, ni, nj, fi, fj, ia, h->dt);
     if (h->d_geo) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->d_geo);
@@ -824,9 +942,9 @@ int upload(rtlbfsc_ctx* h)
     d.tiles_x = (ni + kTileX - 1) / kTileX;
     d.tiles_y = (nj + ty - 1) / ty;
     d.units = d.tiles_x * d.tiles_y;
-    d.gi = base + oi;
-    d.gj = base + oj;
-    d.ia = base + oia;
+    d.fri = base + oi;
+    d.frj = base + oj;
+    d.cg = base + ocg;
     d.dta = base + odta;
     d.gi_d = base + oi_d;
     d.gj_d = base + oj_d;
@@ -1350,20 +1468,20 @@ extern "C" int rtlbfsc_op_counts(double* face_ops, double* cell_ops, double* sfu
         gL[k] = {0.001 * (k + 1), false};
         gR[k] = {0.002 * (k + 1), false};
     }
-    rtlbfsc::FaceGeo<CntC> fg;
+    rtlbfsc::FaceRec<CntC> fg;
     CntC x{0.3, false};
-    fg.Sx = fg.Sy = fg.wR = fg.nx = fg.ny = fg.len = fg.tL = fg.tR = x;
+    fg.nx = fg.ny = fg.len = fg.tL = fg.tR = x;
     fg.h = fg.cL = fg.cR = fg.m_nu_2h = fg.m_chi_2h = fg.m_tf15 = fg.m_tg15 = x;
-    fg.pad = {0.0, true};
     CntC F[4];
     rtlbfsc::face_c<CntC>(vL, gL, vR, gR, fg, CntC{1.0, false}, CntC{0.0, true}, CntC{0.0, true},
                           CntC{0.5, false}, F);
     const rtlbfsc::TallyC f = rtlbfsc::g_tc;
     // Per cell besides its two faces: working values 4, Green-Gauss gradients
-    // over four face vectors (4 fields x (4 differences, 4 weights, 8 FMA-
-    // products, 2 scalings) = 72), flux divergence 4 x 4 = 16, sources 8,
-    // increments and new values 15, fixed-point increments 4, residual 16.
-    const double other = 135.0, other_sfu = 4.0;
+    // with the coefficients w_f S_f / A of each cell precomputed (4 fields x
+    // (4 differences, 8 products and FMAs) = 48), flux divergence 4 x 4 = 16,
+    // sources 8, increments and new values 15, fixed-point increments 4,
+    // residual 16.
+    const double other = 111.0, other_sfu = 4.0;
     if (face_ops) *face_ops = (double)f.ops;
     if (cell_ops) *cell_ops = 2.0 * (double)f.ops + other;
     if (sfu_ops) *sfu_ops = 2.0 * (double)f.sfu + other_sfu;

@@ -163,6 +163,40 @@ def test_mass_conserved_on_the_annulus(cv):
     assert abs(m1 - m0) / m0 < 1e-13
 
 
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_full_size_cylinder_450x300_step(cv, precision):
+    """The bench's cylinder workload at full size, in its launch
+    configuration (automatic tile height): Section 4.3's 450 x 300 O-mesh,
+    Re = 20, Gr = 100, Pr = 0.7, buoyancy along the free stream; two steps
+    from a perturbed free stream of cold fluid, every cell against the
+    oracle, and the FP64 wall heat."""
+    import math
+    X, Y = inputs.cylinder_o_mesh(450, 300)
+    uinf = 0.1 / math.sqrt(3.0)
+    nu = uinf / 20.0
+    chi = nu / 0.7
+    wmin = float(np.min(np.diff(np.hypot(X, Y), axis=0)))
+    p = cv.ProblemC(X=X, Y=Y, nu=nu, chi=chi, beta_g=100.0 * nu * nu, dt=0.2 * wmin * wmin / chi,
+                    kappa=1.0, gdir=(1.0, 0.0), T_ref=0.0, bc_kind=(P, P, D, F),
+                    bc_T=(0.0, 0.0, 1.0, 0.0), inf=(1.0, uinf, 0.0, 0.0))
+    rho, u, v, T = inputs.perturbed_state(450, 300, seed=4503)
+    st = (rho, u + uinf, v, 0.2 * T)
+    ref, rr, rc = cv.step(p, st, 2)
+    assert rc == 0
+    s = solver(p, True, precision)
+    s.set_state(*st)
+    s.step(2)
+    compare(s.get_state(), ref, 1e-12 if precision == capi.FP64 else 1e-5, precision)
+    if precision == capi.FP64:
+        np.testing.assert_allclose(s.residual()[0], rr, rtol=1e-9)
+        s.set_state(*st)
+        q, perim = s.wall_heat(2)
+        qr, pr = cv.heat(p, st, 2)
+        assert q == pytest.approx(qr, rel=1e-12)
+        assert perim == pytest.approx(pr, rel=1e-13)
+    s.close()
+
+
 @pytest.mark.slow
 def test_table4_gr100_on_the_paper_mesh():
     """Physics of the curvilinear GPU path at the paper's own setting
