@@ -151,7 +151,9 @@ int rtlbfs3d_set_scheme(rtlbfs3d_t h, int scheme);
 /*
  * Work decomposition of the step kernel: tile 0 = 32 x 4 cells, 1 = 16 x 8,
  * 2 = 32 x 8 in x-y (one thread per column, marching up z); kchunk = planes
- * per work unit (0 = automatic: enough units to fill every SM).
+ * per work unit (0 = automatic: enough units to fill every SM; on meshes
+ * whose tile columns fit a wave of resident blocks twice, the shortest chunk
+ * of at least 4 planes whose units fit one wave).
  * ERR_ARG otherwise.
  */
 int rtlbfs3d_set_schedule(rtlbfs3d_t h, int tile, int kchunk);

@@ -877,6 +877,11 @@ void decompose(rtlbfs3d_ctx* h, Desc3& d)
         const long long per_plane = (long long)d.tiles_x * d.tiles_y;
         long long chunks = std::max(1LL, (slots + per_plane - 1) / per_plane);
         kc = (int)std::max(4LL, (h->n[2] + chunks - 1) / chunks);
+        // small meshes (a wave holds two planes of columns or more): the
+        // shortest chunk of at least 4 planes whose units fit one wave, so
+        // that no short second wave follows
+        if (2 * per_plane <= slots)
+            while (kc < h->n[2] && per_plane * ((h->n[2] + kc - 1) / kc) > slots) ++kc;
     }
     kc = std::min(kc, h->n[2]);
     d.kchunk = kc;
