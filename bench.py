@@ -141,6 +141,11 @@ WORKLOADS = {
              "D = 1; Re = 20, Gr = 100, Pr = 0.7, u_inf = 0.1 c_s along +x, buoyancy along the "
              "free stream; FP32 bulk + FP64 reductions",
         ni=450, nj=300, Re=20.0, Gr=100.0, Pr=0.7, precision="fp32", inner=200, kind="curv"),
+    "cylinder3600x2400": dict(
+        desc="roofline probe of the curvilinear kernel: the heated-cylinder O-mesh of Section 4.3 "
+             "refined to 3600 (around) x 2400 (radial) cells (8.64 M cells, 138 MB of state per "
+             "buffer, > L2), same far field, first spacing and physics; FP32",
+        ni=3600, nj=2400, Re=20.0, Gr=100.0, Pr=0.7, precision="fp32", inner=20, kind="curv"),
     "table4": dict(
         desc="Table 4 of Section 4.3 on this GPU: mean Nusselt number (Eq. 73) and separation "
              "angle on the heated cylinder at Re = 20, Pr = 0.7, Gr = 0, 100, 800, 1600, each run "
@@ -1107,8 +1112,9 @@ def curv_setup(capi, inputs, w):
     nu = uinf * 1.0 / w["Re"]
     chi = nu / w["Pr"]
     beta_g = w["Gr"] * nu * nu  # Gr = beta g dT D^3 / nu^2 with D = dT = 1
-    r = np.hypot(X, Y)
-    wmin = float(np.min(np.diff(r, axis=0)))
+    # the smallest cell width, radial or around
+    wmin = min(float(np.min(np.diff(np.hypot(X, Y), axis=0))),
+               float(np.min(np.hypot(np.diff(X, axis=1), np.diff(Y, axis=1)))))
     # half the smallest width, capped by the explicit diffusive limit there
     dt = min(0.5 * wmin, 0.2 * wmin * wmin / max(nu, chi))
     s = capi.SolverC(X, Y, True, prec)

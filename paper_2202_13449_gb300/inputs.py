@@ -168,7 +168,10 @@ def cylinder_o_mesh(ni: int, nj: int, D: float = 1.0, r_far: float = 52.5, first
     lo, hi = 1.0 + 1e-12, 2.0
     for _ in range(200):
         q = 0.5 * (lo + hi)
-        total = d0 * (q ** nj - 1.0) / (q - 1.0)
+        try:
+            total = d0 * (q ** nj - 1.0) / (q - 1.0)
+        except OverflowError:  # q ** nj beyond the double range: far too long
+            total = float("inf")
         if total > r1 - r0:
             hi = q
         else:
