@@ -1103,11 +1103,10 @@ def run_table4(args, w):
     print(json.dumps(line), flush=True)
 
 
-def curv_setup(capi, inputs, w):
-    """The Section 4.3 cylinder: solver and free-stream initial state."""
+def curv_case(inputs, w):
+    """The Section 4.3 cylinder: mesh, physics and the free-stream state."""
     import numpy as np
     X, Y = inputs.cylinder_o_mesh(w["ni"], w["nj"])
-    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
     uinf = 0.1 / np.sqrt(3.0)
     nu = uinf * 1.0 / w["Re"]
     chi = nu / w["Pr"]
@@ -1117,17 +1116,38 @@ def curv_setup(capi, inputs, w):
                float(np.min(np.hypot(np.diff(X, axis=1), np.diff(Y, axis=1)))))
     # half the smallest width, capped by the explicit diffusive limit there
     dt = min(0.5 * wmin, 0.2 * wmin * wmin / max(nu, chi))
+    nj, ni = X.shape[0] - 1, X.shape[1] - 1
+    st = (np.ones((nj, ni)), np.full((nj, ni), uinf), np.zeros((nj, ni)), np.zeros((nj, ni)))
+    return X, Y, st, dict(nu=nu, chi=chi, beta_g=beta_g, dt=dt, uinf=uinf)
+
+
+def curv_setup(capi, inputs, w):
+    """The Section 4.3 cylinder on the GPU: solver and free-stream initial state."""
+    X, Y, st, phys = curv_case(inputs, w)
+    prec = capi.FP32 if w["precision"] == "fp32" else capi.FP64
     s = capi.SolverC(X, Y, True, prec)
-    s.set_physics(nu, chi, beta_g, dt)
+    s.set_physics(phys["nu"], phys["chi"], phys["beta_g"], phys["dt"])
     s.set_lattice(w.get("kappa", 1.0))
     s.set_gravity(1.0, 0.0, 0.0)  # buoyancy along the free stream (aiding flow)
     s.set_bc(2, capi.WALL_DIRICHLET, 1.0)
     s.set_bc(3, capi.FARFIELD)
-    s.set_farfield(1.0, uinf, 0.0, 0.0)
-    nj, ni = X.shape[0] - 1, X.shape[1] - 1
-    st = (np.ones((nj, ni)), np.full((nj, ni), uinf), np.zeros((nj, ni)), np.zeros((nj, ni)))
+    s.set_farfield(1.0, phys["uinf"], 0.0, 0.0)
     s.set_state(*st)
-    return s, st, (X, Y), dict(nu=nu, chi=chi, beta_g=beta_g, dt=dt, uinf=uinf)
+    return s, st, (X, Y), phys
+
+
+def oracle_curv(w):
+    """The same cylinder case for the FP64 curvilinear oracle."""
+    import oracle
+    from oracle import curv as cv
+    from paper_2202_13449_gb300 import inputs
+    oracle.build()
+    X, Y, st, phys = curv_case(inputs, w)
+    p = cv.ProblemC(X=X, Y=Y, nu=phys["nu"], chi=phys["chi"], beta_g=phys["beta_g"],
+                    dt=phys["dt"], kappa=w.get("kappa", 1.0), gdir=(1.0, 0.0), T_ref=0.0,
+                    bc_kind=(cv.PERIODIC, cv.PERIODIC, cv.DIRICHLET, cv.FARFIELD),
+                    bc_T=(0.0, 0.0, 1.0, 0.0), inf=(1.0, phys["uinf"], 0.0, 0.0))
+    return cv, p, st
 
 
 def run_curv(args, w):
@@ -1137,6 +1157,9 @@ def run_curv(args, w):
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    if ws > 1:  # replicas: one O-mesh per rank, no data-path collective
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2202_13449_gb300 import capi, inputs
     capi.lib()
     cells = w["ni"] * w["nj"]
@@ -1146,10 +1169,17 @@ def run_curv(args, w):
     torch.cuda.set_stream(stream)
     s.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
     for _ in range(args.warmup):
         flush.zero_()
         s.step(inner)
-    torch.cuda.synchronize()
+    barrier()
     clk = ClockSampler(local)
     clk.start()
     l0 = capi.launch_count()
@@ -1162,12 +1192,13 @@ def run_curv(args, w):
         s.step(inner)
         b.record(stream)
         ev.append((a, b))
-    torch.cuda.synchronize()
+    barrier()
     launches = capi.launch_count() - l0
     clocks = clk.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    value = cells * inner * args.steps / (ms * 1e-3) / 1e6
+    ms = job_max(sum(a.elapsed_time(b) for a, b in ev))
+    value = cells * inner * args.steps * ws / (ms * 1e-3) / 1e6
     host = pinned(st0)
+    barrier()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
@@ -1175,7 +1206,7 @@ def run_curv(args, w):
         s.step(inner)
         out = s.get_state()
     torch.cuda.synchronize()
-    e2e = cells * inner * e2e_steps / (time.perf_counter() - t0) / 1e6
+    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     assert np.all(np.isfinite(out[3]))
     heat, perim = s.wall_heat(2)
     nu_cyl = heat * 1.0 / (phys["chi"] * 1.0 * perim)  # Eq. 73 with D = dT = 1
@@ -1192,7 +1223,7 @@ def run_curv(args, w):
     traffic = profile_traffic(args.workload, w["precision"], "curv", CURV_SOURCES)
     line = {
         "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
-        "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": 1, "steps": args.steps,
+        "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64",
         "data": "synthetic (seeded; no dataset)",
@@ -1215,17 +1246,10 @@ def run_curv(args, w):
         "clocks": clocks,
         "residual_last_step": res,
     }
-    if not args.no_cpu_baseline:
-        from oracle import curv as cv
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
         import oracle
-        oracle.build()
+        cv, p, st = oracle_curv(w)
         used = oracle.set_threads(os.cpu_count() or 1)
-        X, Y = XY
-        p = cv.ProblemC(X=X, Y=Y, nu=phys["nu"], chi=phys["chi"], beta_g=phys["beta_g"],
-                        dt=phys["dt"], gdir=(1.0, 0.0), T_ref=0.0,
-                        bc_kind=(cv.PERIODIC, cv.PERIODIC, cv.DIRICHLET, cv.FARFIELD),
-                        bc_T=(0.0, 0.0, 1.0, 0.0), inf=(1.0, phys["uinf"], 0.0, 0.0))
-        st = st0
         n, t0 = 0, time.perf_counter()
         while n == 0 or time.perf_counter() - t0 < args.cpu_seconds:
             st, _, _ = cv.step(p, st, 2)
@@ -1235,7 +1259,8 @@ def run_curv(args, w):
                                 "cores": used, "kind": "oracle",
                                 "sample": f"{n} FP64 time steps of the same O-mesh ({dtc:.1f} s)"}
     s.close()
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, w):
@@ -1558,6 +1583,14 @@ def run_reference(args, w):
             for k, (p, _, _) in enumerate(probs):
                 states[k], _, _ = oracle.step(p, states[k], per_step)
         sample = f"the first 16 cavities of the batch ({cells} cells), {per_step} FP64 steps each"
+    elif kind == "curv":
+        cv, p, st0 = oracle_curv(w)
+        cells = w["ni"] * w["nj"]
+        box = [st0]
+
+        def one():
+            box[0], _, _ = cv.step(p, box[0], per_step)
+        sample = f"{per_step} FP64 time steps of the {w['ni']}x{w['nj']} O-mesh"
     elif kind == "cubic":
         _, d3, p, st0 = oracle_cubic(w)
         cells = w["n"] ** 3
