@@ -110,7 +110,8 @@ int rtlbfsc_residual(rtlbfsc_t h, double* res2, long* steps);
  */
 int rtlbfsc_wall_heat(rtlbfsc_t h, int side, double* heat, double* perimeter);
 
-/* Rows of cells per work unit (tile height 8 or 16; 0: automatic). */
+/* Rows of cells per work unit (tile height 8 or 16; 0: automatic, which is
+ * 8). */
 int rtlbfsc_set_schedule(rtlbfsc_t h, int tile_rows);
 
 int rtlbfsc_set_stream(rtlbfsc_t h, void* stream);
