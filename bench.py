@@ -171,7 +171,12 @@ CURV_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_curv.cu",
 STEP_SOURCES = ["paper_2202_13449_gb300/csrc/rtlbfs_step.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_march.cu",
                 "paper_2202_13449_gb300/csrc/rtlbfs_dev.cuh",
-                "paper_2202_13449_gb300/csrc/rtlbfs_kernels.h"]
+                "paper_2202_13449_gb300/csrc/rtlbfs_kernels.h",
+                "paper_2202_13449_gb300/csrc/rtlbfs_tile.cuh",
+                "paper_2202_13449_gb300/csrc/rtlbfs_persist.cu"]
+# schedule kernel kinds of the 2D solver: short names and device kernel names
+SCHED_NAMES = ["march", "tile", "persist"]
+SCHED_KERNELS = ["rtlbfs::march_kernel", "rtlbfs::step_kernel", "rtlbfs::persist_kernel"]
 
 
 def kernel_hash(sources=None) -> str:
@@ -393,7 +398,7 @@ def run_batch(args, w):
     if args.schedule == "auto":
         sched = b.autotune(16)
     else:
-        sched = (0 if args.schedule.startswith("march") else 1, 0, 0.0)
+        sched = (SCHED_NAMES.index(args.schedule.split(":")[0]), 0, 0.0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         flush.zero_()
@@ -422,8 +427,8 @@ def run_batch(args, w):
     value = cells * inner * args.steps * ws / (ms * 1e-3) / 1e6
     rs = 4 if prec == capi.FP32 else 8
     per_launch = ms * 1e-3 / (inner * args.steps)
-    kname = ["rtlbfs::march_kernel", "rtlbfs::step_kernel"][sched[0]]
-    traffic = profile_traffic(args.workload, w["precision"], ["march", "tile"][sched[0]])
+    kname = SCHED_KERNELS[sched[0]]
+    traffic = profile_traffic(args.workload, w["precision"], SCHED_NAMES[sched[0]])
     alu, hbm = rooflines(kname, cells, per_launch, rs, traffic, clocks)
 
     # e2e through the C ABI with host buffers: every cavity's state up from
@@ -455,7 +460,7 @@ def run_batch(args, w):
                    "cells": cells, "time_steps_per_bench_step": inner,
                    "state_bytes_per_buffer": 4 * rs * cells,
                    "l2": "inputs larger than L2; also flushed between bench steps",
-                   "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1]},
+                   "schedule": {"kernel": SCHED_NAMES[sched[0]], "chunk_rows": sched[1]},
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
@@ -674,7 +679,7 @@ def run_rb_steady(args, w):
                                     f"the last {W} samples (every {k} steps) bottom and top mean "
                                     "Nu within 5 % and the mean moved < 2 % against the previous "
                                     "window; Nu per unit wall length across the layer height"},
-            "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1]},
+            "schedule": {"kernel": SCHED_NAMES[sched[0]], "chunk_rows": sched[1]},
             "steady_at_step": steady_at, "onset_at_step": onset_at * k if onset_at else None,
             "nusselt_mean": m,
             "nusselt_bottom_last": bottom[-1], "nusselt_top_last": top[-1],
@@ -1305,7 +1310,7 @@ def run_ours(args, w):
     if args.schedule == "auto":
         sched = s.autotune(max(16, min(256, 2_000_000 // cells + 16)))
     else:
-        k = 0 if args.schedule.startswith("march") else 1
+        k = SCHED_NAMES.index(args.schedule.split(":")[0])
         rows = int(args.schedule.split(":")[1]) if ":" in args.schedule else 0
         s.set_schedule(k, rows)
         sched = (k, rows, 0.0)
@@ -1359,8 +1364,8 @@ def run_ours(args, w):
 
     rs = 4 if w["precision"] == "fp32" else 8
     per_launch_s = ms_max * 1e-3 / (inner * args.steps)
-    kname = ["rtlbfs::march_kernel", "rtlbfs::step_kernel"][sched[0]]
-    traffic = profile_traffic(args.workload, w["precision"], ["march", "tile"][sched[0]])
+    kname = SCHED_KERNELS[sched[0]]
+    traffic = profile_traffic(args.workload, w["precision"], SCHED_NAMES[sched[0]])
     alu, hbm = rooflines(kname, cells, per_launch_s, rs, traffic, clocks, w.get("scheme", 0))
     res, steps_total = s.residual()
     line = {
@@ -1379,7 +1384,7 @@ def run_ours(args, w):
         "config": {"workload": args.workload, "description": w["desc"], "cells": cells,
                    "time_steps_per_bench_step": inner, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between bench steps (256 MB write)",
-                   "schedule": {"kernel": ["march", "tile"][sched[0]], "chunk_rows": sched[1],
+                   "schedule": {"kernel": SCHED_NAMES[sched[0]], "chunk_rows": sched[1],
                                 "autotune_ms_per_step": round(sched[2], 5)},
                    "e2e_host_buffers": "pinned",
                    "state_bytes_per_buffer": 4 * rs * cells},
@@ -1653,7 +1658,7 @@ def main():
     ap.add_argument("--slots", type=int, default=256, help="serve: concurrent cavities")
     ap.add_argument("--fp64-sample", type=int, default=20, help="serve: FP64 comparator sample")
     ap.add_argument("--schedule", default="auto",
-                    help="auto (autotuner), tile, or march[:rows per unit]")
+                    help="auto (autotuner), or march|tile|persist[:rows per unit or tile]")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

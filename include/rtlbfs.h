@@ -204,15 +204,28 @@ int rtlbfs_set_scheme(rtlbfs_t h, int scheme);
  * chunk_rows 0 = chosen from the GPU size), kernel 1 = shared-memory tiles
  * of 32 columns by chunk_rows rows (16, 14, 12, 10, 8, 4 or 2 in FP32; 16,
  * 8, 4 or 2 in FP64; 0 = the height whose tile count fills the SMs most
- * evenly).
+ * evenly), kernel 2 = the same tiles in one persistent cooperative launch
+ * per chunk of steps, each tile waiting only for the eight around it (the
+ * RTLBFS stage, every tile resident at once and at least 2 cells wide; the
+ * step then fails with ERR_ARG otherwise).  Every kernel stops at the same
+ * step under run_to_steady.
  * ERR_ARG on other values, and on anything but the tile kernel at height
  * 16 (or 0) under the TLBFS face stage.
  */
 int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows);
 
 /*
+ * For tests of the persistent kernel's bounded waits: tile `tile` (>= 0)
+ * never reports its progress, so its neighbours' waits run out after about
+ * a second and the step returns ERR_CUDA ("stalled"); -1 restores normal
+ * running.  Never needed otherwise.
+ */
+int rtlbfs_debug_withhold_tile(rtlbfs_t h, int tile);
+
+/*
  * Autotuner: time every candidate schedule (the tile kernel at each tile
- * height and the marching kernel with 8..256 rows per unit) for `steps` steps each on a
+ * height, the persistent tile kernel at each height it can take, and the
+ * marching kernel with 8..256 rows per unit) for `steps` steps each on a
  * device-side snapshot of the current state, restore the state exactly
  * (fields, step counter, residual) and keep the fastest schedule.  Writes
  * the choice and its time per step if the pointers are non-null.  Needs

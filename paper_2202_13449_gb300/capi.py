@@ -69,6 +69,7 @@ _SIGS = {
     "rtlbfs_nusselt": (C.c_int, [_vp, C.c_int, _dp]),
     "rtlbfs_set_stream": (C.c_int, [_vp, _vp]),
     "rtlbfs_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "rtlbfs_debug_withhold_tile": (C.c_int, [_vp, C.c_int]),
     "rtlbfs_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_double)]),
     "rtlbfs_sync": (C.c_int, [_vp]),
@@ -310,9 +311,15 @@ class Solver:
     def set_schedule(self, kernel: int = 0, chunk_rows: int = 0):
         """kernel 0: warp-marching strips (chunk_rows rows per unit), 1:
         shared-memory tiles (chunk_rows = tile height: 16, 14, 12, 10, 8, 4 or
-        2 in FP32; 16, 8, 4 or 2 in FP64); chunk_rows 0 picks automatically."""
+        2 in FP32; 16, 8, 4 or 2 in FP64), 2: the same tiles in a persistent
+        launch (one cavity whose tiles all fit at once); chunk_rows 0 picks
+        automatically."""
         self._check(lib().rtlbfs_set_schedule(self._h, int(kernel), int(chunk_rows)),
                     "set_schedule")
+
+    def debug_withhold_tile(self, tile: int):
+        """Tests only: the persistent kernel's tile that never reports progress."""
+        self._check(lib().rtlbfs_debug_withhold_tile(self._h, int(tile)), "debug_withhold_tile")
 
     def autotune(self, steps: int = 64):
         """Pick the fastest schedule on a snapshot of the state (restored);

@@ -286,6 +286,14 @@ int rtlbfs_set_schedule(rtlbfs_t h, int kernel, int chunk_rows)
     return finish(h, rc);
 }
 
+int rtlbfs_debug_withhold_tile(rtlbfs_t h, int tile)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    if (tile < -1) return argfail(h, "tile must be >= -1");
+    h->eng->set_withhold(tile);
+    return RTLBFS_OK;
+}
+
 int rtlbfs_autotune(rtlbfs_t h, int steps, int* kernel, int* chunk_rows, double* ms_per_step)
 {
     if (!cav(h)) return RTLBFS_ERR_ARG;

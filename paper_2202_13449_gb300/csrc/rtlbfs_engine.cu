@@ -15,6 +15,7 @@ std::atomic<long long> g_launches{0};
 
 namespace {
 constexpr int kGraphChunk = 64;  // step launches per captured graph
+constexpr int kPersistChunk = 1 << 16;  // steps per persistent launch
 constexpr int kPartialMax = 2048;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -96,6 +97,9 @@ Engine::~Engine()
     cudaFree(d_partial_);
     cudaFree(d_scalar_);
     cudaFree(d_stage_);
+    cudaFree(d_tstep_);
+    cudaFree(d_pctl_);
+    if (h_stalled_) cudaFreeHost(h_stalled_);
     if (h_scalar_) cudaFreeHost(h_scalar_);
     if (own_stream_) cudaStreamDestroy(own_stream_);
 }
@@ -134,6 +138,11 @@ int Engine::init()
     }
     CK(step_occupancy(precision_, kTileYDefault, kSchemeTLBFS, &occ_tlbfs_));
     if (occ_tlbfs_ < 1) return fail(RTLBFS_ERR_CUDA, "TLBFS step kernel does not fit on an SM");
+    CK(persist_prepare(precision_));
+    for (int h : kTileHeights) {
+        if (!tile_height_ok(precision_, h)) continue;
+        CK(persist_occupancy(precision_, h, &occ_persist_[h]));
+    }
     CK(march_prepare(precision_));
     CK(march_occupancy(precision_, &occ_march_));
     if (occ_march_ < 1) return fail(RTLBFS_ERR_CUDA, "march kernel does not fit on an SM");
@@ -172,6 +181,8 @@ int Engine::init()
     CK(cudaMalloc(&d_partial_, sizeof(double) * partial_cap_));
     CK(cudaMalloc(&d_scalar_, sizeof(double) * 8));
     CK(cudaMallocHost(&h_scalar_, sizeof(double) * 8));
+    CK(cudaMalloc(&d_pctl_, sizeof(PersistCtl)));
+    CK(cudaMallocHost(&h_stalled_, sizeof(int)));
     return RTLBFS_OK;
 }
 
@@ -413,7 +424,7 @@ int Engine::set_scheme(int scheme)
 
 int Engine::set_kernel(int kind)
 {
-    if (kind != 0 && kind != 1) return fail(RTLBFS_ERR_ARG, "kernel kind must be 0 or 1");
+    if (kind < 0 || kind > 2) return fail(RTLBFS_ERR_ARG, "kernel kind must be 0, 1 or 2");
     if (scheme_ == kSchemeTLBFS && kind != 1)
         return fail(RTLBFS_ERR_ARG, "the TLBFS face stage runs on the tile kernel (1)");
     if (kind != kernel_) {
@@ -432,7 +443,7 @@ int Engine::set_chunk_rows(int rows)
     if (rows < 0) return fail(RTLBFS_ERR_ARG, "chunk rows must be >= 0");
     if (scheme_ == kSchemeTLBFS && kernel_ == 1 && rows != 0 && rows != kTileYDefault)
         return fail(RTLBFS_ERR_ARG, "the TLBFS tile kernel has height 16 (or 0)");
-    if (kernel_ == 1 && rows != 0 && !tile_height_ok(precision_, rows))
+    if (kernel_ >= 1 && rows != 0 && !tile_height_ok(precision_, rows))
         return fail(RTLBFS_ERR_ARG, precision_ == RTLBFS_FP64
                                         ? "FP64 tile height must be one of 16, 8, 4, 2 (or 0)"
                                         : "tile height must be one of 16, 14, 12, 10, 8, 4, 2 (or 0)");
@@ -470,7 +481,7 @@ int Engine::pick_tile_height() const
 int Engine::rebuild_tiles()
 {
     std::vector<int4> t;
-    if (kernel_ == 1) {
+    if (kernel_ >= 1) {
         const int h = chunk_rows_ > 0 ? chunk_rows_ : pick_tile_height();
         if (h != tile_h_ && gexec_) {  // the graph baked the other tile kernel
             cudaGraphExecDestroy(gexec_);
@@ -564,7 +575,18 @@ int Engine::prepare_launch()
     }
     // persistent grid: every SM full, never more blocks than work units
     int want;
-    if (kernel_ == 1) {
+    if (kernel_ == 2) {
+        int rc = persist_check();
+        if (rc) return rc;
+        if (ntiles_ > tstep_cap_) {
+            CK(cudaStreamSynchronize(stream_));
+            cudaFree(d_tstep_);
+            d_tstep_ = nullptr;
+            CK(cudaMalloc(&d_tstep_, sizeof(int) * ntiles_));
+            tstep_cap_ = ntiles_;
+        }
+        want = ntiles_;
+    } else if (kernel_ == 1) {
         const int occ = scheme_ == kSchemeTLBFS ? occ_tlbfs_ : occ_tile_[tile_h_];
         want = std::max(1, std::min(sms_ * occ, std::max(ntiles_, 1)));
     } else {
@@ -717,11 +739,55 @@ int Engine::arm(int slot, long long nsteps, double tol)
     return RTLBFS_OK;
 }
 
+// The persistent tile kernel takes one RTLBFS cavity whose tiles are all
+// resident at once and at least two cells wide and high (a tile's 2-cell
+// halo then lies in the eight tiles around it).
+int Engine::persist_check()
+{
+    persist_slot_ = -1;
+    int active = 0, slot = -1;
+    for (int s = 0; s < capacity_; ++s)
+        if (slots_[s].active) {
+            ++active;
+            slot = s;
+        }
+    if (active != 1) return fail(RTLBFS_ERR_ARG, "the persistent kernel takes exactly one cavity");
+    if (scheme_ != kSchemeRTLBFS)
+        return fail(RTLBFS_ERR_ARG, "the persistent kernel runs the RTLBFS face stage only");
+    const Cavity& c = slots_[slot];
+    if ((c.nx % kTileX) == 1 || (c.ny % tile_h_) == 1)
+        return fail(RTLBFS_ERR_ARG, "the persistent kernel needs tiles at least 2 cells wide");
+    if ((long long)ntiles_ > (long long)sms_ * occ_persist_[tile_h_])
+        return fail(RTLBFS_ERR_ARG, "the mesh has more tiles than fit on the GPU at once");
+    persist_slot_ = slot;
+    return RTLBFS_OK;
+}
+
 int Engine::launch_steps(long long launches)
 {
     int rc = prepare_launch();
     if (rc) return rc;
     if (ntiles_ == 0 || launches <= 0) return RTLBFS_OK;
+    if (kernel_ == 2) {
+        // chunks of steps, one launch each; a wait that ran out is an error
+        const Cavity& c = slots_[persist_slot_];
+        for (long long left = launches; left > 0;) {
+            const int n = (int)std::min<long long>(left, kPersistChunk);
+            CK(cudaMemsetAsync(d_tstep_, 0, sizeof(int) * ntiles_, stream_));
+            CK(cudaMemsetAsync(d_pctl_, 0, sizeof(PersistCtl), stream_));
+            CK(launch_persist(precision_, tile_h_, ntiles_, stream_, &d_desc_[persist_slot_],
+                              &d_ctl_[persist_slot_], d_tiles_ + c.first_tile, d_tstep_, d_pctl_,
+                              n, withhold_));
+            g_launches++;
+            CK(cudaMemcpyAsync(h_stalled_, &d_pctl_->stalled, sizeof(int), cudaMemcpyDeviceToHost,
+                               stream_));
+            CK(cudaStreamSynchronize(stream_));
+            if (*h_stalled_)
+                return fail(RTLBFS_ERR_CUDA, "persistent step stalled: a bounded wait ran out");
+            left -= n;
+        }
+        return RTLBFS_OK;
+    }
     long long left = launches;
     if (left >= kGraphChunk) {
         if (!gexec_) {
@@ -783,6 +849,24 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
     for (int h : kTileHeights)
         if (tile_height_ok(precision_, h) && (scheme_ == kSchemeRTLBFS || h == kTileYDefault))
             cands.push_back({1, h});
+    // the persistent tile kernel, at each height whose tiles all fit at once
+    // (engines of one slot only: a batch could grow past one cavity later)
+    int active = 0, aslot = -1;
+    for (int s = 0; s < capacity_; ++s)
+        if (slots_[s].active) {
+            ++active;
+            aslot = s;
+        }
+    if (capacity_ == 1 && active == 1 && scheme_ == kSchemeRTLBFS)
+        for (int h : kTileHeights) {
+            if (!tile_height_ok(precision_, h)) continue;
+            const Cavity& c = slots_[aslot];
+            const long long tiles =
+                (long long)((c.nx + kTileX - 1) / kTileX) * ((c.ny + h - 1) / h);
+            if ((c.nx % kTileX) != 1 && (c.ny % h) != 1 &&
+                tiles <= (long long)sms_ * occ_persist_[h])
+                cands.push_back({2, h});
+        }
     for (int H : {8, 16, 32, 64, 128, 256}) {
         if (scheme_ == kSchemeTLBFS) break;
         if (H > maxny && H != 8) break;

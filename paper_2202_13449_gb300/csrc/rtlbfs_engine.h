@@ -83,8 +83,13 @@ public:
     int cuda_fail(cudaError_t e, const char* what);
     int active_tiles() const { return ntiles_; }
     int grid() const { return grid_; }
-    // step kernel: 0 = warp-marching strips (default), 1 = shared-memory tiles
+    // step kernel: 0 = warp-marching strips (default), 1 = shared-memory
+    // tiles, 2 = the tile kernel in persistent form (one cavity whose tiles
+    // all fit on the GPU at once; many steps per launch)
     int set_kernel(int kind);
+    // tests only: the persistent kernel's tile that never reports progress
+    // (-1: none), to exercise its bounded waits
+    void set_withhold(int tile) { withhold_ = tile; }
     int kernel() const { return kernel_; }
     // rows per work unit (0 = automatic): chunk rows of a warp-marching
     // unit, or the tile height of the tile kernel (one of kTileHeights)
@@ -109,6 +114,14 @@ private:
     int sms_ = 0, grid_ = 0;
     int occ_tile_[32] = {};  // resident tile blocks per SM, by tile height
     int occ_tlbfs_ = 0;      // the same for the TLBFS tile kernel
+    int occ_persist_[32] = {};  // the same for the persistent tile kernel
+    int* d_tstep_ = nullptr;    // persistent kernel: last step of each tile
+    int tstep_cap_ = 0;
+    PersistCtl* d_pctl_ = nullptr;
+    int* h_stalled_ = nullptr;  // pinned
+    int withhold_ = -1;
+    int persist_slot_ = -1;     // the one active cavity, once eligible
+    int persist_check();        // sets persist_slot_ or fails with the reason
     int scheme_ = 0;
     int tile_h_ = 16;        // tile height of the current tile list
     int pick_tile_height() const;

@@ -56,6 +56,26 @@ cudaError_t march_prepare(int precision);
 cudaError_t march_occupancy(int precision, int* blocks_per_sm);
 cudaError_t launch_march(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
                          CavityCtl* ctls, const int4* units, const int* nunits);
+
+// Run control of the persistent tile kernel (rtlbfs_persist.cu), zeroed
+// before each launch: the residual sums and arrivals of step k in slot
+// k % 3, the last step whose stop test is done, and the stall mark.
+struct PersistCtl {
+    int fin;
+    int stalled;
+    unsigned arrive[3];
+    int pad;
+    double acc[3][4];
+};
+// One cavity, one block per tile (ntiles of them, all resident: check
+// persist_occupancy), nsteps steps; tiles: that cavity's tile list; tstep:
+// ntiles ints zeroed before the launch.  withhold >= 0 (tests only): that
+// tile never reports its progress, so the waits of its neighbours run out.
+cudaError_t persist_prepare(int precision);
+cudaError_t persist_occupancy(int precision, int tile_h, int* blocks_per_sm);
+cudaError_t launch_persist(int precision, int tile_h, int ntiles, cudaStream_t s,
+                           const CavityDesc* desc, CavityCtl* ctl, const int4* tiles, int* tstep,
+                           PersistCtl* pc, int nsteps, int withhold);
 cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
                            const CavityCtl* ctls, int slot, const NuLines& ln, int which,
                            long long count, double scale, double* partial, int max_blocks,

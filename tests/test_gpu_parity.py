@@ -355,7 +355,7 @@ def test_autotune_keeps_the_state(orc):
     before = s.get_state()
     (_, _), steps = s.residual()
     kernel, rows, ms = s.autotune(16)
-    assert kernel in (0, 1) and ms > 0
+    assert kernel in (0, 1, 2) and ms > 0
     after = s.get_state()
     assert s.residual()[1] == steps
     for a, b in zip(before, after):
