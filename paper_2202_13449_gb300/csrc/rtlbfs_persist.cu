@@ -151,7 +151,7 @@ persist_kernel(const CavityDesc* __restrict__ dp, CavityCtl* __restrict__ ctl,
         const int rb = c0 ^ ((k - 1) & 1);  // buffer with the state after step k - 1
         tile_step<P, TX, TY, NT, 0, true>(sm, &sm.desc, i0, j0,
                                           static_cast<const Vec4<S>*>(dp->f[rb][0]),
-                                          static_cast<Vec4<S>*>(dp->f[rb ^ 1][0]));
+                                          static_cast<Vec4<S>*>(dp->f[rb ^ 1][0]), true);
         __syncthreads();
         if (tid == 0) {
             double a[4] = {0.0, 0.0, 0.0, 0.0};

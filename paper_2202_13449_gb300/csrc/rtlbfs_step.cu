@@ -51,18 +51,21 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     }
     chain_sync();
 
+    __syncthreads();  // the staged descriptor and lines
+
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tile = tiles[t];
         const int slot = tile.x, i0 = tile.y, j0 = tile.z;
-        if (t != (int)blockIdx.x) stage_tile(sm, &descs[slot], i0, j0);  // later tiles
-        __syncthreads();
-        const CavityDesc* dp = &sm.desc;
+        // the first tile uses what was staged; later tiles (batches) read
+        // their descriptor in place and load their lines beside the state
+        const bool first = t == (int)blockIdx.x;
+        const CavityDesc* dp = first ? &sm.desc : &descs[slot];
         CavityCtl* ctl = &ctls[slot];
         if (ctl->done) continue;  // uniform across the block
         const int cur = ctl->cur;
         tile_step<P, TX, TY, NT, SCHEME, false>(sm, dp, i0, j0,
                                                 static_cast<const Vec4<S>*>(dp->f[cur][0]),
-                                                static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]));
+                                                static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]), first);
         __syncthreads();
         if (tid == 0) {
             double a[4] = {0.0, 0.0, 0.0, 0.0};

@@ -231,23 +231,15 @@ __device__ __forceinline__ T ld_state(const T* p)
     }
 }
 
-// What a tile needs that no time step changes: a copy of its cavity's
-// descriptor (sm.desc) and the mesh lines of the tile and its halo.  Kernels
-// call it before they wait for the previous step, so these loads overlap
-// that step's tail instead of heading this step's chain of dependent loads;
-// a barrier must separate it from tile_step.
+// The mesh lines of a tile and its halo into shared memory.
 template <class P, int TX, int TY, int NT>
-__device__ __forceinline__ void stage_tile(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* gdp,
-                                           int i0, int j0)
+__device__ __forceinline__ void stage_lines(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* gdp,
+                                            int i0, int j0)
 {
     using Sm = TileSmem<P, TX, TY, NT>;
     using R = typename P::R;
     constexpr int BX = Sm::BX, BY = Sm::BY;
-    static_assert(sizeof(CavityDesc) % 8 == 0, "descriptor of 8-byte words");
     const int tid = threadIdx.x;
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(gdp);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sm.desc);
-    for (int k = tid; k < (int)(sizeof(CavityDesc) / 8); k += NT) dst[k] = src[k];
     const int nx = gdp->nx, ny = gdp->ny;
     const CellLine<R>* xc = static_cast<const CellLine<R>*>(gdp->xcell);
     const CellLine<R>* yc = static_cast<const CellLine<R>*>(gdp->ycell);
@@ -259,16 +251,34 @@ __device__ __forceinline__ void stage_tile(TileSmem<P, TX, TY, NT>& sm, const Ca
     for (int k = tid; k < TY + 1; k += NT) sm.yl[k] = yl[min(j0 + k, ny)];
 }
 
+// What a tile needs that no time step changes: a copy of its cavity's
+// descriptor (sm.desc) and the mesh lines of the tile and its halo.  Kernels
+// call it before they wait for the previous step, so these loads overlap
+// that step's tail instead of heading this step's chain of dependent loads;
+// a barrier must separate it from tile_step (called with lines_staged).
+template <class P, int TX, int TY, int NT>
+__device__ __forceinline__ void stage_tile(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* gdp,
+                                           int i0, int j0)
+{
+    static_assert(sizeof(CavityDesc) % 8 == 0, "descriptor of 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(gdp);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sm.desc);
+    for (int k = threadIdx.x; k < (int)(sizeof(CavityDesc) / 8); k += NT) dst[k] = src[k];
+    stage_lines(sm, gdp, i0, j0);
+}
+
 // One tile of one time step on cavity *dp, tile origin (i0, j0): phases 1-4
 // below read the state from fin and write the new state to fout; the
 // tile's four residual sums are left in FP64 in sm.red (a row per warp) for
-// the caller to add after a barrier.  The tile must have been staged
-// (stage_tile); dp may point at the staged copy.
+// the caller to add after a barrier.  lines_staged: stage_tile has put the
+// tile's mesh lines in shared memory (dp may then point at its copy of the
+// descriptor); otherwise phase 1 loads them beside the state.
 template <class P, int TX, int TY, int NT, int SCHEME, bool LDCG>
 __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* dp,
                                           int i0, int j0,
                                           const Vec4<typename P::S>* __restrict__ fin,
-                                          Vec4<typename P::S>* __restrict__ fout)
+                                          Vec4<typename P::S>* __restrict__ fout,
+                                          bool lines_staged)
 {
     using Sm = TileSmem<P, TX, TY, NT>;
     using S = typename P::S;
@@ -286,7 +296,8 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     // ghost resolution, no mirror rules, no wall faces (block-uniform).
     const bool interior = i0 >= 2 && j0 >= 2 && i0 + TX + 2 <= nx && j0 + TY + 2 <= ny;
 
-    // ---- 1. the haloed tile (its mesh lines are staged by stage_tile) ----
+    // ---- 1. mesh lines (unless staged) and the haloed tile -------------
+    if (!lines_staged) stage_lines(sm, dp, i0, j0);
     {
         constexpr int NB = BX * BY;
         constexpr int NR = (NB + NT - 1) / NT;
