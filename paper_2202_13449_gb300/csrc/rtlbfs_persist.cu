@@ -153,10 +153,9 @@ persist_kernel(const CavityDesc* __restrict__ dp, CavityCtl* __restrict__ ctl,
                                           static_cast<const Vec4<S>*>(dp->f[rb][0]),
                                           static_cast<Vec4<S>*>(dp->f[rb ^ 1][0]), true);
         __syncthreads();
+        double a[4];
+        if (tid < 32) tile_sums(sm, a);
         if (tid == 0) {
-            double a[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < NT / 32; ++w)
-                for (int q = 0; q < 4; ++q) a[q] += sm.red[w][q];
             double* acc = pc->acc[k % 3];
             for (int q = 0; q < 4; ++q) atomicAdd(&acc[q], a[q]);
             __threadfence();  // the tile's new state (all threads, before the barrier) and sums

@@ -67,10 +67,9 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
                                                 static_cast<const Vec4<S>*>(dp->f[cur][0]),
                                                 static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]), first);
         __syncthreads();
+        double a[4];
+        if (tid < 32) tile_sums(sm, a);
         if (tid == 0) {
-            double a[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int w = 0; w < NT / 32; ++w)
-                for (int q = 0; q < 4; ++q) a[q] += sm.red[w][q];
             for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
             __threadfence();
             const unsigned prev = atomicAdd(&ctl->arrive, 1u);

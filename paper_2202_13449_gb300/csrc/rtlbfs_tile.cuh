@@ -31,7 +31,7 @@ struct TileSmem {
     FaceLine<R> yl[TY + 1];
     CellLine<R> xc[BX];
     CellLine<R> yc[BY];
-    double red[NT / 32][4];
+    R red[NT / 32][4];  // per-warp residual partials (tile_sums adds them)
     CavityDesc desc;  // the tile's cavity, staged by stage_tile
     int last;
 };
@@ -267,10 +267,29 @@ __device__ __forceinline__ void stage_tile(TileSmem<P, TX, TY, NT>& sm, const Ca
     stage_lines(sm, gdp, i0, j0);
 }
 
+// The tile's four residual sums from the per-warp partials in sm.red:
+// warp 0 adds them in the arithmetic type (shuffles; on GB300 an FP64
+// instruction occupies the narrow FP64 pipe for 16 cycles, so a serial FP64
+// loop here lengthened every block's tail) and returns them in FP64, the
+// precision of the sums across tiles.  Call from all of warp 0, after the
+// barrier that follows tile_step.
+template <class P, int TX, int TY, int NT>
+__device__ __forceinline__ void tile_sums(const TileSmem<P, TX, TY, NT>& sm, double a[4])
+{
+    using R = typename P::R;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        R v = lane < NT / 32 ? sm.red[lane][q] : R(0);
+        v = warp_sum(v);
+        a[q] = (double)v;
+    }
+}
+
 // One tile of one time step on cavity *dp, tile origin (i0, j0): phases 1-4
 // below read the state from fin and write the new state to fout; the
-// tile's four residual sums are left in FP64 in sm.red (a row per warp) for
-// the caller to add after a barrier.  lines_staged: stage_tile has put the
+// tile's four residual sums are left in sm.red (a row per warp) for the
+// caller to add (tile_sums) after a barrier.  lines_staged: stage_tile has put the
 // tile's mesh lines in shared memory (dp may then point at its copy of the
 // descriptor); otherwise phase 1 loads them beside the state.
 template <class P, int TX, int TY, int NT, int SCHEME, bool LDCG>
@@ -462,10 +481,10 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     s2 = warp_sum(s2);
     s3 = warp_sum(s3);
     if ((tid & 31) == 0) {
-        sm.red[tid >> 5][0] = (double)s0;
-        sm.red[tid >> 5][1] = (double)s1;
-        sm.red[tid >> 5][2] = (double)s2;
-        sm.red[tid >> 5][3] = (double)s3;
+        sm.red[tid >> 5][0] = s0;
+        sm.red[tid >> 5][1] = s1;
+        sm.red[tid >> 5][2] = s2;
+        sm.red[tid >> 5][3] = s3;
     }
 }
 
