@@ -323,7 +323,7 @@ struct SmemC {
     CellGrad<R> g[GY][GX];      // coefficients, overwritten by the gradients
     R v[4][BY][BX];
     R dta[TY][TX];
-    double red[NT / 32][4];
+    R red[NT / 32][4];  // per-warp residual partials
 };
 
 template <class P, int TX, int TY>
@@ -541,16 +541,26 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
         s3 += __shfl_xor_sync(0xffffffffu, s3, o);
     }
     if ((tid & 31) == 0) {
-        sm.red[tid >> 5][0] = (double)s0;
-        sm.red[tid >> 5][1] = (double)s1;
-        sm.red[tid >> 5][2] = (double)s2;
-        sm.red[tid >> 5][3] = (double)s3;
+        sm.red[tid >> 5][0] = s0;
+        sm.red[tid >> 5][1] = s1;
+        sm.red[tid >> 5][2] = s2;
+        sm.red[tid >> 5][3] = s3;
     }
     __syncthreads();
+    // warp 0 adds the warp partials in the arithmetic type (a serial FP64
+    // loop would hold GB300's narrow FP64 pipe at the tail of every block);
+    // the tile sums go to the FP64 sums across tiles
+    double acc4[4];
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            R v = tid < NT / 32 ? sm.red[tid][q] : R(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc4[q] = (double)v;
+        }
+    }
     if (tid == 0) {
-        double acc4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int w = 0; w < NT / 32; ++w)
-            for (int q = 0; q < 4; ++q) acc4[q] += sm.red[w][q];
         for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], acc4[q]);
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->arrive, 1u);
