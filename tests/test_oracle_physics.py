@@ -12,8 +12,12 @@ that hold for the exact method regardless of how it is coded.
   exp(-2 nu k^2 t).
 * Energy: the Gaussian hill of Section 4.1 (Eqs. 66-68) against its closed
   form, second-order convergence of E_2 (Fig. 7's claim).
-* Steady cavity: energy balance Nu_hot = Nu_cold = Nu_1/2, and the physical
-  values of Table 1 at Ra = 1e3.
+* Nusselt normalisation: on the conduction state every Nusselt number is 1
+  on square cavities (uniform and tanh meshes, L, dT, chi away from 1), the
+  sign follows the heat flow, and a rectangle's wall numbers count the wall
+  length.
+* Steady cavity: energy balance Nu_hot = Nu_cold = Nu_1/2, wall number equal
+  to Eq. 69's Nu_a to the truncation error, Table 1 at Ra = 1e3 and 1e4.
 """
 import json
 import os
@@ -259,6 +263,61 @@ def test_gaussian_hill_second_order(orc):
     assert o1 > 1.8 and o2 > 1.8, (errs, o1, o2)
 
 
+# ---------------------------------------------------------------- Nusselt normalisation
+def _conduction_x(orc, xf, yf, T_h, T_c, chi):
+    """Ra -> 0 cavity: hot west wall T_h, cold east wall T_c, adiabatic south
+    and north, at rest with T linear in x (a discrete fixed point, pinned
+    above)."""
+    p = orc.Problem(xf=xf, yf=yf, nu=0.05, chi=chi, beta_g=0.0, T_ref=0.5 * (T_h + T_c),
+                    dT=abs(T_h - T_c), bc_T=(T_h, T_c, 0.0, 0.0))
+    return p, inputs.conduction_state(xf, yf, T_west=T_h, T_east=T_c)
+
+
+@pytest.mark.parametrize("phi", [0.0, 1.7])
+def test_conduction_nusselt_numbers_are_one(orc, phi):
+    """The Nusselt normalisation against the mathematics of pure conduction.
+    A square cavity of side L with the walls at T_h and T_c conducts the heat
+    flux chi (T_h - T_c) / L through every vertical line, so the heat through
+    a wall, per chi dT, is exactly 1; so is Eq. 69's Nu_a (u = 0, dT/dx =
+    -dT / L, integrated over L^2 and divided by chi dT L).  L = 37, dT = 2.5
+    and chi = 0.037 are all away from 1, and the tanh meshes (Eq. 74) give
+    unequal face areas, so a missing face-area weight, chi or dT fails."""
+    L, n = 37.0, 20
+    xf = orc.tanh_faces(n, L, phi)
+    yf = orc.tanh_faces(n + 6, L, phi)
+    p, st = _conduction_x(orc, xf, yf, 3.25, 0.75, 0.037)
+    for which in (orc.NU_W, orc.NU_E, orc.NU_HALF, orc.NU_A):
+        assert orc.nusselt(p, st, which) == pytest.approx(1.0, rel=1e-13), which
+    # no heat crosses the adiabatic walls
+    assert orc.nusselt(p, st, orc.NU_S) == 0.0 and orc.nusselt(p, st, orc.NU_N) == 0.0
+    # sign: the numbers are heat flow along +x; with the hot wall on the east
+    # the heat flows towards -x
+    p2, st2 = _conduction_x(orc, xf, yf, 0.75, 3.25, 0.037)
+    for which in (orc.NU_W, orc.NU_E, orc.NU_HALF, orc.NU_A):
+        assert orc.nusselt(p2, st2, which) == pytest.approx(-1.0, rel=1e-13), which
+
+
+def test_conduction_nusselt_of_a_rectangle_counts_the_wall_length(orc):
+    """On an Lx x Ly rectangle the conducted heat through a vertical wall is
+    chi dT Ly / Lx: the wall numbers are the whole wall's heat per chi dT
+    (Ly / Lx here), and Eq. 69 divided by Lx gives the same; heated from
+    below (Rayleigh-Benard walls, periodic in x) the bottom and top walls
+    carry chi dT Lx / Ly."""
+    xf = inputs.random_faces(14, 41, L=37.0)
+    yf = inputs.random_faces(9, 42, L=23.0)
+    p, st = _conduction_x(orc, xf, yf, 1.0, 0.0, 0.21)
+    for which in (orc.NU_W, orc.NU_E, orc.NU_HALF, orc.NU_A):
+        assert orc.nusselt(p, st, which) == pytest.approx(23.0 / 37.0, rel=1e-13), which
+    rb = orc.Problem(xf=xf, yf=yf, nu=0.05, chi=0.21, beta_g=0.0, T_ref=1.5, dT=2.0,
+                     bc_kind=(orc.PERIODIC, orc.PERIODIC, orc.DIRICHLET, orc.DIRICHLET),
+                     bc_T=(0.0, 0.0, 2.5, 0.5))
+    st_rb = inputs.rb_state(xf, yf, T_south=2.5, T_north=0.5, amp=0.0)
+    _, res, rc = orc.step(rb, st_rb, 3)  # the profile is a fixed point here too
+    assert rc == 0 and res[1] < 1e-14
+    for which in (orc.NU_S, orc.NU_N):
+        assert orc.nusselt(rb, st_rb, which) == pytest.approx(37.0 / 23.0, rel=1e-13), which
+
+
 # ---------------------------------------------------------------- steady cavity
 def test_steady_cavity_energy_balance(orc):
     p = orc.cavity_problem(24, 1e4, phi=1.0)
@@ -273,6 +332,14 @@ def test_steady_cavity_energy_balance(orc):
     np.testing.assert_allclose(cols, nw, rtol=1e-6)
     # no heat leaves through the adiabatic walls
     assert orc.nusselt(p, st, orc.NU_S) == 0.0 and orc.nusselt(p, st, orc.NU_N) == 0.0
+    # the wall number and Eq. 69's volume integral are two discretisations of
+    # the same steady heat transport: they agree to the mesh's truncation
+    # error, and both are within 1 % of Table 1's Nu_a at Ra = 1e4
+    gold = json.load(open(os.path.join(HERE, "golden", "table1_nu_a.json")))["Nu_a"]["1e4"]
+    na = orc.nusselt(p, st, orc.NU_A)
+    assert abs(nw - na) < 2e-3 * na, (nw, na)
+    assert nw == pytest.approx(gold, rel=0.01)
+    assert na == pytest.approx(gold, rel=0.01)
 
 
 @pytest.mark.slow

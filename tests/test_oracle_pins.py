@@ -370,3 +370,60 @@ def test_flux_is_second_order_close_to_distribution_form(orc, nd):
     d = np.array(d)
     orders = np.log2(d[:-1] / d[1:])
     assert np.all(orders > 1.8), (d, orders)
+
+
+# ---------------------------------------------------------------- R12 residual
+def _r12_from_states(st0, st1):
+    """The steady residual of reading R12 (the L2 analogue of Section 3.3's
+    Eq. 65), evaluated from its definition on two states: the cell speeds
+    |u| = sqrt(u^2 + v^2), a plain sum over cells, the new state's norm as
+    the denominator."""
+    m0 = np.hypot(st0[1], st0[2])
+    m1 = np.hypot(st1[1], st1[2])
+    ru = np.sqrt(np.sum((m1 - m0) ** 2)) / np.sqrt(np.sum(m1 ** 2))
+    rT = np.sqrt(np.sum((st1[3] - st0[3]) ** 2)) / np.sqrt(np.sum(st1[3] ** 2))
+    return float(ru), float(rT)
+
+
+@pytest.mark.parametrize("kinds", [(0, 0, 1, 1), (2, 2, 0, 1)])
+def test_residual_is_relative_l2_change_of_speed_and_temperature(orc, kinds):
+    """The residual a step returns equals R12 evaluated here from the state
+    before and after that step.  The alternative readings a slip would give
+    -- componentwise velocity differences, the old state's norm as the
+    denominator, no square root -- are checked to differ on the same states,
+    so the comparison can tell them apart."""
+    nx, ny = 13, 11
+    p = orc.Problem(xf=inputs.random_faces(nx, 21), yf=inputs.random_faces(ny, 22), nu=0.03,
+                    chi=0.04, beta_g=2e-4, dt=0.2, bc_kind=kinds)
+    st = inputs.perturbed_state(nx, ny, 23)
+    for _ in range(3):  # three consecutive steps, each checked
+        st1, res, rc = orc.step(p, st, 1)
+        assert rc == 0
+        ru, rT = _r12_from_states(st, st1)
+        assert res[0] == pytest.approx(ru, rel=1e-13, abs=0)
+        assert res[1] == pytest.approx(rT, rel=1e-13, abs=0)
+        # the readings a slip would produce are far from R12 on this state
+        comp = np.sqrt(np.sum((st1[1] - st[1]) ** 2 + (st1[2] - st[2]) ** 2)) / np.sqrt(
+            np.sum(np.hypot(st1[1], st1[2]) ** 2))
+        old_den = np.sqrt(np.sum((np.hypot(st1[1], st1[2]) - np.hypot(st[1], st[2])) ** 2)) / \
+            np.sqrt(np.sum(np.hypot(st[1], st[2]) ** 2))
+        for alt in (comp, old_den, ru ** 2):
+            assert abs(alt - ru) > 1e-3 * ru
+        st = st1
+    # after several steps the returned residual is the last step's
+    st3, res3, rc = orc.step(p, inputs.perturbed_state(nx, ny, 23), 3)
+    assert rc == 0
+    np.testing.assert_allclose(res3, res, rtol=1e-13, atol=0)
+
+
+def test_residual_of_a_resting_state_has_zero_denominator(orc):
+    """R12 with |u|^{n+1} = 0 everywhere: the velocity residual's denominator
+    is zero, which reads as infinity (no convergence is claimed for a fluid
+    at rest); the temperature of the Ra -> 0 conduction profile does not
+    change, so R_T is zero to round-off."""
+    p = orc.cavity_problem(12, 1e4, phi=1.5)
+    p.beta_g = 0.0
+    _, res, rc = orc.step(p, inputs.conduction_state(p.xf, p.yf), 1)
+    assert rc == 0
+    assert res[0] == np.inf
+    assert 0.0 <= res[1] < 1e-14
