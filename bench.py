@@ -101,6 +101,15 @@ WORKLOADS = {
              "log-uniform 64..1024, Ra log-uniform 1e3..1e8, Pr in {0.71, 7.0}, seed 42; "
              "continuous batching, FP32 bulk + FP64 reductions",
         count=10000, seed=42, rate=200.0, precision="fp32", kind="serve"),
+    "serve_steady": dict(
+        desc="time to steady state in the request loop: the requests of the 10,000-request "
+             "trace (seed 42, Poisson arrivals at 200/s, side log-uniform 64..1024, Ra "
+             "log-uniform 1e3..1e8, Pr in {0.71, 7.0}) with side <= 128 and Ra <= 1e5, at "
+             "their own arrival times (1,012 requests over 49 s), each run to max(R_u, R_T) "
+             "< 1e-7 or 1e6 steps; continuous batching, FP32 bulk + FP64 reductions; the "
+             "plain per-request FP64 form on converged requests for the comparison",
+        count=10000, seed=42, rate=200.0, n_max=128, ra_max=1e5, max_steps=1_000_000,
+        time_limit=300.0, precision="fp32", kind="serve"),
     "cavity512_accuracy": dict(
         desc="accuracy run of the 512x512 tanh cavity (Ra=1e8, Pr=0.71, Ma=0.1): the FP32 path "
              "(fixed-point state, FP64 reductions) against the FP64 path at step checkpoints "
@@ -211,6 +220,24 @@ def profile_traffic(workload: str, precision: str, kernel: str, sources=None):
     return None
 
 
+_ALU_PEAKS = {}
+
+
+def alu_peak(rs: int):
+    """(peak T op/s, source) of the plain FP32 (rs = 4) or FP64 (rs = 8)
+    arithmetic, measured on this device by the library's FMA-rate probe
+    (independent FMA chains on every SM, CUDA-event timed; one FMA is one
+    operation of the op count), best of three launches, cached per process."""
+    if rs not in _ALU_PEAKS:
+        from paper_2202_13449_gb300 import capi
+        kind, reps = (capi.RATE_FP32, 200000) if rs == 4 else (capi.RATE_FP64, 5000)
+        best = max(capi.fma_rate(kind, reps)[0] for _ in range(3))
+        name = "FFMA" if rs == 4 else "DFMA"
+        _ALU_PEAKS[rs] = (best / 1e12, f"measured: {name} rate of rtlbfs_fma_rate (best of 3, "
+                                       f"{reps} x 8 chains per thread, every SM)")
+    return _ALU_PEAKS[rs]
+
+
 def rooflines(kernel: str, cells: int, per_launch_s: float, rs: int, traffic, clocks,
               scheme: int = 0):
     """(ALU roofline, HBM roofline) of the step kernel for launches of
@@ -220,21 +247,21 @@ def rooflines(kernel: str, cells: int, per_launch_s: float, rs: int, traffic, cl
     _, ops_cell, sfu_cell = capi.op_counts(scheme)
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    if rs == 4:
-        alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        unit, src = "T FP32 op/s", f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz max SM clock"
-    else:  # the FP64 path runs on GB300's narrow FP64 units
-        alu_peak = 1.25 / 2
-        unit, src = "T FP64 op/s", "nominal FP64 1.25 TFLOP/s = 0.625 T fused multiply-adds/s"
+    peak_alu, src = alu_peak(rs)
+    unit = "T FP32 op/s" if rs == 4 else "T FP64 op/s"
+    derived = sms * 128 * mhz * 1e6 / 1e12 if rs == 4 else None
     alu = ops_cell * cells / per_launch_s / 1e12
     alg_bytes = 8 * rs * cells  # read 4 fields + write 4 fields per cell
     hbm = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    alu_line = {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
-                "unit": unit, "frac": round(alu / alu_peak, 4), "traffic": traffic,
+    alu_line = {"bound": "alu", "achieved": round(alu, 3), "peak": round(peak_alu, 3),
+                "unit": unit, "frac": round(alu / peak_alu, 4), "traffic": traffic,
                 "kernel": kernel, "ops_per_cell_update": ops_cell,
                 "sfu_ops_per_cell_update": sfu_cell, "peak_source": src,
                 "alg_ops_per_launch": ops_cell * cells}
+    if derived:
+        alu_line["peak_derived"] = {"value": round(derived, 3), "frac": round(alu / derived, 4),
+                                    "source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     hbm_line = {"bound": "hbm", "achieved": round(hbm, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(hbm / peak, 4), "traffic": traffic, "kernel": kernel,
                 "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes}
@@ -497,31 +524,43 @@ def run_serve(args, w):
     from paper_2202_13449_gb300 import capi, inputs
     capi.lib()
     trace = inputs.serving_trace(w["count"], w["seed"], w["rate"])
+    # a documented sub-trace keeps the requests' own arrival times
+    trace = [r for r in trace if r.n <= w.get("n_max", r.n) and r.Ra <= w.get("ra_max", r.Ra)]
     reqs = shard([(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace], rank, ws)
-    cap, tol = args.max_steps, args.tol
+    cap = w.get("max_steps", 2000) if args.max_steps is None else args.max_steps
+    tol = args.tol
+    time_limit = w.get("time_limit", 60.0) if args.time_limit is None else args.time_limit
     clk = ClockSampler(local)
     clk.start()
     l0 = capi.launch_count()
     res, el = capi.serve(reqs, max_slots=args.slots, tol=tol, max_steps=cap, chunk_steps=128,
-                         precision=capi.FP32, time_limit_s=args.time_limit, mem_fraction=0.5)
+                         precision=capi.FP32, time_limit_s=time_limit, mem_fraction=0.5)
     launches = capi.launch_count() - l0
     clocks = clk.stop()
     done = [(q, r) for q, r in zip(reqs, res) if r["status"] >= 0]
     finished_job = int(job_sum(len(done)))
     el_job = job_max(el)
     diverged = sum(1 for _, r in done if r["status"] == capi.SLOT_DIVERGED)
-    lat = np.array([r["t_finish"] - q[0] for q, r in done]) if done else np.array([np.nan])
-    conv = sum(1 for _, r in done if r["status"] == capi.SLOT_CONVERGED)
+    retire = np.array([r["t_finish"] - q[0] for q, r in done]) if done else np.array([np.nan])
+    converged = [(q, r) for q, r in done if r["status"] == capi.SLOT_CONVERGED]
+    conv = len(converged)
+    steady = (np.array([r["t_finish"] - q[0] for q, r in converged]) if converged
+              else np.array([np.nan]))
     capped = sum(1 for _, r in done if r["status"] == capi.SLOT_MAX_STEPS)
-    # plain per-request FP64 on the first finished requests, alone, one at a time
-    sample = done[:args.fp64_sample] if rank == 0 else []
+    # plain per-request FP64 on a sample of the requests (converged ones when
+    # there are any), each alone, one at a time, to the same tolerance and cap
+    pool = converged if converged else done
+    sample = pool[:args.fp64_sample] if rank == 0 else []
     t0 = time.perf_counter()
-    errs = []
+    errs, conv64, steps32, steps64 = [], 0, 0, 0
     for q, r in sample:
         xf = inputs.uniform_faces(q[1])
         s = capi.Solver(xf, xf, capi.FP64)
         s.set_params(q[2], q[3], 0.1, 0.0)
-        s.run_to_steady(tol, cap)
+        rc64, n64, _ = s.run_to_steady(tol, cap)
+        conv64 += rc64 == capi.OK
+        steps32 += r["steps"]
+        steps64 += n64
         nu64 = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
         nu32 = 0.5 * (r["nu_hot"] + r["nu_cold"])
         errs.append(abs(nu32 - nu64) / abs(nu64))
@@ -537,18 +576,25 @@ def run_serve(args, w):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; no dataset)",
         "config": {"workload": args.workload, "description": w["desc"],
-                   "requests": w["count"], "requests_this_rank": len(reqs),
-                   "max_steps_cap": cap, "tol": tol, "time_limit_s": args.time_limit,
+                   "requests": len(trace), "requests_this_rank": len(reqs),
+                   "max_steps_cap": cap, "tol": tol, "time_limit_s": time_limit,
                    "slots": args.slots, "parallelism": f"trace sharded over {ws} GPU(s)"},
         "finished": finished_job, "converged": conv, "hit_step_cap": capped, "diverged": diverged,
         "unfinished": len(reqs) - len(done),
         "counts_scope": "finished: the whole job; converged/capped/diverged/unfinished and the "
                         "latency percentiles: rank 0's share of the trace",
-        "time_to_steady_s": {"p50": float(np.nanpercentile(lat, 50)),
-                             "p99": float(np.nanpercentile(lat, 99)),
-                             "note": "arrival to retirement; queue-dominated at this load"},
-        "fp64_per_request": {"requests": len(sample), "solves_per_s": round(len(sample) / t64, 3)
-                             if t64 > 0 else None,
+        "arrival_to_retirement_s": {"p50": float(np.nanpercentile(retire, 50)),
+                                    "p99": float(np.nanpercentile(retire, 99)),
+                                    "note": "every finished request (converged, capped or "
+                                            "diverged)"},
+        "time_to_steady_s": ({"p50": float(np.nanpercentile(steady, 50)),
+                              "p99": float(np.nanpercentile(steady, 99)),
+                              "requests": conv,
+                              "note": "arrival to retirement of the converged requests"}
+                             if conv else None),
+        "fp64_per_request": {"requests": len(sample), "of": "converged" if converged else "finished",
+                             "solves_per_s": round(len(sample) / t64, 3) if t64 > 0 else None,
+                             "converged": conv64, "steps_fp32": steps32, "steps_fp64": steps64,
                              "max_rel_err_mean_wall_nu_fp32_vs_fp64": max(errs) if errs else None},
         "e2e": {"value": round(finished_job / el_job, 3) if el_job > 0 else None,
                 "unit": "solves/s",
@@ -889,14 +935,8 @@ def run_cubic(args, w):
     per_launch_s = ms_max * 1e-3 / (inner * args.steps)
     rs = 4 if w["precision"] == "fp32" else 8
     _, ops_cell, sfu_cell = capi.op_counts3()
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    if rs == 4:
-        alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        unit, src = "T FP32 op/s", f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz max SM clock"
-    else:
-        alu_peak = 1.25 / 2
-        unit, src = "T FP64 op/s", "nominal FP64 1.25 TFLOP/s = 0.625 T fused multiply-adds/s"
+    peak_alu, src = alu_peak(rs)
+    unit = "T FP32 op/s" if rs == 4 else "T FP64 op/s"
     traffic = profile_traffic(args.workload, w["precision"], "step3", STEP3_SOURCES)
     alu = ops_cell * cells / per_launch_s / 1e12
     alg_bytes = 10 * rs * cells  # read 5 fields + write 5 fields per cell
@@ -928,8 +968,8 @@ def run_cubic(args, w):
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
-                     "unit": unit, "frac": round(alu / alu_peak, 4), "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(peak_alu, 3),
+                     "unit": unit, "frac": round(alu / peak_alu, 4), "traffic": traffic,
                      "kernel": "rtlbfs3::step3_kernel", "ops_per_cell_update": ops_cell,
                      "sfu_ops_per_cell_update": sfu_cell, "peak_source": src,
                      "alg_ops_per_launch": ops_cell * cells},
@@ -1218,9 +1258,7 @@ def run_curv(args, w):
     per_launch = ms * 1e-3 / (inner * args.steps)
     rs = 4 if w["precision"] == "fp32" else 8
     _, ops_cell, sfu_cell = capi.op_counts_curv()
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    peak_alu, src = alu_peak(rs)
     alu = ops_cell * cells / per_launch / 1e12
     alg_bytes = 8 * rs * cells
     peak, peak_kind = peaks()
@@ -1238,11 +1276,11 @@ def run_curv(args, w):
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": 4 * cells * 8, "d2h_bytes_per_step": 4 * cells * 8},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(alu_peak, 3),
-                     "unit": "T FP32 op/s", "frac": round(alu / alu_peak, 4), "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": round(alu, 3), "peak": round(peak_alu, 3),
+                     "unit": "T FP32 op/s" if rs == 4 else "T FP64 op/s",
+                     "frac": round(alu / peak_alu, 4), "traffic": traffic,
                      "kernel": "rtlbfsc::curv_step_kernel", "ops_per_cell_update": ops_cell,
-                     "sfu_ops_per_cell_update": sfu_cell,
-                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
+                     "sfu_ops_per_cell_update": sfu_cell, "peak_source": src},
         "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / per_launch / 1e9, 1),
                          "peak": peak, "unit": "GB/s",
                          "frac": round(alg_bytes / per_launch / 1e9 / peak, 4), "traffic": traffic,
@@ -1537,14 +1575,28 @@ def run_reference(args, w):
     kind = w.get("kind")
     if kind == "serve":
         # each bench step: the next request of the trace, probed for 2 steps
-        # and scaled to the step cap (most requests of this trace hit it)
+        # and scaled to the steps it needs: the step cap, or for a sub-trace
+        # whose requests converge, the estimate of the thermal diffusion time
+        # 10 N sqrt(Ra Pr) / Delta t (Delta t = 0.5 on these unit-cell meshes)
+        # when that is below the cap
         trace = inputs.serving_trace(w["count"], w["seed"], w["rate"])
+        trace = [r for r in trace
+                 if r.n <= w.get("n_max", r.n) and r.Ra <= w.get("ra_max", r.Ra)]
         reqs = [(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace]
+        cap = w.get("max_steps", 2000) if args.max_steps is None else args.max_steps
+
+        def need(q):
+            if "n_max" not in w:
+                return cap
+            return int(min(cap, 10 * q[1] * (q[2] * q[3]) ** 0.5 / 0.5))
+
         for k in range(args.warmup):
-            oracle_solve_estimate(oracle, inputs, *reqs[k % len(reqs)][1:], args.max_steps)
+            q = reqs[k % len(reqs)]
+            oracle_solve_estimate(oracle, inputs, *q[1:], need(q))
         est = 0.0
         for k in range(args.steps):
-            est += oracle_solve_estimate(oracle, inputs, *reqs[k % len(reqs)][1:], args.max_steps)
+            q = reqs[k % len(reqs)]
+            est += oracle_solve_estimate(oracle, inputs, *q[1:], need(q))
         value = args.steps / est
         line = {
             "impl": "reference",
@@ -1554,7 +1606,7 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
             "config": {"workload": args.workload, "description": w["desc"],
-                       "max_steps_cap": args.max_steps,
+                       "max_steps_cap": cap,
                        "note": "reference arm = the FP64 CPU oracle (the paper ships no code); "
                                "one request per bench step, extrapolated from 2 timed steps"},
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -1562,7 +1614,9 @@ def run_reference(args, w):
             "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": used,
                              "kind": "oracle",
                              "sample": f"the first {args.steps} requests of the trace, 2 timed "
-                                       f"FP64 steps each, scaled to {args.max_steps} steps"},
+                                       f"FP64 steps each, scaled to "
+                                       + ("10 N sqrt(Ra Pr) / 0.5 steps (at most the cap)"
+                                          if "n_max" in w else f"{cap} steps")},
         }
         print(json.dumps(line), flush=True)
         return
@@ -1651,10 +1705,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
-    ap.add_argument("--max-steps", type=int, default=2000, help="serve: step cap per request")
+    ap.add_argument("--max-steps", type=int, default=None,
+                    help="serve: step cap per request (default: the workload's, else 2000)")
     ap.add_argument("--tol", type=float, default=1e-7,
                     help="serve: steady tolerance (above the FP32 residual floor ~1.4e-8)")
-    ap.add_argument("--time-limit", type=float, default=60.0, help="serve: wall-clock cap (s)")
+    ap.add_argument("--time-limit", type=float, default=None,
+                    help="serve: wall-clock cap in s (default: the workload's, else 60)")
     ap.add_argument("--slots", type=int, default=256, help="serve: concurrent cavities")
     ap.add_argument("--fp64-sample", type=int, default=20, help="serve: FP64 comparator sample")
     ap.add_argument("--schedule", default="auto",

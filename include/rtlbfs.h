@@ -46,7 +46,28 @@ extern "C" {
 
 /* arithmetic of the bulk step */
 #define RTLBFS_FP64 0 /* every stage in FP64 */
-#define RTLBFS_FP32 1 /* FP32 bulk storing rho - 1, FP64 residual/Nusselt sums */
+#define RTLBFS_FP32 1 /* FP32 bulk on a 32-bit fixed-point state, FP64 residual/Nusselt sums */
+
+/*
+ * The FP32 mode's state.  Each cell is stored as four 32-bit fixed-point
+ * numbers: rho - 1 in units of 2^-32, u and v in units of 2^-31, and
+ * T / T_unit in units of 2^-30.  The step's arithmetic is FP32.  Its
+ * increments are added to the stored integers exactly, and gradients use
+ * exact integer differences.  Representable ranges:
+ *     |rho - 1| < 0.49,  |u|, |v| < 0.99,  |T| < 1.98 T_unit.
+ * T_unit is a power of two, at least 1, chosen per handle so that the
+ * Dirichlet wall temperatures and T_ref +- dT/2 (rtlbfs_set_params_ref) lie
+ * within +-1.5 T_unit, and the state last given to rtlbfs_set_state within
+ * +-1.9 T_unit.  With the defaults (walls at 1 and 0) T_unit = 1.  The
+ * temperature resolution is 2^-30 T_unit.  A configuration change that
+ * needs a larger unit rounds the stored temperatures to it; the unit never
+ * shrinks under a running state (rtlbfs_set_state picks it afresh).  The
+ * arithmetic stays FP32 on absolute temperatures, so temperatures far from
+ * zero compared with dT lose FP32 precision in the face sums.
+ * A step whose new values leave a range reports RTLBFS_ERR_DIVERGED, in the
+ * same way as a non-finite FP64 residual.  A state outside the ranges is
+ * rejected by rtlbfs_set_state with RTLBFS_ERR_ARG.
+ */
 
 /* sides and boundary kinds */
 #define RTLBFS_WEST 0
@@ -140,7 +161,9 @@ int rtlbfs_set_physics(rtlbfs_t h, double nu, double chi, double beta_g);
 /*
  * Copy a host state in (rho, u, v, T: ny*nx doubles each, caller-owned)
  * and reset the step counter and residual.  In FP32 mode the fields are
- * rounded to float, rho stored as rho - 1.
+ * rounded to the fixed-point storage described at RTLBFS_FP32, after the
+ * temperature unit has been picked for this state; ERR_ARG if a value is
+ * NaN or outside the representable ranges.
  */
 int rtlbfs_set_state(rtlbfs_t h, const double* rho, const double* u, const double* v,
                      const double* T);
@@ -266,12 +289,14 @@ void rtlbfs_destroy(rtlbfs_t h);
 /*
  * Allocation-free Nusselt number of a caller-owned FP64 state.  The paper
  * has no counterpart: this entry point exists for callers that cannot
- * allocate device memory when they call in -- real-time or graph-built
- * pipelines where a cudaMalloc could block or fail, hosts that hand the
- * library only memory they own -- and for fields that live in the caller's
- * buffers rather than in a handle.  It computes what rtlbfs_nusselt computes
- * (same selectors `which`, same FP64 arithmetic) and allocates nothing: no
- * cudaMalloc, cudaFree or allocating library call.
+ * allocate device memory when they call in -- a real-time loop, where a
+ * cudaMalloc may block on the device or fail at an unpredictable moment,
+ * and hosts that hand the library only memory they own -- and for fields
+ * that live in the caller's buffers rather than in a handle.  It computes
+ * what rtlbfs_nusselt computes (same selectors `which`, same FP64
+ * arithmetic) and allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library call.  Host arrays (xf, yf, bc_*) are read before the call
+ * returns; the work is queued on `stream`.
  *
  *   nx, ny         cells, each at most 8192 (larger: RTLBFS_ERR_ARG)
  *   xf, yf         host face coordinates (nx+1, ny+1), strictly ascending

@@ -27,7 +27,9 @@ NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
 HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
 HEADERS = [HEADER, os.path.join(_build.ROOT, "include", "rtlbfs_batch.h"),
            os.path.join(_build.ROOT, "include", "rtlbfs3d.h"),
-           os.path.join(_build.ROOT, "include", "rtlbfs_curv.h")]
+           os.path.join(_build.ROOT, "include", "rtlbfs_curv.h"),
+           os.path.join(_build.ROOT, "include", "rtlbfs_measure.h")]
+RATE_FP32, RATE_FP32X2, RATE_FP64 = 0, 1, 2  # kinds of fma_rate
 SLOT_EMPTY, SLOT_RUNNING, SLOT_CONVERGED, SLOT_MAX_STEPS, SLOT_DIVERGED = -1, 0, 1, 2, 3
 
 
@@ -76,6 +78,7 @@ _SIGS = {
     "rtlbfs_last_error": (C.c_char_p, [_vp]),
     "rtlbfs_destroy": (None, [_vp]),
     "rtlbfs_launch_count": (C.c_longlong, []),
+    "rtlbfs_fma_rate": (C.c_int, [C.c_int, C.c_int, _dp, _dp]),
     "rtlbfs_op_counts": (C.c_int, [_dp, _dp, _dp]),
     "rtlbfs_op_counts_scheme": (C.c_int, [C.c_int, _dp, _dp, _dp]),
     "rtlbfs_set_scheme": (C.c_int, [_vp, C.c_int]),
@@ -232,6 +235,17 @@ def nusselt_noalloc(xf, yf, rho_ptr, u_ptr, v_ptr, T_ptr, nu, chi, kappa, dT, bc
 
 def launch_count() -> int:
     return int(lib().rtlbfs_launch_count())
+
+
+def fma_rate(kind: int, reps: int):
+    """(FMAs per second, ms) of the current device for RATE_FP32 (FFMA),
+    RATE_FP32X2 (FFMA2, two FMAs each) or RATE_FP64, from one timed launch
+    of independent FMA chains on every SM (include/rtlbfs_measure.h)."""
+    r, ms = C.c_double(), C.c_double()
+    rc = lib().rtlbfs_fma_rate(int(kind), int(reps), C.byref(r), C.byref(ms))
+    if rc:
+        raise RTLBFSError(rc, "rtlbfs_fma_rate")
+    return r.value, ms.value
 
 
 def op_counts(scheme: int = 0):

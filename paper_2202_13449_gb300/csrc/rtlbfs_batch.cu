@@ -304,8 +304,8 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
             r.status = slot_status(ctl[s]);
             double nh = NAN, nc = NAN;
             if (r.status != RTLBFS_SLOT_DIVERGED) {
-                eng.nusselt(s, rtlbfs::kNuWest, &nh);
-                eng.nusselt(s, rtlbfs::kNuEast, &nc);
+                if ((rc = eng.nusselt(s, rtlbfs::kNuWest, &nh))) return rc;
+                if ((rc = eng.nusselt(s, rtlbfs::kNuEast, &nc))) return rc;
             }
             r.nu_hot = nh;
             r.nu_cold = nc;

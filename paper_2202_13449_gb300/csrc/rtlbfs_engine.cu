@@ -316,11 +316,34 @@ int Engine::resolve_params(Cavity& c)
     return RTLBFS_OK;
 }
 
+double Engine::temp_unit(const Cavity& c) const
+{
+    if (precision_ != RTLBFS_FP32) return 1.0;
+    double m = std::max(std::fabs(c.T_ref - 0.5 * c.dT), std::fabs(c.T_ref + 0.5 * c.dT));
+    for (int s = 0; s < 4; ++s)
+        if (c.kind[s] == kDirichlet) m = std::max(m, std::fabs(c.bcT[s]));
+    double u = 1.0;
+    while ((m > 1.5 * u || c.state_Tmax > 1.9 * u) && u < 1e300) u *= 2.0;
+    return u;
+}
+
 int Engine::upload_lines(int slot)
 {
     Cavity& c = slots_[slot];
     int rc = resolve_params(c);
     if (rc) return rc;
+    // a configuration that needs a larger temperature unit: the stored
+    // temperatures of both buffers follow it (rounded to the new unit); the
+    // unit never shrinks under a live state
+    const double unit = temp_unit(c);
+    if (unit > c.T_unit) {
+        const int shift = (int)std::lround(std::log2(unit / c.T_unit));
+        if (shift > 30) return fail(RTLBFS_ERR_ARG, "temperatures too large for the FP32 state");
+        CK(launch_rescale_T(stream_, c.d_fields, 2LL * c.pitch * c.ny, shift));
+        g_launches++;
+        c.T_unit = unit;
+    }
+    const double Tu = c.T_unit;
     const bool xp = c.kind[kSideW] == kPeriodic, yp = c.kind[kSideS] == kPeriodic;
     std::vector<unsigned char> buf(c.lines_bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) { std::memcpy(buf.data() + off, src, n); };
@@ -359,9 +382,10 @@ int Engine::upload_lines(int slot)
     d.nx = c.nx;
     d.ny = c.ny;
     d.pitch = c.pitch;
+    // every temperature in the state's unit T_unit (buoyancy per unit of it)
     for (int s = 0; s < 4; ++s) {
         d.kind[s] = c.kind[s];
-        d.bcT[s] = c.bcT[s];
+        d.bcT[s] = c.bcT[s] / Tu;
         d.bcU[s] = c.bcU[s];
     }
     d.tiles_x = (c.nx + kTileX - 1) / kTileX;
@@ -369,22 +393,22 @@ int Engine::upload_lines(int slot)
     d.scheme = scheme_;
     d.ntiles = c.ntiles;  // work units of this cavity in the current list
     d.tile_begin = c.first_tile;
-    d.beta_g = c.beta_g;
-    d.T_ref = c.T_ref;
+    d.beta_g = c.beta_g * Tu;
+    d.T_ref = c.T_ref / Tu;
     d.fx = c.fx;
     d.fy = c.fy;
     d.dt = c.dt;
-    d.dT = c.dT;
+    d.dT = c.dT / Tu;
     d.nu = c.nu;
     d.chi = c.chi;
-    d.f_beta_g = (float)c.beta_g;
-    d.f_T_ref = (float)c.T_ref;
+    d.f_beta_g = (float)d.beta_g;
+    d.f_T_ref = (float)d.T_ref;
     d.f_fx = (float)c.fx;
     d.f_fy = (float)c.fy;
     d.f_dt = (float)c.dt;
     for (int s2 = 0; s2 < 4; ++s2) {
         d.f_bcU[s2] = (float)c.bcU[s2];
-        d.f_bcT[s2] = (float)c.bcT[s2];
+        d.f_bcT[s2] = (float)d.bcT[s2];
     }
     const size_t rec = 4 * rsize_ * (size_t)c.pitch * c.ny;  // cell records of one buffer
     for (int b = 0; b < 2; ++b) {
@@ -620,11 +644,19 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (!rho || !u || !v || !T) return fail(RTLBFS_ERR_ARG, "null state array");
+    const size_t n = (size_t)c->nx * c->ny;
+    if (precision_ == RTLBFS_FP32) {
+        // the new state replaces the old one: pick its temperature unit afresh
+        double m = 0.0;
+        for (size_t k = 0; k < n; ++k) m = std::max(m, std::fabs(T[k]));  // NaN: caught below
+        c->state_Tmax = std::isfinite(m) ? m : 0.0;
+        c->T_unit = temp_unit(*c);
+        c->dirty = true;
+    }
     if (c->dirty) {
         int rc = upload_lines(slot);
         if (rc) return rc;
     }
-    const size_t n = (size_t)c->nx * c->ny;
     if (stage_cap_ < 4 * n) {
         CK(cudaStreamSynchronize(stream_));
         cudaFree(d_stage_);
@@ -639,7 +671,8 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     const CavityDesc& d = h_desc_[slot];
     int* d_bad = reinterpret_cast<int*>(d_scalar_ + 7);
     CK(cudaMemsetAsync(d_bad, 0, sizeof(int), stream_));
-    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, d.f[0][0], d_bad));
+    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, c->T_unit,
+                       d.f[0][0], d_bad));
     g_launches++;
     int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
@@ -655,7 +688,7 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     if (h_bad)
         return fail(RTLBFS_ERR_ARG, "state not representable in the FP32 mode's fixed-point "
                                     "storage: NaN, |rho-1| >= 0.49, |u|,|v| >= 0.99 or "
-                                    "|T| >= 1.98");
+                                    "|T| >= 1.98 T_unit");
     return RTLBFS_OK;
 }
 
@@ -679,7 +712,7 @@ int Engine::get_state(int slot, double* rho, double* u, double* v, double* T)
         stage_cap_ = 4 * n;
     }
     const CavityDesc& d = h_desc_[slot];
-    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch,
+    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, c->ny, c->pitch, c->T_unit,
                         d.f[ctl.cur & 1][0]));
     g_launches++;
     double* dst[4] = {rho, u, v, T};
@@ -694,6 +727,10 @@ int Engine::set_conduction_state(int slot)
 {
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    // a new state from the configuration: its temperature unit afresh
+    c->state_Tmax = 0.0;
+    c->T_unit = temp_unit(*c);
+    c->dirty = true;
     if (c->dirty) {
         int rc = upload_lines(slot);
         if (rc) return rc;
@@ -708,6 +745,7 @@ int Engine::set_conduction_state(int slot)
             Tcol[i] = c->bcT[kSideW] + (c->bcT[kSideE] - c->bcT[kSideW]) * s;
         }
     }
+    for (double& t : Tcol) t /= c->T_unit;  // exact: a power of two
     if (stage_cap_ < (size_t)c->nx) {
         CK(cudaStreamSynchronize(stream_));
         cudaFree(d_stage_);
@@ -965,14 +1003,13 @@ int Engine::nusselt(int slot, int which, double* out)
     ln.xc = reinterpret_cast<const CellLine<double>*>(L + c->off_xcd);
     ln.yc = reinterpret_cast<const CellLine<double>*>(L + c->off_ycd);
     long long count;
-    double scale = 1.0 / (c->chi * c->dT);
+    double scale = 1.0 / (c->chi * d.dT);  // dT in the state's temperature unit
     if (which == kNuWest || which == kNuEast || which == kNuHalf) count = c->ny;
     else if (which == kNuSouth || which == kNuNorth) count = c->nx;
     else {
         count = (long long)c->nx * c->ny;
         scale /= (c->xf.back() - c->xf.front());
     }
-    (void)d;
     CK(launch_nusselt(precision_, stream_, d_desc_, d_ctl_, slot, ln, which, count, scale,
                       d_partial_, partial_cap_, d_scalar_));
     g_launches += 2;

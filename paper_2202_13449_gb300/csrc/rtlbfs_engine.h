@@ -29,6 +29,11 @@ struct Cavity {
     int kind[4] = {kDirichlet, kDirichlet, kAdiabatic, kAdiabatic};
     double bcT[4] = {1.0, 0.0, 0.0, 0.0};
     double bcU[4] = {0.0, 0.0, 0.0, 0.0};
+    // FP32: the device state stores T / T_unit in fixed point; T_unit is a
+    // power of two >= 1, chosen so the configured temperatures lie within
+    // +-1.5 T_unit and the last uploaded state within +-1.9 T_unit (always 1
+    // in FP64).  State_Tmax: max |T| of the last state set_state uploaded.
+    double T_unit = 1.0, state_Tmax = 0.0;
     // device memory
     void* d_fields = nullptr;  // 2 buffers x 4 fields x ny x pitch
     void* d_lines = nullptr;   // R lines then FP64 lines
@@ -105,6 +110,7 @@ public:
 
 private:
     int upload_lines(int slot);
+    double temp_unit(const Cavity& c) const;  // the T_unit the configuration asks for
     int rebuild_tiles();
     int prepare_launch();
 

@@ -80,10 +80,13 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
                            const CavityCtl* ctls, int slot, const NuLines& ln, int which,
                            long long count, double scale, double* partial, int max_blocks,
                            double* out);
+// T_unit: temperature unit of the stored state (stored T = T / T_unit)
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* cells, int* bad);
+                            int pitch, double T_unit, void* cells, int* bad);
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny,
-                             int pitch, const void* cells);
+                             int pitch, double T_unit, const void* cells);
+// FP32 records: stored temperatures divided by 2^shift (1 <= shift <= 30)
+cudaError_t launch_rescale_T(cudaStream_t s, void* cells, long long count, int shift);
 // rho = 1, u = v = 0, T = Tcol[i] in every row (one buffer of cell records)
 cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol, int nx, int ny,
                               int pitch, void* cells);

@@ -226,16 +226,20 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 
 // State conversion: FP64 host-layout staging (rho, u, v, T planes of n
 // cells, row-major nx) <-> device storage (rho - 1, u, v, T with row pitch).
+// T_unit: the temperature unit of the stored state (a power of two; 1 in
+// FP64): the stored temperature is T / T_unit.
 template <class P>
 __global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, int pitch,
-                                Vec4<typename P::S>* __restrict__ cells, int* __restrict__ bad)
+                                double T_unit, Vec4<typename P::S>* __restrict__ cells,
+                                int* __restrict__ bad)
 {
     const long long n = (long long)nx * ny;
+    const double Tinv = 1.0 / T_unit;  // exact: a power of two
     bool b = false;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = k % nx, j = k / nx;
-        const double x[4] = {st[k] - 1.0, st[n + k], st[2 * n + k], st[3 * n + k]};
+        const double x[4] = {st[k] - 1.0, st[n + k], st[2 * n + k], st[3 * n + k] * Tinv};
         for (int q = 0; q < 4; ++q) b = b || !P::representable(x[q], q);
         cells[(size_t)j * pitch + i] = {P::from_double(x[0], 0), P::from_double(x[1], 1),
                                         P::from_double(x[2], 2), P::from_double(x[3], 3)};
@@ -245,7 +249,7 @@ __global__ void state_in_kernel(const double* __restrict__ st, int nx, int ny, i
 
 template <class P>
 __global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pitch,
-                                 const Vec4<typename P::S>* __restrict__ cells)
+                                 double T_unit, const Vec4<typename P::S>* __restrict__ cells)
 {
     const long long n = (long long)nx * ny;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -255,8 +259,18 @@ __global__ void state_out_kernel(double* __restrict__ st, int nx, int ny, int pi
         st[k] = 1.0 + P::to_double(c.x, 0);
         st[n + k] = P::to_double(c.y, 1);
         st[2 * n + k] = P::to_double(c.z, 2);
-        st[3 * n + k] = P::to_double(c.w, 3);
+        st[3 * n + k] = P::to_double(c.w, 3) * T_unit;
     }
+}
+
+// Stored temperatures of `count` cell records divided by 2^shift (rounded
+// to nearest): the state follows a temperature unit that grew by 2^shift.
+__global__ void rescale_T_kernel(Vec4<int>* __restrict__ cells, long long count, int shift)
+{
+    const int half = 1 << (shift - 1);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x)
+        cells[k].w = (int)(((long long)cells[k].w + half) >> shift);
 }
 
 template <class P>
@@ -392,32 +406,42 @@ cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* desc
 }
 
 cudaError_t launch_state_in(int precision, cudaStream_t s, const double* st, int nx, int ny,
-                            int pitch, void* cells, int* bad)
+                            int pitch, double T_unit, void* cells, int* bad)
 {
     const long long n = (long long)nx * ny;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+        state_in_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, T_unit,
                                                        static_cast<Vec4<double>*>(cells), bad);
     else
-        state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+        state_in_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, T_unit,
                                                        static_cast<Vec4<int>*>(cells), bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_state_out(int precision, cudaStream_t s, double* st, int nx, int ny, int pitch,
-                             const void* cells)
+                             double T_unit, const void* cells)
 {
     const long long n = (long long)nx * ny;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (precision == 0)
-        state_out_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+        state_out_kernel<StoreD><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, T_unit,
                                                         static_cast<const Vec4<double>*>(cells));
     else
-        state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch,
+        state_out_kernel<StoreQ><<<blocks, 256, 0, s>>>(st, nx, ny, pitch, T_unit,
                                                         static_cast<const Vec4<int>*>(cells));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescale_T(cudaStream_t s, void* cells, long long count, int shift)
+{
+    if (shift < 1 || shift > 30) return cudaErrorInvalidValue;
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    rescale_T_kernel<<<blocks, 256, 0, s>>>(static_cast<Vec4<int>*>(cells), count, shift);
     return cudaGetLastError();
 }
 
@@ -448,10 +472,10 @@ cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nste
 // ---------------------------------------------------------------------------
 // Allocation-free Nusselt number (rtlbfs_nusselt_noalloc).
 //
-// For callers that must not allocate device memory at call time -- code
-// running where a cudaMalloc could block or fail unpredictably (a real-time
-// loop, a CUDA-graph-built pipeline, a host that gives the library only a
-// fixed memory pool), or that keeps its fields in buffers it owns -- the
+// For callers that must not allocate device memory at call time: a
+// real-time loop, where cudaMalloc can block on the device or fail at an
+// unpredictable moment, or a host that gives the library only a fixed pool
+// of memory it owns, and keeps its fields in its own buffers.  The
 // wall/average Nusselt reduction runs on caller-owned device fields with all
 // of its working memory in one file-scope device array: the cavity
 // descriptor, the FP64 mesh lines and the per-block partial sums.  Every GPU
@@ -536,6 +560,17 @@ __global__ void noalloc_lines_kernel(const double* __restrict__ f, int n, int pe
     }
 }
 
+// The call's descriptor, passed by value (no host staging of a stack
+// object), and the run control the reduction reads (buffer 0 current).
+__global__ void noalloc_setup_kernel(CavityDesc d, CavityDesc* __restrict__ desc,
+                                     CavityCtl* __restrict__ ctl)
+{
+    *desc = d;
+    CavityCtl c;
+    memset(&c, 0, sizeof(c));
+    *ctl = c;
+}
+
 namespace {
 std::atomic<void*> g_noalloc_ptr[64];
 }
@@ -595,10 +630,10 @@ extern "C" int rtlbfs_nusselt_noalloc(int nx, int ny, const double* xf, const do
     d.f[0][1] = const_cast<double*>(u);
     d.f[0][2] = const_cast<double*>(v);
     d.f[0][3] = const_cast<double*>(T);
-    // the copies read their pageable sources before returning
-    if (cudaMemcpyAsync(&sc->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(&sc->ctl, 0, sizeof(CavityCtl), st) != cudaSuccess ||  // cur = 0
-        cudaMemcpyAsync(sc->xf, xf, sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st) !=
+    noalloc_setup_kernel<<<1, 1, 0, st>>>(d, &sc->desc, &sc->ctl);
+    // the face coordinates are caller-owned pageable host memory: each copy
+    // has read its source when it returns
+    if (cudaMemcpyAsync(sc->xf, xf, sizeof(double) * (nx + 1), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(sc->yf, yf, sizeof(double) * (ny + 1), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
@@ -625,6 +660,6 @@ extern "C" int rtlbfs_nusselt_noalloc(int nx, int ny, const double* xf, const do
     nusselt_partial_kernel<StoreRho><<<blocks, 256, 0, st>>>(&sc->desc, &sc->ctl, 0, ln, which,
                                                             sc->partial);
     sum_partials_kernel<<<1, 256, 0, st>>>(sc->partial, blocks, scale, nu_out);
-    g_launches += 4;
+    g_launches += 5;
     return cudaGetLastError() == cudaSuccess ? RTLBFS_OK : RTLBFS_ERR_CUDA;
 }

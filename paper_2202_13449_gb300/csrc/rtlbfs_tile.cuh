@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "rtlbfs_dev.cuh"
 #include "rtlbfs_kernels.h"
@@ -292,6 +293,17 @@ __device__ __forceinline__ void tile_sums(const TileSmem<P, TX, TY, NT>& sm, dou
 // caller to add (tile_sums) after a barrier.  lines_staged: stage_tile has put the
 // tile's mesh lines in shared memory (dp may then point at its copy of the
 // descriptor); otherwise phase 1 loads them beside the state.
+//
+// Work of a thread.  The tile's TX x TY cells are split into CPT = TX*TY/NT
+// cells per thread at fixed places: thread (c, r) = (tid % CW, tid / CW),
+// CW = TX / CPT, owns cells (c + m CW, r), m < CPT.  In every phase a thread
+// first works on its own cells (and their west and south faces), whose
+// shared-memory places are fixed offsets from one base, then on a share of
+// the phase's remainder: the halo ring of the load, the gradient ring, the
+// east face column and north face row of the tile.  The remainders go to the
+// lowest threads, so they keep as few warps as possible busy for the extra
+// round.  With CW = 16 or 32 lanes of a warp read consecutive records: no
+// bank conflicts.
 template <class P, int TX, int TY, int NT, int SCHEME, bool LDCG>
 __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* dp,
                                           int i0, int j0,
@@ -303,7 +315,11 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     using S = typename P::S;
     using R = typename P::R;
     constexpr int BX = Sm::BX, BY = Sm::BY, GX = Sm::GX, GY = Sm::GY;
+    constexpr int CPT = TX * TY / NT;
+    constexpr int CW = TX / CPT;
+    static_assert(CPT * NT == TX * TY && CW * CPT == TX && CW * TY == NT, "thread layout");
     const int tid = threadIdx.x;
+    const int tc = tid % CW, tr = tid / CW;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
     const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
     // temperature reference of this tile: its (clamped) centre cell
@@ -318,84 +334,116 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     // ---- 1. mesh lines (unless staged) and the haloed tile -------------
     if (!lines_staged) stage_lines(sm, dp, i0, j0);
     {
-        constexpr int NB = BX * BY;
-        constexpr int NR = (NB + NT - 1) / NT;
-        Vec4<S> v[NR];
-        int ms[NR];
-        bool ok[NR];
-        if (interior) {
-            const Vec4<S>* base = fin + (size_t)(j0 - 2) * pitch + (i0 - 2);
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {  // issue every load first
-                const int k = tid + q * NT;
-                ms[q] = -1;
-                ok[q] = k < NB;
-                v[q] = {S(0), S(0), S(0), S(0)};
-                if (ok[q]) v[q] = ld_state<LDCG>(&base[(size_t)(k / BX) * pitch + (k % BX)]);
+        // box positions (column, row) of load k: own cells, then the ring
+        // (the two rows below, the two above, two columns each side)
+        constexpr int NRING = BX * BY - TX * TY;
+        constexpr int RQ = (NRING + NT - 1) / NT;
+        constexpr int NL = CPT + RQ;
+        auto place = [&](int k, int& bc, int& br) -> bool {
+            if (k < CPT) {
+                bc = tc + k * CW + 2;
+                br = tr + 2;
+                return true;
             }
-        } else {
+            const int t = tid + (k - CPT) * NT;
+            if (t < 2 * BX) {
+                br = t >= BX;
+                bc = t - br * BX;
+            } else if (t < 4 * BX) {
+                const int u = t - 2 * BX;
+                br = BY - 2 + (u >= BX);
+                bc = u - (u >= BX) * BX;
+            } else {
+                const int u = t - 4 * BX;
+                br = 2 + (u >> 2);
+                bc = (u & 1) + ((u & 2) ? BX - 2 : 0);
+            }
+            return t < NRING;
+        };
+        Vec4<S> v[NL];
+        int ms[NL];
+        bool ok[NL];
 #pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                const int k = tid + q * NT;
-                const int c = k % BX, r = k / BX;
+        for (int k = 0; k < NL; ++k) {  // issue every load first
+            int bc = 0, br = 0;
+            ok[k] = place(k, bc, br);
+            ms[k] = -1;
+            v[k] = {S(0), S(0), S(0), S(0)};
+            if (interior) {
+                if (ok[k])
+                    v[k] = ld_state<LDCG>(&fin[(size_t)(j0 - 2 + br) * pitch + (i0 - 2 + bc)]);
+            } else {
                 int si = 0, sj = 0;
-                ms[q] = -1;
-                ok[q] = k < NB &&
-                        resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms[q]);
-                v[q] = {S(0), S(0), S(0), S(0)};
-                if (ok[q]) v[q] = ld_state<LDCG>(&fin[(size_t)sj * pitch + si]);
+                ok[k] = ok[k] && resolve_cell(nx, ny, xper, yper, i0 - 2 + bc, j0 - 2 + br, si,
+                                              sj, ms[k]);
+                if (ok[k]) v[k] = ld_state<LDCG>(&fin[(size_t)sj * pitch + si]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int k = tid + q * NT;
-            if (k >= NB) continue;
-            const Vec4<S> x = v[q];
+        for (int k = 0; k < NL; ++k) {
+            int bc = 0, br = 0;
+            if (!place(k, bc, br)) continue;
+            const Vec4<S> x = v[k];
             Vec4<R> y = {R(0), R(0), R(0), R(0)};
-            if (ok[q]) {
+            if (ok[k]) {
                 y = {P::val(x.x, 0), P::val(x.y, 1), P::val(x.z, 2), P::diff(x.w, qTz, 3)};
-                if (ms[q] >= 0) y = mirror_values<P>(*dp, ms[q], y, Tz);
+                if (ms[k] >= 0) y = mirror_values<P>(*dp, ms[k], y, Tz);
             }
-            sm.val[k / BX][k % BX] = y;
+            sm.val[br][bc] = y;
         }
     }
     __syncthreads();
 
     // ---- 2. gradients on the tile plus a 1-cell ring ----------------
-    for (int k = tid; k < GX * GY; k += NT) {
-        const int gc = k % GX, gr = k / GX;
-        int c = gc + 1, r = gr + 1;  // box position
-        int si, sj, ms = -1;
-        Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
-        if (interior ||
-            resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
-            // a wall ghost takes its partner's gradient, mirrored
-            if (ms == kSideW) c += 1;
-            else if (ms == kSideE) c -= 1;
-            else if (ms == kSideS) r += 1;
-            else if (ms == kSideN) r -= 1;
-            gg_gradient_r(sm.val[r][c], sm.val[r][c + 1], sm.val[r][c - 1], sm.val[r + 1][c],
-                          sm.val[r - 1][c], sm.xc[c].is_next, sm.xc[c - 1].is_next,
-                          sm.yc[r].is_next, sm.yc[r - 1].is_next, gxv, gyv);
-            if (ms >= 0) mirror_grad(*dp, ms, gxv, gyv);
+    {
+        constexpr int NGR = GX * GY - TX * TY;
+        constexpr int GQ = CPT + (NGR + NT - 1) / NT;
+#pragma unroll 1
+        for (int k = 0; k < GQ; ++k) {
+            int gc, gr;
+            if (k < CPT) {
+                gc = tc + k * CW + 1;
+                gr = tr + 1;
+            } else {
+                const int t = tid + (k - CPT) * NT;
+                if (t >= NGR) break;
+                if (t < 2 * GX) {
+                    gr = t >= GX ? GY - 1 : 0;
+                    gc = t - (t >= GX) * GX;
+                } else {
+                    const int u = t - 2 * GX;
+                    gr = 1 + (u >> 1);
+                    gc = (u & 1) ? GX - 1 : 0;
+                }
+            }
+            int c = gc + 1, r = gr + 1;  // box position
+            int si, sj, ms = -1;
+            Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
+            if (interior ||
+                resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+                // a wall ghost takes its partner's gradient, mirrored
+                if (ms == kSideW) c += 1;
+                else if (ms == kSideE) c -= 1;
+                else if (ms == kSideS) r += 1;
+                else if (ms == kSideN) r -= 1;
+                gg_gradient_r(sm.val[r][c], sm.val[r][c + 1], sm.val[r][c - 1], sm.val[r + 1][c],
+                              sm.val[r - 1][c], sm.xc[c].is_next, sm.xc[c - 1].is_next,
+                              sm.yc[r].is_next, sm.yc[r - 1].is_next, gxv, gyv);
+                if (ms >= 0) mirror_grad(*dp, ms, gxv, gyv);
+            }
+            sm.gx[gr][gc] = gxv;
+            sm.gy[gr][gc] = gyv;
         }
-        sm.gx[gr][gc] = gxv;
-        sm.gy[gr][gc] = gyv;
     }
     __syncthreads();
 
     // ---- 3. faces ----------------------------------------------------
-    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
-    for (int k = tid; k < NXF + NYF; k += NT) {
-        const bool isx = k < NXF;
-        int fc, fr;
-        if (isx) {
-            fc = k % (TX + 1);
-            fr = k / (TX + 1);
-        } else {
-            fc = (k - NXF) % TX;
-            fr = (k - NXF) / TX;
-        }
+    // x-face (fc, fr) between cells fc - 1 and fc of row fr; y-face (fc, fr)
+    // between rows fr - 1 and fr of column fc.  Own: the west and south faces
+    // of the thread's cells; then the tile's east column (threads 0..TY-1)
+    // and north row (threads TY..TY+TX-1) of faces.
+    auto face = [&](auto isx_c, int fc, int fr) {
+        constexpr bool isx = decltype(isx_c)::value;
         const int gi = i0 + fc, gj = j0 + fr;
         const bool valid = interior || (isx ? (gi <= nx && gj < ny) : (gi < nx && gj <= ny));
         Vec4<R> out = {R(0), R(0), R(0), R(0)};
@@ -424,6 +472,34 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
         }
         if (isx) sm.fx[fr][fc] = out;
         else sm.fy[fr][fc] = out;
+    };
+    {
+        using XF = std::true_type;
+        using YF = std::false_type;
+        constexpr int TQ = (TX + TY + NT - 1) / NT;  // rounds of the east/north faces
+#pragma unroll 1
+        for (int k = 0; k < CPT + TQ; ++k) {
+            int fc = tc + k * CW, fr = tr;
+            if (k >= CPT) {
+                const int t = tid + (k - CPT) * NT;
+                if (t >= TY) break;
+                fc = TX;
+                fr = t;
+            }
+            face(XF(), fc, fr);
+        }
+#pragma unroll 1
+        for (int k = 0; k < CPT + TQ; ++k) {
+            int fc = tc + k * CW, fr = tr;
+            if (k >= CPT) {
+                const int t = tid + (k - CPT) * NT - TY;
+                if (t >= TX) break;
+                if (t < 0) continue;
+                fc = t;
+                fr = TY;
+            }
+            face(YF(), fc, fr);
+        }
     }
     __syncthreads();
 
@@ -434,16 +510,17 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
         const R dt = P::dt(dp), bg = P::beta_g(dp), Tr = P::T_ref(dp);
         const R fxb = P::fx(dp), fyb = P::fy(dp);
         bool bad = false;
-        for (int k = tid; k < TX * TY; k += NT) {
-            const int tc = k % TX, tr = k / TX;
-            const int gi = i0 + tc, gj = j0 + tr;
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const int cc = tc + m * CW;
+            const int gi = i0 + cc, gj = j0 + tr;
             if (gi >= nx || gj >= ny) continue;
             const size_t o = (size_t)gj * pitch + gi;
             const Vec4<S> q = ld_state<LDCG>(&fin[o]);
-            const Vec4<R> p = sm.val[tr + 2][tc + 2];
-            const Vec4<R> Fw = sm.fx[tr][tc], Fe = sm.fx[tr][tc + 1];
-            const Vec4<R> Fs = sm.fy[tr][tc], Fn = sm.fy[tr + 1][tc];
-            const R ax = sm.xc[tc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
+            const Vec4<R> p = sm.val[tr + 2][cc + 2];
+            const Vec4<R> Fw = sm.fx[tr][cc], Fe = sm.fx[tr][cc + 1];
+            const Vec4<R> Fs = sm.fy[tr][cc], Fn = sm.fy[tr + 1][cc];
+            const R ax = sm.xc[cc + 2].dt_w, ay = sm.yc[tr + 2].dt_w;
             const R dr = p.x, u = p.y, v = p.z, T = Tz + p.w;
             const R rho = one + dr;
             // Dt/dV sum_k F_k dS_k for mass, momentum, energy

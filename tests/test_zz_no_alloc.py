@@ -1,9 +1,10 @@
 """The allocation-free Nusselt entry point against the handle API.
 
 rtlbfs_nusselt_noalloc serves callers that cannot allocate device memory
-when they call in (real-time or graph-built pipelines, fixed memory pools):
-it takes caller-owned FP64 device fields and keeps its working memory in a
-file-scope device array.  Here torch owns the fields; two consecutive calls
+when they call in (a real-time loop, where cudaMalloc may block or fail at an
+unpredictable moment; a host that lends the library only a fixed memory
+pool): it takes caller-owned FP64 device fields and keeps its working memory
+in a file-scope device array.  Here torch owns the fields; two consecutive calls
 (which reuse that array) must each agree with rtlbfs_nusselt of a handle
 holding the same state, to the FP64 tolerance of the other GPU tests.
 """
@@ -18,13 +19,19 @@ pytestmark = pytest.mark.gpu
 def test_noalloc_nusselt_matches_handle_twice():
     import torch
     torch.cuda.init()
-    D, A = capi.WALL_DIRICHLET, capi.WALL_ADIABATIC
+    D, A, P = capi.WALL_DIRICHLET, capi.WALL_ADIABATIC, capi.PERIODIC
     cases = [
         # (nx, ny, kinds, bc_T, bc_u, which list, seed)
         (38, 22, (D, D, A, A), (1.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0),
          [capi.NU_WEST, capi.NU_EAST, capi.NU_AVG, capi.NU_HALF], 5),
         (29, 41, (A, D, D, D), (0.0, 0.2, 0.9, 0.3), (0.01, 0.0, 0.0, 0.02),
          [capi.NU_SOUTH, capi.NU_NORTH, capi.NU_EAST, capi.NU_AVG], 6),
+        # periodic in x: the wrapped widths of the mesh-line builder
+        (33, 18, (P, P, D, D), (0.0, 0.0, 1.0, 0.0), (0.0, 0.0, 0.0, 0.03),
+         [capi.NU_SOUTH, capi.NU_NORTH, capi.NU_AVG], 7),
+        # periodic in y
+        (24, 27, (D, A, P, P), (0.8, 0.0, 0.0, 0.0), (0.0, 0.02, 0.0, 0.0),
+         [capi.NU_WEST, capi.NU_EAST, capi.NU_AVG, capi.NU_HALF], 8),
     ]
     stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
