@@ -106,18 +106,112 @@ struct CavityDesc {
     const void* ycell;            // CellLine<R>[ny+4]
 };
 
-// Mutable per-cavity run control (device-written between steps).
+// Run control of a cavity: the state of its run after the last step whose
+// stop test has been made.
 struct CavityCtl {
     int cur;                  // buffer holding the current state
     int done;                 // 1: this cavity takes no more steps
     int status;               // kRunning, kConverged, kMaxSteps, kDiverged
-    unsigned int arrive;      // tiles of this cavity finished in this step
-    long long steps;          // steps taken since the last state upload
+    int pend;                 // 1: step `steps` was taken, its stop test not yet made
+    long long steps;          // steps tested since the last state upload
     long long max_steps;      // done when steps reaches this
     double tol;               // done when max(R_u, R_T) < tol (tol < 0: never)
-    double res[2];            // (R_u, R_T) of the last step
-    double acc[4];            // running sums of this step: sum (d|u|)^2, |u|^2, (dT)^2, T^2
+    double res[2];            // (R_u, R_T) of the last tested step (see res_stale)
+    double sums[4];           // residual sums of the last tested step
+    int res_stale;            // 1: res not yet formed from sums (finalize_run does it)
+    int pad;
 };
+
+// Device record of a cavity's run.  A step launch never waits for its own
+// residual: its units add their sums for step k into acc[k % 3] and the
+// stop test of step k is made by every unit of the next launch as it
+// starts.  A launch of parity par reads only h[par]; the cavity's first
+// unit writes the header after the test (and after this launch's step) to
+// h[par ^ 1] and clears acc[(k + 1) % 3] for the step after.  Between
+// launches h[0] is the header the host reads (a finalising launch makes
+// the last test and copies the result to both headers).
+struct CavityRun {
+    CavityCtl h[2];
+    double acc[3][4];         // per step: sum (d|u|)^2, |u|^2, (dT)^2, T^2
+};
+
+// R12 from the residual sums of a step: ||d|u|||_2 / |||u|^{n+1}||_2 (or
+// the same for T); a zero denominator gives infinity.
+__host__ __device__ inline double r12(double num, double den)
+{
+    return den > 0.0 ? sqrt(num) / sqrt(den) : INFINITY;
+}
+
+// r12(num, den) < tol, decided without the FP64 square roots and division
+// unless the ratio lies within 2 % of tol^2: the same outcome as the
+// formula (its rounding error is ~1e-16 relative), a fraction of its
+// latency on the narrow FP64 units of this GPU.
+__host__ __device__ inline bool r12_below(double num, double den, double tol)
+{
+    if (!(den > 0.0) || !(tol > 0.0)) return false;
+    const double q = tol * tol * den;
+    if (q >= 2.2250738585072014e-308 && q < 1e300) {
+        if (num < 0.98 * q) return true;
+        if (num > 1.02 * q) return false;
+    }
+    return r12(num, den) < tol;
+}
+
+// The stop test of the pending step of c (pend = 1), from that step's
+// residual sums s: the header after it (res formed later, res_stale set).
+// A header without a pending step is returned as is.  Outcomes as with
+// R = r12(...): diverged when R_u or R_T is not a number or a sum is not a
+// number, converged when max(R_u, R_T) < tol, else capped at max_steps.
+__host__ __device__ inline CavityCtl stop_test(CavityCtl c, const double s[4])
+{
+    if (!c.pend) return c;
+    const double su = s[0], du = s[1], sT = s[2], dT = s[3];
+    for (int q = 0; q < 4; ++q) c.sums[q] = s[q];
+    c.res_stale = 1;
+    c.steps += 1;
+    c.cur ^= 1;
+    c.pend = 0;
+    // r12 is NaN exactly when num is NaN or both are infinite (den > 0)
+    const bool nan_u = isnan(su) || (du > 0.0 && isinf(su) && isinf(du));
+    const bool nan_T = isnan(sT) || (dT > 0.0 && isinf(sT) && isinf(dT));
+    int status = kRunning;
+    if (nan_u || nan_T) status = kDiverged;
+    else if (r12_below(su, du, c.tol) && r12_below(sT, dT, c.tol)) status = kConverged;
+    else if (c.steps >= c.max_steps) status = kMaxSteps;
+    c.status = status;
+    if (status != kRunning) c.done = 1;
+    return c;
+}
+
+// Header of parity par after the stop test of its pending step (one
+// thread; the header and all three sum slots are loaded at once, so this
+// is one round trip).
+__device__ inline CavityCtl run_head(const CavityRun* r, int par)
+{
+    const CavityCtl c = r->h[par];
+    double a[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[k][q] = r->acc[k][q];
+    const int slot = (int)(c.steps % 3);
+    const double* s = slot == 0 ? a[0] : (slot == 1 ? a[1] : a[2]);
+    return stop_test(c, s);
+}
+
+// What the cavity's first unit of a launch of parity par writes: the
+// tested header d, with the step this launch takes pending unless the
+// cavity is done, and the sum slot of the step after cleared.
+__device__ inline void run_publish(CavityRun* r, int par, CavityCtl d)
+{
+    if (!d.done) {
+        d.pend = 1;
+        double* z = r->acc[(int)((d.steps + 1) % 3)];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[q] = 0.0;
+    }
+    r->h[par ^ 1] = d;
+}
 
 // Four values of one cell; 16-byte aligned for 4-byte R, 32 for double, so
 // a cell record moves in one (or two) vector memory instructions.

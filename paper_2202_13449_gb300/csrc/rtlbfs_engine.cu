@@ -165,16 +165,17 @@ int Engine::init()
     h_desc_.resize(capacity_);
     std::memset(h_desc_.data(), 0, sizeof(CavityDesc) * capacity_);
     CK(cudaMalloc(&d_desc_, sizeof(CavityDesc) * capacity_));
-    CK(cudaMalloc(&d_ctl_, sizeof(CavityCtl) * capacity_));
-    CK(cudaMemset(d_ctl_, 0, sizeof(CavityCtl) * capacity_));
-    std::vector<CavityCtl> c0(capacity_);
-    for (auto& c : c0) {
-        std::memset(&c, 0, sizeof(c));
-        c.done = 1;
-        c.tol = -1.0;
-        c.res[0] = c.res[1] = INFINITY;
+    CK(cudaMalloc(&d_ctl_, sizeof(CavityRun) * capacity_));
+    std::vector<CavityRun> c0(capacity_);
+    for (auto& r : c0) {
+        std::memset(&r, 0, sizeof(r));
+        for (auto& c : r.h) {
+            c.done = 1;
+            c.tol = -1.0;
+            c.res[0] = c.res[1] = INFINITY;
+        }
     }
-    CK(cudaMemcpy(d_ctl_, c0.data(), sizeof(CavityCtl) * capacity_, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_ctl_, c0.data(), sizeof(CavityRun) * capacity_, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d_ntiles_, sizeof(int)));
     CK(cudaMemset(d_ntiles_, 0, sizeof(int)));
     partial_cap_ = kPartialMax;
@@ -264,9 +265,20 @@ int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_ou
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
-    // from pageable memory: staged before the call returns, ordered on the stream
-    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
+    int rc = put_run(slot, z);
+    if (rc) return rc;
     *slot_out = slot;
+    return RTLBFS_OK;
+}
+
+int Engine::put_run(int slot, const CavityCtl& c)
+{
+    CavityRun r;
+    std::memset(&r, 0, sizeof(r));
+    r.h[0] = c;
+    r.h[1] = c;
+    // from pageable memory: staged before the call returns, ordered on the stream
+    CK(cudaMemcpyAsync(&d_ctl_[slot], &r, sizeof(r), cudaMemcpyHostToDevice, stream_));
     return RTLBFS_OK;
 }
 
@@ -683,8 +695,8 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
-    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
-    CK(cudaStreamSynchronize(stream_));  // z lives on this stack frame
+    int rcz = put_run(slot, z);
+    if (rcz) return rcz;
     if (h_bad)
         return fail(RTLBFS_ERR_ARG, "state not representable in the FP32 mode's fixed-point "
                                     "storage: NaN, |rho-1| >= 0.49, |u|,|v| >= 0.99 or "
@@ -764,8 +776,7 @@ int Engine::set_conduction_state(int slot)
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
-    CK(cudaMemcpyAsync(&d_ctl_[slot], &z, sizeof(z), cudaMemcpyHostToDevice, stream_));
-    return RTLBFS_OK;
+    return put_run(slot, z);
 }
 
 int Engine::arm(int slot, long long nsteps, double tol)
@@ -814,7 +825,7 @@ int Engine::launch_steps(long long launches)
             CK(cudaMemsetAsync(d_tstep_, 0, sizeof(int) * ntiles_, stream_));
             CK(cudaMemsetAsync(d_pctl_, 0, sizeof(PersistCtl), stream_));
             CK(launch_persist(precision_, tile_h_, ntiles_, stream_, &d_desc_[persist_slot_],
-                              &d_ctl_[persist_slot_], d_tiles_ + c.first_tile, d_tstep_, d_pctl_,
+                              &d_ctl_[persist_slot_].h[0], d_tiles_ + c.first_tile, d_tstep_, d_pctl_,
                               n, withhold_));
             g_launches++;
             CK(cudaMemcpyAsync(h_stalled_, &d_pctl_->stalled, sizeof(int), cudaMemcpyDeviceToHost,
@@ -826,7 +837,17 @@ int Engine::launch_steps(long long launches)
         }
         return RTLBFS_OK;
     }
+    // launch k of this chain has parity k & 1 (graphs hold an even number
+    // of launches); the chain ends with the stop test of its last step
     long long left = launches;
+    int par = 0;
+    auto launch = [&](cudaStream_t st, int p) {
+        return kernel_ == 1 ? launch_step(precision_, tile_h_, scheme_, grid_, st, d_desc_, d_ctl_,
+                                          d_tiles_, d_ntiles_, p)
+                            : launch_march(precision_, grid_, st, d_desc_, d_ctl_, d_tiles_,
+                                           d_ntiles_, p);
+    };
+    static_assert(kGraphChunk % 2 == 0, "graphs of an even number of launches");
     if (left >= kGraphChunk) {
         if (!gexec_) {
             cudaStream_t cs = nullptr;
@@ -834,9 +855,7 @@ int Engine::launch_steps(long long launches)
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
-                    e = kernel_ == 1 ? launch_step(precision_, tile_h_, scheme_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
-                                     : launch_march(precision_, grid_, cs, d_desc_, d_ctl_, d_tiles_, d_ntiles_);
+                for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) e = launch(cs, k & 1);
                 cudaError_t e2 = cudaStreamEndCapture(cs, &g);
                 if (e == cudaSuccess) e = e2;
             }
@@ -853,10 +872,12 @@ int Engine::launch_steps(long long launches)
         }
     }
     for (; left > 0; --left) {
-        CK(kernel_ == 1 ? launch_step(precision_, tile_h_, scheme_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_)
-                        : launch_march(precision_, grid_, stream_, d_desc_, d_ctl_, d_tiles_, d_ntiles_));
+        CK(launch(stream_, par));
+        par ^= 1;
         g_launches++;
     }
+    CK(launch_finalize(stream_, d_ctl_, capacity_, par));
+    g_launches++;
     return RTLBFS_OK;
 }
 
@@ -866,8 +887,8 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
     CK(cudaStreamSynchronize(stream_));
     // snapshot every active cavity's fields and the run control
     std::vector<void*> snap(capacity_, nullptr);
-    std::vector<CavityCtl> ctl_save(capacity_);
-    CK(cudaMemcpy(ctl_save.data(), d_ctl_, sizeof(CavityCtl) * capacity_, cudaMemcpyDeviceToHost));
+    std::vector<CavityRun> ctl_save(capacity_);
+    CK(cudaMemcpy(ctl_save.data(), d_ctl_, sizeof(CavityRun) * capacity_, cudaMemcpyDeviceToHost));
     int maxny = 1;
     for (int s = 0; s < capacity_; ++s) {
         if (!slots_[s].active) continue;
@@ -941,7 +962,7 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
             if (snap[s])
                 cudaMemcpyAsync(slots_[s].d_fields, snap[s], slots_[s].fields_bytes,
                                 cudaMemcpyDeviceToDevice, stream_);
-        cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityCtl) * capacity_,
+        cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityRun) * capacity_,
                         cudaMemcpyHostToDevice, stream_);
         cudaStreamSynchronize(stream_);
     }
@@ -950,7 +971,7 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
         if (snap[s])
             cudaMemcpyAsync(slots_[s].d_fields, snap[s], slots_[s].fields_bytes,
                             cudaMemcpyDeviceToDevice, stream_);
-    cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityCtl) * capacity_, cudaMemcpyHostToDevice,
+    cudaMemcpyAsync(d_ctl_, ctl_save.data(), sizeof(CavityRun) * capacity_, cudaMemcpyHostToDevice,
                     stream_);
     cudaStreamSynchronize(stream_);
     for (void* p : snap) cudaFree(p);
@@ -972,7 +993,8 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
 int Engine::read_ctl(int slot, CavityCtl* out)
 {
     if (slot < 0 || slot >= capacity_) return fail(RTLBFS_ERR_ARG, "no such slot");
-    CK(cudaMemcpyAsync(out, &d_ctl_[slot], sizeof(CavityCtl), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(out, &d_ctl_[slot].h[0], sizeof(CavityCtl), cudaMemcpyDeviceToHost,
+                       stream_));
     CK(cudaStreamSynchronize(stream_));
     return RTLBFS_OK;
 }
@@ -981,7 +1003,9 @@ int Engine::read_ctls(std::vector<CavityCtl>& out)
 {
     out.resize(capacity_);
     CK(cudaStreamSynchronize(stream_));
-    CK(cudaMemcpy(out.data(), d_ctl_, sizeof(CavityCtl) * capacity_, cudaMemcpyDeviceToHost));
+    // the tested header h[0] of every slot, in one strided copy
+    CK(cudaMemcpy2D(out.data(), sizeof(CavityCtl), d_ctl_, sizeof(CavityRun), sizeof(CavityCtl),
+                    capacity_, cudaMemcpyDeviceToHost));
     return RTLBFS_OK;
 }
 

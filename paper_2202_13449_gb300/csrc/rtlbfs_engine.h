@@ -137,7 +137,8 @@ private:
     std::vector<Cavity> slots_;
     std::vector<CavityDesc> h_desc_;
     CavityDesc* d_desc_ = nullptr;
-    CavityCtl* d_ctl_ = nullptr;
+    CavityRun* d_ctl_ = nullptr;       // run control per slot (two headers, sums)
+    int put_run(int slot, const CavityCtl& c);  // both headers = c, sums cleared
     int4* d_tiles_ = nullptr;
     int* d_ntiles_ = nullptr;
     int tile_cap_ = 0, ntiles_ = 0;

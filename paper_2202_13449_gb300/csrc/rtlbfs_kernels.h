@@ -49,13 +49,18 @@ struct NuLines {
 constexpr int kSchemeRTLBFS = 0, kSchemeTLBFS = 1;
 cudaError_t step_prepare(int precision);
 cudaError_t step_occupancy(int precision, int tile_h, int scheme, int* blocks_per_sm);
+// par: parity of the launch within a chain of step launches (launch k of
+// a chain reads run header k & 1 and writes the other, see CavityRun)
 cudaError_t launch_step(int precision, int tile_h, int scheme, int grid, cudaStream_t s,
-                        const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
-                        const int* ntiles);
+                        const CavityDesc* descs, CavityRun* runs, const int4* tiles,
+                        const int* ntiles, int par);
 cudaError_t march_prepare(int precision);
 cudaError_t march_occupancy(int precision, int* blocks_per_sm);
 cudaError_t launch_march(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
-                         CavityCtl* ctls, const int4* units, const int* nunits);
+                         CavityRun* runs, const int4* units, const int* nunits, int par);
+// the stop test of the last step of a chain whose next launch would have
+// parity par, for cavities 0..n-1: both headers become the tested header
+cudaError_t launch_finalize(cudaStream_t s, CavityRun* runs, int n, int par);
 
 // Run control of the persistent tile kernel (rtlbfs_persist.cu), zeroed
 // before each launch: the residual sums and arrivals of step k in slot
@@ -77,7 +82,7 @@ cudaError_t launch_persist(int precision, int tile_h, int ntiles, cudaStream_t s
                            const CavityDesc* desc, CavityCtl* ctl, const int4* tiles, int* tstep,
                            PersistCtl* pc, int nsteps, int withhold);
 cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
-                           const CavityCtl* ctls, int slot, const NuLines& ln, int which,
+                           const CavityRun* runs, int slot, const NuLines& ln, int which,
                            long long count, double scale, double* partial, int max_blocks,
                            double* out);
 // T_unit: temperature unit of the stored state (stored T = T / T_unit)
@@ -90,7 +95,7 @@ cudaError_t launch_rescale_T(cudaStream_t s, void* cells, long long count, int s
 // rho = 1, u = v = 0, T = Tcol[i] in every row (one buffer of cell records)
 cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol, int nx, int ny,
                               int pitch, void* cells);
-cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
+cudaError_t launch_arm(cudaStream_t s, CavityRun* runs, int slot, long long nsteps, double tol,
                        int reset_counter);
 
 }  // namespace rtlbfs

@@ -138,8 +138,8 @@ struct MarchMin<StoreQ> {
 
 template <class P>
 __global__ void __launch_bounds__(kMarchThreads, MarchMin<P>::value)
-march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
-             const int4* __restrict__ units, const int* __restrict__ nunits_ptr)
+march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
+             const int4* __restrict__ units, const int* __restrict__ nunits_ptr, int par)
 {
     using S = typename P::S;
     using R = typename P::R;
@@ -153,9 +153,18 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         const int4 wu = units[ui];
         const int slot = wu.x, c0 = wu.y, j0 = wu.z, j1 = wu.w;
         const CavityDesc* dp = descs + slot;
-        CavityCtl* ctl = ctls + slot;
-        if (ctl->done) continue;  // warp-uniform
-        const int cur = ctl->cur;
+        CavityRun* run = runs + slot;
+        // the stop test of the cavity's previous step (lane 0; the cavity's
+        // first unit also publishes the header for the next launch)
+        int plan = 0;
+        if (lane == 0) {
+            const CavityCtl d = run_head(run, par);
+            if (ui == dp->tile_begin) run_publish(run, par, d);
+            plan = d.done | (d.cur << 1) | ((int)(d.steps % 3) << 2);
+        }
+        plan = __shfl_sync(0xffffffffu, plan, 0);
+        if (plan & 1) continue;  // warp-uniform
+        const int cur = (plan >> 1) & 1, slot3 = plan >> 2;
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
         const Vec4<S>* __restrict__ fin = static_cast<const Vec4<S>*>(dp->f[cur][0]);
@@ -408,33 +417,13 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
         s1 = wsum(s1);
         s2 = wsum(s2);
         s3 = wsum(s3);
+        // the step's residual sums; the next launch tests them
         if (lane == 0) {
-            atomicAdd(&ctl->acc[0], (double)s0);
-            atomicAdd(&ctl->acc[1], (double)s1);
-            atomicAdd(&ctl->acc[2], (double)s2);
-            atomicAdd(&ctl->acc[3], (double)s3);
-            __threadfence();
-            const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-            if (prev == (unsigned)dp->ntiles - 1u) {
-                __threadfence();
-                volatile double* acc = ctl->acc;
-                const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
-                const double ru = du > 0.0 ? sqrt(su) / sqrt(du) : INFINITY;
-                const double rT = dT > 0.0 ? sqrt(sT) / sqrt(dT) : INFINITY;
-                ctl->res[0] = ru;
-                ctl->res[1] = rT;
-                ctl->steps += 1;
-                ctl->cur = cur ^ 1;
-                int status = kRunning;
-                if (isnan(ru) || isnan(rT) || isnan(su) || isnan(sT)) status = kDiverged;
-                else if (fmax(ru, rT) < ctl->tol) status = kConverged;
-                else if (ctl->steps >= ctl->max_steps) status = kMaxSteps;
-                ctl->status = status;
-                if (status != kRunning) ctl->done = 1;
-                for (int q = 0; q < 4; ++q) acc[q] = 0.0;
-                ctl->arrive = 0u;
-                __threadfence();
-            }
+            double* acc = run->acc[slot3];
+            atomicAdd(&acc[0], (double)s0);
+            atomicAdd(&acc[1], (double)s1);
+            atomicAdd(&acc[2], (double)s2);
+            atomicAdd(&acc[3], (double)s3);
         }
         __syncwarp();
     }
@@ -456,13 +445,13 @@ cudaError_t march_occupancy(int precision, int* blocks_per_sm)
 }
 
 cudaError_t launch_march(int precision, int grid, cudaStream_t s, const CavityDesc* descs,
-                         CavityCtl* ctls, const int4* units, const int* nunits)
+                         CavityRun* runs, const int4* units, const int* nunits, int par)
 {
     if (precision == 0)
-        return launch_chained(march_kernel<StoreD>, grid, kMarchThreads, 0, s, descs, ctls, units,
-                              nunits);
-    return launch_chained(march_kernel<StoreQ>, grid, kMarchThreads, 0, s, descs, ctls, units,
-                          nunits);
+        return launch_chained(march_kernel<StoreD>, grid, kMarchThreads, 0, s, descs, runs, units,
+                              nunits, par);
+    return launch_chained(march_kernel<StoreQ>, grid, kMarchThreads, 0, s, descs, runs, units,
+                          nunits, par);
 }
 
 }  // namespace rtlbfs

@@ -34,8 +34,8 @@ namespace rtlbfs {
 
 template <class P, int TX, int TY, int NT, int SCHEME>
 __global__ void __launch_bounds__(NT, MinBlocks<P, NT>::value)
-step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
-            const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr)
+step_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
+            const int4* __restrict__ tiles, const int* __restrict__ ntiles_ptr, int par)
 {
     using Sm = TileSmem<P, TX, TY, NT>;
     using S = typename P::S;
@@ -51,52 +51,56 @@ step_kernel(const CavityDesc* __restrict__ descs, CavityCtl* __restrict__ ctls,
     }
     chain_sync();
 
-    __syncthreads();  // the staged descriptor and lines
-
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int4 tile = tiles[t];
         const int slot = tile.x, i0 = tile.y, j0 = tile.z;
+        CavityRun* run = &runs[slot];
+        // the stop test of the cavity's previous step (one thread; its first
+        // tile also publishes the header for the next launch)
+        if (tid == 0) {
+            const CavityCtl d = run_head(run, par);
+            if (t == descs[slot].tile_begin) run_publish(run, par, d);
+            sm.plan[0] = d.done;
+            sm.plan[1] = d.cur;
+            sm.plan[2] = (int)(d.steps % 3);
+        }
+        __syncthreads();  // the plan (and, on the first tile, the staged descriptor and lines)
+        const int done = sm.plan[0], cur = sm.plan[1], slot3 = sm.plan[2];
+        if (done) {  // uniform across the block
+            __syncthreads();  // everyone has read the plan before it is rewritten
+            continue;
+        }
         // the first tile uses what was staged; later tiles (batches) read
         // their descriptor in place and load their lines beside the state
         const bool first = t == (int)blockIdx.x;
         const CavityDesc* dp = first ? &sm.desc : &descs[slot];
-        CavityCtl* ctl = &ctls[slot];
-        if (ctl->done) continue;  // uniform across the block
-        const int cur = ctl->cur;
         tile_step<P, TX, TY, NT, SCHEME, false>(sm, dp, i0, j0,
                                                 static_cast<const Vec4<S>*>(dp->f[cur][0]),
                                                 static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]), first);
         __syncthreads();
         double a[4];
         if (tid < 32) tile_sums(sm, a);
-        if (tid == 0) {
-            for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
-            __threadfence();
-            const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-            if (prev == (unsigned)dp->ntiles - 1u) {
-                // last tile of this cavity in this step: finalize
-                __threadfence();
-                volatile double* acc = ctl->acc;
-                const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
-                const double ru = du > 0.0 ? sqrt(su) / sqrt(du) : INFINITY;
-                const double rT = dT > 0.0 ? sqrt(sT) / sqrt(dT) : INFINITY;
-                ctl->res[0] = ru;
-                ctl->res[1] = rT;
-                ctl->steps += 1;
-                ctl->cur = cur ^ 1;
-                int status = kRunning;
-                if (isnan(ru) || isnan(rT) || isnan(su) || isnan(sT)) status = kDiverged;
-                else if (fmax(ru, rT) < ctl->tol) status = kConverged;
-                else if (ctl->steps >= ctl->max_steps) status = kMaxSteps;
-                ctl->status = status;
-                if (status != kRunning) ctl->done = 1;
-                for (int q = 0; q < 4; ++q) acc[q] = 0.0;
-                ctl->arrive = 0u;
-                __threadfence();
-            }
-        }
+        // the step's residual sums; the next launch tests them
+        if (tid == 0)
+            for (int q = 0; q < 4; ++q) atomicAdd(&run->acc[slot3][q], a[q]);
         __syncthreads();
     }
+}
+
+// The stop test of the last step of a chain of launches of parity par:
+// both headers of every cavity become its tested header (host-readable).
+__global__ void finalize_kernel(CavityRun* __restrict__ runs, int n, int par)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    CavityCtl d = run_head(&runs[s], par);
+    if (d.res_stale) {  // (R_u, R_T) of the last tested step
+        d.res[0] = r12(d.sums[0], d.sums[1]);
+        d.res[1] = r12(d.sums[2], d.sums[3]);
+        d.res_stale = 0;
+    }
+    runs[s].h[0] = d;
+    runs[s].h[1] = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -171,11 +175,11 @@ __device__ double energy_flux_d(const CavityDesc& d, int f, const NuLines& ln, i
 // Partial sums of a Nusselt number: one partial per block, in block order.
 template <class P>
 __global__ void __launch_bounds__(256)
-nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityCtl* __restrict__ ctls,
+nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityRun* __restrict__ runs,
                        int slot, NuLines ln, int which, double* __restrict__ partial)
 {
     const CavityDesc& d = descs[slot];
-    const int f = ctls[slot].cur;  // buffer holding the current state
+    const int f = runs[slot].h[0].cur;  // buffer holding the current state
     long long count;
     if (which == kNuWest || which == kNuEast || which == kNuHalf) count = d.ny;
     else if (which == kNuSouth || which == kNuNorth) count = d.nx;
@@ -287,21 +291,28 @@ __global__ void conduction_kernel(const double* __restrict__ Tcol, int nx, int n
 }
 
 // Arm the run control of one cavity: take `nsteps` more steps (stop early
-// when max(R_u, R_T) < tol, tol < 0: never).
-__global__ void arm_kernel(CavityCtl* ctls, int slot, long long nsteps, double tol,
+// when max(R_u, R_T) < tol, tol < 0: never).  Runs on a tested header
+// (pend = 0: after finalize_kernel or a state upload).
+__global__ void arm_kernel(CavityRun* runs, int slot, long long nsteps, double tol,
                            int reset_counter)
 {
-    CavityCtl* c = &ctls[slot];
+    CavityRun* r = &runs[slot];
+    CavityCtl c = r->h[0];
     if (reset_counter) {
-        c->steps = 0;
-        c->res[0] = c->res[1] = INFINITY;
+        c.steps = 0;
+        c.res[0] = c.res[1] = INFINITY;
+        for (int q = 0; q < 4; ++q) c.sums[q] = 0.0;
+        c.res_stale = 0;
     }
-    c->max_steps = c->steps + nsteps;
-    c->tol = tol;
-    c->status = kRunning;
-    c->done = nsteps > 0 ? 0 : 1;
-    c->arrive = 0u;
-    for (int q = 0; q < 4; ++q) c->acc[q] = 0.0;
+    c.max_steps = c.steps + nsteps;
+    c.tol = tol;
+    c.status = kRunning;
+    c.done = nsteps > 0 ? 0 : 1;
+    c.pend = 0;
+    r->h[0] = c;
+    r->h[1] = c;
+    for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < 4; ++q) r->acc[k][q] = 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -325,10 +336,10 @@ struct TileKernel {
     {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, NT, smem);
     }
-    static cudaError_t launch(int grid, cudaStream_t s, const CavityDesc* descs, CavityCtl* ctls,
-                              const int4* tiles, const int* ntiles)
+    static cudaError_t launch(int grid, cudaStream_t s, const CavityDesc* descs, CavityRun* runs,
+                              const int4* tiles, const int* ntiles, int par)
     {
-        return launch_chained(fn, grid, NT, smem, s, descs, ctls, tiles, ntiles);
+        return launch_chained(fn, grid, NT, smem, s, descs, runs, tiles, ntiles, par);
     }
 };
 
@@ -381,16 +392,22 @@ cudaError_t step_occupancy(int precision, int tile_h, int scheme, int* blocks_pe
 }
 
 cudaError_t launch_step(int precision, int tile_h, int scheme, int grid, cudaStream_t s,
-                        const CavityDesc* descs, CavityCtl* ctls, const int4* tiles,
-                        const int* ntiles)
+                        const CavityDesc* descs, CavityRun* runs, const int4* tiles,
+                        const int* ntiles, int par)
 {
     return with_tile_kernel(precision, tile_h, scheme, [&](auto k) {
-        return k.launch(grid, s, descs, ctls, tiles, ntiles);
+        return k.launch(grid, s, descs, runs, tiles, ntiles, par);
     });
 }
 
+cudaError_t launch_finalize(cudaStream_t s, CavityRun* runs, int n, int par)
+{
+    finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(runs, n, par);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nusselt(int precision, cudaStream_t s, const CavityDesc* descs,
-                           const CavityCtl* ctls, int slot, const NuLines& ln, int which,
+                           const CavityRun* ctls, int slot, const NuLines& ln, int which,
                            long long count, double scale, double* partial, int max_blocks,
                            double* out)
 {
@@ -460,7 +477,7 @@ cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol,
     return cudaGetLastError();
 }
 
-cudaError_t launch_arm(cudaStream_t s, CavityCtl* ctls, int slot, long long nsteps, double tol,
+cudaError_t launch_arm(cudaStream_t s, CavityRun* ctls, int slot, long long nsteps, double tol,
                        int reset_counter)
 {
     arm_kernel<<<1, 1, 0, s>>>(ctls, slot, nsteps, tol, reset_counter);
@@ -491,7 +508,7 @@ constexpr int kNoAllocPartials = 1024;   // reduction blocks
 
 struct NoAllocScratch {
     CavityDesc desc;
-    CavityCtl ctl;
+    CavityRun ctl;
     double xf[kNoAllocMaxN + 1];
     double yf[kNoAllocMaxN + 1];
     FaceLine<double> xl[kNoAllocMaxN + 1];
@@ -563,10 +580,10 @@ __global__ void noalloc_lines_kernel(const double* __restrict__ f, int n, int pe
 // The call's descriptor, passed by value (no host staging of a stack
 // object), and the run control the reduction reads (buffer 0 current).
 __global__ void noalloc_setup_kernel(CavityDesc d, CavityDesc* __restrict__ desc,
-                                     CavityCtl* __restrict__ ctl)
+                                     CavityRun* __restrict__ ctl)
 {
     *desc = d;
-    CavityCtl c;
+    CavityRun c;
     memset(&c, 0, sizeof(c));
     *ctl = c;
 }

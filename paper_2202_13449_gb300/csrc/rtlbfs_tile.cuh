@@ -34,7 +34,8 @@ struct TileSmem {
     CellLine<R> yc[BY];
     R red[NT / 32][4];  // per-warp residual partials (tile_sums adds them)
     CavityDesc desc;  // the tile's cavity, staged by stage_tile
-    int last;
+    int plan[3];      // the tile's step after its cavity's stop test: done, cur, sum slot
+    int last;         // persistent kernel: this block finalises the step
 };
 
 // Resolve global cell (gi, gj) of a cavity, ghosts included: the source
