@@ -195,7 +195,9 @@ __device__ inline CavityCtl run_head(const CavityRun* r, int par)
 #pragma unroll
         for (int q = 0; q < 4; ++q) a[k][q] = r->acc[k][q];
     const int slot = (int)(c.steps % 3);
-    const double* s = slot == 0 ? a[0] : (slot == 1 ? a[1] : a[2]);
+    double s[4];  // selected by value: no local-memory copy of a
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] = slot == 0 ? a[0][q] : (slot == 1 ? a[1][q] : a[2][q]);
     return stop_test(c, s);
 }
 

@@ -28,6 +28,12 @@ struct TileSmem {
     Vec4<R> gy[GY][GX];
     Vec4<R> fx[TY][TX + 1];
     Vec4<R> fy[TY + 1][TX];
+    // the stored records of the tile's own cells, as loaded: the update
+    // adds its increments to them instead of reading the state again.  Only
+    // where the 16-byte records leave room for four resident blocks per SM
+    // (FP32 tiles up to 14 rows); elsewhere the update re-reads them (L2).
+    static constexpr bool kRaw = sizeof(S) == 4 && TY <= 14;
+    Vec4<S> raw[kRaw ? TY : 1][kRaw ? TX : 1];
     FaceLine<R> xl[TX + 1];
     FaceLine<R> yl[TY + 1];
     CellLine<R> xc[BX];
@@ -380,6 +386,10 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
                 if (ok[k]) v[k] = ld_state<LDCG>(&fin[(size_t)sj * pitch + si]);
             }
         }
+        if constexpr (Sm::kRaw) {
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) sm.raw[tr][tc + k * CW] = v[k];
+        }
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
             int bc = 0, br = 0;
@@ -517,7 +527,9 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             const int gi = i0 + cc, gj = j0 + tr;
             if (gi >= nx || gj >= ny) continue;
             const size_t o = (size_t)gj * pitch + gi;
-            const Vec4<S> q = ld_state<LDCG>(&fin[o]);
+            Vec4<S> q;
+            if constexpr (Sm::kRaw) q = sm.raw[tr][cc];
+            else q = ld_state<LDCG>(&fin[o]);
             const Vec4<R> p = sm.val[tr + 2][cc + 2];
             const Vec4<R> Fw = sm.fx[tr][cc], Fe = sm.fx[tr][cc + 1];
             const Vec4<R> Fs = sm.fy[tr][cc], Fn = sm.fy[tr + 1][cc];
