@@ -34,6 +34,7 @@
 #include "rtlbfs3d.h"
 #include "rtlbfs3d_dev.cuh"
 #include "rtlbfs_dev.cuh"
+#include "rtlbfs_kernels.h"
 
 namespace rtlbfs {
 extern std::atomic<long long> g_launches;
@@ -76,15 +77,10 @@ struct Desc3 {
     const void* cline_d[3];
 };
 
-// Run control, written by the device between steps.
-struct Ctl3 {
-    int cur, done, status;
-    unsigned int arrive;
-    long long steps, max_steps;
-    double tol;
-    double res[2];
-    double acc[4];
-};
+// Run control: the two-header record of the 2D solver (the stop test of
+// step k is made by the launch of step k + 1; see CavityRun).
+using rtlbfs::CavityCtl;
+using rtlbfs::CavityRun;
 
 // Constants of a mesh in the arithmetic type R and mirror constants in the
 // storage type S of a policy.
@@ -175,6 +171,7 @@ struct Smem3 {
     R xisn[BX], xdtw[BX];   // CellLine is_next, dt_w of the ringed tile
     R yisn[BY], ydtw[BY];
     double red[NT / 32][4];
+    int plan[3];  // after the stop test: done, cur, sum slot
 };
 
 // FaceLine from its per-field arrays
@@ -258,7 +255,7 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
 
 template <class P, int TX, int TY, int SCH>
 __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__ dp,
-                                                       Ctl3* __restrict__ ctl)
+                                                       CavityRun* __restrict__ run, int par)
 {
     using S = typename P::S;
     using R = typename P::R;
@@ -268,9 +265,20 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
     Sm& sm = *reinterpret_cast<Sm*>(smraw);
 
     chain_sync();
-    if (ctl->done) return;  // uniform: written by the previous launch
-    const Desc3& d = *dp;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    // the stop test of the previous step (thread 0; unit 0 publishes the
+    // header for the next launch)
+    if (tid == 0) {
+        const CavityCtl dc = rtlbfs::run_head(run, par);
+        if (blockIdx.x == 0) rtlbfs::run_publish(run, par, dc);
+        sm.plan[0] = dc.done;
+        sm.plan[1] = dc.cur;
+        sm.plan[2] = (int)(dc.steps % 3);
+    }
+    __syncthreads();
+    if (sm.plan[0]) return;  // uniform
+    const int slot3 = sm.plan[2];
+    const Desc3& d = *dp;
     const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
     int u = blockIdx.x;
     const int tix = u % d.tiles_x;
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
     const int i0 = tix * TX, j0 = tiy * TY, k0 = ch * d.kchunk, k1 = min(nz, k0 + d.kchunk);
     const bool xper = d.kind[0] == kPeriodic, yper = d.kind[2] == kPeriodic;
     const bool zper = d.kind[4] == kPeriodic;
-    const int cur = ctl->cur;
+    const int cur = sm.plan[1];
     const Vec4<S>* __restrict__ rin = static_cast<const Vec4<S>*>(d.rec[cur]);
     const S* __restrict__ tin = static_cast<const S*>(d.tem[cur]);
     Vec4<S>* __restrict__ rout = static_cast<Vec4<S>*>(d.rec[cur ^ 1]);
@@ -545,29 +553,8 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
         double a[4] = {0.0, 0.0, 0.0, 0.0};
         for (int w = 0; w < NT / 32; ++w)
             for (int q = 0; q < 4; ++q) a[q] += sm.red[w][q];
-        for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], a[q]);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-        if (prev == (unsigned)d.units - 1u) {
-            __threadfence();
-            volatile double* acc = ctl->acc;
-            const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
-            const double ru = du > 0.0 ? sqrt(su) / sqrt(du) : INFINITY;
-            const double rT = dT > 0.0 ? sqrt(sT) / sqrt(dT) : INFINITY;
-            ctl->res[0] = ru;
-            ctl->res[1] = rT;
-            ctl->steps += 1;
-            ctl->cur = cur ^ 1;
-            int status = kRunning;
-            if (isnan(ru) || isnan(rT) || isnan(su) || isnan(sT)) status = kDiverged;
-            else if (fmax(ru, rT) < ctl->tol) status = kConverged;
-            else if (ctl->steps >= ctl->max_steps) status = kMaxSteps;
-            ctl->status = status;
-            if (status != kRunning) ctl->done = 1;
-            for (int q = 0; q < 4; ++q) acc[q] = 0.0;
-            ctl->arrive = 0u;
-            __threadfence();
-        }
+        // the step's residual sums; the next launch tests them
+        for (int q = 0; q < 4; ++q) atomicAdd(&run->acc[slot3][q], a[q]);
     }
 }
 
@@ -749,11 +736,13 @@ void build_lines(const std::vector<double>& f, bool periodic, double kappa, doub
 }
 
 template <class P, int TX, int TY>
-cudaError_t launch_step(int units, int scheme, cudaStream_t s, const Desc3* d, Ctl3* c)
+cudaError_t launch_step(int units, int scheme, cudaStream_t s, const Desc3* d, CavityRun* c,
+                        int par)
 {
     const size_t sm = sizeof(Smem3<P, TX, TY>);
-    if (scheme == 1) return launch_chained(step3_kernel<P, TX, TY, 1>, units, TX * TY, sm, s, d, c);
-    return launch_chained(step3_kernel<P, TX, TY, 0>, units, TX * TY, sm, s, d, c);
+    if (scheme == 1)
+        return launch_chained(step3_kernel<P, TX, TY, 1>, units, TX * TY, sm, s, d, c, par);
+    return launch_chained(step3_kernel<P, TX, TY, 0>, units, TX * TY, sm, s, d, c, par);
 }
 
 // shared-memory opt-in and resident blocks per SM of both face stages
@@ -799,9 +788,10 @@ struct rtlbfs3d_ctx {
     void* d_state = nullptr;  // 2 x (Vec4<S>[cells] + S[cells])
     void* d_lines = nullptr;
     Desc3* d_desc = nullptr;
-    Ctl3* d_ctl = nullptr;
+    CavityRun* d_ctl = nullptr;
     double* d_acc = nullptr;
-    Ctl3* h_ctl = nullptr;  // pinned
+    CavityCtl* h_ctl = nullptr;  // pinned: the tested header h[0]
+    CavityRun* h_run = nullptr;  // pinned: staging of a new run record
     double* h_acc = nullptr;
     size_t cells = 0, ssize = 0;
     // one state buffer: records (rho - 1, u, v, w) then T, each part
@@ -971,40 +961,50 @@ int upload(rtlbfs3d_ctx* h)
     return RTLBFS_OK;
 }
 
-cudaError_t launch_one(rtlbfs3d_ctx* h, cudaStream_t s)
+cudaError_t launch_one(rtlbfs3d_ctx* h, cudaStream_t s, int par)
 {
     const int units = h->desc.units;
     rtlbfs::g_launches++;
     const int sc = h->scheme;
     if (h->precision == RTLBFS_FP64) {
         switch (h->tile) {
-        case 0: return launch_step<StoreD, 32, 4>(units, sc, s, h->d_desc, h->d_ctl);
-        case 1: return launch_step<StoreD, 16, 8>(units, sc, s, h->d_desc, h->d_ctl);
-        default: return launch_step<StoreD, 32, 8>(units, sc, s, h->d_desc, h->d_ctl);
+        case 0: return launch_step<StoreD, 32, 4>(units, sc, s, h->d_desc, h->d_ctl, par);
+        case 1: return launch_step<StoreD, 16, 8>(units, sc, s, h->d_desc, h->d_ctl, par);
+        default: return launch_step<StoreD, 32, 8>(units, sc, s, h->d_desc, h->d_ctl, par);
         }
     }
     switch (h->tile) {
-    case 0: return launch_step<StoreQ, 32, 4>(units, sc, s, h->d_desc, h->d_ctl);
-    case 1: return launch_step<StoreQ, 16, 8>(units, sc, s, h->d_desc, h->d_ctl);
-    default: return launch_step<StoreQ, 32, 8>(units, sc, s, h->d_desc, h->d_ctl);
+    case 0: return launch_step<StoreQ, 32, 4>(units, sc, s, h->d_desc, h->d_ctl, par);
+    case 1: return launch_step<StoreQ, 16, 8>(units, sc, s, h->d_desc, h->d_ctl, par);
+    default: return launch_step<StoreQ, 32, 8>(units, sc, s, h->d_desc, h->d_ctl, par);
     }
+}
+
+// the run record with both headers c and cleared sums (h_ctl becomes c)
+int put_run(rtlbfs3d_ctx* h, const CavityCtl& c)
+{
+    std::memset(h->h_run, 0, sizeof(CavityRun));
+    h->h_run->h[0] = c;
+    h->h_run->h[1] = c;
+    *h->h_ctl = c;
+    CK3(cudaMemcpyAsync(h->d_ctl, h->h_run, sizeof(CavityRun), cudaMemcpyHostToDevice, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));  // h_run is reused
+    return RTLBFS_OK;
 }
 
 // arm the run control for up to nsteps more steps (tol < 0: no early stop)
 int arm(rtlbfs3d_ctx* h, long long nsteps, double tol)
 {
-    CK3(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl3), cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaMemcpyAsync(h->h_ctl, &h->d_ctl->h[0], sizeof(CavityCtl), cudaMemcpyDeviceToHost,
+                        h->stream));
     CK3(cudaStreamSynchronize(h->stream));
-    Ctl3 c = *h->h_ctl;
+    CavityCtl c = *h->h_ctl;
     c.done = 0;
     c.status = kRunning;
-    c.arrive = 0;
+    c.pend = 0;
     c.max_steps = c.steps + nsteps;
     c.tol = tol;
-    for (int q = 0; q < 4; ++q) c.acc[q] = 0.0;
-    *h->h_ctl = c;
-    CK3(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(Ctl3), cudaMemcpyHostToDevice, h->stream));
-    return RTLBFS_OK;
+    return put_run(h, c);
 }
 
 int ensure_graph(rtlbfs3d_ctx* h)
@@ -1017,7 +1017,8 @@ int ensure_graph(rtlbfs3d_ctx* h)
     }
     CK3(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_one(h, h->cap);
+    static_assert(kGraphSteps % 2 == 0, "graphs of an even number of launches");
+    for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_one(h, h->cap, i & 1);
     rtlbfs::g_launches -= kGraphSteps;  // captured, not launched
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->cap, &g);
@@ -1037,21 +1038,28 @@ int launch_steps(rtlbfs3d_ctx* h, long long count)
 {
     int rc = ensure_graph(h);
     if (rc) return rc;
+    // launch k of the chain has parity k & 1; the chain ends with the stop
+    // test of its last step
+    int par = 0;
     while (count >= kGraphSteps) {
         CK3(cudaGraphLaunch(h->gexec, h->stream));
         rtlbfs::g_launches += kGraphSteps;
         count -= kGraphSteps;
     }
     for (long long i = 0; i < count; ++i) {
-        cudaError_t e = launch_one(h, h->stream);
+        cudaError_t e = launch_one(h, h->stream, par);
         if (e != cudaSuccess) return h->cuda_fail(e, "step launch");
+        par ^= 1;
     }
+    CK3(rtlbfs::launch_finalize(h->stream, h->d_ctl, 1, par));
+    rtlbfs::g_launches++;
     return RTLBFS_OK;
 }
 
 int read_ctl(rtlbfs3d_ctx* h)
 {
-    CK3(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl3), cudaMemcpyDeviceToHost, h->stream));
+    CK3(cudaMemcpyAsync(h->h_ctl, &h->d_ctl->h[0], sizeof(CavityCtl), cudaMemcpyDeviceToHost,
+                        h->stream));
     CK3(cudaStreamSynchronize(h->stream));
     return RTLBFS_OK;
 }
@@ -1111,14 +1119,16 @@ int rtlbfs3d_create(int nx, int ny, int nz, const double* xf, const double* yf, 
     h->stream = h->own;
     if (cudaMalloc(&h->d_state, 2 * h->buf_bytes) != cudaSuccess) return bail(RTLBFS_ERR_OOM);
     if (cudaMalloc(&h->d_desc, sizeof(Desc3)) != cudaSuccess ||
-        cudaMalloc(&h->d_ctl, sizeof(Ctl3)) != cudaSuccess ||
+        cudaMalloc(&h->d_ctl, sizeof(CavityRun)) != cudaSuccess ||
         cudaMalloc(&h->d_acc, sizeof(double)) != cudaSuccess)
         return bail(RTLBFS_ERR_OOM);
-    if (cudaMallocHost(&h->h_ctl, sizeof(Ctl3)) != cudaSuccess ||
+    if (cudaMallocHost(&h->h_ctl, sizeof(CavityCtl)) != cudaSuccess ||
+        cudaMallocHost(&h->h_run, sizeof(CavityRun)) != cudaSuccess ||
         cudaMallocHost(&h->h_acc, sizeof(double)) != cudaSuccess)
         return bail(RTLBFS_ERR_OOM);
-    std::memset(h->h_ctl, 0, sizeof(Ctl3));
-    if (cudaMemcpy(h->d_ctl, h->h_ctl, sizeof(Ctl3), cudaMemcpyHostToDevice) != cudaSuccess)
+    std::memset(h->h_run, 0, sizeof(CavityRun));
+    std::memset(h->h_ctl, 0, sizeof(CavityCtl));
+    if (cudaMemcpy(h->d_ctl, h->h_run, sizeof(CavityRun), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(RTLBFS_ERR_CUDA);
     // default state: rest, rho = 1, T linear in x between the walls
     {
@@ -1243,10 +1253,10 @@ int rtlbfs3d_set_state(rtlbfs3d_t h, const double* rho, const double* u, const d
     }
     CK3(cudaStreamSynchronize(h->stream));
     CK3(cudaMemcpy(h->d_state, buf.data(), buf.size(), cudaMemcpyHostToDevice));
-    std::memset(h->h_ctl, 0, sizeof(Ctl3));
-    h->h_ctl->res[0] = h->h_ctl->res[1] = INFINITY;
-    CK3(cudaMemcpy(h->d_ctl, h->h_ctl, sizeof(Ctl3), cudaMemcpyHostToDevice));
-    return RTLBFS_OK;
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.res[0] = z.res[1] = INFINITY;
+    return put_run(h, z);
 }
 
 int rtlbfs3d_get_state(rtlbfs3d_t h, double* rho, double* u, double* v, double* w, double* T)
@@ -1328,7 +1338,7 @@ int rtlbfs3d_run_to_steady(rtlbfs3d_t h, double tol, long max_steps, double time
         }
         rc = read_ctl(h);
         if (rc) return rc;
-        const Ctl3& c = *h->h_ctl;
+        const CavityCtl& c = *h->h_ctl;
         if (c.done || queued >= max_steps) {
             if (c.status == kConverged)
                 out = RTLBFS_OK;
@@ -1347,11 +1357,14 @@ int rtlbfs3d_run_to_steady(rtlbfs3d_t h, double tol, long max_steps, double time
         }
     }
     // stop any remaining armed steps from running later
-    h->h_ctl->done = 1;
-    CK3(cudaMemcpyAsync(&h->d_ctl->done, &h->h_ctl->done, sizeof(int), cudaMemcpyHostToDevice,
-                        h->stream));
     rc = read_ctl(h);
     if (rc) return rc;
+    {
+        CavityCtl c = *h->h_ctl;
+        c.done = 1;
+        rc = put_run(h, c);
+        if (rc) return rc;
+    }
     if (steps_taken) *steps_taken = (long)(h->h_ctl->steps - start);
     if (res2) {
         res2[0] = h->h_ctl->res[0];
@@ -1467,7 +1480,7 @@ int rtlbfs3d_autotune(rtlbfs3d_t h, int steps, int* tile, double* ms_per_step)
     void* snap = nullptr;
     CK3(cudaStreamSynchronize(h->stream));
     CK3(cudaMalloc(&snap, bytes));
-    Ctl3 saved;
+    CavityCtl saved;
     int rc = read_ctl(h);
     if (rc) {
         cudaFree(snap);
@@ -1508,8 +1521,10 @@ int rtlbfs3d_autotune(rtlbfs3d_t h, int steps, int* tile, double* ms_per_step)
     cudaStreamSynchronize(h->stream);
     cudaMemcpy(h->d_state, snap, bytes, cudaMemcpyDeviceToDevice);
     cudaFree(snap);
-    *h->h_ctl = saved;
-    cudaMemcpy(h->d_ctl, h->h_ctl, sizeof(Ctl3), cudaMemcpyHostToDevice);
+    {
+        const int prc = put_run(h, saved);
+        if (!rc) rc = prc;
+    }
     if (rc) return rc;
     h->tile = best;
     h->dirty = true;
@@ -1548,6 +1563,7 @@ void rtlbfs3d_destroy(rtlbfs3d_t h)
     cudaFree(h->d_ctl);
     cudaFree(h->d_acc);
     cudaFreeHost(h->h_ctl);
+    cudaFreeHost(h->h_run);
     cudaFreeHost(h->h_acc);
     if (h->own) cudaStreamDestroy(h->own);
     if (h->cap) cudaStreamDestroy(h->cap);

@@ -38,6 +38,7 @@
 #include "rtlbfs.h"
 #include "rtlbfs_curv.h"
 #include "rtlbfs_dev.cuh"
+#include "rtlbfs_kernels.h"
 
 namespace rtlbfs {
 extern std::atomic<long long> g_launches;
@@ -141,14 +142,10 @@ struct DescC {
     const void* ia_d;
 };
 
-struct CtlC {
-    int cur, done, status;
-    unsigned int arrive;
-    long long steps, max_steps;
-    double tol;
-    double res[2];
-    double acc[4];
-};
+// Run control: the two-header record of the rectilinear solver (the stop
+// test of step k is made by the launch of step k + 1; see CavityRun).
+using rtlbfs::CavityCtl;
+using rtlbfs::CavityRun;
 
 template <class P>
 struct CstC;
@@ -324,11 +321,12 @@ struct SmemC {
     R v[4][BY][BX];
     R dta[TY][TX];
     R red[NT / 32][4];  // per-warp residual partials
+    int plan[3];        // after the stop test: done, cur, sum slot
 };
 
 template <class P, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restrict__ dp,
-                                                           CtlC* __restrict__ ctl)
+                                                           CavityRun* __restrict__ run, int par)
 {
     using S = typename P::S;
     using R = typename P::R;
@@ -376,11 +374,21 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
     cp_async_commit();
 
     chain_sync();
-    if (ctl->done) {  // uniform: written by the previous launch
+    // the stop test of the previous step (thread 0; unit 0 publishes the
+    // header for the next launch)
+    if (tid == 0) {
+        const CavityCtl dc = rtlbfs::run_head(run, par);
+        if (blockIdx.x == 0) rtlbfs::run_publish(run, par, dc);
+        sm.plan[0] = dc.done;
+        sm.plan[1] = dc.cur;
+        sm.plan[2] = (int)(dc.steps % 3);
+    }
+    __syncthreads();
+    if (sm.plan[0]) {  // uniform
         cp_async_wait_all();
         return;
     }
-    const int cur = ctl->cur;
+    const int cur = sm.plan[1], slot3 = sm.plan[2];
     const Vec4<S>* __restrict__ rin = static_cast<const Vec4<S>*>(d.rec[cur]);
     Vec4<S>* __restrict__ rout = static_cast<Vec4<S>*>(d.rec[cur ^ 1]);
     const S qTz = rin[(size_t)min(j0 + TY / 2, nj - 1) * ni + min(i0 + TX / 2, ni - 1)].w;
@@ -560,31 +568,9 @@ __global__ void __launch_bounds__(TX* TY) curv_step_kernel(const DescC* __restri
             acc4[q] = (double)v;
         }
     }
-    if (tid == 0) {
-        for (int q = 0; q < 4; ++q) atomicAdd(&ctl->acc[q], acc4[q]);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-        if (prev == (unsigned)d.units - 1u) {
-            __threadfence();
-            volatile double* acc = ctl->acc;
-            const double su = acc[0], du = acc[1], sT = acc[2], dT = acc[3];
-            const double ru = du > 0.0 ? sqrt(su) / sqrt(du) : INFINITY;
-            const double rT = dT > 0.0 ? sqrt(sT) / sqrt(dT) : INFINITY;
-            ctl->res[0] = ru;
-            ctl->res[1] = rT;
-            ctl->steps += 1;
-            ctl->cur = cur ^ 1;
-            int status = kRunning;
-            if (isnan(ru) || isnan(rT) || isnan(su) || isnan(sT)) status = kDiverged;
-            else if (fmax(ru, rT) < ctl->tol) status = kConverged;
-            else if (ctl->steps >= ctl->max_steps) status = kMaxSteps;
-            ctl->status = status;
-            if (status != kRunning) ctl->done = 1;
-            for (int q = 0; q < 4; ++q) acc[q] = 0.0;
-            ctl->arrive = 0u;
-            __threadfence();
-        }
-    }
+    // the step's residual sums; the next launch tests them
+    if (tid == 0)
+        for (int q = 0; q < 4; ++q) atomicAdd(&run->acc[slot3][q], acc4[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,10 +665,10 @@ constexpr int kTileX = 32;
 constexpr int kGraphSteps = 32;
 
 template <class P, int TY>
-cudaError_t launch_c(int units, cudaStream_t s, const DescC* d, CtlC* c)
+cudaError_t launch_c(int units, cudaStream_t s, const DescC* d, CavityRun* c, int par)
 {
     const size_t sm = sizeof(SmemC<P, kTileX, TY>);
-    return launch_chained(curv_step_kernel<P, kTileX, TY>, units, kTileX * TY, sm, s, d, c);
+    return launch_chained(curv_step_kernel<P, kTileX, TY>, units, kTileX * TY, sm, s, d, c, par);
 }
 
 template <class P, int TY>
@@ -715,9 +701,10 @@ struct rtlbfsc_ctx {
     void* d_state = nullptr;
     void* d_geo = nullptr;
     DescC* d_desc = nullptr;
-    CtlC* d_ctl = nullptr;
+    CavityRun* d_ctl = nullptr;
     double* d_acc = nullptr;
-    CtlC* h_ctl = nullptr;
+    CavityCtl* h_ctl = nullptr;  // pinned: the tested header h[0]
+    CavityRun* h_run = nullptr;  // pinned: staging of a new run record
     double* h_acc = nullptr;
     DescC desc{};
     bool dirty = true;
@@ -995,21 +982,34 @@ int upload(rtlbfsc_ctx* h)
     return RTLBFS_OK;
 }
 
-cudaError_t launch_one(rtlbfsc_ctx* h, cudaStream_t s)
+cudaError_t launch_one(rtlbfsc_ctx* h, cudaStream_t s, int par)
 {
     rtlbfs::g_launches++;
     const int ty = tile_rows_of(h);
     if (h->precision == RTLBFS_FP64)
-        return ty == 16 ? launch_c<StoreD, 16>(h->desc.units, s, h->d_desc, h->d_ctl)
-                        : launch_c<StoreD, 8>(h->desc.units, s, h->d_desc, h->d_ctl);
-    return ty == 16 ? launch_c<StoreQ, 16>(h->desc.units, s, h->d_desc, h->d_ctl)
-                    : launch_c<StoreQ, 8>(h->desc.units, s, h->d_desc, h->d_ctl);
+        return ty == 16 ? launch_c<StoreD, 16>(h->desc.units, s, h->d_desc, h->d_ctl, par)
+                        : launch_c<StoreD, 8>(h->desc.units, s, h->d_desc, h->d_ctl, par);
+    return ty == 16 ? launch_c<StoreQ, 16>(h->desc.units, s, h->d_desc, h->d_ctl, par)
+                    : launch_c<StoreQ, 8>(h->desc.units, s, h->d_desc, h->d_ctl, par);
 }
 
 int read_ctl(rtlbfsc_ctx* h)
 {
-    CKC(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(CtlC), cudaMemcpyDeviceToHost, h->stream));
+    CKC(cudaMemcpyAsync(h->h_ctl, &h->d_ctl->h[0], sizeof(CavityCtl), cudaMemcpyDeviceToHost,
+                        h->stream));
     CKC(cudaStreamSynchronize(h->stream));
+    return RTLBFS_OK;
+}
+
+// the run record with both headers c and cleared sums (h_ctl becomes c)
+int put_run(rtlbfsc_ctx* h, const CavityCtl& c)
+{
+    std::memset(h->h_run, 0, sizeof(CavityRun));
+    h->h_run->h[0] = c;
+    h->h_run->h[1] = c;
+    *h->h_ctl = c;
+    CKC(cudaMemcpyAsync(h->d_ctl, h->h_run, sizeof(CavityRun), cudaMemcpyHostToDevice, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));  // h_run is reused
     return RTLBFS_OK;
 }
 
@@ -1017,16 +1017,13 @@ int arm(rtlbfsc_ctx* h, long long nsteps, double tol)
 {
     int rc = read_ctl(h);
     if (rc) return rc;
-    CtlC c = *h->h_ctl;
+    CavityCtl c = *h->h_ctl;
     c.done = 0;
     c.status = kRunning;
-    c.arrive = 0;
+    c.pend = 0;
     c.max_steps = c.steps + nsteps;
     c.tol = tol;
-    for (int q = 0; q < 4; ++q) c.acc[q] = 0.0;
-    *h->h_ctl = c;
-    CKC(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(CtlC), cudaMemcpyHostToDevice, h->stream));
-    return RTLBFS_OK;
+    return put_run(h, c);
 }
 
 int launch_steps(rtlbfsc_ctx* h, long long count)
@@ -1039,7 +1036,8 @@ int launch_steps(rtlbfsc_ctx* h, long long count)
         }
         CKC(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
-        for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_one(h, h->cap);
+        static_assert(kGraphSteps % 2 == 0, "graphs of an even number of launches");
+        for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_one(h, h->cap, i & 1);
         rtlbfs::g_launches -= kGraphSteps;
         cudaGraph_t g = nullptr;
         cudaError_t ee = cudaStreamEndCapture(h->cap, &g);
@@ -1051,15 +1049,21 @@ int launch_steps(rtlbfsc_ctx* h, long long count)
         h->gunits = h->desc.units;
         h->gty = ty;
     }
+    // launch k of the chain has parity k & 1; the chain ends with the stop
+    // test of its last step
+    int par = 0;
     while (count >= kGraphSteps) {
         CKC(cudaGraphLaunch(h->gexec, h->stream));
         rtlbfs::g_launches += kGraphSteps;
         count -= kGraphSteps;
     }
     for (long long i = 0; i < count; ++i) {
-        cudaError_t e = launch_one(h, h->stream);
+        cudaError_t e = launch_one(h, h->stream, par);
         if (e != cudaSuccess) return h->cuda_fail(e, "step launch");
+        par ^= 1;
     }
+    CKC(rtlbfs::launch_finalize(h->stream, h->d_ctl, 1, par));
+    rtlbfs::g_launches++;
     return RTLBFS_OK;
 }
 
@@ -1108,10 +1112,11 @@ int rtlbfsc_create(int ni, int nj, const double* X, const double* Y, int periodi
     h->stream = h->own;
     if (cudaMalloc(&h->d_state, 2 * h->buf_bytes) != cudaSuccess ||
         cudaMalloc(&h->d_desc, sizeof(DescC)) != cudaSuccess ||
-        cudaMalloc(&h->d_ctl, sizeof(CtlC)) != cudaSuccess ||
+        cudaMalloc(&h->d_ctl, sizeof(CavityRun)) != cudaSuccess ||
         cudaMalloc(&h->d_acc, sizeof(double)) != cudaSuccess)
         return bail(RTLBFS_ERR_OOM);
-    if (cudaMallocHost(&h->h_ctl, sizeof(CtlC)) != cudaSuccess ||
+    if (cudaMallocHost(&h->h_ctl, sizeof(CavityCtl)) != cudaSuccess ||
+        cudaMallocHost(&h->h_run, sizeof(CavityRun)) != cudaSuccess ||
         cudaMallocHost(&h->h_acc, sizeof(double)) != cudaSuccess)
         return bail(RTLBFS_ERR_OOM);
     std::vector<double> one(h->cells, 1.0), zero(h->cells, 0.0);
@@ -1221,10 +1226,10 @@ int rtlbfsc_set_state(rtlbfsc_t h, const double* rho, const double* u, const dou
     }
     CKC(cudaStreamSynchronize(h->stream));
     CKC(cudaMemcpy(h->d_state, buf.data(), buf.size(), cudaMemcpyHostToDevice));
-    std::memset(h->h_ctl, 0, sizeof(CtlC));
-    h->h_ctl->res[0] = h->h_ctl->res[1] = INFINITY;
-    CKC(cudaMemcpy(h->d_ctl, h->h_ctl, sizeof(CtlC), cudaMemcpyHostToDevice));
-    return RTLBFS_OK;
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.res[0] = z.res[1] = INFINITY;
+    return put_run(h, z);
 }
 
 int rtlbfsc_get_state(rtlbfsc_t h, double* rho, double* u, double* v, double* T)
@@ -1294,7 +1299,7 @@ int rtlbfsc_run_to_steady(rtlbfsc_t h, double tol, long max_steps, double timeou
         }
         rc = read_ctl(h);
         if (rc) return rc;
-        const CtlC& c = *h->h_ctl;
+        const CavityCtl& c = *h->h_ctl;
         if (c.done || queued >= max_steps) {
             if (c.status == kConverged)
                 out = RTLBFS_OK;
@@ -1310,11 +1315,15 @@ int rtlbfsc_run_to_steady(rtlbfsc_t h, double tol, long max_steps, double timeou
             break;
         }
     }
-    h->h_ctl->done = 1;
-    CKC(cudaMemcpyAsync(&h->d_ctl->done, &h->h_ctl->done, sizeof(int), cudaMemcpyHostToDevice,
-                        h->stream));
+    // stop any remaining armed steps from running later
     rc = read_ctl(h);
     if (rc) return rc;
+    {
+        CavityCtl c = *h->h_ctl;
+        c.done = 1;
+        rc = put_run(h, c);
+        if (rc) return rc;
+    }
     if (steps_taken) *steps_taken = (long)(h->h_ctl->steps - start);
     if (res2) {
         res2[0] = h->h_ctl->res[0];
@@ -1403,6 +1412,7 @@ void rtlbfsc_destroy(rtlbfsc_t h)
     cudaFree(h->d_ctl);
     cudaFree(h->d_acc);
     cudaFreeHost(h->h_ctl);
+    cudaFreeHost(h->h_run);
     cudaFreeHost(h->h_acc);
     if (h->own) cudaStreamDestroy(h->own);
     if (h->cap) cudaStreamDestroy(h->cap);

@@ -325,6 +325,9 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     constexpr int CPT = TX * TY / NT;
     constexpr int CW = TX / CPT;
     static_assert(CPT * NT == TX * TY && CW * CPT == TX && CW * TY == NT, "thread layout");
+    // the gradient and face loops unrolled where that stays within the
+    // register budget of four resident blocks (FP32 tiles of 4+ rows)
+    constexpr int UNROLL = (sizeof(R) == 4 && TY >= 4) ? 8 : 1;
     const int tid = threadIdx.x;
     const int tc = tid % CW, tr = tid / CW;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
@@ -409,7 +412,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     {
         constexpr int NGR = GX * GY - TX * TY;
         constexpr int GQ = CPT + (NGR + NT - 1) / NT;
-#pragma unroll 1
+#pragma unroll(UNROLL)
         for (int k = 0; k < GQ; ++k) {
             int gc, gr;
             if (k < CPT) {
@@ -488,7 +491,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
         using XF = std::true_type;
         using YF = std::false_type;
         constexpr int TQ = (TX + TY + NT - 1) / NT;  // rounds of the east/north faces
-#pragma unroll 1
+#pragma unroll(UNROLL)
         for (int k = 0; k < CPT + TQ; ++k) {
             int fc = tc + k * CW, fr = tr;
             if (k >= CPT) {
@@ -499,7 +502,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             }
             face(XF(), fc, fr);
         }
-#pragma unroll 1
+#pragma unroll(UNROLL)
         for (int k = 0; k < CPT + TQ; ++k) {
             int fc = tc + k * CW, fr = tr;
             if (k >= CPT) {
