@@ -86,6 +86,12 @@ WORKLOADS = {
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 1.07 GB per buffer, > L2)",
         nx=8192, ny=8192, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=10,
         kind="cavity"),
+    "cavity8192_strips": dict(
+        desc="one mesh over N GPUs: the 8192x8192 tanh (phi=2.0) cavity, Ra=1e8, Pr=0.71, "
+             "Ma=0.1, FP32 bulk + FP64 reductions, split into N row strips (one per GPU) that "
+             "exchange their two boundary rows before every step; N = 1: the whole mesh",
+        nx=8192, ny=8192, phi=2.0, Ra=1e8, Pr=0.71, Ma=0.1, precision="fp32", inner=10,
+        kind="strips"),
     "cavity4096": dict(
         desc="profiling case: differentially heated cavity 4096x4096, tanh phi=2.0, Ra=1e8, "
              "Pr=0.71, Ma=0.1, FP32 bulk + FP64 reductions (state 268 MB per buffer, > L2)",
@@ -1327,6 +1333,8 @@ def run_ours(args, w):
         return run_batch(args, w)
     if w.get("kind") == "serve":
         return run_serve(args, w)
+    if w.get("kind") == "strips":
+        return run_strips(args, w)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -1444,10 +1452,125 @@ def run_ours(args, w):
         print(json.dumps(line), flush=True)
 
 
+def run_strips(args, w):
+    """One mesh split by rows over the ranks (strong scaling): rank r steps
+    rows split_rows(ny, N)[r] and exchanges its two boundary rows with its
+    neighbours before every step (host planes over gloo; the state and the
+    residual stay on each GPU).  value = the mesh's cell-updates / the
+    slowest rank's device time, exchanges included."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("cpu:gloo,cuda:nccl", device_id=torch.device("cuda", local))
+    from paper_2202_13449_gb300 import capi, strips
+    capi.lib()
+    nx, ny = w["nx"], w["ny"]
+    xf = capi.tanh_faces(nx, float(nx), w["phi"])
+    yf = capi.tanh_faces(ny, float(ny), w["phi"])
+    j0, j1 = strips.split_rows(ny, ws)[rank]
+    s = capi.Solver(xf, yf, capi.FP32 if w["precision"] == "fp32" else capi.FP64, rows=(j0, j1))
+    dt = 0.5 * float(min(np.min(np.diff(xf)), np.min(np.diff(yf))))
+    s.set_params(w["Ra"], w["Pr"], w["Ma"], dt)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s.set_stream(stream)
+    sched = s.autotune(16) if args.schedule == "auto" else None
+    ex = strips.StripExchange(rank, ws, nx, mode="host", timeout_s=120.0) if ws > 1 else None
+    inner = args.inner or w["inner"]
+    cells_mine = nx * (j1 - j0)
+    state = {"k": 0}
+
+    def steps(n):
+        for _ in range(n):
+            if ex is not None:
+                ex.exchange(s, state["k"])
+            s.step(1)
+            state["k"] += 1
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        steps(inner)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = capi.launch_count()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        steps(inner)
+        b.record(stream)
+        ev.append((a, b))
+    barrier()
+    launches = capi.launch_count() - l0
+    clocks = clk.stop()
+    ms_max = job_max(sum(a.elapsed_time(b) for a, b in ev))
+    updates = nx * ny * inner * args.steps
+    value = updates / (ms_max * 1e-3) / 1e6
+    sums, _ = s.residual_sums()
+    res = strips.global_residual(sums)
+    # e2e: each rank's strip state up from pinned host buffers and down again
+    host = pinned([np.ones((j1 - j0, nx)), np.zeros((j1 - j0, nx)), np.zeros((j1 - j0, nx)),
+                   np.tile(1.0 - (0.5 * (xf[1:] + xf[:-1]) / xf[-1]), (j1 - j0, 1))])
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        s.set_state(*host)
+        state["k"] = 0
+        steps(inner)
+        out = s.get_state()
+    torch.cuda.synchronize()
+    e2e = nx * ny * inner * 2 / job_max(time.perf_counter() - t0) / 1e6
+    assert np.all(np.isfinite(out[3]))
+    per_step_s = ms_max * 1e-3 / (inner * args.steps)
+    kname = SCHED_KERNELS[sched[0]] if sched else "rtlbfs::march_kernel"
+    alu, hbm = rooflines(kname, cells_mine, per_step_s, 4, None, clocks)
+    line = {
+        "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
+        "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "cells": nx * ny,
+                   "time_steps_per_bench_step": inner,
+                   "parallelism": f"row strips x{ws} (2-row halo exchange per step, gloo)",
+                   "rows_rank0": list(strips.split_rows(ny, ws)[0]),
+                   "l2": "flushed between bench steps (256 MB write)",
+                   "schedule": ({"kernel": SCHED_NAMES[sched[0]], "chunk_rows": sched[1]}
+                                if sched else args.schedule)},
+        "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
+                "h2d_bytes_per_step": 32 * nx * ny, "d2h_bytes_per_step": 32 * nx * ny},
+        "gpu_launches": int(job_sum(launches)),
+        "roofline": alu, "roofline_hbm": hbm,
+        "roofline_note": "per GPU, its strip's cell-updates over the job's time per step "
+                         "(halo exchanges included)",
+        "clocks": clocks,
+        "residual_last_step": list(res),
+    }
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def oracle_problem(oracle, inputs, w):
     import numpy as np
     nx, ny = w["nx"], w["ny"]
-    if w["kind"] == "cavity":
+    if w["kind"] in ("cavity", "strips"):
         xf = oracle.tanh_faces(nx, float(nx), w["phi"])
         yf = oracle.tanh_faces(ny, float(ny), w["phi"])
         nu, chi, bg = oracle.params_from_ra(w["Ra"], w["Pr"], w["Ma"], float(nx))

@@ -77,6 +77,7 @@ extern "C" {
 #define RTLBFS_WALL_DIRICHLET 0 /* no-slip wall, fixed temperature */
 #define RTLBFS_WALL_ADIABATIC 1 /* no-slip wall, zero heat flux */
 #define RTLBFS_PERIODIC 2       /* must be set on both opposite sides */
+#define RTLBFS_HALO 3           /* a row strip's inner side (rtlbfs_create_strip only) */
 
 /* Nusselt selectors of rtlbfs_nusselt */
 #define RTLBFS_NU_WEST 0  /* energy flux through the west wall / (chi dT) */
@@ -322,6 +323,86 @@ int rtlbfs_nusselt_noalloc(int nx, int ny, const double* xf, const double* yf,
                            double nu, double chi, double kappa, double dT, const int* bc_kind,
                            const double* bc_T, const double* bc_u, int which, double* nu_out,
                            void* stream);
+
+/*
+ * Row strips: one mesh split across GPUs (or processes) by rows.  The
+ * explicit step (Section 3.2) reads each cell's neighbours up to two cells
+ * away: a face needs the Green-Gauss gradients (Eq. 55) of its two cells,
+ * and a gradient needs the values of the cell's neighbours (Eq. 56).  So a
+ * strip of rows j0 <= j < j1 can take a step once it holds the two rows
+ * beyond each of its inner sides, as they were after the previous step.
+ * Exchanging those two rows between neighbouring strips before every step
+ * gives exactly the step of the whole mesh.  The paper has no counterpart
+ * (it runs serial programs); this is the decomposition of the sweep.
+ *
+ * rtlbfs_create_strip: a handle for rows j0 <= j < j1 (j1 - j0 >= 2) of
+ * an nx x ny_mesh mesh with faces xf[0..nx], yf[0..ny_mesh] (the whole
+ * mesh's faces; copied).  Its south side (if j0 > 0) and north side (if
+ * j1 < ny_mesh) are halo sides: no wall, the two rows beyond are set by
+ * rtlbfs_strip_set_halo (or written to the device addresses of
+ * rtlbfs_strip_rows) before each step.  The other sides behave as in
+ * rtlbfs_create_mesh (walls by rtlbfs_set_bc); parameters, the dt rule
+ * (smallest cell of the whole mesh) and the reference length (the x width)
+ * are those of the whole mesh.  Fields of the strip's own rows are (j1 -
+ * j0) x nx.  Nusselt numbers of a strip are its share of the whole
+ * mesh's (west, east, mid-plane and Eq. 69 sums add over strips; south and
+ * north only where that side is a wall); they read the halo rows too, so
+ * exchange halos after the last step before taking them.  Stepping takes whole steps; the
+ * stop test of rtlbfs_run_to_steady would see one strip only, so a
+ * decomposed run sums rtlbfs_residual_sums over the strips instead.
+ * ERR_ARG on bad sizes or faces.
+ */
+int rtlbfs_create_strip(int nx, int ny_mesh, const double* xf, const double* yf, int j0, int j1,
+                        int precision, rtlbfs_t* out);
+
+/* The strip's two rows next to side (RTLBFS_SOUTH: rows j0, j0 + 1;
+ * RTLBFS_NORTH: rows j1 - 2, j1 - 1) of the current state as four planes
+ * rho, u, v, T of 2 x nx doubles each (row-major, southern row first):
+ * what the neighbour across that side needs.  rows: host, caller-owned,
+ * 8 x nx doubles.  ERR_ARG if side is not a halo side. */
+int rtlbfs_strip_get_rows(rtlbfs_t h, int side, double* rows);
+
+/* Set the two halo rows beyond side (RTLBFS_SOUTH: rows j0 - 2, j0 - 1;
+ * RTLBFS_NORTH: rows j1, j1 + 1) of the current state from planes in the
+ * layout of rtlbfs_strip_get_rows (the neighbour's rows as it returned
+ * them).  ERR_ARG if side is not a halo side or (FP32) a value is not
+ * representable. */
+int rtlbfs_strip_set_halo(rtlbfs_t h, int side, const double* rows);
+
+/* Device address and size (*bytes) of the two rows next to side (halo =
+ * 0: the strip's own rows; 1: the halo rows beyond) in state buffer
+ * `buffer` (0 or 1), in the device record layout (cell records, row pitch
+ * included; the two rows are contiguous).  For exchanges between devices
+ * (NCCL send/recv, peer copies) without the host: a step reads buffer
+ * rtlbfs_current_buffer() and writes the other one, so before the next
+ * step the own rows of the new current buffer go to the neighbour's halo
+ * rows of its new current buffer (same record layout and size when both
+ * strips have the same nx and precision; in FP32 the strips must also store
+ * temperature in the same unit, see RTLBFS_FP32, which holds when their
+ * configured temperatures set it).  The library owns the memory. */
+int rtlbfs_strip_rows(rtlbfs_t h, int side, int halo, int buffer, void** dev, size_t* bytes);
+
+/* Copy the strip's own two rows next to side in state buffer `buffer` to
+ * the device buffer dev (rtlbfs_strip_rows' bytes, caller-owned device
+ * memory), or copy dev into the halo rows beyond side of that buffer:
+ * device-to-device copies queued on the handle's stream (no host wait, no
+ * allocation).  With the strips' steps counted from a state upload, the
+ * current buffer after k steps is k % 2, so a caller can exchange halos
+ * through its own device buffers (NCCL send/recv or peer copies) without
+ * reading the run control.  ERR_ARG if side is not a halo side. */
+int rtlbfs_strip_pack(rtlbfs_t h, int side, int buffer, void* dev);
+int rtlbfs_strip_unpack(rtlbfs_t h, int side, int buffer, const void* dev);
+
+/* The state buffer (0 or 1) holding the current state. */
+int rtlbfs_current_buffer(rtlbfs_t h, int* buffer);
+
+/* The residual sums of the last step (the sums behind R12, Eq. 65's L2
+ * analogue): sums[0] = sum (|u|^{n+1} - |u|^n)^2, sums[1] = sum
+ * |u|^{n+1}^2, sums[2] = sum (T^{n+1} - T^n)^2, sums[3] = sum T^{n+1}^2
+ * over the handle's cells, FP64; summed over the strips of a mesh they give
+ * R_u = sqrt(s0 / s1), R_T = sqrt(s2 / s3) of the whole mesh.  *steps: the
+ * step count (may be null). */
+int rtlbfs_residual_sums(rtlbfs_t h, double* sums, long* steps);
 
 /* Number of kernel launches issued by the library since load (for the
  * benchmark's launch count). */

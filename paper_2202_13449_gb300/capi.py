@@ -21,7 +21,7 @@ ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_ST
 FP64, FP32 = 0, 1
 RTLBFS, TLBFS = 0, 1  # face stages (set_scheme)
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
-WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC = 0, 1, 2
+WALL_DIRICHLET, WALL_ADIABATIC, PERIODIC, HALO = 0, 1, 2, 3
 NU_WEST, NU_EAST, NU_SOUTH, NU_NORTH, NU_AVG, NU_HALF = 0, 1, 2, 3, 4, 5
 
 HEADER = os.path.join(_build.ROOT, "include", "rtlbfs.h")
@@ -57,6 +57,16 @@ _SIGS = {
     "rtlbfs_tanh_faces": (C.c_int, [C.c_int, C.c_double, C.c_double, _dp]),
     "rtlbfs_create_mesh": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_int, C.POINTER(_vp)]),
     "rtlbfs_set_params": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "rtlbfs_create_strip": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_int,
+                                      C.POINTER(_vp)]),
+    "rtlbfs_strip_get_rows": (C.c_int, [_vp, C.c_int, _dp]),
+    "rtlbfs_strip_set_halo": (C.c_int, [_vp, C.c_int, _dp]),
+    "rtlbfs_strip_rows": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(_vp),
+                                    C.POINTER(C.c_size_t)]),
+    "rtlbfs_current_buffer": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "rtlbfs_strip_pack": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    "rtlbfs_strip_unpack": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    "rtlbfs_residual_sums": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
     "rtlbfs_set_params_ref": (C.c_int, [_vp] + [C.c_double] * 7),
     "rtlbfs_set_lattice": (C.c_int, [_vp, C.c_double]),
     "rtlbfs_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double]),
@@ -260,20 +270,75 @@ def op_counts(scheme: int = 0):
 
 
 class Solver:
-    """One cavity on the GPU (a handle of ``include/rtlbfs.h``)."""
+    """One cavity on the GPU (a handle of ``include/rtlbfs.h``).  With
+    ``rows=(j0, j1)`` the handle is the row strip j0 <= j < j1 of the mesh
+    (rtlbfs_create_strip): its fields are (j1 - j0) x nx."""
 
-    def __init__(self, xf, yf, precision: int = FP64):
+    def __init__(self, xf, yf, precision: int = FP64, rows=None):
         L = lib()
         self.xf = np.ascontiguousarray(xf, dtype=np.float64)
         self.yf = np.ascontiguousarray(yf, dtype=np.float64)
         self.nx, self.ny = len(self.xf) - 1, len(self.yf) - 1
         self.precision = precision
+        self.rows = None
         h = _vp()
-        rc = L.rtlbfs_create_mesh(self.nx, self.ny, _ptr(self.xf), _ptr(self.yf), int(precision),
-                                  C.byref(h))
+        if rows is None:
+            rc = L.rtlbfs_create_mesh(self.nx, self.ny, _ptr(self.xf), _ptr(self.yf),
+                                      int(precision), C.byref(h))
+        else:
+            j0, j1 = int(rows[0]), int(rows[1])
+            rc = L.rtlbfs_create_strip(self.nx, self.ny, _ptr(self.xf), _ptr(self.yf), j0, j1,
+                                       int(precision), C.byref(h))
+            self.rows = (j0, j1)
+            self.ny = j1 - j0
         if rc:
-            raise RTLBFSError(rc, "rtlbfs_create_mesh")
+            raise RTLBFSError(rc, "rtlbfs_create_mesh" if rows is None else "rtlbfs_create_strip")
         self._h = h
+
+    # -- row strips (rtlbfs_create_strip)
+    def strip_get_rows(self, side: int) -> np.ndarray:
+        """The strip's two rows next to `side` as an array (4, 2, nx)."""
+        out = np.empty(8 * self.nx)
+        self._check(lib().rtlbfs_strip_get_rows(self._h, int(side), _ptr(out)), "strip_get_rows")
+        return out.reshape(4, 2, self.nx)
+
+    def strip_set_halo(self, side: int, rows):
+        """Set the two halo rows beyond `side` from an array (4, 2, nx)."""
+        a = _f64(rows, 8 * self.nx)
+        self._check(lib().rtlbfs_strip_set_halo(self._h, int(side), _ptr(a)), "strip_set_halo")
+
+    def strip_rows(self, side: int, halo: bool, buffer: int):
+        """(device address, bytes) of the two own (halo=False) or halo rows
+        next to `side` in state buffer `buffer`."""
+        p, n = _vp(), C.c_size_t()
+        self._check(lib().rtlbfs_strip_rows(self._h, int(side), int(bool(halo)), int(buffer),
+                                            C.byref(p), C.byref(n)), "strip_rows")
+        return int(p.value or 0), int(n.value)
+
+    def strip_pack(self, side: int, buffer: int, dev_ptr: int):
+        """Queue a copy of the own rows next to `side` (buffer `buffer`) to
+        the device address dev_ptr (strip_rows' bytes)."""
+        self._check(lib().rtlbfs_strip_pack(self._h, int(side), int(buffer), _vp(dev_ptr)),
+                    "strip_pack")
+
+    def strip_unpack(self, side: int, buffer: int, dev_ptr: int):
+        """Queue a copy from device address dev_ptr into the halo rows
+        beyond `side` (buffer `buffer`)."""
+        self._check(lib().rtlbfs_strip_unpack(self._h, int(side), int(buffer), _vp(dev_ptr)),
+                    "strip_unpack")
+
+    def current_buffer(self) -> int:
+        b = C.c_int()
+        self._check(lib().rtlbfs_current_buffer(self._h, C.byref(b)), "current_buffer")
+        return int(b.value)
+
+    def residual_sums(self):
+        """(sums of the last step (4,), step count): see rtlbfs_residual_sums."""
+        out = np.empty(4)
+        steps = C.c_long()
+        self._check(lib().rtlbfs_residual_sums(self._h, _ptr(out), C.byref(steps)),
+                    "residual_sums")
+        return out, int(steps.value)
 
     # -- helpers
     def _check(self, rc: int, what: str):

@@ -88,6 +88,91 @@ int rtlbfs_create_mesh(int nx, int ny, const double* xf, const double* yf, int p
     return RTLBFS_OK;
 }
 
+int rtlbfs_create_strip(int nx, int ny_mesh, const double* xf, const double* yf, int j0, int j1,
+                        int precision, rtlbfs_t* out)
+{
+    if (!out) return RTLBFS_ERR_ARG;
+    *out = nullptr;
+    rtlbfs_ctx* h = new (std::nothrow) rtlbfs_ctx;
+    if (!h) return RTLBFS_ERR_OOM;
+    h->eng = new (std::nothrow) Engine(precision, 1);
+    if (!h->eng) {
+        delete h;
+        return RTLBFS_ERR_OOM;
+    }
+    int rc = h->eng->init();
+    if (rc == RTLBFS_OK) rc = h->eng->add_strip(nx, ny_mesh, xf, yf, j0, j1, &h->slot);
+    if (rc == RTLBFS_OK) rc = h->eng->set_conduction_state(h->slot);
+    if (rc != RTLBFS_OK) {
+        delete h->eng;
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return RTLBFS_OK;
+}
+
+int rtlbfs_strip_get_rows(rtlbfs_t h, int side, double* rows)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->get_rows(h->slot, side, 0, rows));
+}
+
+int rtlbfs_strip_set_halo(rtlbfs_t h, int side, const double* rows)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->set_rows(h->slot, side, 1, rows));
+}
+
+int rtlbfs_strip_rows(rtlbfs_t h, int side, int halo, int buffer, void** dev, size_t* bytes)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->strip_rows(h->slot, side, halo ? 1 : 0, buffer, dev, bytes));
+}
+
+int rtlbfs_residual_sums(rtlbfs_t h, double* sums, long* steps)
+{
+    if (!cav(h) || !sums) return RTLBFS_ERR_ARG;
+    CavityCtl ctl;
+    int rc = h->eng->read_ctl(h->slot, &ctl);
+    if (rc) return finish(h, rc);
+    for (int q = 0; q < 4; ++q) sums[q] = ctl.sums[q];
+    if (steps) *steps = (long)ctl.steps;
+    return RTLBFS_OK;
+}
+
+int rtlbfs_strip_pack(rtlbfs_t h, int side, int buffer, void* dev)
+{
+    if (!cav(h) || !dev) return RTLBFS_ERR_ARG;
+    void* p = nullptr;
+    size_t n = 0;
+    int rc = h->eng->strip_rows(h->slot, side, 0, buffer, &p, &n);
+    if (rc) return finish(h, rc);
+    cudaError_t e = cudaMemcpyAsync(dev, p, n, cudaMemcpyDeviceToDevice, h->eng->stream());
+    return e == cudaSuccess ? RTLBFS_OK : finish(h, h->eng->cuda_fail(e, "rtlbfs_strip_pack"));
+}
+
+int rtlbfs_strip_unpack(rtlbfs_t h, int side, int buffer, const void* dev)
+{
+    if (!cav(h) || !dev) return RTLBFS_ERR_ARG;
+    void* p = nullptr;
+    size_t n = 0;
+    int rc = h->eng->strip_rows(h->slot, side, 1, buffer, &p, &n);
+    if (rc) return finish(h, rc);
+    cudaError_t e = cudaMemcpyAsync(p, dev, n, cudaMemcpyDeviceToDevice, h->eng->stream());
+    return e == cudaSuccess ? RTLBFS_OK : finish(h, h->eng->cuda_fail(e, "rtlbfs_strip_unpack"));
+}
+
+int rtlbfs_current_buffer(rtlbfs_t h, int* buffer)
+{
+    if (!cav(h) || !buffer) return RTLBFS_ERR_ARG;
+    CavityCtl ctl;
+    int rc = h->eng->read_ctl(h->slot, &ctl);
+    if (rc) return finish(h, rc);
+    *buffer = ctl.cur & 1;
+    return RTLBFS_OK;
+}
+
 int rtlbfs_set_params(rtlbfs_t h, double Ra, double Pr, double Ma, double dt)
 {
     Cavity* c = cav(h);
@@ -139,6 +224,7 @@ int rtlbfs_set_bc(rtlbfs_t h, int side, int kind, double T_wall, double u_wall)
     if (!c) return RTLBFS_ERR_ARG;
     if (side < 0 || side > 3) return argfail(h, "side must be 0..3");
     if (kind < 0 || kind > 2) return argfail(h, "kind must be 0..2");
+    if (c->kind[side] == rtlbfs::kHalo) return argfail(h, "that side of the strip is a halo side");
     c->kind[side] = kind;
     c->bcT[side] = T_wall;
     c->bcU[side] = u_wall;

@@ -50,6 +50,11 @@ cudaError_t launch_chained(void (*fn)(K...), unsigned grid, unsigned block, size
 
 constexpr int kSideW = 0, kSideE = 1, kSideS = 2, kSideN = 3;
 constexpr int kDirichlet = 0, kAdiabatic = 1, kPeriodic = 2;
+// A south or north side that borders another row strip of the same mesh:
+// the two rows beyond it are stored below / above the strip's own rows
+// (rows -2, -1 and ny, ny + 1 of its buffers) and filled by a halo
+// exchange before each step; no mirror rule, no wall face.
+constexpr int kHalo = 3;
 
 // Status of a cavity's run, written by the device.
 constexpr int kRunning = 0, kConverged = 1, kMaxSteps = 2, kDiverged = 3;

@@ -37,16 +37,24 @@ double line_width(const std::vector<double>& f, int i, bool periodic)
     return f[k + 1] - f[k];
 }
 
+// hw: widths of the cells beyond a halo end ({w(-1), w(-2)} for the low
+// end, {w(n), w(n+1)} for the high end), null for a wall or periodic end.
 template <typename R>
 void build_lines(const Cavity& c, const std::vector<double>& f, bool periodic, double kappa,
                  double nu, double chi, double dt, std::vector<FaceLine<R>>& fl,
-                 std::vector<CellLine<R>>& cl)
+                 std::vector<CellLine<R>>& cl, const double* hw_lo = nullptr,
+                 const double* hw_hi = nullptr)
 {
     const int n = (int)f.size() - 1;
     (void)c;
+    auto width = [&](int i) {
+        if (i < 0 && i >= -2 && hw_lo) return hw_lo[-1 - i];
+        if (i >= n && i <= n + 1 && hw_hi) return hw_hi[i - n];
+        return line_width(f, i, periodic);
+    };
     fl.resize(n + 1);
     for (int i = 0; i <= n; ++i) {
-        const double wl = line_width(f, i - 1, periodic), wr = line_width(f, i, periodic);
+        const double wl = width(i - 1), wr = width(i);
         const double h = kappa * std::min(wl, wr);
         FaceLine<R> x;
         x.h = (R)h;
@@ -61,7 +69,7 @@ void build_lines(const Cavity& c, const std::vector<double>& f, bool periodic, d
     }
     cl.resize(n + 4);
     for (int i = -2; i <= n + 1; ++i) {
-        const double w = line_width(f, i, periodic), wn = line_width(f, i + 1, periodic);
+        const double w = width(i), wn = width(i + 1);
         CellLine<R> y;
         y.w = (R)w;
         y.is_next = (R)(1.0 / (w + wn));
@@ -202,7 +210,7 @@ Cavity* Engine::cavity(int slot)
     return &slots_[slot];
 }
 
-int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_out)
+int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_out, int halo_rows)
 {
     if (nx < 1 || ny < 1 || !xf || !yf) return fail(RTLBFS_ERR_ARG, "bad mesh size or null faces");
     if ((long long)nx * ny > (1LL << 31)) return fail(RTLBFS_ERR_ARG, "mesh too large");
@@ -228,7 +236,8 @@ int Engine::add(int nx, int ny, const double* xf, const double* yf, int* slot_ou
     for (int j = 0; j < ny; ++j) wmin = std::min(wmin, yf[j + 1] - yf[j]);
     c.dt = 0.5 * wmin;
     c.Lref = 0.0;  // 0: the domain width in x
-    c.fields_bytes = 8 * rsize_ * (size_t)c.pitch * ny;
+    c.halo_rows = halo_rows;
+    c.fields_bytes = 8 * rsize_ * (size_t)c.pitch * (ny + 2 * halo_rows);
     // line layout: R lines, then FP64 lines, each block 256-byte aligned
     const size_t fr = precision_ == RTLBFS_FP64 ? sizeof(FaceLine<double>) : sizeof(FaceLine<float>);
     const size_t cr = precision_ == RTLBFS_FP64 ? sizeof(CellLine<double>) : sizeof(CellLine<float>);
@@ -318,6 +327,7 @@ int Engine::resolve_params(Cavity& c)
         double wmin = 1e300;
         for (int i = 0; i < c.nx; ++i) wmin = std::min(wmin, c.xf[i + 1] - c.xf[i]);
         for (int j = 0; j < c.ny; ++j) wmin = std::min(wmin, c.yf[j + 1] - c.yf[j]);
+        if (c.wmin_mesh > 0.0) wmin = c.wmin_mesh;  // a strip: the whole mesh's rule
         c.dt = std::min(0.5 * wmin, 0.2 * wmin * wmin / std::max(c.nu, c.chi));
     }
     if (!(c.dt > 0) || !(c.kappa > 0)) return fail(RTLBFS_ERR_ARG, "dt and kappa must be positive");
@@ -325,6 +335,121 @@ int Engine::resolve_params(Cavity& c)
     const bool yp = c.kind[kSideS] == kPeriodic, yp2 = c.kind[kSideN] == kPeriodic;
     if (xp != xp2 || yp != yp2)
         return fail(RTLBFS_ERR_ARG, "periodic sides must come in opposite pairs");
+    if (c.kind[kSideW] == kHalo || c.kind[kSideE] == kHalo)
+        return fail(RTLBFS_ERR_ARG, "halo sides are south or north sides of a row strip");
+    if ((c.kind[kSideS] == kHalo || c.kind[kSideN] == kHalo) && c.halo_rows < 2)
+        return fail(RTLBFS_ERR_ARG, "halo sides need a row strip (rtlbfs_create_strip)");
+    return RTLBFS_OK;
+}
+
+int Engine::add_strip(int nx, int ny_mesh, const double* xf, const double* yf, int j0, int j1,
+                      int* slot_out)
+{
+    if (!xf || !yf || nx < 1 || ny_mesh < 2 || j0 < 0 || j1 > ny_mesh || j1 - j0 < 2)
+        return fail(RTLBFS_ERR_ARG, "a strip needs 0 <= j0, j1 <= ny, at least 2 rows");
+    for (int j = 0; j < ny_mesh; ++j)
+        if (!(yf[j + 1] > yf[j])) return fail(RTLBFS_ERR_ARG, "yf must be strictly ascending");
+    int slot = -1;
+    int rc = add(nx, j1 - j0, xf, yf + j0, &slot, 2);
+    if (rc) return rc;
+    Cavity& c = slots_[slot];
+    auto w = [&](int j) { return yf[j + 1] - yf[j]; };
+    if (j0 > 0) {  // rows j0 - 1, j0 - 2 of the mesh lie beyond the south side
+        c.kind[kSideS] = kHalo;
+        c.halo_w[0][0] = w(j0 - 1);
+        c.halo_w[0][1] = j0 >= 2 ? w(j0 - 2) : w(j0 - 1);
+    }
+    if (j1 < ny_mesh) {  // rows j1, j1 + 1 beyond the north side
+        c.kind[kSideN] = kHalo;
+        c.halo_w[1][0] = w(j1);
+        c.halo_w[1][1] = j1 + 1 < ny_mesh ? w(j1 + 1) : w(j1);
+    }
+    double wmin = 1e300;
+    for (int i = 0; i < nx; ++i) wmin = std::min(wmin, xf[i + 1] - xf[i]);
+    for (int j = 0; j < ny_mesh; ++j) wmin = std::min(wmin, w(j));
+    c.wmin_mesh = wmin;
+    c.dt = 0.5 * wmin;
+    c.dirty = true;
+    *slot_out = slot;
+    return RTLBFS_OK;
+}
+
+int Engine::strip_rows(int slot, int side, int ghost, int buffer, void** ptr, size_t* bytes)
+{
+    Cavity* c = cavity(slot);
+    if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if ((side != kSideS && side != kSideN) || buffer < 0 || buffer > 1 || !ptr || !bytes)
+        return fail(RTLBFS_ERR_ARG, "side must be south or north, buffer 0 or 1");
+    if (c->kind[side] != kHalo) return fail(RTLBFS_ERR_ARG, "that side is not a halo side");
+    if (c->dirty) {
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
+    // first row of the pair: own rows 0, 1 / ny-2, ny-1; halo rows -2, -1 / ny, ny+1
+    const int r = side == kSideS ? (ghost ? -2 : 0) : (ghost ? c->ny : c->ny - 2);
+    const size_t row = 4 * rsize_ * (size_t)c->pitch;
+    *ptr = static_cast<unsigned char*>(h_desc_[slot].f[buffer][0]) + (long long)r * (long long)row;
+    *bytes = 2 * row;
+    return RTLBFS_OK;
+}
+
+int Engine::get_rows(int slot, int side, int ghost, double* host)
+{
+    Cavity* c = cavity(slot);
+    if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+    CavityCtl ctl;
+    int rc = read_ctl(slot, &ctl);
+    if (rc) return rc;
+    void* p = nullptr;
+    size_t bytes = 0;
+    if ((rc = strip_rows(slot, side, ghost, ctl.cur & 1, &p, &bytes))) return rc;
+    const size_t n = 2 * (size_t)c->nx;
+    if (stage_cap_ < 4 * n) {
+        cudaFree(d_stage_);
+        d_stage_ = nullptr;
+        CK(cudaMalloc(&d_stage_, sizeof(double) * 4 * n));
+        stage_cap_ = 4 * n;
+    }
+    CK(launch_state_out(precision_, stream_, d_stage_, c->nx, 2, c->pitch, c->T_unit, p));
+    g_launches++;
+    double* dst[4] = {host, host + n, host + 2 * n, host + 3 * n};
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(dst[k], d_stage_ + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                           stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::set_rows(int slot, int side, int ghost, const double* host)
+{
+    Cavity* c = cavity(slot);
+    if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+    CavityCtl ctl;
+    int rc = read_ctl(slot, &ctl);
+    if (rc) return rc;
+    void* p = nullptr;
+    size_t bytes = 0;
+    if ((rc = strip_rows(slot, side, ghost, ctl.cur & 1, &p, &bytes))) return rc;
+    const size_t n = 2 * (size_t)c->nx;
+    if (stage_cap_ < 4 * n) {
+        CK(cudaStreamSynchronize(stream_));
+        cudaFree(d_stage_);
+        d_stage_ = nullptr;
+        CK(cudaMalloc(&d_stage_, sizeof(double) * 4 * n));
+        stage_cap_ = 4 * n;
+    }
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(d_stage_ + k * n, host + k * n, sizeof(double) * n,
+                           cudaMemcpyHostToDevice, stream_));
+    int* d_bad = reinterpret_cast<int*>(d_scalar_ + 7);
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), stream_));
+    CK(launch_state_in(precision_, stream_, d_stage_, c->nx, 2, c->pitch, c->T_unit, p, d_bad));
+    g_launches++;
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if (h_bad)
+        return fail(RTLBFS_ERR_ARG, "halo rows not representable in the FP32 fixed-point state");
     return RTLBFS_OK;
 }
 
@@ -351,19 +476,21 @@ int Engine::upload_lines(int slot)
     if (unit > c.T_unit) {
         const int shift = (int)std::lround(std::log2(unit / c.T_unit));
         if (shift > 30) return fail(RTLBFS_ERR_ARG, "temperatures too large for the FP32 state");
-        CK(launch_rescale_T(stream_, c.d_fields, 2LL * c.pitch * c.ny, shift));
+        CK(launch_rescale_T(stream_, c.d_fields, 2LL * c.pitch * (c.ny + 2 * c.halo_rows), shift));
         g_launches++;
         c.T_unit = unit;
     }
     const double Tu = c.T_unit;
     const bool xp = c.kind[kSideW] == kPeriodic, yp = c.kind[kSideS] == kPeriodic;
+    const double* hw_lo = c.kind[kSideS] == kHalo ? c.halo_w[0] : nullptr;
+    const double* hw_hi = c.kind[kSideN] == kHalo ? c.halo_w[1] : nullptr;
     std::vector<unsigned char> buf(c.lines_bytes, 0);
     auto put = [&](size_t off, const void* src, size_t n) { std::memcpy(buf.data() + off, src, n); };
     {
         std::vector<FaceLine<double>> fx, fy;
         std::vector<CellLine<double>> cx, cy;
         build_lines<double>(c, c.xf, xp, c.kappa, c.nu, c.chi, c.dt, fx, cx);
-        build_lines<double>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy);
+        build_lines<double>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy, hw_lo, hw_hi);
         put(c.off_xld, fx.data(), fx.size() * sizeof(fx[0]));
         put(c.off_yld, fy.data(), fy.size() * sizeof(fy[0]));
         put(c.off_xcd, cx.data(), cx.size() * sizeof(cx[0]));
@@ -379,7 +506,7 @@ int Engine::upload_lines(int slot)
         std::vector<FaceLine<float>> fx, fy;
         std::vector<CellLine<float>> cx, cy;
         build_lines<float>(c, c.xf, xp, c.kappa, c.nu, c.chi, c.dt, fx, cx);
-        build_lines<float>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy);
+        build_lines<float>(c, c.yf, yp, c.kappa, c.nu, c.chi, c.dt, fy, cy, hw_lo, hw_hi);
         put(c.off_xl, fx.data(), fx.size() * sizeof(fx[0]));
         put(c.off_yl, fy.data(), fy.size() * sizeof(fy[0]));
         put(c.off_xc, cx.data(), cx.size() * sizeof(cx[0]));
@@ -422,9 +549,11 @@ int Engine::upload_lines(int slot)
         d.f_bcU[s2] = (float)c.bcU[s2];
         d.f_bcT[s2] = (float)d.bcT[s2];
     }
-    const size_t rec = 4 * rsize_ * (size_t)c.pitch * c.ny;  // cell records of one buffer
+    // cell records of one buffer (with a strip's halo rows below and above)
+    const size_t rec = 4 * rsize_ * (size_t)c.pitch * (c.ny + 2 * c.halo_rows);
+    const size_t row0 = 4 * rsize_ * (size_t)c.pitch * c.halo_rows;
     for (int b = 0; b < 2; ++b) {
-        d.f[b][0] = static_cast<unsigned char*>(c.d_fields) + (size_t)b * rec;
+        d.f[b][0] = static_cast<unsigned char*>(c.d_fields) + (size_t)b * rec + row0;
         d.f[b][1] = d.f[b][2] = d.f[b][3] = nullptr;
     }
     unsigned char* L = static_cast<unsigned char*>(c.d_lines);
@@ -804,6 +933,8 @@ int Engine::persist_check()
     if (scheme_ != kSchemeRTLBFS)
         return fail(RTLBFS_ERR_ARG, "the persistent kernel runs the RTLBFS face stage only");
     const Cavity& c = slots_[slot];
+    if (c.halo_rows)
+        return fail(RTLBFS_ERR_ARG, "the persistent kernel takes whole meshes, not row strips");
     if ((c.nx % kTileX) == 1 || (c.ny % tile_h_) == 1)
         return fail(RTLBFS_ERR_ARG, "the persistent kernel needs tiles at least 2 cells wide");
     if ((long long)ntiles_ > (long long)sms_ * occ_persist_[tile_h_])
@@ -916,7 +1047,7 @@ int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
             ++active;
             aslot = s;
         }
-    if (capacity_ == 1 && active == 1 && scheme_ == kSchemeRTLBFS)
+    if (capacity_ == 1 && active == 1 && scheme_ == kSchemeRTLBFS && !slots_[aslot].halo_rows)
         for (int h : kTileHeights) {
             if (!tile_height_ok(precision_, h)) continue;
             const Cavity& c = slots_[aslot];
@@ -1015,6 +1146,8 @@ int Engine::nusselt(int slot, int which, double* out)
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (which < kNuWest || which > kNuHalf) return fail(RTLBFS_ERR_ARG, "bad Nusselt selector");
     if (which == kNuHalf && (c->nx % 2)) return fail(RTLBFS_ERR_ARG, "Nu_1/2 needs nx even");
+    if ((which == kNuSouth || which == kNuNorth) && c->kind[which] == kHalo)
+        return fail(RTLBFS_ERR_ARG, "no wall on a strip's halo side");
     if (c->dirty) {  // the reduction reads this cavity's lines and descriptor
         int rc = upload_lines(slot);
         if (rc) return rc;

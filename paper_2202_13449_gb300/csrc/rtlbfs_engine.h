@@ -34,6 +34,14 @@ struct Cavity {
     // +-1.5 T_unit and the last uploaded state within +-1.9 T_unit (always 1
     // in FP64).  State_Tmax: max |T| of the last state set_state uploaded.
     double T_unit = 1.0, state_Tmax = 0.0;
+    // A row strip of a larger mesh (create_strip): halo_rows = 2 extra rows
+    // below and above the strip's own rows in every buffer, for the halo
+    // sides (kHalo); halo_w[0] = widths of rows -1, -2 and halo_w[1] =
+    // widths of rows ny, ny+1 in the whole mesh; wmin_mesh > 0: the
+    // smallest cell width of the whole mesh (the dt rule of resolve_params).
+    int halo_rows = 0;
+    double halo_w[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    double wmin_mesh = 0.0;
     // device memory
     void* d_fields = nullptr;  // 2 buffers x 4 fields x ny x pitch
     void* d_lines = nullptr;   // R lines then FP64 lines
@@ -57,7 +65,18 @@ public:
     int capacity() const { return capacity_; }
 
     // slots
-    int add(int nx, int ny, const double* xf, const double* yf, int* slot);
+    int add(int nx, int ny, const double* xf, const double* yf, int* slot, int halo_rows = 0);
+    // rows j0 <= j < j1 of an nx x ny_mesh mesh as a cavity whose south /
+    // north sides inside the mesh are halo sides (kHalo)
+    int add_strip(int nx, int ny_mesh, const double* xf, const double* yf, int j0, int j1,
+                  int* slot);
+    // the 2 rows next to side S/N (ghost = 0: the strip's own rows; 1: the
+    // halo rows beyond it) of buffer b: device address and bytes (contiguous)
+    int strip_rows(int slot, int side, int ghost, int buffer, void** ptr, size_t* bytes);
+    // the same rows of the current state as FP64 planes rho, u, v, T of
+    // 2 x nx values each (host arrays), out of or into the state
+    int get_rows(int slot, int side, int ghost, double* host);
+    int set_rows(int slot, int side, int ghost, const double* host);
     int remove(int slot);
     Cavity* cavity(int slot);
     static size_t bytes_for(int precision, int nx, int ny);

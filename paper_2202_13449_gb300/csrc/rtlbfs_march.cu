@@ -29,12 +29,16 @@ namespace {
 // Source index of cell coordinate c on a line of n cells with the given
 // ends: wrap when periodic; the ghost at -1 / n mirrors cell 0 / n-1 (mside
 // set); anything else outside is unused (returns false).
+// (halo_lo / halo_hi: the two cells beyond that end are stored ones, see
+// kHalo.)
 __device__ __forceinline__ bool resolve_1d(int c, int n, bool per, int side_lo, int side_hi,
-                                           int& src, int& mside)
+                                           int& src, int& mside, bool halo_lo = false,
+                                           bool halo_hi = false)
 {
     mside = -1;
     src = c;
     if (c >= 0 && c < n) return true;
+    if ((c < 0 && halo_lo && c >= -2) || (c >= n && halo_hi && c <= n + 1)) return true;
     if (per) {
         src = ((c % n) + n) % n;
         return true;
@@ -167,6 +171,9 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
         const int cur = (plan >> 1) & 1, slot3 = plan >> 2;
         const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
         const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
+        const bool hlo = dp->kind[kSideS] == kHalo, hhi = dp->kind[kSideN] == kHalo;
+        // south / north sides that are walls (not periodic, not a strip's halo)
+        const bool wall_s = !yper && !hlo, wall_n = !yper && !hhi;
         const Vec4<S>* __restrict__ fin = static_cast<const Vec4<S>*>(dp->f[cur][0]);
         Vec4<S>* __restrict__ fout = static_cast<Vec4<S>*>(dp->f[cur ^ 1][0]);
         const CellLine<R>* xc = static_cast<const CellLine<R>*>(dp->xcell);
@@ -192,13 +199,13 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
         // raw row r of this lane's column (ghost rule applied later in conv)
         auto fetch = [&](int r, Vec4<S>& q) {
             int rs, yms;
-            const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms);
+            const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms, hlo, hhi);
             q = {S(0), S(0), S(0), S(0)};
-            if (colok && rowok && !(xms >= 0 && yms >= 0)) q = fin[(size_t)rs * pitch + gs];
+            if (colok && rowok && !(xms >= 0 && yms >= 0)) q = fin[(long long)rs * pitch + gs];
         };
         auto conv = [&](int r, Vec4<S> q) -> Vec4<R> {
             int rs, yms;
-            const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms);
+            const bool rowok = resolve_1d(r, ny, yper, kSideS, kSideN, rs, yms, hlo, hhi);
             if (!(colok && rowok && !(xms >= 0 && yms >= 0))) return {R(0), R(0), R(0), R(0)};
             Vec4<R> y = {P::val(q.x, 0), P::val(q.y, 1), P::val(q.z, 2), P::diff(q.w, qTz, 3)};
             if (xms >= 0) y = mirror_values_m<P>(dp, xms, y, Tz);
@@ -240,7 +247,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
                          const Vec4<R>& vyr, const Vec4<R>& gxyr, const Vec4<R>& gyyr,
                          Vec4<R>& Fxo, Vec4<R>& Fyo) {
             const FaceLine<R> fly = yl[min(max(jf, 0), ny)];
-            const int ws = (!yper && jf == 0) ? kSideS : ((!yper && jf == ny) ? kSideN : -1);
+            const int ws = (wall_s && jf == 0) ? kSideS : ((wall_n && jf == ny) ? kSideN : -1);
             const R uwy = ws >= 0 ? P::bcU(dp, ws) : R(0);
             const R uwx = wsx >= 0 ? P::bcU(dp, wsx) : R(0);
             CellNT<V2> L, Rr;
@@ -304,7 +311,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
             }
             {
                 const FaceLine<R> fly = yl[min(max(jf, 0), ny)];
-                const int ws = (!yper && jf == 0) ? kSideS : ((!yper && jf == ny) ? kSideN : -1);
+                const int ws = (wall_s && jf == 0) ? kSideS : ((wall_n && jf == ny) ? kSideN : -1);
                 CellNT<R> L = {{vyl.x, vyl.z, vyl.y, R(0)}, {gyyl.x, gyyl.z, gyyl.y, gyyl.w},
                                {gxyl.x, gxyl.z, gxyl.y, gxyl.w}};
                 CellNT<R> Rr = {{vyr.x, vyr.z, vyr.y, vyr.w - vyl.w},
@@ -334,7 +341,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
             Vec4<R> gxm1, gym1;
             grad(j0 - 1, vm2, vm1, v0, gxm1, gym1);
             grad(j0, vm1, v0, v1, gx0, gy0);
-            if (!yper && j0 == 0) {  // row -1 is the south ghost: mirror row 0
+            if (wall_s && j0 == 0) {  // row -1 is the south ghost: mirror row 0
                 gxm1 = gx0;
                 gym1 = gy0;
                 mirror_grad_m(dp->kind[kSideS], kSideS, gxm1, gym1);
@@ -357,7 +364,7 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
             if (upd_lane) qo = fin[(size_t)j * pitch + g];  // raw state of the updated cell (L1)
             // gradients of row j+1 (a north ghost row mirrors row j)
             grad(j + 1, v0, v1, v2, gx1, gy1);
-            if (!yper && j + 1 == ny) {
+            if (wall_n && j + 1 == ny) {
                 gx1 = gx0;
                 gy1 = gy0;
                 mirror_grad_m(dp->kind[kSideN], kSideN, gx1, gy1);

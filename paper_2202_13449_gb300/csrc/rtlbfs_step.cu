@@ -111,7 +111,7 @@ __device__ bool load_cell_d(const CavityDesc& d, int b, int gi, int gj, Vec4<dou
 {
     int si, sj, ms;
     if (!resolve_cell(d, gi, gj, si, sj, ms)) return false;
-    const size_t o = (size_t)sj * d.pitch + si;
+    const long long o = (long long)sj * d.pitch + si;
     const Vec4<typename P::S> x = P::load4(&d, b, o);
     v = {P::to_double(x.x, 0), P::to_double(x.y, 1), P::to_double(x.z, 2), P::to_double(x.w, 3)};
     if (ms >= 0) v = mirror_values<StoreD>(d, ms, v, 0.0);  // FP64, T absolute
@@ -163,7 +163,10 @@ __device__ double energy_flux_d(const CavityDesc& d, int f, const NuLines& ln, i
     face_cells<double>(nd == 0, vl, vr, 0.0, gxl, gyl, gxr, gyr, L, Rr, Tbar);
     int wside = -1;
     if (nd == 0 && !xper) wside = i == 0 ? kSideW : (i == d.nx ? kSideE : -1);
-    if (nd == 1 && !yper) wside = j == 0 ? kSideS : (j == d.ny ? kSideN : -1);
+    if (nd == 1 && !yper)
+        wside = (j == 0 && d.kind[kSideS] != kHalo)
+                    ? kSideS
+                    : ((j == d.ny && d.kind[kSideN] != kHalo) ? kSideN : -1);
     const FaceLine<double> fl = nd == 0 ? ln.xl[i] : ln.yl[j];
     double F[4];
     const double keep = wside >= 0 ? 0.0 : 1.0, uw = wside >= 0 ? d.bcU[wside] : 0.0;

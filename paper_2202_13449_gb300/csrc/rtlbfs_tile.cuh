@@ -48,8 +48,11 @@ struct TileSmem {
 // cell (si, sj) to read, and the wall side whose mirror rule applies
 // (-1: none).  Returns false for positions no stencil uses (corner ghosts,
 // cells beyond the ghost layer of a wall).
-__device__ __forceinline__ bool resolve_cell(int nx, int ny, bool xper, bool yper, int gi, int gj,
-                                             int& si, int& sj, int& mside)
+// With halo sides (south: hlo, north: hhi) rows -2, -1 (ny, ny + 1) are
+// stored rows of the strip's buffers (sj outside [0, ny)).
+__device__ __forceinline__ bool resolve_cell(int nx, int ny, bool xper, bool yper, bool hlo,
+                                             bool hhi, int gi, int gj, int& si, int& sj,
+                                             int& mside)
 {
     si = gi;
     sj = gj;
@@ -68,7 +71,9 @@ __device__ __forceinline__ bool resolve_cell(int nx, int ny, bool xper, bool ype
         }
     }
     if (gj < 0 || gj >= ny) {
-        if (yper) {
+        if ((gj < 0 && hlo && gj >= -2) || (gj >= ny && hhi && gj <= ny + 1)) {
+            sj = gj;  // a halo row (a wall ghost of it keeps its x mirror)
+        } else if (yper) {
             sj = ((gj % ny) + ny) % ny;
         } else if ((gj == -1 || gj == ny) && mside < 0) {
             sj = gj < 0 ? 0 : ny - 1;
@@ -83,8 +88,8 @@ __device__ __forceinline__ bool resolve_cell(int nx, int ny, bool xper, bool ype
 __device__ __forceinline__ bool resolve_cell(const CavityDesc& d, int gi, int gj, int& si,
                                              int& sj, int& mside)
 {
-    return resolve_cell(d.nx, d.ny, d.kind[kSideW] == kPeriodic, d.kind[kSideS] == kPeriodic, gi,
-                        gj, si, sj, mside);
+    return resolve_cell(d.nx, d.ny, d.kind[kSideW] == kPeriodic, d.kind[kSideS] == kPeriodic,
+                        d.kind[kSideS] == kHalo, d.kind[kSideN] == kHalo, gi, gj, si, sj, mside);
 }
 
 // Ghost values across wall `side` from the partner's working values y =
@@ -332,6 +337,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
     const int tc = tid % CW, tr = tid / CW;
     const int nx = dp->nx, ny = dp->ny, pitch = dp->pitch;
     const bool xper = dp->kind[kSideW] == kPeriodic, yper = dp->kind[kSideS] == kPeriodic;
+    const bool hlo = dp->kind[kSideS] == kHalo, hhi = dp->kind[kSideN] == kHalo;
     // temperature reference of this tile: its (clamped) centre cell
     const int ic = min(i0 + TX / 2, nx - 1), jc = min(j0 + TY / 2, ny - 1);
     const S qTz = ld_state<LDCG>(&fin[(size_t)jc * pitch + ic]).w;
@@ -384,9 +390,9 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
                     v[k] = ld_state<LDCG>(&fin[(size_t)(j0 - 2 + br) * pitch + (i0 - 2 + bc)]);
             } else {
                 int si = 0, sj = 0;
-                ok[k] = ok[k] && resolve_cell(nx, ny, xper, yper, i0 - 2 + bc, j0 - 2 + br, si,
-                                              sj, ms[k]);
-                if (ok[k]) v[k] = ld_state<LDCG>(&fin[(size_t)sj * pitch + si]);
+                ok[k] = ok[k] && resolve_cell(nx, ny, xper, yper, hlo, hhi, i0 - 2 + bc,
+                                              j0 - 2 + br, si, sj, ms[k]);
+                if (ok[k]) v[k] = ld_state<LDCG>(&fin[(long long)sj * pitch + si]);
             }
         }
         if constexpr (Sm::kRaw) {
@@ -434,7 +440,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             int si, sj, ms = -1;
             Vec4<R> gxv = {R(0), R(0), R(0), R(0)}, gyv = gxv;
             if (interior ||
-                resolve_cell(nx, ny, xper, yper, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
+                resolve_cell(nx, ny, xper, yper, hlo, hhi, i0 - 2 + c, j0 - 2 + r, si, sj, ms)) {
                 // a wall ghost takes its partner's gradient, mirrored
                 if (ms == kSideW) c += 1;
                 else if (ms == kSideE) c -= 1;
@@ -473,7 +479,8 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             int wside = -1;
             if (!interior) {
                 if (isx && !xper) wside = gi == 0 ? kSideW : (gi == nx ? kSideE : -1);
-                if (!isx && !yper) wside = gj == 0 ? kSideS : (gj == ny ? kSideN : -1);
+                if (!isx && !yper)
+                    wside = (gj == 0 && !hlo) ? kSideS : ((gj == ny && !hhi) ? kSideN : -1);
             }
             const R uw = wside >= 0 ? P::bcU(dp, wside) : R(0);
             R F[4];
