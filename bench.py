@@ -112,10 +112,10 @@ WORKLOADS = {
              "trace (seed 42, Poisson arrivals at 200/s, side log-uniform 64..1024, Ra "
              "log-uniform 1e3..1e8, Pr in {0.71, 7.0}) with side <= 128 and Ra <= 1e5, at "
              "their own arrival times (1,012 requests over 49 s), each run to max(R_u, R_T) "
-             "< 1e-7 or 1e6 steps; continuous batching, FP32 bulk + FP64 reductions; the "
+             "< 3e-8 or 1e6 steps; continuous batching, FP32 bulk + FP64 reductions; the "
              "plain per-request FP64 form on converged requests for the comparison",
         count=10000, seed=42, rate=200.0, n_max=128, ra_max=1e5, max_steps=1_000_000,
-        time_limit=300.0, precision="fp32", kind="serve"),
+        time_limit=300.0, tol=3e-8, precision="fp32", kind="serve"),
     "cavity512_accuracy": dict(
         desc="accuracy run of the 512x512 tanh cavity (Ra=1e8, Pr=0.71, Ma=0.1): the FP32 path "
              "(fixed-point state, FP64 reductions) against the FP64 path at step checkpoints "
@@ -534,7 +534,7 @@ def run_serve(args, w):
     trace = [r for r in trace if r.n <= w.get("n_max", r.n) and r.Ra <= w.get("ra_max", r.Ra)]
     reqs = shard([(r.t_arrive, r.n, r.Ra, r.Pr) for r in trace], rank, ws)
     cap = w.get("max_steps", 2000) if args.max_steps is None else args.max_steps
-    tol = args.tol
+    tol = w.get("tol", 1e-7) if args.tol is None else args.tol
     time_limit = w.get("time_limit", 60.0) if args.time_limit is None else args.time_limit
     clk = ClockSampler(local)
     clk.start()
@@ -557,21 +557,32 @@ def run_serve(args, w):
     # there are any), each alone, one at a time, to the same tolerance and cap
     pool = converged if converged else done
     sample = pool[:args.fp64_sample] if rank == 0 else []
-    t0 = time.perf_counter()
-    errs, conv64, steps32, steps64 = [], 0, 0, 0
+    # The accuracy of both forms against the steady state itself: each FP64
+    # run is continued (untimed) to Eq. 65's 1e-9, whose mean wall Nusselt
+    # number is the reference.  At a tolerance R the state still lies about
+    # R x (the slowest decay time in steps) from steady, so both forms carry
+    # that convergence error; the comparison is at equal tolerance.
+    t64 = 0.0
+    errs, errs32, errs64, conv64, steps32, steps64 = [], [], [], 0, 0, 0
     for q, r in sample:
         xf = inputs.uniform_faces(q[1])
         s = capi.Solver(xf, xf, capi.FP64)
         s.set_params(q[2], q[3], 0.1, 0.0)
+        t0 = time.perf_counter()
         rc64, n64, _ = s.run_to_steady(tol, cap)
+        nu64 = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+        t64 += time.perf_counter() - t0
         conv64 += rc64 == capi.OK
         steps32 += r["steps"]
         steps64 += n64
-        nu64 = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
         nu32 = 0.5 * (r["nu_hot"] + r["nu_cold"])
         errs.append(abs(nu32 - nu64) / abs(nu64))
+        rc_ref, _, _ = s.run_to_steady(1e-9, 20 * cap)
+        if rc_ref == capi.OK:
+            nu_ref = 0.5 * (s.nusselt(capi.NU_WEST) + s.nusselt(capi.NU_EAST))
+            errs32.append(abs(nu32 - nu_ref) / abs(nu_ref))
+            errs64.append(abs(nu64 - nu_ref) / abs(nu_ref))
         s.close()
-    t64 = time.perf_counter() - t0
     admitted = [(q, r) for q, r in zip(reqs, res) if r["t_admit"] >= 0]
     h2d = sum(32 * q[1] * q[1] + 16 * (q[1] + 1) for q, _ in admitted)
     updates = sum(q[1] * q[1] * r["steps"] for q, r in done)
@@ -601,7 +612,13 @@ def run_serve(args, w):
         "fp64_per_request": {"requests": len(sample), "of": "converged" if converged else "finished",
                              "solves_per_s": round(len(sample) / t64, 3) if t64 > 0 else None,
                              "converged": conv64, "steps_fp32": steps32, "steps_fp64": steps64,
-                             "max_rel_err_mean_wall_nu_fp32_vs_fp64": max(errs) if errs else None},
+                             "max_rel_err_mean_wall_nu_fp32_vs_fp64": max(errs) if errs else None,
+                             "reference": "the same FP64 run continued to max(R_u, R_T) < 1e-9",
+                             "references": len(errs32),
+                             "max_rel_err_mean_wall_nu_fp32_vs_reference":
+                                 max(errs32) if errs32 else None,
+                             "max_rel_err_mean_wall_nu_fp64_vs_reference":
+                                 max(errs64) if errs64 else None},
         "e2e": {"value": round(finished_job / el_job, 3) if el_job > 0 else None,
                 "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * len(done),
@@ -1393,10 +1410,26 @@ def run_ours(args, w):
     updates = cells * inner * args.steps * ws
     value = updates / (ms_max * 1e-3) / 1e6
 
-    # e2e through the C ABI with host buffers
+    # e2e through the C ABI with host buffers: the state's cell records
+    # (rtlbfs_set_state_raw / get_state_raw, exact, 16 B a cell in FP32),
+    # and the four FP64 planes (rtlbfs_set_state / get_state, 32 B a cell
+    # plus a conversion kernel each way)
     import numpy as np
-    host = pinned(st0)
     e2e_steps = max(1, min(args.steps, 5))
+    rec0, tu0 = s.get_state_raw()
+    rec_in = torch.empty(s.raw_bytes(), dtype=torch.uint8, pin_memory=True)
+    rec_out = torch.empty(s.raw_bytes(), dtype=torch.uint8, pin_memory=True)
+    rec_in.numpy()[...] = rec0
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state_raw(rec_in.numpy(), tu0)
+        s.step(inner)
+        s.get_state_raw(rec_out.numpy())
+    torch.cuda.synchronize()
+    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
+    bytes_rec = s.raw_bytes()
+    host = pinned(st0)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -1404,7 +1437,7 @@ def run_ours(args, w):
         s.step(inner)
         out = s.get_state()
     torch.cuda.synchronize()
-    e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
+    e2e_planes = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     assert np.all(np.isfinite(out[3]))
     bytes_io = 4 * cells * 8
 
@@ -1435,7 +1468,11 @@ def run_ours(args, w):
                    "e2e_host_buffers": "pinned",
                    "state_bytes_per_buffer": 4 * rs * cells},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
-                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+                "h2d_bytes_per_step": bytes_rec, "d2h_bytes_per_step": bytes_rec,
+                "api": "rtlbfs_set_state_raw / rtlbfs_step / rtlbfs_get_state_raw, pinned"},
+        "e2e_planes": {"value": round(e2e_planes, 2), "unit": "M cell-updates/s",
+                       "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+                       "api": "rtlbfs_set_state / rtlbfs_step / rtlbfs_get_state, pinned"},
         "gpu_launches": int(launches),
         "roofline": alu,
         "roofline_hbm": hbm,
@@ -1830,8 +1867,9 @@ def main():
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--max-steps", type=int, default=None,
                     help="serve: step cap per request (default: the workload's, else 2000)")
-    ap.add_argument("--tol", type=float, default=1e-7,
-                    help="serve: steady tolerance (above the FP32 residual floor ~1.4e-8)")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="serve: steady tolerance (default: the workload's, else 1e-7; keep it "
+                         "above the FP32 residual floor ~1.4e-8)")
     ap.add_argument("--time-limit", type=float, default=None,
                     help="serve: wall-clock cap in s (default: the workload's, else 60)")
     ap.add_argument("--slots", type=int, default=256, help="serve: concurrent cavities")

@@ -173,6 +173,26 @@ int rtlbfs_set_state(rtlbfs_t h, const double* rho, const double* u, const doubl
 int rtlbfs_get_state(rtlbfs_t h, double* rho, double* u, double* v, double* T);
 
 /*
+ * The state as the device stores it: ny x nx cell records, row-major
+ * without row padding, each record (rho - 1, u, v, T) -- FP64: four
+ * doubles (32 bytes); FP32: four 32-bit fixed-point integers (16 bytes)
+ * in the units given at RTLBFS_FP32, temperature in units of 2^-30 *T_unit.
+ * Exact in both directions (a checkpoint taken with get and restored with
+ * set continues bit for bit), half the bytes of the four FP64 planes in
+ * FP32, and no conversion kernel.  rtlbfs_state_raw_bytes: the size of
+ * `records` (nx * ny * 16 or 32; 0 for a bad handle).  get writes the
+ * records and the temperature unit (T_unit may be null); set takes them
+ * (T_unit: 1 in FP64, a power of two >= 1 in FP32, else ERR_ARG; a
+ * configuration that needs a larger unit rescales the stored temperatures)
+ * and, like rtlbfs_set_state, resets the step counter and residual.
+ * records: host memory, caller-owned (pinned memory lets the copies run
+ * as DMA); both calls return after the copy.
+ */
+size_t rtlbfs_state_raw_bytes(rtlbfs_t h);
+int rtlbfs_get_state_raw(rtlbfs_t h, void* records, double* T_unit);
+int rtlbfs_set_state_raw(rtlbfs_t h, const void* records, double T_unit);
+
+/*
  * Advance exactly nsteps explicit steps (no convergence stop).  The steps
  * run as CUDA-graph replays on the handle's stream; the call returns after
  * they complete.  ERR_DIVERGED if the residual became non-finite (the

@@ -64,6 +64,9 @@ _SIGS = {
     "rtlbfs_strip_rows": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(_vp),
                                     C.POINTER(C.c_size_t)]),
     "rtlbfs_current_buffer": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "rtlbfs_state_raw_bytes": (C.c_size_t, [_vp]),
+    "rtlbfs_get_state_raw": (C.c_int, [_vp, _vp, _dp]),
+    "rtlbfs_set_state_raw": (C.c_int, [_vp, _vp, C.c_double]),
     "rtlbfs_strip_pack": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
     "rtlbfs_strip_unpack": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
     "rtlbfs_residual_sums": (C.c_int, [_vp, _dp, C.POINTER(C.c_long)]),
@@ -423,6 +426,27 @@ class Solver:
         out = [np.empty((self.ny, self.nx)) for _ in range(4)]
         self._check(lib().rtlbfs_get_state(self._h, *[_ptr(a) for a in out]), "get_state")
         return tuple(out)
+
+    def raw_bytes(self) -> int:
+        return int(lib().rtlbfs_state_raw_bytes(self._h))
+
+    def get_state_raw(self, out=None):
+        """(records, T_unit): the state's cell records as a uint8 array (or
+        into `out`, any writable buffer of raw_bytes() bytes, e.g. a pinned
+        torch tensor's numpy view) and the temperature unit."""
+        if out is None:
+            out = np.empty(self.raw_bytes(), dtype=np.uint8)
+        tu = C.c_double()
+        self._check(lib().rtlbfs_get_state_raw(self._h, _vp(out.ctypes.data), C.byref(tu)),
+                    "get_state_raw")
+        return out, tu.value
+
+    def set_state_raw(self, records, T_unit: float = 1.0):
+        a = np.ascontiguousarray(records).view(np.uint8).reshape(-1)
+        if a.size != self.raw_bytes():
+            raise ValueError(f"expected {self.raw_bytes()} bytes, got {a.size}")
+        self._check(lib().rtlbfs_set_state_raw(self._h, _vp(a.ctypes.data), float(T_unit)),
+                    "set_state_raw")
 
     # -- stepping
     def step(self, n: int):

@@ -21,6 +21,7 @@
 // done, so launches need no host round trip.  HBM sees one read and one
 // write of the five fields per cell (halo re-reads hit L2).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -1036,6 +1037,10 @@ int ensure_graph(rtlbfs3d_ctx* h)
 // queue `count` step launches (graph replays plus single launches)
 int launch_steps(rtlbfs3d_ctx* h, long long count)
 {
+    nvtxRangePushA("rtlbfs3d: step launches");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     int rc = ensure_graph(h);
     if (rc) return rc;
     // launch k of the chain has parity k & 1; the chain ends with the stop

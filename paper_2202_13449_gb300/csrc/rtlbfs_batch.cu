@@ -296,6 +296,7 @@ int rtlbfs_serve(const rtlbfs_request* reqs, int nreq, const rtlbfs_serve_opts* 
         }
         if ((rc = eng.launch_steps(opts->chunk_steps))) return rc;
         if ((rc = eng.read_ctls(ctl))) return rc;
+        rtlbfs::Nvtx retire("rtlbfs: serve retire");
         for (int s = 0; s < opts->max_slots; ++s) {
             const int k = slot_req[s];
             if (k < 0 || !ctl[s].done) continue;

@@ -268,6 +268,24 @@ int rtlbfs_get_state(rtlbfs_t h, double* rho, double* u, double* v, double* T)
     return finish(h, h->eng->get_state(h->slot, rho, u, v, T));
 }
 
+size_t rtlbfs_state_raw_bytes(rtlbfs_t h)
+{
+    Cavity* c = cav(h);
+    return c ? h->eng->record_bytes() * (size_t)c->nx * c->ny : 0;
+}
+
+int rtlbfs_get_state_raw(rtlbfs_t h, void* records, double* T_unit)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->get_records(h->slot, records, T_unit));
+}
+
+int rtlbfs_set_state_raw(rtlbfs_t h, const void* records, double T_unit)
+{
+    if (!cav(h)) return RTLBFS_ERR_ARG;
+    return finish(h, h->eng->set_records(h->slot, records, T_unit));
+}
+
 int rtlbfs_step(rtlbfs_t h, long nsteps)
 {
     if (!cav(h)) return RTLBFS_ERR_ARG;

@@ -26,6 +26,7 @@
 //      along the gravity direction, and the residual sums; the last unit
 //      finalises the step (residual, step counter, buffer flip, stop test).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -1028,6 +1029,10 @@ int arm(rtlbfsc_ctx* h, long long nsteps, double tol)
 
 int launch_steps(rtlbfsc_ctx* h, long long count)
 {
+    nvtxRangePushA("rtlbfsc: step launches");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     const int ty = tile_rows_of(h);
     if (!h->gexec || h->gunits != h->desc.units || h->gty != ty) {
         if (h->gexec) {

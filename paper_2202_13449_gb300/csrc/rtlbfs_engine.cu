@@ -395,6 +395,7 @@ int Engine::strip_rows(int slot, int side, int ghost, int buffer, void** ptr, si
 
 int Engine::get_rows(int slot, int side, int ghost, double* host)
 {
+    Nvtx range("rtlbfs: strip rows out");
     Cavity* c = cavity(slot);
     if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
     CavityCtl ctl;
@@ -422,6 +423,7 @@ int Engine::get_rows(int slot, int side, int ghost, double* host)
 
 int Engine::set_rows(int slot, int side, int ghost, const double* host)
 {
+    Nvtx range("rtlbfs: strip halo in");
     Cavity* c = cavity(slot);
     if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
     CavityCtl ctl;
@@ -782,6 +784,7 @@ int Engine::sync()
 int Engine::set_state(int slot, const double* rho, const double* u, const double* v,
                       const double* T)
 {
+    Nvtx range("rtlbfs: state in");
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (!rho || !u || !v || !T) return fail(RTLBFS_ERR_ARG, "null state array");
@@ -835,6 +838,7 @@ int Engine::set_state(int slot, const double* rho, const double* u, const double
 
 int Engine::get_state(int slot, double* rho, double* u, double* v, double* T)
 {
+    Nvtx range("rtlbfs: state out");
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (!rho || !u || !v || !T) return fail(RTLBFS_ERR_ARG, "null state array");
@@ -860,6 +864,60 @@ int Engine::get_state(int slot, double* rho, double* u, double* v, double* T)
     for (int k = 0; k < 4; ++k)
         CK(cudaMemcpyAsync(dst[k], d_stage_ + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
                            stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::get_records(int slot, void* host, double* T_unit)
+{
+    Nvtx range("rtlbfs: state records out");
+    Cavity* c = cavity(slot);
+    if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+    if (c->dirty) {
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
+    CavityCtl ctl;
+    int rc = read_ctl(slot, &ctl);
+    if (rc) return rc;
+    const size_t rec = record_bytes();
+    CK(cudaMemcpy2DAsync(host, rec * c->nx, h_desc_[slot].f[ctl.cur & 1][0], rec * c->pitch,
+                         rec * c->nx, c->ny, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if (T_unit) *T_unit = c->T_unit;
+    return RTLBFS_OK;
+}
+
+int Engine::set_records(int slot, const void* host, double T_unit)
+{
+    Nvtx range("rtlbfs: state records in");
+    Cavity* c = cavity(slot);
+    if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+    int e2 = 0;
+    const double m = std::frexp(T_unit, &e2);  // a power of two: m = 0.5
+    if (precision_ == RTLBFS_FP64 ? T_unit != 1.0 : !(T_unit >= 1.0 && m == 0.5))
+        return fail(RTLBFS_ERR_ARG, "T_unit must be 1 (FP64) or a power of two >= 1 (FP32)");
+    c->state_Tmax = 0.0;
+    c->T_unit = T_unit;  // the records' unit; a configuration needing more rescales them
+    c->dirty = true;
+    int rc = upload_lines(slot);
+    if (rc) return rc;
+    const size_t rec = record_bytes();
+    CK(cudaMemcpy2DAsync(h_desc_[slot].f[0][0], rec * c->pitch, host, rec * c->nx, rec * c->nx,
+                         c->ny, cudaMemcpyHostToDevice, stream_));
+    if (c->T_unit != T_unit) {  // the configuration asked for a larger unit
+        const int shift = (int)std::lround(std::log2(c->T_unit / T_unit));
+        CK(launch_rescale_T(stream_, h_desc_[slot].f[0][0], (long long)c->pitch * c->ny, shift));
+        g_launches++;
+    }
+    CavityCtl z;
+    std::memset(&z, 0, sizeof(z));
+    z.cur = 0;
+    z.done = 1;
+    z.tol = -1.0;
+    z.res[0] = z.res[1] = INFINITY;
+    rc = put_run(slot, z);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(stream_));
     return RTLBFS_OK;
 }
@@ -945,6 +1003,7 @@ int Engine::persist_check()
 
 int Engine::launch_steps(long long launches)
 {
+    Nvtx range("rtlbfs: step launches");
     int rc = prepare_launch();
     if (rc) return rc;
     if (ntiles_ == 0 || launches <= 0) return RTLBFS_OK;
@@ -997,6 +1056,7 @@ int Engine::launch_steps(long long launches)
             gchunk_ = kGraphChunk;
         }
         while (left >= gchunk_) {
+            Nvtx replay("rtlbfs: step graph replay");
             CK(cudaGraphLaunch(gexec_, stream_));
             g_launches += gchunk_;
             left -= gchunk_;
@@ -1014,6 +1074,7 @@ int Engine::launch_steps(long long launches)
 
 int Engine::autotune(int steps, int* kernel_out, int* rows_out, double* ms_out)
 {
+    Nvtx range("rtlbfs: autotune");
     if (steps < 1) return fail(RTLBFS_ERR_ARG, "autotune needs steps >= 1");
     CK(cudaStreamSynchronize(stream_));
     // snapshot every active cavity's fields and the run control
@@ -1142,6 +1203,7 @@ int Engine::read_ctls(std::vector<CavityCtl>& out)
 
 int Engine::nusselt(int slot, int which, double* out)
 {
+    Nvtx range("rtlbfs: Nusselt sum");
     Cavity* c = cavity(slot);
     if (!c) return fail(RTLBFS_ERR_ARG, "no such slot");
     if (which < kNuWest || which > kNuHalf) return fail(RTLBFS_ERR_ARG, "bad Nusselt selector");

@@ -9,12 +9,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rtlbfs_dev.cuh"
 #include "rtlbfs_kernels.h"
 
 namespace rtlbfs {
 
 extern std::atomic<long long> g_launches;
+
+// A named NVTX range over a scope (steps, graph replays, reductions, state
+// copies), so that a timeline profile shows the library's phases; a no-op
+// when no profiler is attached.
+struct Nvtx {
+    explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx&) = delete;
+    Nvtx& operator=(const Nvtx&) = delete;
+};
 
 // Host record of one cavity.
 struct Cavity {
@@ -90,6 +102,12 @@ public:
                   const double* T);
     int get_state(int slot, double* rho, double* u, double* v, double* T);
     int set_conduction_state(int slot);
+    // the state as its cell records (ny x nx, no row padding; FP32: the
+    // fixed-point records with temperature in units of *T_unit), exact both
+    // ways; host memory (pinned memory makes the copies asynchronous DMA)
+    int get_records(int slot, void* host, double* T_unit);
+    int set_records(int slot, const void* host, double T_unit);
+    size_t record_bytes() const { return 4 * rsize_; }
 
     // run control: arm a slot for up to nsteps steps (tol < 0: no early stop)
     int arm(int slot, long long nsteps, double tol);

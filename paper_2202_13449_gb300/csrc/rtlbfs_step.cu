@@ -175,6 +175,24 @@ __device__ double energy_flux_d(const CavityDesc& d, int f, const NuLines& ln, i
     return F[3];
 }
 
+// Sum over a block of up to 256 threads in FP64: warp shuffles, then the
+// warps' sums by warp 0 (thread 0 holds the result).
+__device__ __forceinline__ double block_sum_d(double v)
+{
+    __shared__ double wsum[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)((blockDim.x + 31) >> 5) ? wsum[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
 // Partial sums of a Nusselt number: one partial per block, in block order.
 template <class P>
 __global__ void __launch_bounds__(256)
@@ -206,29 +224,18 @@ nusselt_partial_kernel(const CavityDesc* __restrict__ descs, const CavityRun* __
             s += (p.y * p.w - d.chi * gx.w) * ln.xc[i + 2].w * ln.yc[j + 2].w;
         }
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ partial, int n, double scale,
-                                    double* __restrict__ out)
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ partial,
+                                                           int n, double scale,
+                                                           double* __restrict__ out)
 {
-    __shared__ double red[256];
     double s = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) s += partial[k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0] * scale;
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) *out = s * scale;
 }
 
 // State conversion: FP64 host-layout staging (rho, u, v, T planes of n
