@@ -208,6 +208,9 @@ int rtlbfs_step(rtlbfs_t h, long nsteps);
  * limit) bounds its wall time, checked between chunks of steps.  Writes
  * the steps taken by this call and the last (R_u, R_T) if the pointers are
  * non-null.  Returns OK, ERR_NOT_CONVERGED, ERR_TIMEOUT or ERR_DIVERGED.
+ * In FP32 the residual settles at a floor set by the state's fixed-point
+ * quantum over the flow's velocity scale (about 1e-8 for strong flows,
+ * above 3e-8 for weak ones): use tol >= 1e-7 there; FP64 reaches 1e-15.
  */
 int rtlbfs_run_to_steady(rtlbfs_t h, double tol, long max_steps, double timeout_s,
                          long* steps_taken, double* residual);
