@@ -323,20 +323,20 @@ struct CellNT {
 // operations.  The powers of h cancel in Eqs. 46-48.  The energy rho*T at a
 // node is written Tbar + e with e = tau + drho*T, tau = T - Tbar, so every
 // difference of rho*T is a difference of e.
+//
+// The first stage, face_columns, forms the column coefficients c_a and s_a
+// of the four primitives; face_flux_columns does the rest.
 template <typename V>
-__host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const CellNT<V>& Rc, V Tbar,
-                                          const FaceLine<V>& fl, V keep, V u_wall, V F[4])
+__host__ __device__ __forceinline__ void face_columns(const CellNT<V>& L, const CellNT<V>& Rc,
+                                                      const FaceLine<V>& fl, V A[4], V Sa[4],
+                                                      V M[4], V Sm[4], V B[4], V Sb[4])
 {
     using T = vtraits<V>;
-    const V half = T::bc(0.5), one = T::bc(1.0), two = T::bc(2.0), three = T::bc(3.0);
-    const V m2 = T::bc(-2.0), mhalf = T::bc(-0.5);
-    const V cs2 = T::bc(1.0 / 3.0), mcs2 = T::bc(-1.0 / 3.0);
-    const V hcs2 = T::bc(0.5 / 3.0);  // c_s^2 / 2
+    const V half = T::bc(0.5);
     const V h = fl.h;
     const V wL = fl.cL + h, mwR = fl.cR - h;  // wL, -wR
     const V hh = h * half;
     // column coefficients: A (a = -1), M (a = 0), B (a = +1); S* slopes in b
-    V A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         A[k] = vfma(L.gn[k], fl.cL, L.q[k]);
@@ -346,6 +346,20 @@ __host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const Cel
         M[k] = half * (vfma(L.gn[k], wL, L.q[k]) + vfma(Rc.gn[k], mwR, Rc.q[k]));
         Sm[k] = hh * (L.gt[k] + Rc.gt[k]);
     }
+}
+
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux_columns(const V A[4], const V Sa[4], const V M[4],
+                                                           const V Sm[4], const V B[4],
+                                                           const V Sb[4], V Tbar,
+                                                           const FaceLine<V>& fl, V keep, V u_wall,
+                                                           V F[4])
+{
+    using T = vtraits<V>;
+    const V half = T::bc(0.5), one = T::bc(1.0), two = T::bc(2.0), three = T::bc(3.0);
+    const V m2 = T::bc(-2.0), mhalf = T::bc(-0.5);
+    const V cs2 = T::bc(1.0 / 3.0), mcs2 = T::bc(-1.0 / 3.0);
+    const V hcs2 = T::bc(0.5 / 3.0);  // c_s^2 / 2
     // centres (b = 0) of the three columns: rho u_n, rho u_t, products
     const V TA = Tbar + A[3], TM = Tbar + M[3], TB = Tbar + B[3];
     const V mnA = vfma(A[0], A[1], A[1]), mnM = vfma(M[0], M[1], M[1]), mnB = vfma(B[0], B[1], B[1]);
@@ -404,6 +418,117 @@ __host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const Cel
     // (rho u_n T)* - (rho u_n T)^n = Tbar (mn* - mn0) + mn* a* - mn0 a0
     F[3] = vfma(fl.m_chi_2h, dx_e,
                 vfma(fl.m_tg15, vfma(Tbar, mns_ - mnM, vfma(mns_, as_, T::bc(0.0) - mnM * M[3])), QnM));
+}
+
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux(const CellNT<V>& L, const CellNT<V>& Rc, V Tbar,
+                                          const FaceLine<V>& fl, V keep, V u_wall, V F[4])
+{
+    V A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+    face_columns<V>(L, Rc, fl, A, Sa, M, Sm, B, Sb);
+    face_flux_columns<V>(A, Sa, M, Sm, B, Sb, Tbar, fl, keep, u_wall, F);
+}
+
+// Green-Gauss gradients of a cell p from its four neighbours in the
+// CellLine form of Eqs. 55-56 (ixe = is_next of the cell, ixw that of its
+// west neighbour; iyn, iys along y), FP32, two components per packed
+// FP32x2 instruction:
+//   g_x = (e - p) ixe + (p - w) ixw,  g_y = (n - p) iyn + (p - s) iys.
+__device__ __forceinline__ void gg_gradient_f32(const Vec4<float>& p, const Vec4<float>& e,
+                                                const Vec4<float>& w, const Vec4<float>& n,
+                                                const Vec4<float>& s, float ixe, float ixw,
+                                                float iyn, float iys, Vec4<float>& gx,
+                                                Vec4<float>& gy)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 xe = make_float2(ixe, ixe), xw = make_float2(ixw, ixw);
+    const float2 yn = make_float2(iyn, iyn), ys = make_float2(iys, iys);
+    const float2 P[2] = {make_float2(p.x, p.y), make_float2(p.z, p.w)};
+    const float2 E[2] = {make_float2(e.x, e.y), make_float2(e.z, e.w)};
+    const float2 W[2] = {make_float2(w.x, w.y), make_float2(w.z, w.w)};
+    const float2 N[2] = {make_float2(n.x, n.y), make_float2(n.z, n.w)};
+    const float2 S[2] = {make_float2(s.x, s.y), make_float2(s.z, s.w)};
+    float2 gxp[2], gyp[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        // a - b as fma(b, -1, a): exact, one rounding like the subtraction
+        gxp[i] = __ffma2_rn(__ffma2_rn(P[i], m1, E[i]), xe, __fmul2_rn(__ffma2_rn(W[i], m1, P[i]), xw));
+        gyp[i] = __ffma2_rn(__ffma2_rn(P[i], m1, N[i]), yn, __fmul2_rn(__ffma2_rn(S[i], m1, P[i]), ys));
+    }
+    gx = {gxp[0].x, gxp[0].y, gxp[1].x, gxp[1].y};
+    gy = {gyp[0].x, gyp[0].y, gyp[1].x, gyp[1].y};
+}
+
+// Flux balance of a cell, FP32, in packed pairs (mass, x-momentum) and
+// (y-momentum, energy): div = ax (F_e - F_w) + ay (F_n - F_s), ax and ay the
+// time step over the cell's widths.
+__device__ __forceinline__ void flux_div_f32(const Vec4<float>& Fw, const Vec4<float>& Fe,
+                                             const Vec4<float>& Fs, const Vec4<float>& Fn, float ax,
+                                             float ay, float& d0, float& d1, float& d2, float& d3)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 ax2 = make_float2(ax, ax), ay2 = make_float2(ay, ay);
+    const float2 d01 = __ffma2_rn(
+        __ffma2_rn(make_float2(Fw.x, Fw.y), m1, make_float2(Fe.x, Fe.y)), ax2,
+        __fmul2_rn(__ffma2_rn(make_float2(Fs.x, Fs.y), m1, make_float2(Fn.x, Fn.y)), ay2));
+    const float2 d23 = __ffma2_rn(
+        __ffma2_rn(make_float2(Fw.z, Fw.w), m1, make_float2(Fe.z, Fe.w)), ax2,
+        __fmul2_rn(__ffma2_rn(make_float2(Fs.z, Fs.w), m1, make_float2(Fn.z, Fn.w)), ay2));
+    d0 = d01.x;
+    d1 = d01.y;
+    d2 = d23.x;
+    d3 = d23.y;
+}
+
+// face_columns in FP32 from the two cells' working values (rho - 1, u, v,
+// T - Tz) and their gradients along the face normal (gn) and tangent (gt),
+// all in storage order, two components per packed FP32x2 instruction: the
+// pairs (rho, u) and (v, T) of a record sit in adjacent registers.  The
+// same operations as face_columns on the face-frame cells of face_cells
+// (bit for bit); ISX: x-face (n = x), else y-face (n = y: u_n = v, u_t = u).
+template <bool ISX>
+__device__ __forceinline__ void face_columns_f32(const Vec4<float>& vl, const Vec4<float>& vr,
+                                                 const Vec4<float>& gnl, const Vec4<float>& gtl,
+                                                 const Vec4<float>& gnr, const Vec4<float>& gtr,
+                                                 const FaceLine<float>& fl, float A[4],
+                                                 float Sa[4], float M[4], float Sm[4], float B[4],
+                                                 float Sb[4])
+{
+    const float h = fl.h;
+    const float wL = fl.cL + h, mwR = fl.cR - h, hh = h * 0.5f;
+    const float2 cL2 = make_float2(fl.cL, fl.cL), cR2 = make_float2(fl.cR, fl.cR);
+    const float2 wL2 = make_float2(wL, wL), mwR2 = make_float2(mwR, mwR);
+    const float2 h2 = make_float2(h, h), hh2 = make_float2(hh, hh), half2 = make_float2(0.5f, 0.5f);
+    // the left cell's temperature is carried by Tbar = Tz + T_L
+    const float2 ql[2] = {make_float2(vl.x, vl.y), make_float2(vl.z, 0.0f)};
+    const float2 qr[2] = {make_float2(vr.x, vr.y), make_float2(vr.z, vr.w - vl.w)};
+    const float2 nl[2] = {make_float2(gnl.x, gnl.y), make_float2(gnl.z, gnl.w)};
+    const float2 tl[2] = {make_float2(gtl.x, gtl.y), make_float2(gtl.z, gtl.w)};
+    const float2 nr[2] = {make_float2(gnr.x, gnr.y), make_float2(gnr.z, gnr.w)};
+    const float2 tr[2] = {make_float2(gtr.x, gtr.y), make_float2(gtr.z, gtr.w)};
+    float2 a[2], sa[2], m[2], sm[2], b[2], sb[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        a[i] = __ffma2_rn(nl[i], cL2, ql[i]);
+        sa[i] = __fmul2_rn(tl[i], h2);
+        b[i] = __ffma2_rn(nr[i], cR2, qr[i]);
+        sb[i] = __fmul2_rn(tr[i], h2);
+        m[i] = __fmul2_rn(half2, __fadd2_rn(__ffma2_rn(nl[i], wL2, ql[i]), __ffma2_rn(nr[i], mwR2, qr[i])));
+        sm[i] = __fmul2_rn(hh2, __fadd2_rn(tl[i], tr[i]));
+    }
+    // face-frame order: (rho, u_n, u_t, T)
+    auto put = [](const float2* v, float* d) {
+        d[0] = v[0].x;
+        d[1] = ISX ? v[0].y : v[1].x;
+        d[2] = ISX ? v[1].x : v[0].y;
+        d[3] = v[1].y;
+    };
+    put(a, A);
+    put(sa, Sa);
+    put(m, M);
+    put(sm, Sm);
+    put(b, B);
+    put(sb, Sb);
 }
 
 // The original TLBFS face stage (Section 2.2), from the same inputs as

@@ -220,14 +220,18 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
             const Vec4<R> vw = shfl_up1(v), ve = shfl_dn1(v);
             const int ri = min(max(r + 2, 1), ny + 3);
             const R isy_n = yc[ri].is_next, isy_s = yc[ri - 1].is_next;
-            gx.x = (ve.x - v.x) * isx_e + (v.x - vw.x) * isx_w;
-            gx.y = (ve.y - v.y) * isx_e + (v.y - vw.y) * isx_w;
-            gx.z = (ve.z - v.z) * isx_e + (v.z - vw.z) * isx_w;
-            gx.w = (ve.w - v.w) * isx_e + (v.w - vw.w) * isx_w;
-            gy.x = (vn.x - v.x) * isy_n + (v.x - vs.x) * isy_s;
-            gy.y = (vn.y - v.y) * isy_n + (v.y - vs.y) * isy_s;
-            gy.z = (vn.z - v.z) * isy_n + (v.z - vs.z) * isy_s;
-            gy.w = (vn.w - v.w) * isy_n + (v.w - vs.w) * isy_s;
+            if constexpr (sizeof(R) == 4) {
+                gg_gradient_f32(v, ve, vw, vn, vs, isx_e, isx_w, isy_n, isy_s, gx, gy);
+            } else {
+                gx.x = (ve.x - v.x) * isx_e + (v.x - vw.x) * isx_w;
+                gx.y = (ve.y - v.y) * isx_e + (v.y - vw.y) * isx_w;
+                gx.z = (ve.z - v.z) * isx_e + (v.z - vw.z) * isx_w;
+                gx.w = (ve.w - v.w) * isx_e + (v.w - vw.w) * isx_w;
+                gy.x = (vn.x - v.x) * isy_n + (v.x - vs.x) * isy_s;
+                gy.y = (vn.y - v.y) * isy_n + (v.y - vs.y) * isy_s;
+                gy.z = (vn.z - v.z) * isy_n + (v.z - vs.z) * isy_s;
+                gy.w = (vn.w - v.w) * isy_n + (v.w - vs.w) * isy_s;
+            }
             if (xghosts) {
                 const Vec4<R> gxd = shfl_dn1(gx), gyd = shfl_dn1(gy);
                 const Vec4<R> gxu = shfl_up1(gx), gyu = shfl_up1(gy);
@@ -300,25 +304,39 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
                          const Vec4<R>& vyr, const Vec4<R>& gxyr, const Vec4<R>& gyyr,
                          Vec4<R>& Fxo, Vec4<R>& Fyo) {
             {
-                CellNT<R> L = {{vxl.x, vxl.y, vxl.z, R(0)}, {gxxl.x, gxxl.y, gxxl.z, gxxl.w},
-                               {gyxl.x, gyxl.y, gyxl.z, gyxl.w}};
-                CellNT<R> Rr = {{vxr.x, vxr.y, vxr.z, vxr.w - vxl.w},
-                                {gxxr.x, gxxr.y, gxxr.z, gxxr.w}, {gyxr.x, gyxr.y, gyxr.z, gyxr.w}};
                 R F[4];
-                face_flux<R>(L, Rr, Tz + vxl.w, flx, wsx >= 0 ? R(0) : R(1),
-                             wsx >= 0 ? P::bcU(dp, wsx) : R(0), F);
+                if constexpr (sizeof(R) == 4) {  // FP32: packed column stage
+                    R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+                    face_columns_f32<true>(vxl, vxr, gxxl, gyxl, gxxr, gyxr, flx, A, Sa, M, Sm, B, Sb);
+                    face_flux_columns<R>(A, Sa, M, Sm, B, Sb, Tz + vxl.w, flx, wsx >= 0 ? R(0) : R(1),
+                                         wsx >= 0 ? P::bcU(dp, wsx) : R(0), F);
+                } else {
+                    CellNT<R> L = {{vxl.x, vxl.y, vxl.z, R(0)}, {gxxl.x, gxxl.y, gxxl.z, gxxl.w},
+                                   {gyxl.x, gyxl.y, gyxl.z, gyxl.w}};
+                    CellNT<R> Rr = {{vxr.x, vxr.y, vxr.z, vxr.w - vxl.w},
+                                    {gxxr.x, gxxr.y, gxxr.z, gxxr.w}, {gyxr.x, gyxr.y, gyxr.z, gyxr.w}};
+                    face_flux<R>(L, Rr, Tz + vxl.w, flx, wsx >= 0 ? R(0) : R(1),
+                                 wsx >= 0 ? P::bcU(dp, wsx) : R(0), F);
+                }
                 Fxo = {F[0], F[1], F[2], F[3]};
             }
             {
                 const FaceLine<R> fly = yl[min(max(jf, 0), ny)];
                 const int ws = (wall_s && jf == 0) ? kSideS : ((wall_n && jf == ny) ? kSideN : -1);
-                CellNT<R> L = {{vyl.x, vyl.z, vyl.y, R(0)}, {gyyl.x, gyyl.z, gyyl.y, gyyl.w},
-                               {gxyl.x, gxyl.z, gxyl.y, gxyl.w}};
-                CellNT<R> Rr = {{vyr.x, vyr.z, vyr.y, vyr.w - vyl.w},
-                                {gyyr.x, gyyr.z, gyyr.y, gyyr.w}, {gxyr.x, gxyr.z, gxyr.y, gxyr.w}};
                 R F[4];
-                face_flux<R>(L, Rr, Tz + vyl.w, fly, ws >= 0 ? R(0) : R(1),
-                             ws >= 0 ? P::bcU(dp, ws) : R(0), F);
+                if constexpr (sizeof(R) == 4) {
+                    R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+                    face_columns_f32<false>(vyl, vyr, gyyl, gxyl, gyyr, gxyr, fly, A, Sa, M, Sm, B, Sb);
+                    face_flux_columns<R>(A, Sa, M, Sm, B, Sb, Tz + vyl.w, fly, ws >= 0 ? R(0) : R(1),
+                                         ws >= 0 ? P::bcU(dp, ws) : R(0), F);
+                } else {
+                    CellNT<R> L = {{vyl.x, vyl.z, vyl.y, R(0)}, {gyyl.x, gyyl.z, gyyl.y, gyyl.w},
+                                   {gxyl.x, gxyl.z, gxyl.y, gxyl.w}};
+                    CellNT<R> Rr = {{vyr.x, vyr.z, vyr.y, vyr.w - vyl.w},
+                                    {gyyr.x, gyyr.z, gyyr.y, gyyr.w}, {gxyr.x, gxyr.z, gxyr.y, gxyr.w}};
+                    face_flux<R>(L, Rr, Tz + vyl.w, fly, ws >= 0 ? R(0) : R(1),
+                                 ws >= 0 ? P::bcU(dp, ws) : R(0), F);
+                }
                 Fyo = {F[0], F[2], F[1], F[3]};
             }
         };
@@ -388,10 +406,15 @@ march_kernel(const CavityDesc* __restrict__ descs, CavityRun* __restrict__ runs,
                 const R ay = yc[j + 2].dt_w;
                 const R dr = v0.x, u = v0.y, v = v0.z, T = Tz + v0.w;
                 const R rho = one + dr;
-                const R div0 = ax * (Fe.x - Fx.x) + ay * (Fn.x - Fs.x);
-                const R div1 = ax * (Fe.y - Fx.y) + ay * (Fn.y - Fs.y);
-                const R div2 = ax * (Fe.z - Fx.z) + ay * (Fn.z - Fs.z);
-                const R div3 = ax * (Fe.w - Fx.w) + ay * (Fn.w - Fs.w);
+                R div0, div1, div2, div3;
+                if constexpr (sizeof(R) == 4) {
+                    flux_div_f32(Fx, Fe, Fs, Fn, ax, ay, div0, div1, div2, div3);
+                } else {
+                    div0 = ax * (Fe.x - Fx.x) + ay * (Fn.x - Fs.x);
+                    div1 = ax * (Fe.y - Fx.y) + ay * (Fn.y - Fs.y);
+                    div2 = ax * (Fe.z - Fx.z) + ay * (Fn.z - Fs.z);
+                    div3 = ax * (Fe.w - Fx.w) + ay * (Fn.w - Fs.w);
+                }
                 const R src_x = rho * P::fx(dp);
                 const R src_y = rho * (P::beta_g(dp) * (T - P::T_ref(dp)) + P::fy(dp));
                 const R dtc = P::dt(dp);

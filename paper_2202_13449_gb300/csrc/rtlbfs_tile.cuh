@@ -186,6 +186,16 @@ __device__ __forceinline__ void gg_gradient_r(const Vec4<R>& p, const Vec4<R>& e
     gy.w = (n.w - p.w) * iyn + (p.w - s.w) * iys;
 }
 
+// The same in FP32, two components per packed FP32x2 instruction.
+__device__ __forceinline__ void gg_gradient_r(const Vec4<float>& p, const Vec4<float>& e,
+                                              const Vec4<float>& w, const Vec4<float>& n,
+                                              const Vec4<float>& s, float ixe, float ixw,
+                                              float iyn, float iys, Vec4<float>& gx,
+                                              Vec4<float>& gy)
+{
+    gg_gradient_f32(p, e, w, n, s, ixe, ixw, iyn, iys, gx, gy);
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v)
 {
@@ -484,10 +494,21 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             }
             const R uw = wside >= 0 ? P::bcU(dp, wside) : R(0);
             R F[4];
-            if constexpr (SCHEME == 1)
+            if constexpr (SCHEME == 1) {
                 face_flux_tlbfs<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
-            else
+            } else if constexpr (sizeof(R) == 4) {
+                // FP32: the column stage in packed pairs of the storage order
+                const Vec4<R> gl = isx ? sm.gx[lr - 1][lc - 1] : sm.gy[lr - 1][lc - 1];
+                const Vec4<R> tl = isx ? sm.gy[lr - 1][lc - 1] : sm.gx[lr - 1][lc - 1];
+                const Vec4<R> gr = isx ? sm.gx[rr - 1][rc - 1] : sm.gy[rr - 1][rc - 1];
+                const Vec4<R> tr = isx ? sm.gy[rr - 1][rc - 1] : sm.gx[rr - 1][rc - 1];
+                R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+                face_columns_f32<isx>(sm.val[lr][lc], sm.val[rr][rc], gl, tl, gr, tr, fl, A, Sa, M,
+                                      Sm, B, Sb);
+                face_flux_columns<R>(A, Sa, M, Sm, B, Sb, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
+            } else {
                 face_flux<R>(L, Rr, Tbar, fl, wside >= 0 ? R(0) : R(1), uw, F);
+            }
             if (isx) out = {F[0], F[1], F[2], F[3]};
             else out = {F[0], F[2], F[1], F[3]};
         }
@@ -547,10 +568,15 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
             const R dr = p.x, u = p.y, v = p.z, T = Tz + p.w;
             const R rho = one + dr;
             // Dt/dV sum_k F_k dS_k for mass, momentum, energy
-            const R div0 = ax * (Fe.x - Fw.x) + ay * (Fn.x - Fs.x);
-            const R div1 = ax * (Fe.y - Fw.y) + ay * (Fn.y - Fs.y);
-            const R div2 = ax * (Fe.z - Fw.z) + ay * (Fn.z - Fs.z);
-            const R div3 = ax * (Fe.w - Fw.w) + ay * (Fn.w - Fs.w);
+            R div0, div1, div2, div3;
+            if constexpr (sizeof(R) == 4) {
+                flux_div_f32(Fw, Fe, Fs, Fn, ax, ay, div0, div1, div2, div3);
+            } else {
+                div0 = ax * (Fe.x - Fw.x) + ay * (Fn.x - Fs.x);
+                div1 = ax * (Fe.y - Fw.y) + ay * (Fn.y - Fs.y);
+                div2 = ax * (Fe.z - Fw.z) + ay * (Fn.z - Fs.z);
+                div3 = ax * (Fe.w - Fw.w) + ay * (Fn.w - Fs.w);
+            }
             // Boussinesq source (Eq. 64, hot fluid rises) and body force
             const R src_x = rho * fxb;
             const R src_y = rho * (bg * (T - Tr) + fyb);
