@@ -243,10 +243,15 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
     const R uw1 = wside >= 0 ? Cst<P>::uw(d, wside, a1) : R(0);
     const R uw2 = wside >= 0 ? Cst<P>::uw(d, wside, a2) : R(0);
     R F[5];
-    if (SCH == 1)
+    if constexpr (SCH == 1) {
         face_flux3_tlbfs<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
-    else
+    } else if constexpr (sizeof(R) == 4) {  // FP32: the node stage in packed pairs
+        R O[5], Pn[3][2][5], En[3][4][5];
+        face3_nodes_f32(L, Rc, fl, O, Pn, En);
+        face_flux3_nodes<R>(O, Pn, En, Tz + tauL, fl, keep, uw1, uw2, F);
+    } else {
         face_flux3<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
+    }
     out[0] = F[0];
     out[1 + ax] = F[1];
     out[1 + a1] = F[2];

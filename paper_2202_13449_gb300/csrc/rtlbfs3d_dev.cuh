@@ -49,15 +49,16 @@ struct CellNT3 {
 // keep = 1 on an interior face, 0 on a wall face whose tangential velocity
 // is (uw1, uw2): no mass through the wall, (rho u_t)* = rho* u_wall,t.
 // F = (mass, n-, t1-, t2-momentum, energy) flux along +n.
+//
+// The first stage, face3_nodes, forms the 19 node values of the five
+// primitives; face_flux3_nodes does the rest.
 template <typename V>
-__host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const CellNT3<V>& Rc,
-                                                   V Tbar, const FaceLine<V>& fl, V keep, V uw1,
-                                                   V uw2, V F[5])
+__host__ __device__ __forceinline__ void face3_nodes(const CellNT3<V>& L, const CellNT3<V>& Rc,
+                                                    const FaceLine<V>& fl, V O[5], V P[3][2][5],
+                                                    V E[3][4][5])
 {
     using T = vtraits<V>;
-    const V zero = T::bc(0.0), half = T::bc(0.5), quarter = T::bc(0.25), one = T::bc(1.0);
-    const V two = T::bc(2.0), m2 = T::bc(-2.0), mhalf = T::bc(-0.5);
-    const V cs2 = T::bc(1.0 / 3.0), hcs2 = T::bc(0.5 / 3.0);
+    const V half = T::bc(0.5);
     const V h = fl.h;
     const V wL = fl.cL + h, mwR = fl.cR - h;  // wL, -wR: centre-to-face distances
     const V hh = h * half;
@@ -80,7 +81,6 @@ __host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const C
     // node values: centre O, axis nodes P[a][s] (s = 0: -e_a, 1: +e_a), edge
     // nodes E[p][c] for the pairs p = (n,t1), (n,t2), (t1,t2) and the
     // corners c = (+,+), (+,-), (-,+), (-,-)
-    V O[5], P[3][2][5], E[3][4][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         O[k] = Mc[k];
@@ -104,6 +104,18 @@ __host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const C
         E[2][2][k] = mm + M2[k];
         E[2][3][k] = mm - M2[k];
     }
+}
+
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux3_nodes(const V O[5], const V P[3][2][5],
+                                                         const V E[3][4][5], V Tbar,
+                                                         const FaceLine<V>& fl, V keep, V uw1,
+                                                         V uw2, V F[5])
+{
+    using T = vtraits<V>;
+    const V zero = T::bc(0.0), half = T::bc(0.5), quarter = T::bc(0.25), one = T::bc(1.0);
+    const V two = T::bc(2.0), m2 = T::bc(-2.0), mhalf = T::bc(-0.5);
+    const V cs2 = T::bc(1.0 / 3.0), hcs2 = T::bc(0.5 / 3.0);
     constexpr int PA[3] = {0, 0, 1}, PB[3] = {1, 2, 2};  // axes of the edge pairs
 
     // momenta m_a = u_a + drho u_a at the centre and the axis nodes
@@ -235,6 +247,87 @@ __host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const C
         const V Q0 = mO[0] * (Tbar + O[4]);
         const V dQ = vfma(Tbar, ms[0] - mO[0], vfma(ms[0], taus, zero - mO[0] * O[4]));
         F[4] = vfma(fl.m_chi_2h, de[0], vfma(fl.m_tg15, dQ, Q0));
+    }
+}
+
+template <typename V>
+__host__ __device__ __forceinline__ void face_flux3(const CellNT3<V>& L, const CellNT3<V>& Rc,
+                                                   V Tbar, const FaceLine<V>& fl, V keep, V uw1,
+                                                   V uw2, V F[5])
+{
+    V O[5], P[3][2][5], E[3][4][5];
+    face3_nodes<V>(L, Rc, fl, O, P, E);
+    face_flux3_nodes<V>(O, P, E, Tbar, fl, keep, uw1, uw2, F);
+}
+
+// face3_nodes in FP32, components (0, 1) and (2, 3) in packed FP32x2 pairs
+// (component 4 alone): the same operations, bit for bit (a - b formed as
+// fma(b, -1, a), exact like the subtraction).
+__device__ __forceinline__ void face3_nodes_f32(const CellNT3<float>& L, const CellNT3<float>& Rc,
+                                                const FaceLine<float>& fl, float O[5],
+                                                float P[3][2][5], float E[3][4][5])
+{
+    const float h = fl.h;
+    const float wL = fl.cL + h, mwR = fl.cR - h, hh = h * 0.5f;
+    const float2 cL2 = make_float2(fl.cL, fl.cL), cR2 = make_float2(fl.cR, fl.cR);
+    const float2 wL2 = make_float2(wL, wL), mwR2 = make_float2(mwR, mwR);
+    const float2 h2 = make_float2(h, h), hh2 = make_float2(hh, hh);
+    const float2 half2 = make_float2(0.5f, 0.5f), m1 = make_float2(-1.0f, -1.0f);
+    auto pr = [](const float* a, int i) { return make_float2(a[2 * i], a[2 * i + 1]); };
+    auto sub = [&](float2 a, float2 b) { return __ffma2_rn(b, m1, a); };
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float2 q = pr(L.q, i), gn = pr(L.gn, i), g1 = pr(L.g1, i), g2 = pr(L.g2, i);
+        const float2 qr = pr(Rc.q, i), gnr = pr(Rc.gn, i), g1r = pr(Rc.g1, i), g2r = pr(Rc.g2, i);
+        const float2 Ac = __ffma2_rn(gn, cL2, q), A1 = __fmul2_rn(g1, h2), A2 = __fmul2_rn(g2, h2);
+        const float2 Bc = __ffma2_rn(gnr, cR2, qr), B1 = __fmul2_rn(g1r, h2),
+                     B2 = __fmul2_rn(g2r, h2);
+        const float2 Mc = __fmul2_rn(half2, __fadd2_rn(__ffma2_rn(gn, wL2, q), __ffma2_rn(gnr, mwR2, qr)));
+        const float2 M1 = __fmul2_rn(hh2, __fadd2_rn(g1, g1r)), M2 = __fmul2_rn(hh2, __fadd2_rn(g2, g2r));
+        const float2 pp = __fadd2_rn(Mc, M1), mm = sub(Mc, M1);
+        const float2 v[19] = {Mc,
+                              Ac, Bc, mm, pp, sub(Mc, M2), __fadd2_rn(Mc, M2),
+                              __fadd2_rn(Bc, B1), sub(Bc, B1), __fadd2_rn(Ac, A1), sub(Ac, A1),
+                              __fadd2_rn(Bc, B2), sub(Bc, B2), __fadd2_rn(Ac, A2), sub(Ac, A2),
+                              __fadd2_rn(pp, M2), sub(pp, M2), __fadd2_rn(mm, M2), sub(mm, M2)};
+        float* dst[19] = {&O[0],
+                          &P[0][0][0], &P[0][1][0], &P[1][0][0], &P[1][1][0], &P[2][0][0], &P[2][1][0],
+                          &E[0][0][0], &E[0][1][0], &E[0][2][0], &E[0][3][0],
+                          &E[1][0][0], &E[1][1][0], &E[1][2][0], &E[1][3][0],
+                          &E[2][0][0], &E[2][1][0], &E[2][2][0], &E[2][3][0]};
+#pragma unroll
+        for (int n = 0; n < 19; ++n) {
+            dst[n][2 * i] = v[n].x;
+            dst[n][2 * i + 1] = v[n].y;
+        }
+    }
+    {  // component 4
+        const float q = L.q[4], gn = L.gn[4], g1 = L.g1[4], g2 = L.g2[4];
+        const float qr = Rc.q[4], gnr = Rc.gn[4], g1r = Rc.g1[4], g2r = Rc.g2[4];
+        const float Ac = fmaf(gn, fl.cL, q), A1 = g1 * h, A2 = g2 * h;
+        const float Bc = fmaf(gnr, fl.cR, qr), B1 = g1r * h, B2 = g2r * h;
+        const float Mc = 0.5f * (fmaf(gn, wL, q) + fmaf(gnr, mwR, qr));
+        const float M1 = hh * (g1 + g1r), M2 = hh * (g2 + g2r);
+        const float pp = Mc + M1, mm = Mc - M1;
+        O[4] = Mc;
+        P[0][0][4] = Ac;
+        P[0][1][4] = Bc;
+        P[1][0][4] = mm;
+        P[1][1][4] = pp;
+        P[2][0][4] = Mc - M2;
+        P[2][1][4] = Mc + M2;
+        E[0][0][4] = Bc + B1;
+        E[0][1][4] = Bc - B1;
+        E[0][2][4] = Ac + A1;
+        E[0][3][4] = Ac - A1;
+        E[1][0][4] = Bc + B2;
+        E[1][1][4] = Bc - B2;
+        E[1][2][4] = Ac + A2;
+        E[1][3][4] = Ac - A2;
+        E[2][0][4] = pp + M2;
+        E[2][1][4] = pp - M2;
+        E[2][2][4] = mm + M2;
+        E[2][3][4] = mm - M2;
     }
 }
 
