@@ -52,6 +52,7 @@ using rtlbfs::chain_sync;
 using rtlbfs::launch_chained;
 using rtlbfs::FaceLine;
 using rtlbfs::face_flux;
+using rtlbfs::face_flux_columns;
 using rtlbfs::kConverged;
 using rtlbfs::kDiverged;
 using rtlbfs::kMaxSteps;
@@ -242,6 +243,38 @@ __host__ __device__ __forceinline__ void mirror_grad_c(int kind, R nx, R ny, R g
     }
 }
 
+// face_columns in FP32 on face-frame cells whose components were formed
+// in registers (a curvilinear face's rotated values): pairs (rho, u_n) and
+// (u_t, T) in packed FP32x2 instructions, the same operations bit for bit.
+__device__ __forceinline__ void face_columns_nt_f32(const rtlbfs::CellNT<float>& L, const rtlbfs::CellNT<float>& Rc,
+                                                    const FaceLine<float>& fl, float A[4],
+                                                    float Sa[4], float M[4], float Sm[4],
+                                                    float B[4], float Sb[4])
+{
+    const float h = fl.h;
+    const float wL = fl.cL + h, mwR = fl.cR - h, hh = h * 0.5f;
+    const float2 cL2 = make_float2(fl.cL, fl.cL), cR2 = make_float2(fl.cR, fl.cR);
+    const float2 wL2 = make_float2(wL, wL), mwR2 = make_float2(mwR, mwR);
+    const float2 h2 = make_float2(h, h), hh2 = make_float2(hh, hh), half2 = make_float2(0.5f, 0.5f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int k = 2 * i;
+        const float2 ql = make_float2(L.q[k], L.q[k + 1]), qr = make_float2(Rc.q[k], Rc.q[k + 1]);
+        const float2 nl = make_float2(L.gn[k], L.gn[k + 1]), nr = make_float2(Rc.gn[k], Rc.gn[k + 1]);
+        const float2 tl = make_float2(L.gt[k], L.gt[k + 1]), tr = make_float2(Rc.gt[k], Rc.gt[k + 1]);
+        const float2 a = __ffma2_rn(nl, cL2, ql), sa = __fmul2_rn(tl, h2);
+        const float2 b = __ffma2_rn(nr, cR2, qr), sb = __fmul2_rn(tr, h2);
+        const float2 m = __fmul2_rn(half2, __fadd2_rn(__ffma2_rn(nl, wL2, ql), __ffma2_rn(nr, mwR2, qr)));
+        const float2 sm = __fmul2_rn(hh2, __fadd2_rn(tl, tr));
+        A[k] = a.x, A[k + 1] = a.y;
+        Sa[k] = sa.x, Sa[k + 1] = sa.y;
+        B[k] = b.x, B[k + 1] = b.y;
+        Sb[k] = sb.x, Sb[k + 1] = sb.y;
+        M[k] = m.x, M[k + 1] = m.y;
+        Sm[k] = sm.x, Sm[k + 1] = sm.y;
+    }
+}
+
 // One face: values v[4] = (rho - 1, u, v, T - Tz) and gradients g[8] of the
 // two cells, the face geometry, the wall flag and tangential wall velocity.
 // Returns the fluxes times the face length in x, y components.
@@ -286,7 +319,18 @@ __host__ __device__ __forceinline__ void face_c(const R vL[4], const R gL[8], co
     fl.pad = R(0);
     const R uwt = uwx * tx + uwy * ty;
     R F[4];
-    face_flux<R>(L, Rr, Tz + tauL, fl, keep, uwt, F);
+#ifdef __CUDA_ARCH__
+    constexpr bool packed = sizeof(R) == 4;  // FP32 on the device: packed column stage
+#else
+    constexpr bool packed = false;
+#endif
+    if constexpr (packed) {
+        R A[4], Sa[4], M[4], Sm[4], B[4], Sb[4];
+        face_columns_nt_f32(L, Rr, fl, A, Sa, M, Sm, B, Sb);
+        face_flux_columns<R>(A, Sa, M, Sm, B, Sb, Tz + tauL, fl, keep, uwt, F);
+    } else {
+        face_flux<R>(L, Rr, Tz + tauL, fl, keep, uwt, F);
+    }
     out[0] = F[0] * fg.len;
     out[1] = (F[1] * nx + F[2] * tx) * fg.len;
     out[2] = (F[1] * ny + F[2] * ty) * fg.len;
