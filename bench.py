@@ -161,6 +161,18 @@ WORKLOADS = {
              "refined to 3600 (around) x 2400 (radial) cells (8.64 M cells, 138 MB of state per "
              "buffer, > L2), same far field, first spacing and physics; FP32",
         ni=3600, nj=2400, Re=20.0, Gr=100.0, Pr=0.7, precision="fp32", inner=20, kind="curv"),
+    "cavity_tables": dict(
+        desc="Tables 1-3 of Section 4.2 on this GPU: the differentially heated square cavity at "
+             "Ra = 1e3 ... 1e8 on the paper's meshes (uniform 100^2, 150^2, 200^2, 250^2; "
+             "300^2 and 400^2 stretched in Eq. 74's tanh form to first cells of 0.0004 L and "
+             "0.0002 L), Pr = 0.71, V_c = 0.1, FP32, each from the conduction state to a steady "
+             "state: max(R_u, R_T) < tol on the uniform meshes; on the stretched ones (time steps "
+             "of 0.04-0.06 against 0.5, where a per-step tolerance says little) until the reported "
+             "quantities change by less than window_tol over window_conv_times convective times "
+             "L/V_c, or the time limit; centreline velocity maxima, streamfunction maximum, Nu_a "
+             "(Eq. 69) and Nu_1/2 against the paper's RTLBFS values",
+        tol=1e-7, max_steps=50_000_000, time_limit=300.0, window_conv_times=20.0,
+        window_tol=2e-4, precision="fp32", kind="cavity_tables"),
     "table4": dict(
         desc="Table 4 of Section 4.3 on this GPU: mean Nusselt number (Eq. 73) and separation "
              "angle on the heated cylinder at Re = 20, Pr = 0.7, Gr = 0, 100, 800, 1600, each run "
@@ -1173,6 +1185,138 @@ def run_table4(args, w):
     print(json.dumps(line), flush=True)
 
 
+def stretch_to_first_cell(n, L, w1):
+    """The phi of Eq. 74's tanh faces on [0, L] whose first cell is w1 wide
+    (the first width falls as phi grows; bisection)."""
+    from paper_2202_13449_gb300 import capi
+    lo, hi = 1e-3, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        f = capi.tanh_faces(n, L, mid)
+        if f[1] - f[0] > w1:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def run_cavity_tables(args, w):
+    """Tables 1-3 on the GPU: each case from the conduction state to a
+    steady state (max(R_u, R_T) < tol, the step cap or the time limit),
+    then the paper's quantities from the state and the Nusselt reductions.
+    The line's value is the largest relative deviation of the velocity,
+    streamfunction and Nusselt maxima of the converged cases from the
+    paper's RTLBFS values."""
+    import numpy as np
+    import torch
+    from paper_2202_13449_gb300 import capi, inputs, post
+    torch.cuda.set_device(0)
+    capi.lib()
+    with open(os.path.join(ROOT, "tests", "golden", "tables123_cavity.json")) as f:
+        gold = json.load(f)
+    Pr, Vc = gold["Pr"], gold["Vc"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    launches0 = capi.launch_count()
+    clk = ClockSampler(0)
+    clk.start()
+    max_steps = args.max_steps or w["max_steps"]
+    tlim = args.time_limit or w["time_limit"]
+    tol = args.tol or w["tol"]
+    rows, worst, cu, total_ms = [], 0.0, 0.0, 0.0
+    for g in gold["cases"]:
+        n, L = g["n"], float(g["n"])
+        if g["wall"] > 0.0:
+            phi = stretch_to_first_cell(n, L, g["wall"] * L)
+            xf = capi.tanh_faces(n, L, phi)
+        else:
+            phi = 0.0
+            xf = inputs.uniform_faces(n, L)
+        s = capi.Solver(xf, xf, capi.FP32)
+        s.set_params(g["Ra"], Pr, Vc, 0.0)  # dt by the library's stability rule
+        s.set_stream(stream)
+        s.autotune(32)  # this mesh's schedule, on a snapshot of the initial state
+        nu = Vc * L * np.sqrt(Pr / g["Ra"])  # the library's mapping (Eq. 63, V_c = Ma)
+        chi = nu / Pr
+        wmin = float(np.min(np.diff(xf)))
+        dt = min(0.5 * wmin, 0.2 * wmin * wmin / max(nu, chi))  # the library's rule
+
+        def quantities():
+            rho, u, v, T = s.get_state()
+            umax, uy, vmax, vx = post.cavity_centrelines(xf, xf, u, v)
+            q = {"u_max": umax * L / chi, "u_max_y": uy, "v_max": vmax * L / chi,
+                 "v_max_x": vx, "Nu_a": s.nusselt(capi.NU_AVG),
+                 "Nu_half": s.nusselt(capi.NU_HALF)}
+            pmax, px, py = post.streamfunction_max(xf, xf, u)
+            q.update({"psi_max": pmax / chi, "psi_max_x": px, "psi_max_y": py})
+            return q
+
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        windows, change = 0, None
+        if g["wall"] == 0.0:
+            a.record(stream)
+            rc, steps, res = s.run_to_steady(tol, max_steps, timeout_s=tlim)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            got = quantities()
+        else:
+            chunk = int(round(w["window_conv_times"] * (L / Vc) / dt))
+            t0 = time.time()
+            steps, ms, prev, rc = 0, 0.0, None, capi.ERR_TIMEOUT
+            while time.time() - t0 < tlim and steps + chunk <= max_steps:
+                a.record(stream)
+                s.step(chunk)
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b)
+                steps += chunk
+                windows += 1
+                got = quantities()
+                keys = ("u_max", "v_max", "Nu_a", "Nu_half", "psi_max")
+                if prev is not None:
+                    change = max(abs(got[k] - prev[k]) / abs(got[k]) for k in keys)
+                    if change < w["window_tol"]:
+                        rc = 0
+                        break
+                prev = got
+            (res_u, res_T), _ = s.residual()
+            res = [res_u, res_T]
+        total_ms += ms
+        cu += float(n * n) * steps
+        s.close()
+        dev = {}
+        for k, ref in g.items():
+            if k in ("Ra", "n", "wall"):
+                continue
+            if k.endswith(("_x", "_y")):
+                dev[k] = round(abs(got[k] - ref), 4)  # positions: absolute, in L
+            else:
+                dev[k] = round(abs(got[k] - ref) / abs(ref), 4)
+                if rc == 0:
+                    worst = max(worst, dev[k])
+        rows.append({"Ra": g["Ra"], "n": n, "phi": round(phi, 5), "status": rc, "steps": steps,
+                     "dt": dt, "residual": res, "device_s": round(ms / 1e3, 2),
+                     "windows": windows, "last_window_change": change,
+                     "got": {k: round(v2, 5) for k, v2 in got.items()},
+                     "paper": {k: g[k] for k in dev}, "deviation": dev})
+    clocks = clk.stop()
+    line = {
+        "metric": "max relative deviation from the paper's Tables 1-3 (converged cases)",
+        "value": round(worst, 4), "unit": "ratio", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "tol": tol,
+                   "max_steps": max_steps, "time_limit_s": tlim},
+        "cases": rows,
+        "throughput_M_cell_updates_per_s": round(cu / (total_ms * 1e-3) / 1e6, 1),
+        "gpu_launches": int(capi.launch_count() - launches0),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def curv_case(inputs, w):
     """The Section 4.3 cylinder: mesh, physics and the free-stream state."""
     import numpy as np
@@ -1338,6 +1482,8 @@ def run_ours(args, w):
         return run_table6(args, w)
     if w.get("kind") == "table4":
         return run_table4(args, w)
+    if w.get("kind") == "cavity_tables":
+        return run_cavity_tables(args, w)
     if w.get("kind") == "cubic":
         return run_cubic(args, w)
     if w.get("kind") == "schemes":
@@ -1883,7 +2029,8 @@ def main():
         args.warmup = 3
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6", "table4"):
+        if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6", "table4",
+                             "cavity_tables"):
             print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
                               "time to a steady state of the GPU path; the oracle's rate is the "
                               "rb1024x512 / cavity512 reference lines"}))
