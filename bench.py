@@ -1264,7 +1264,7 @@ def run_cavity_tables(args, w):
         else:
             chunk = int(round(w["window_conv_times"] * (L / Vc) / dt))
             t0 = time.time()
-            steps, ms, prev, rc = 0, 0.0, None, capi.ERR_TIMEOUT
+            steps, ms, prev, rc, got = 0, 0.0, None, capi.ERR_TIMEOUT, None
             while time.time() - t0 < tlim and steps + chunk <= max_steps:
                 a.record(stream)
                 s.step(chunk)
@@ -1281,6 +1281,8 @@ def run_cavity_tables(args, w):
                         rc = 0
                         break
                 prev = got
+            if got is None:  # no window fitted in the limits
+                got = quantities()
             (res_u, res_T), _ = s.residual()
             res = [res_u, res_T]
         total_ms += ms
