@@ -493,8 +493,29 @@ def run_batch(args, w):
         for s in slots:
             out = b.get_state(s)
     torch.cuda.synchronize()
+    e2e_planes = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
+    # the same through the state records (rtlbfs_batch_get/set_state_raw):
+    # the device's own cell records up and down, no conversion kernel
+    rec_in, rec_out, tunit = {}, {}, {}
+    for s in slots:
+        b.set_state(s, *host[s])
+        nb = b.raw_bytes(s)
+        rec_in[s] = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
+        rec_out[s] = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
+        tunit[s] = b.get_state_raw(s, out=rec_in[s])[1]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s in slots:
+            b.set_state_raw(s, rec_in[s], tunit[s])
+            b.arm(s, 0.0, inner)
+        b.step(inner)
+        for s in slots:
+            b.get_state_raw(s, out=rec_out[s])
+    torch.cuda.synchronize()
     e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     bytes_io = 4 * 8 * cells
+    bytes_rec = 4 * rs * cells
     line = {
         "metric": "M cell-updates/s (whole job) and fraction of the ALU and HBM rooflines",
         "value": round(value, 2), "unit": "M cell-updates/s", "n_gpus": ws,
@@ -508,9 +529,15 @@ def run_batch(args, w):
                    "schedule": {"kernel": SCHED_NAMES[sched[0]], "chunk_rows": sched[1]},
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
-                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
-                "note": "per bench step: all states uploaded from pinned host memory, "
-                        f"{inner} batched time steps, all states downloaded"},
+                "h2d_bytes_per_step": bytes_rec, "d2h_bytes_per_step": bytes_rec,
+                "api": "rtlbfs_batch_set_state_raw / rtlbfs_batch_step / "
+                       "rtlbfs_batch_get_state_raw, pinned",
+                "note": "per bench step: every cavity's state records uploaded from pinned host "
+                        f"memory, {inner} batched time steps, every state downloaded"},
+        "e2e_planes": {"value": round(e2e_planes, 2), "unit": "M cell-updates/s",
+                       "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+                       "api": "rtlbfs_batch_set_state / rtlbfs_batch_step / "
+                              "rtlbfs_batch_get_state, pinned (four FP64 planes)"},
         "gpu_launches": int(launches),
         "roofline": alu,
         "roofline_hbm": hbm,

@@ -69,6 +69,23 @@ int rtlbfs_batch_set_state(rtlbfs_batch_t b, int slot, const double* rho, const 
 int rtlbfs_batch_get_state(rtlbfs_batch_t b, int slot, double* rho, double* u, double* v,
                            double* T);
 
+/*
+ * A slot's state as the device stores it (as rtlbfs_get_state_raw /
+ * rtlbfs_set_state_raw of include/rtlbfs.h): ny x nx cell records without
+ * row padding, 16 bytes in FP32 (fixed point, temperature in units of
+ * 2^-30 * T_unit) or 32 in FP64; exact in both directions, half the bytes
+ * of the FP64 planes in FP32 and no conversion kernel.
+ * rtlbfs_batch_state_raw_bytes: the size of a slot's records (0 for a bad
+ * handle or slot).  get writes the records and the temperature unit
+ * (T_unit may be null); set takes them (T_unit 1 in FP64, a power of two
+ * >= 1 in FP32, else ERR_ARG) and, like rtlbfs_batch_set_state, resets the
+ * slot's step counter and run control.  records: caller-owned host memory
+ * (pinned memory lets the copies run as DMA); both return after the copy.
+ */
+size_t rtlbfs_batch_state_raw_bytes(rtlbfs_batch_t b, int slot);
+int rtlbfs_batch_get_state_raw(rtlbfs_batch_t b, int slot, void* records, double* T_unit);
+int rtlbfs_batch_set_state_raw(rtlbfs_batch_t b, int slot, const void* records, double T_unit);
+
 /* Let a slot take up to max_steps more steps, stopping after the first step
  * with max(R_u, R_T) < tol (tol <= 0: never). */
 int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps);

@@ -104,6 +104,9 @@ _SIGS = {
     "rtlbfs_batch_set_lattice": (C.c_int, [_vp, C.c_int, C.c_double]),
     "rtlbfs_batch_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
     "rtlbfs_batch_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp]),
+    "rtlbfs_batch_state_raw_bytes": (C.c_size_t, [_vp, C.c_int]),
+    "rtlbfs_batch_get_state_raw": (C.c_int, [_vp, C.c_int, _vp, _dp]),
+    "rtlbfs_batch_set_state_raw": (C.c_int, [_vp, C.c_int, _vp, C.c_double]),
     "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
     "rtlbfs_batch_step": (C.c_int, [_vp, C.c_long]),
     "rtlbfs_batch_poll": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_long), _dp]),
@@ -535,6 +538,27 @@ class Batch:
         self._check(lib().rtlbfs_batch_get_state(self._h, slot, *[_ptr(a) for a in out]),
                     "batch_get_state")
         return tuple(out)
+
+    def raw_bytes(self, slot) -> int:
+        return int(lib().rtlbfs_batch_state_raw_bytes(self._h, int(slot)))
+
+    def get_state_raw(self, slot, out=None):
+        """(records, T_unit) of a slot: its cell records as a uint8 array (or
+        into `out`, any writable buffer of raw_bytes(slot) bytes) and the
+        temperature unit."""
+        if out is None:
+            out = np.empty(self.raw_bytes(slot), dtype=np.uint8)
+        tu = C.c_double()
+        self._check(lib().rtlbfs_batch_get_state_raw(self._h, int(slot), _vp(out.ctypes.data),
+                                                     C.byref(tu)), "batch_get_state_raw")
+        return out, tu.value
+
+    def set_state_raw(self, slot, records, T_unit: float = 1.0):
+        a = np.ascontiguousarray(records).view(np.uint8).reshape(-1)
+        if a.size != self.raw_bytes(slot):
+            raise ValueError(f"expected {self.raw_bytes(slot)} bytes, got {a.size}")
+        self._check(lib().rtlbfs_batch_set_state_raw(self._h, int(slot), _vp(a.ctypes.data),
+                                                     float(T_unit)), "batch_set_state_raw")
 
     def arm(self, slot, tol, max_steps):
         self._check(lib().rtlbfs_batch_arm(self._h, slot, float(tol), int(max_steps)), "batch_arm")

@@ -147,6 +147,25 @@ int rtlbfs_batch_get_state(rtlbfs_batch_t b, int slot, double* rho, double* u, d
     return bfinish(b, b->eng->get_state(slot, rho, u, v, T));
 }
 
+size_t rtlbfs_batch_state_raw_bytes(rtlbfs_batch_t b, int slot)
+{
+    if (!b) return 0;
+    const rtlbfs::Cavity* c = b->eng->cavity(slot);  // null for a bad slot
+    return c ? b->eng->record_bytes() * (size_t)c->nx * (size_t)c->ny : 0;
+}
+
+int rtlbfs_batch_get_state_raw(rtlbfs_batch_t b, int slot, void* records, double* T_unit)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    return bfinish(b, b->eng->get_records(slot, records, T_unit));
+}
+
+int rtlbfs_batch_set_state_raw(rtlbfs_batch_t b, int slot, const void* records, double T_unit)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    return bfinish(b, b->eng->set_records(slot, records, T_unit));
+}
+
 int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps)
 {
     if (!b || max_steps < 0) return RTLBFS_ERR_ARG;

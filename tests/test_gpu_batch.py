@@ -160,3 +160,50 @@ def test_batch_workload_stays_stable_with_the_automatic_step():
     assert all(st == capi.SLOT_MAX_STEPS for st in status[:len(specs)]), status
     assert all(k == 300 for k in steps[:len(specs)])
     b.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_batch_raw_checkpoint_resumes_bit_for_bit(precision):
+    """Every slot's records taken after some batched steps and restored into
+    a fresh batch continue bit for bit like the uninterrupted batch."""
+    def build():
+        b = capi.Batch(precision, 8)
+        slots = []
+        for nx, ny, phi, Ra, seed in SPECS:
+            xf = capi.tanh_faces(nx, float(nx), phi)
+            yf = capi.tanh_faces(ny, float(nx) * ny / nx, phi)
+            dt = 0.5 * float(min(np.min(np.diff(xf)), np.min(np.diff(yf))))
+            s = b.add(xf, yf, Ra, 0.71, 0.1, dt)
+            b.set_state(s, *inputs.perturbed_state(nx, ny, seed=seed))
+            slots.append(s)
+        return b, slots
+
+    a, sa = build()
+    for s in sa:
+        a.arm(s, 0.0, 20)
+    a.step(20)
+    recs = [a.get_state_raw(s) for s in sa]
+    for s, (r, _) in zip(sa, recs):
+        rec_bytes = 16 if precision == capi.FP32 else 32
+        nx, ny = SPECS[sa.index(s)][0], SPECS[sa.index(s)][1]
+        assert r.size == a.raw_bytes(s) == nx * ny * rec_bytes
+    for s in sa:
+        a.arm(s, 0.0, 15)
+    a.step(15)
+    want = [a.get_state(s) for s in sa]
+    b, sb = build()
+    for s, (r, tu) in zip(sb, recs):
+        b.set_state_raw(s, r, tu)
+        b.arm(s, 0.0, 15)
+    b.step(15)
+    for s_a, s_b, wv in zip(sa, sb, want):
+        got = b.get_state(s_b)
+        for q in range(4):
+            np.testing.assert_array_equal(got[q], wv[q])
+        np.testing.assert_array_equal(b.get_state_raw(s_b)[0], a.get_state_raw(s_a)[0])
+    with pytest.raises(capi.RTLBFSError):
+        b.set_state_raw(sb[0], recs[0][0], 3.0)  # not a power of two
+    with pytest.raises(ValueError):
+        b.set_state_raw(sb[0], recs[0][0][:-16], recs[0][1])
+    a.close()
+    b.close()
