@@ -503,15 +503,17 @@ def run_batch(args, w):
         rec_in[s] = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
         rec_out[s] = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
         tunit[s] = b.get_state_raw(s, out=rec_in[s])[1]
+    ins = [rec_in[s] for s in slots]
+    outs = [rec_out[s] for s in slots]
+    units = [tunit[s] for s in slots]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        b.set_states_raw(slots, ins, units)  # every slot's records in one call
         for s in slots:
-            b.set_state_raw(s, rec_in[s], tunit[s])
             b.arm(s, 0.0, inner)
         b.step(inner)
-        for s in slots:
-            b.get_state_raw(s, out=rec_out[s])
+        b.get_states_raw(slots, outs)
     torch.cuda.synchronize()
     e2e = cells * inner * e2e_steps * ws / job_max(time.perf_counter() - t0) / 1e6
     bytes_io = 4 * 8 * cells
@@ -530,8 +532,8 @@ def run_batch(args, w):
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": bytes_rec, "d2h_bytes_per_step": bytes_rec,
-                "api": "rtlbfs_batch_set_state_raw / rtlbfs_batch_step / "
-                       "rtlbfs_batch_get_state_raw, pinned",
+                "api": "rtlbfs_batch_set_states_raw / rtlbfs_batch_step / "
+                       "rtlbfs_batch_get_states_raw (all slots in one call each), pinned",
                 "note": "per bench step: every cavity's state records uploaded from pinned host "
                         f"memory, {inner} batched time steps, every state downloaded"},
         "e2e_planes": {"value": round(e2e_planes, 2), "unit": "M cell-updates/s",

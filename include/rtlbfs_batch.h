@@ -86,6 +86,21 @@ size_t rtlbfs_batch_state_raw_bytes(rtlbfs_batch_t b, int slot);
 int rtlbfs_batch_get_state_raw(rtlbfs_batch_t b, int slot, void* records, double* T_unit);
 int rtlbfs_batch_set_state_raw(rtlbfs_batch_t b, int slot, const void* records, double T_unit);
 
+/*
+ * The same for n slots in one call: slots[k]'s records from / to
+ * records[k] (each rtlbfs_batch_state_raw_bytes(b, slots[k]) bytes of
+ * caller-owned host memory) and its unit T_units[k] (T_units may be null
+ * for get).  Every copy is queued on the batch's stream and the call
+ * synchronises once, so with pinned buffers the copies run back to back
+ * as DMA.  Arguments are checked before any copy: ERR_ARG for n < 0, a
+ * null array, a slot not in use, a null record pointer or (set) a bad
+ * unit; nothing is copied then.
+ */
+int rtlbfs_batch_get_states_raw(rtlbfs_batch_t b, int n, const int* slots, void* const* records,
+                                double* T_units);
+int rtlbfs_batch_set_states_raw(rtlbfs_batch_t b, int n, const int* slots,
+                                const void* const* records, const double* T_units);
+
 /* Let a slot take up to max_steps more steps, stopping after the first step
  * with max(R_u, R_T) < tol (tol <= 0: never). */
 int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps);

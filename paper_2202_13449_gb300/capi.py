@@ -107,6 +107,8 @@ _SIGS = {
     "rtlbfs_batch_state_raw_bytes": (C.c_size_t, [_vp, C.c_int]),
     "rtlbfs_batch_get_state_raw": (C.c_int, [_vp, C.c_int, _vp, _dp]),
     "rtlbfs_batch_set_state_raw": (C.c_int, [_vp, C.c_int, _vp, C.c_double]),
+    "rtlbfs_batch_get_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
+    "rtlbfs_batch_set_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
     "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
     "rtlbfs_batch_step": (C.c_int, [_vp, C.c_long]),
     "rtlbfs_batch_poll": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_long), _dp]),
@@ -559,6 +561,33 @@ class Batch:
             raise ValueError(f"expected {self.raw_bytes(slot)} bytes, got {a.size}")
         self._check(lib().rtlbfs_batch_set_state_raw(self._h, int(slot), _vp(a.ctypes.data),
                                                      float(T_unit)), "batch_set_state_raw")
+
+    def get_states_raw(self, slots, outs):
+        """Records of several slots in one call, into the writable buffers
+        outs[k] (raw_bytes(slots[k]) bytes each); returns their T_units."""
+        n = len(slots)
+        sl = np.ascontiguousarray(slots, dtype=np.int32)
+        ptrs = (_vp * n)(*[_vp(np.asarray(o).ctypes.data) for o in outs])
+        tu = np.empty(n)
+        self._check(lib().rtlbfs_batch_get_states_raw(self._h, n, _vp(sl.ctypes.data),
+                                                      C.cast(ptrs, _vp), _ptr(tu)),
+                    "batch_get_states_raw")
+        return tu
+
+    def set_states_raw(self, slots, recs, T_units):
+        """Restore several slots' records in one call."""
+        n = len(slots)
+        sl = np.ascontiguousarray(slots, dtype=np.int32)
+        arrs = [np.ascontiguousarray(r).view(np.uint8).reshape(-1) for r in recs]
+        for s, a in zip(slots, arrs):
+            nb = self.raw_bytes(s)  # 0: not a slot in use, refused by the library
+            if nb and a.size != nb:
+                raise ValueError(f"slot {s}: expected {nb} bytes, got {a.size}")
+        ptrs = (_vp * n)(*[_vp(a.ctypes.data) for a in arrs])
+        tu = np.ascontiguousarray(T_units, dtype=np.float64)
+        self._check(lib().rtlbfs_batch_set_states_raw(self._h, n, _vp(sl.ctypes.data),
+                                                      C.cast(ptrs, _vp), _ptr(tu)),
+                    "batch_set_states_raw")
 
     def arm(self, slot, tol, max_steps):
         self._check(lib().rtlbfs_batch_arm(self._h, slot, float(tol), int(max_steps)), "batch_arm")

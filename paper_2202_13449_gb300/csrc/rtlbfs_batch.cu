@@ -166,6 +166,20 @@ int rtlbfs_batch_set_state_raw(rtlbfs_batch_t b, int slot, const void* records, 
     return bfinish(b, b->eng->set_records(slot, records, T_unit));
 }
 
+int rtlbfs_batch_get_states_raw(rtlbfs_batch_t b, int n, const int* slots, void* const* records,
+                                double* T_units)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    return bfinish(b, b->eng->get_records_many(n, slots, records, T_units));
+}
+
+int rtlbfs_batch_set_states_raw(rtlbfs_batch_t b, int n, const int* slots,
+                                const void* const* records, const double* T_units)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    return bfinish(b, b->eng->set_records_many(n, slots, records, T_units));
+}
+
 int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps)
 {
     if (!b || max_steps < 0) return RTLBFS_ERR_ARG;

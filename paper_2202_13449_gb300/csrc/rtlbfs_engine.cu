@@ -891,6 +891,64 @@ int Engine::get_records(int slot, void* host, double* T_unit)
 int Engine::set_records(int slot, const void* host, double T_unit)
 {
     Nvtx range("rtlbfs: state records in");
+    int rc = queue_set_records(slot, host, T_unit);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::set_records_many(int n, const int* slots, const void* const* host,
+                             const double* T_units)
+{
+    Nvtx range("rtlbfs: state records in, many");
+    if (n < 0 || (n > 0 && (!slots || !host || !T_units)))
+        return fail(RTLBFS_ERR_ARG, "null slot, record or unit array");
+    for (int k = 0; k < n; ++k) {
+        if (!cavity(slots[k]) || !host[k]) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+        int e2 = 0;
+        const double m = std::frexp(T_units[k], &e2);
+        if (precision_ == RTLBFS_FP64 ? T_units[k] != 1.0 : !(T_units[k] >= 1.0 && m == 0.5))
+            return fail(RTLBFS_ERR_ARG, "T_unit must be 1 (FP64) or a power of two >= 1 (FP32)");
+    }
+    for (int k = 0; k < n; ++k) {
+        int rc = queue_set_records(slots[k], host[k], T_units[k]);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::get_records_many(int n, const int* slots, void* const* host, double* T_units)
+{
+    Nvtx range("rtlbfs: state records out, many");
+    if (n < 0 || (n > 0 && (!slots || !host)))
+        return fail(RTLBFS_ERR_ARG, "null slot or record array");
+    for (int k = 0; k < n; ++k)
+        if (!cavity(slots[k]) || !host[k]) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
+    for (int k = 0; k < n; ++k)
+        if (slots_[slots[k]].dirty) {
+            int rc = upload_lines(slots[k]);
+            if (rc) return rc;
+        }
+    std::vector<CavityCtl> ctl;
+    int rc = read_ctls(ctl);  // the buffer of every slot's current state
+    if (rc) return rc;
+    const size_t rec = record_bytes();
+    for (int k = 0; k < n; ++k) {
+        const int slot = slots[k];
+        const Cavity* c = &slots_[slot];
+        CK(cudaMemcpy2DAsync(host[k], rec * c->nx, h_desc_[slot].f[ctl[slot].cur & 1][0],
+                             rec * c->pitch, rec * c->nx, c->ny, cudaMemcpyDeviceToHost, stream_));
+        if (T_units) T_units[k] = c->T_unit;
+    }
+    CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+// set_records without the final synchronisation: the copy from the host
+// array is queued (pageable memory is staged before the copy call returns)
+int Engine::queue_set_records(int slot, const void* host, double T_unit)
+{
     Cavity* c = cavity(slot);
     if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
     int e2 = 0;
@@ -898,10 +956,15 @@ int Engine::set_records(int slot, const void* host, double T_unit)
     if (precision_ == RTLBFS_FP64 ? T_unit != 1.0 : !(T_unit >= 1.0 && m == 0.5))
         return fail(RTLBFS_ERR_ARG, "T_unit must be 1 (FP64) or a power of two >= 1 (FP32)");
     c->state_Tmax = 0.0;
-    c->T_unit = T_unit;  // the records' unit; a configuration needing more rescales them
-    c->dirty = true;
-    int rc = upload_lines(slot);
-    if (rc) return rc;
+    // the records' unit; a configuration needing more rescales them.  In
+    // the unit the slot already has, with its lines and descriptor current,
+    // nothing needs uploading again (the unit was checked at that upload).
+    if (T_unit != c->T_unit || c->dirty) {
+        c->T_unit = T_unit;
+        c->dirty = true;
+        int rc = upload_lines(slot);
+        if (rc) return rc;
+    }
     const size_t rec = record_bytes();
     CK(cudaMemcpy2DAsync(h_desc_[slot].f[0][0], rec * c->pitch, host, rec * c->nx, rec * c->nx,
                          c->ny, cudaMemcpyHostToDevice, stream_));
@@ -916,10 +979,7 @@ int Engine::set_records(int slot, const void* host, double T_unit)
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
-    rc = put_run(slot, z);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(stream_));
-    return RTLBFS_OK;
+    return put_run(slot, z);
 }
 
 int Engine::set_conduction_state(int slot)

@@ -107,6 +107,10 @@ public:
     // ways; host memory (pinned memory makes the copies asynchronous DMA)
     int get_records(int slot, void* host, double* T_unit);
     int set_records(int slot, const void* host, double T_unit);
+    // several slots at once: every copy queued, one synchronisation
+    int get_records_many(int n, const int* slots, void* const* host, double* T_units);
+    int set_records_many(int n, const int* slots, const void* const* host, const double* T_units);
+    int queue_set_records(int slot, const void* host, double T_unit);
     size_t record_bytes() const { return 4 * rsize_; }
 
     // run control: arm a slot for up to nsteps steps (tol < 0: no early stop)

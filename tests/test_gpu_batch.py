@@ -207,3 +207,40 @@ def test_batch_raw_checkpoint_resumes_bit_for_bit(precision):
         b.set_state_raw(sb[0], recs[0][0][:-16], recs[0][1])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [capi.FP64, capi.FP32])
+def test_batch_records_of_many_slots_in_one_call(precision):
+    """rtlbfs_batch_get/set_states_raw equal the per-slot calls byte for
+    byte, and refuse bad arguments before copying anything."""
+    b = capi.Batch(precision, 8)
+    slots = []
+    for nx, ny, phi, Ra, seed in SPECS:
+        xf = capi.tanh_faces(nx, float(nx), phi)
+        yf = capi.tanh_faces(ny, float(nx) * ny / nx, phi)
+        s = b.add(xf, yf, Ra, 0.71, 0.1, 0.0)
+        b.set_state(s, *inputs.perturbed_state(nx, ny, seed=seed))
+        b.arm(s, 0.0, 7)
+        slots.append(s)
+    b.step(7)
+    one = [b.get_state_raw(s) for s in slots]
+    outs = [np.zeros(b.raw_bytes(s), dtype=np.uint8) for s in slots]
+    tu = b.get_states_raw(slots, outs)
+    for (r, t), o, u in zip(one, outs, tu):
+        np.testing.assert_array_equal(o, r)
+        assert u == t
+    # set many: scramble every slot, restore all in one call, read back
+    for s in slots:
+        b.set_state(s, *inputs.perturbed_state(*reversed(b.shapes[s]), seed=99))
+    b.set_states_raw(slots, outs, tu)
+    for s, (r, _) in zip(slots, one):
+        np.testing.assert_array_equal(b.get_state_raw(s)[0], r)
+    # a slot not in use, or a bad unit: nothing copied
+    before = [b.get_state_raw(s)[0].copy() for s in slots]
+    with pytest.raises(capi.RTLBFSError):
+        b.set_states_raw(slots[:1] + [7], [outs[0], outs[0]], [tu[0], tu[0]])
+    with pytest.raises(capi.RTLBFSError):
+        b.set_states_raw(slots, outs, [3.0] * len(slots))
+    for s, r in zip(slots, before):
+        np.testing.assert_array_equal(b.get_state_raw(s)[0], r)
+    b.close()
