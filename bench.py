@@ -510,8 +510,7 @@ def run_batch(args, w):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         b.set_states_raw(slots, ins, units)  # every slot's records in one call
-        for s in slots:
-            b.arm(s, 0.0, inner)
+        b.arm_many(slots, 0.0, inner)
         b.step(inner)
         b.get_states_raw(slots, outs)
     torch.cuda.synchronize()
@@ -532,8 +531,8 @@ def run_batch(args, w):
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(e2e, 2), "unit": "M cell-updates/s",
                 "h2d_bytes_per_step": bytes_rec, "d2h_bytes_per_step": bytes_rec,
-                "api": "rtlbfs_batch_set_states_raw / rtlbfs_batch_step / "
-                       "rtlbfs_batch_get_states_raw (all slots in one call each), pinned",
+                "api": "rtlbfs_batch_set_states_raw / rtlbfs_batch_arm_many / rtlbfs_batch_step "
+                       "/ rtlbfs_batch_get_states_raw (all slots in one call each), pinned",
                 "note": "per bench step: every cavity's state records uploaded from pinned host "
                         f"memory, {inner} batched time steps, every state downloaded"},
         "e2e_planes": {"value": round(e2e_planes, 2), "unit": "M cell-updates/s",

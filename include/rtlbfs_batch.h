@@ -105,6 +105,11 @@ int rtlbfs_batch_set_states_raw(rtlbfs_batch_t b, int n, const int* slots,
  * with max(R_u, R_T) < tol (tol <= 0: never). */
 int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps);
 
+/* rtlbfs_batch_arm for n slots (host array, caller-owned, read before the
+ * call returns) in one launch.  ERR_ARG for n < 0, a null array, a slot
+ * not in use or max_steps < 0, before any slot is armed. */
+int rtlbfs_batch_arm_many(rtlbfs_batch_t b, int n, const int* slots, double tol, long max_steps);
+
 /* Launch nsteps batched steps (asynchronous; slots that are done skip). */
 int rtlbfs_batch_step(rtlbfs_batch_t b, long nsteps);
 

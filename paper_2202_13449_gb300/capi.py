@@ -108,6 +108,7 @@ _SIGS = {
     "rtlbfs_batch_get_state_raw": (C.c_int, [_vp, C.c_int, _vp, _dp]),
     "rtlbfs_batch_set_state_raw": (C.c_int, [_vp, C.c_int, _vp, C.c_double]),
     "rtlbfs_batch_get_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
+    "rtlbfs_batch_arm_many": (C.c_int, [_vp, C.c_int, _vp, C.c_double, C.c_long]),
     "rtlbfs_batch_set_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
     "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
     "rtlbfs_batch_step": (C.c_int, [_vp, C.c_long]),
@@ -591,6 +592,12 @@ class Batch:
 
     def arm(self, slot, tol, max_steps):
         self._check(lib().rtlbfs_batch_arm(self._h, slot, float(tol), int(max_steps)), "batch_arm")
+
+    def arm_many(self, slots, tol, max_steps):
+        """arm() for several slots in one launch."""
+        sl = np.ascontiguousarray(slots, dtype=np.int32)
+        self._check(lib().rtlbfs_batch_arm_many(self._h, len(sl), _vp(sl.ctypes.data), float(tol),
+                                                int(max_steps)), "batch_arm_many")
 
     def step(self, nsteps):
         self._check(lib().rtlbfs_batch_step(self._h, int(nsteps)), "batch_step")

@@ -186,6 +186,12 @@ int rtlbfs_batch_arm(rtlbfs_batch_t b, int slot, double tol, long max_steps)
     return bfinish(b, b->eng->arm(slot, max_steps, tol > 0 ? tol : -1.0));
 }
 
+int rtlbfs_batch_arm_many(rtlbfs_batch_t b, int n, const int* slots, double tol, long max_steps)
+{
+    if (!b) return RTLBFS_ERR_ARG;
+    return bfinish(b, b->eng->arm_many(n, slots, max_steps, tol > 0 ? tol : -1.0));
+}
+
 int rtlbfs_batch_step(rtlbfs_batch_t b, long nsteps)
 {
     if (!b || nsteps < 0) return RTLBFS_ERR_ARG;

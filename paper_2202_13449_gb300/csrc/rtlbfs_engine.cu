@@ -105,6 +105,8 @@ Engine::~Engine()
     cudaFree(d_partial_);
     cudaFree(d_scalar_);
     cudaFree(d_stage_);
+    cudaFree(d_slot_list_);
+    cudaFree(d_run_list_);
     cudaFree(d_tstep_);
     cudaFree(d_pctl_);
     if (h_stalled_) cudaFreeHost(h_stalled_);
@@ -910,11 +912,53 @@ int Engine::set_records_many(int n, const int* slots, const void* const* host,
         if (precision_ == RTLBFS_FP64 ? T_units[k] != 1.0 : !(T_units[k] >= 1.0 && m == 0.5))
             return fail(RTLBFS_ERR_ARG, "T_unit must be 1 (FP64) or a power of two >= 1 (FP32)");
     }
+    int rc = grow_lists(n);
+    if (rc) return rc;
+    std::vector<CavityRun> runs(n);
     for (int k = 0; k < n; ++k) {
-        int rc = queue_set_records(slots[k], host[k], T_units[k]);
+        rc = queue_set_records(slots[k], host[k], T_units[k], &runs[k]);
         if (rc) return rc;
     }
+    // every slot's run record in two copies and one launch
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d_slot_list_, slots, sizeof(int) * n, cudaMemcpyHostToDevice, stream_));
+        CK(cudaMemcpyAsync(d_run_list_, runs.data(), sizeof(CavityRun) * n, cudaMemcpyHostToDevice,
+                           stream_));
+        CK(launch_put_runs(stream_, d_ctl_, d_slot_list_, d_run_list_, n));
+        g_launches++;
+    }
     CK(cudaStreamSynchronize(stream_));
+    return RTLBFS_OK;
+}
+
+int Engine::grow_lists(int n)
+{
+    if (n <= list_cap_) return RTLBFS_OK;
+    CK(cudaStreamSynchronize(stream_));
+    cudaFree(d_slot_list_);
+    cudaFree(d_run_list_);
+    d_slot_list_ = nullptr;
+    d_run_list_ = nullptr;
+    list_cap_ = 0;
+    CK(cudaMalloc(&d_slot_list_, sizeof(int) * n));
+    CK(cudaMalloc(&d_run_list_, sizeof(CavityRun) * n));
+    list_cap_ = n;
+    return RTLBFS_OK;
+}
+
+int Engine::arm_many(int n, const int* slots, long long nsteps, double tol)
+{
+    if (n < 0 || (n > 0 && !slots)) return fail(RTLBFS_ERR_ARG, "null slot array");
+    if (nsteps < 0) return fail(RTLBFS_ERR_ARG, "negative step count");
+    for (int k = 0; k < n; ++k)
+        if (!cavity(slots[k])) return fail(RTLBFS_ERR_ARG, "no such slot");
+    if (n == 0) return RTLBFS_OK;
+    int rc = grow_lists(n);
+    if (rc) return rc;
+    // pageable source: staged before the call returns, ordered on the stream
+    CK(cudaMemcpyAsync(d_slot_list_, slots, sizeof(int) * n, cudaMemcpyHostToDevice, stream_));
+    CK(launch_arm_list(stream_, d_ctl_, d_slot_list_, n, nsteps, tol));
+    g_launches++;
     return RTLBFS_OK;
 }
 
@@ -947,7 +991,7 @@ int Engine::get_records_many(int n, const int* slots, void* const* host, double*
 
 // set_records without the final synchronisation: the copy from the host
 // array is queued (pageable memory is staged before the copy call returns)
-int Engine::queue_set_records(int slot, const void* host, double T_unit)
+int Engine::queue_set_records(int slot, const void* host, double T_unit, CavityRun* run_out)
 {
     Cavity* c = cavity(slot);
     if (!c || !host) return fail(RTLBFS_ERR_ARG, "no such slot or null array");
@@ -979,6 +1023,12 @@ int Engine::queue_set_records(int slot, const void* host, double T_unit)
     z.done = 1;
     z.tol = -1.0;
     z.res[0] = z.res[1] = INFINITY;
+    if (run_out) {  // the caller uploads the run record (set_records_many)
+        std::memset(run_out, 0, sizeof(*run_out));
+        run_out->h[0] = z;
+        run_out->h[1] = z;
+        return RTLBFS_OK;
+    }
     return put_run(slot, z);
 }
 

@@ -110,7 +110,8 @@ public:
     // several slots at once: every copy queued, one synchronisation
     int get_records_many(int n, const int* slots, void* const* host, double* T_units);
     int set_records_many(int n, const int* slots, const void* const* host, const double* T_units);
-    int queue_set_records(int slot, const void* host, double T_unit);
+    int queue_set_records(int slot, const void* host, double T_unit, CavityRun* run_out = nullptr);
+    int arm_many(int n, const int* slots, long long nsteps, double tol);
     size_t record_bytes() const { return 4 * rsize_; }
 
     // run control: arm a slot for up to nsteps steps (tol < 0: no early stop)
@@ -191,6 +192,11 @@ private:
     double* d_scalar_ = nullptr;
     double* h_scalar_ = nullptr;   // pinned
     double* d_stage_ = nullptr;
+    // slot lists and run records of the many-slot calls
+    int* d_slot_list_ = nullptr;
+    CavityRun* d_run_list_ = nullptr;
+    int list_cap_ = 0;
+    int grow_lists(int n);
     size_t stage_cap_ = 0;
     cudaGraphExec_t gexec_ = nullptr;
     int gchunk_ = 0;

@@ -97,5 +97,11 @@ cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol,
                               int pitch, void* cells);
 cudaError_t launch_arm(cudaStream_t s, CavityRun* runs, int slot, long long nsteps, double tol,
                        int reset_counter);
+// arm_kernel over the n slots of a device array of slot indices
+cudaError_t launch_arm_list(cudaStream_t s, CavityRun* runs, const int* slots, int n,
+                            long long nsteps, double tol);
+// runs[slots[k]] = src[k] for k < n (device arrays)
+cudaError_t launch_put_runs(cudaStream_t s, CavityRun* runs, const int* slots,
+                            const CavityRun* src, int n);
 
 }  // namespace rtlbfs

@@ -303,10 +303,12 @@ __global__ void conduction_kernel(const double* __restrict__ Tcol, int nx, int n
 // Arm the run control of one cavity: take `nsteps` more steps (stop early
 // when max(R_u, R_T) < tol, tol < 0: never).  Runs on a tested header
 // (pend = 0: after finalize_kernel or a state upload).
-__global__ void arm_kernel(CavityRun* runs, int slot, long long nsteps, double tol,
-                           int reset_counter)
+__global__ void arm_kernel(CavityRun* runs, const int* __restrict__ slot_list, int n, int slot,
+                           long long nsteps, double tol, int reset_counter)
 {
-    CavityRun* r = &runs[slot];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    CavityRun* r = &runs[slot_list ? slot_list[k] : slot];
     CavityCtl c = r->h[0];
     if (reset_counter) {
         c.steps = 0;
@@ -490,7 +492,35 @@ cudaError_t launch_conduction(int precision, cudaStream_t s, const double* Tcol,
 cudaError_t launch_arm(cudaStream_t s, CavityRun* ctls, int slot, long long nsteps, double tol,
                        int reset_counter)
 {
-    arm_kernel<<<1, 1, 0, s>>>(ctls, slot, nsteps, tol, reset_counter);
+    arm_kernel<<<1, 1, 0, s>>>(ctls, nullptr, 1, slot, nsteps, tol, reset_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arm_list(cudaStream_t s, CavityRun* ctls, const int* slots, int n,
+                            long long nsteps, double tol)
+{
+    if (n <= 0) return cudaSuccess;
+    arm_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctls, slots, n, 0, nsteps, tol, 0);
+    return cudaGetLastError();
+}
+
+// Run records of n slots from a device array (slot k's record is src[k]).
+__global__ void put_runs_kernel(CavityRun* runs, const int* __restrict__ slots,
+                                const CavityRun* __restrict__ src, int n)
+{
+    const int k = blockIdx.x;
+    if (k >= n) return;
+    const double* a = reinterpret_cast<const double*>(&src[k]);
+    double* b = reinterpret_cast<double*>(&runs[slots[k]]);
+    for (int w = threadIdx.x; w < (int)(sizeof(CavityRun) / sizeof(double)); w += blockDim.x)
+        b[w] = a[w];
+}
+
+cudaError_t launch_put_runs(cudaStream_t s, CavityRun* ctls, const int* slots,
+                            const CavityRun* src, int n)
+{
+    if (n <= 0) return cudaSuccess;
+    put_runs_kernel<<<n, 32, 0, s>>>(ctls, slots, src, n);
     return cudaGetLastError();
 }
 

@@ -244,3 +244,40 @@ def test_batch_records_of_many_slots_in_one_call(precision):
     for s, r in zip(slots, before):
         np.testing.assert_array_equal(b.get_state_raw(s)[0], r)
     b.close()
+
+
+def test_batch_arm_many_equals_arming_each_slot():
+    """One arm_many launch leaves every slot armed as rtlbfs_batch_arm does:
+    the same stop step and the same fields; a bad slot arms none."""
+    def build():
+        b = capi.Batch(capi.FP32, 8)
+        slots = []
+        for nx, ny, phi, Ra, seed in SPECS:
+            xf = capi.tanh_faces(nx, float(nx), phi)
+            yf = capi.tanh_faces(ny, float(nx) * ny / nx, phi)
+            s = b.add(xf, yf, Ra, 0.71, 0.1, 0.0)
+            b.set_state(s, *inputs.perturbed_state(nx, ny, seed=seed))
+            slots.append(s)
+        return b, slots
+
+    a, sa = build()
+    for s in sa:
+        a.arm(s, 0.0, 9)
+    a.step(12)
+    m, sm = build()
+    with pytest.raises(capi.RTLBFSError):
+        m.arm_many(sm + [7], 0.0, 9)
+    m.step(3)  # nothing armed: no slot moves
+    st0, steps0, _ = m.poll()
+    assert all(steps0[s] == 0 for s in sm)
+    m.arm_many(sm, 0.0, 9)
+    m.step(12)
+    st_a, steps_a, _ = a.poll()
+    st_m, steps_m, _ = m.poll()
+    for s_a, s_m in zip(sa, sm):
+        assert steps_m[s_m] == steps_a[s_a] == 9
+        assert st_m[s_m] == st_a[s_a] == capi.SLOT_MAX_STEPS
+        for q in range(4):
+            np.testing.assert_array_equal(m.get_state(s_m)[q], a.get_state(s_a)[q])
+    a.close()
+    m.close()
