@@ -229,12 +229,14 @@ __device__ __forceinline__ void take3(const Sm& sm, int vs, int gs, int r, int c
 }
 
 // One face between cells L and R (frame of axis ax) with face stage SCH
-// (0 RTLBFS, 1 TLBFS): fluxes in global components.  Tz is the unit's temperature reference; the face reference
-// is the left cell's temperature.
+// (0 RTLBFS, 1 TLBFS), the fluxes in the face frame: F = (mass, n-, t1-,
+// t2-momentum, energy), t1 = axis (ax + 1) % 3, t2 = (ax + 2) % 3.  Tz is the
+// unit's temperature reference; the face reference is the left cell's
+// temperature.
 template <class P, typename R, int SCH>
-__device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, CellNT3<R>& Rc,
-                                      R tauR, const FaceLine<R>& fl, R Tz, int ax, int wside,
-                                      R out[5])
+__device__ __forceinline__ void face3_frame(const Desc3& d, CellNT3<R>& L, R tauL,
+                                            CellNT3<R>& Rc, R tauR, const FaceLine<R>& fl, R Tz,
+                                            int ax, int wside, R F[5])
 {
     L.q[4] = R(0);
     Rc.q[4] = tauR - tauL;
@@ -242,7 +244,6 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
     const R keep = wside >= 0 ? R(0) : R(1);
     const R uw1 = wside >= 0 ? Cst<P>::uw(d, wside, a1) : R(0);
     const R uw2 = wside >= 0 ? Cst<P>::uw(d, wside, a2) : R(0);
-    R F[5];
     if constexpr (SCH == 1) {
         face_flux3_tlbfs<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
     } else if constexpr (sizeof(R) == 4) {  // FP32: the node stage in packed pairs
@@ -252,6 +253,17 @@ __device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, Cel
     } else {
         face_flux3<R>(L, Rc, Tz + tauL, fl, keep, uw1, uw2, F);
     }
+}
+
+// The same with the fluxes in global components (rho, x, y, z, T).
+template <class P, typename R, int SCH>
+__device__ __forceinline__ void face3(const Desc3& d, CellNT3<R>& L, R tauL, CellNT3<R>& Rc,
+                                      R tauR, const FaceLine<R>& fl, R Tz, int ax, int wside,
+                                      R out[5])
+{
+    R F[5];
+    face3_frame<P, R, SCH>(d, L, tauL, Rc, tauR, fl, Tz, ax, wside, F);
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
     out[0] = F[0];
     out[1 + ax] = F[1];
     out[1 + a1] = F[2];
@@ -458,33 +470,70 @@ __global__ void __launch_bounds__(TX* TY) step3_kernel(const Desc3* __restrict__
         __syncthreads();
         // x- and y-faces of plane k
         const int vs = mod3(k), gs = mod2(k);
-        for (int t = tid; t < TY * (TX + 1); t += NT) {
-            const int fj = t / (TX + 1), fi = t % (TX + 1);
-            const int gx = i0 + fi;
-            if (gx > nx || j0 + fj >= ny) continue;
-            CellNT3<R> L, Rr;
-            R tl, tr;
-            take3<R>(sm, vs, gs, fj + 2, fi + 1, 0, L, tl);
-            take3<R>(sm, vs, gs, fj + 2, fi + 2, 0, Rr, tr);
-            const int ws = xper ? -1 : (gx == 0 ? 0 : (gx == nx ? 1 : -1));
-            R F[5];
-            face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.xl, fi), Tz, 0, ws, F);
+        constexpr int NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
+        if constexpr (sizeof(R) == 4) {
+            // FP32: one loop (face t < NXF an x-face, else a y-face), so the
+            // face arithmetic is one copy of code and a thread's rounds cover
+            // both kinds; the fluxes come back in the face frame and are
+            // stored to their global components.  (FP64 keeps two loops: the
+            // shared copy would raise its registers past three blocks per SM.)
+            for (int t = tid; t < NXF + NYF; t += NT) {
+                const bool isx = t < NXF;
+                const int u = isx ? t : t - NXF;
+                const int fj = isx ? u / (TX + 1) : u / TX, fi = isx ? u % (TX + 1) : u % TX;
+                const int g = isx ? i0 + fi : j0 + fj;  // the face's index along its normal
+                if (isx ? (g > nx || j0 + fj >= ny) : (g > ny || i0 + fi >= nx)) continue;
+                const int ax = isx ? 0 : 1;
+                CellNT3<R> L, Rr;
+                R tl, tr;
+                take3<R>(sm, vs, gs, isx ? fj + 2 : fj + 1, isx ? fi + 1 : fi + 2, ax, L, tl);
+                take3<R>(sm, vs, gs, fj + 2, fi + 2, ax, Rr, tr);
+                const bool per = isx ? xper : yper;
+                const int n_ax = isx ? nx : ny;
+                const int ws = per ? -1 : (g == 0 ? 2 * ax : (g == n_ax ? 2 * ax + 1 : -1));
+                R F[5];
+                face3_frame<P, R, SCH>(d, L, tl, Rr, tr,
+                                       isx ? get_line(sm.xl, fi) : get_line(sm.yl, fj), Tz, ax,
+                                       ws, F);
+                // frame (rho, n, t1, t2, T) to global (rho, x, y, z, T): x-face
+                // n = x, t1 = y, t2 = z; y-face n = y, t1 = z, t2 = x
+                R* dst = isx ? &sm.fx[0][fj][fi] : &sm.fy[0][fj][fi];
+                const int qs = isx ? NXF : NYF;  // stride between components
+                dst[0] = F[0];
+                dst[(isx ? 1 : 2) * qs] = F[1];
+                dst[(isx ? 2 : 3) * qs] = F[2];
+                dst[(isx ? 3 : 1) * qs] = F[3];
+                dst[4 * qs] = F[4];
+            }
+        } else {
+            for (int t = tid; t < NXF; t += NT) {
+                const int fj = t / (TX + 1), fi = t % (TX + 1);
+                const int gx = i0 + fi;
+                if (gx > nx || j0 + fj >= ny) continue;
+                CellNT3<R> L, Rr;
+                R tl, tr;
+                take3<R>(sm, vs, gs, fj + 2, fi + 1, 0, L, tl);
+                take3<R>(sm, vs, gs, fj + 2, fi + 2, 0, Rr, tr);
+                const int ws = xper ? -1 : (gx == 0 ? 0 : (gx == nx ? 1 : -1));
+                R F[5];
+                face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.xl, fi), Tz, 0, ws, F);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) sm.fx[q][fj][fi] = F[q];
-        }
-        for (int t = tid; t < (TY + 1) * TX; t += NT) {
-            const int fj = t / TX, fi = t % TX;
-            const int gy = j0 + fj;
-            if (gy > ny || i0 + fi >= nx) continue;
-            CellNT3<R> L, Rr;
-            R tl, tr;
-            take3<R>(sm, vs, gs, fj + 1, fi + 2, 1, L, tl);
-            take3<R>(sm, vs, gs, fj + 2, fi + 2, 1, Rr, tr);
-            const int ws = yper ? -1 : (gy == 0 ? 2 : (gy == ny ? 3 : -1));
-            R F[5];
-            face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.yl, fj), Tz, 1, ws, F);
+                for (int q = 0; q < 5; ++q) sm.fx[q][fj][fi] = F[q];
+            }
+            for (int t = tid; t < NYF; t += NT) {
+                const int fj = t / TX, fi = t % TX;
+                const int gy = j0 + fj;
+                if (gy > ny || i0 + fi >= nx) continue;
+                CellNT3<R> L, Rr;
+                R tl, tr;
+                take3<R>(sm, vs, gs, fj + 1, fi + 2, 1, L, tl);
+                take3<R>(sm, vs, gs, fj + 2, fi + 2, 1, Rr, tr);
+                const int ws = yper ? -1 : (gy == 0 ? 2 : (gy == ny ? 3 : -1));
+                R F[5];
+                face3<P, R, SCH>(d, L, tl, Rr, tr, get_line(sm.yl, fj), Tz, 1, ws, F);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) sm.fy[q][fj][fi] = F[q];
+                for (int q = 0; q < 5; ++q) sm.fy[q][fj][fi] = F[q];
+            }
         }
         R Fu[5] = {R(0), R(0), R(0), R(0), R(0)};
         R c0[5];
