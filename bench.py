@@ -173,6 +173,12 @@ WORKLOADS = {
              "(Eq. 69) and Nu_1/2 against the paper's RTLBFS values",
         tol=1e-7, max_steps=50_000_000, time_limit=300.0, window_conv_times=20.0,
         window_tol=2e-4, precision="fp32", kind="cavity_tables"),
+    "cavity_ra1e8_fp64": dict(
+        desc="Table 3's case (Ra = 1e8, 400^2 stretched to a first cell of 0.0002 L, Pr = 0.71, "
+             "V_c = 0.1): windows of 20 convective times in FP32 from the conduction state, "
+             "then the FP32 state continued in FP64 (exact conversion) in windows of 10, with "
+             "the Table 3 quantities after every window",
+        Ra=1e8, n=400, wall=0.0002, w32=11, w64=3, kind="fp64_continue"),
     "table4": dict(
         desc="Table 4 of Section 4.3 on this GPU: mean Nusselt number (Eq. 73) and separation "
              "angle on the heated cylinder at Re = 20, Pr = 0.7, Gr = 0, 100, 800, 1600, each run "
@@ -1347,6 +1353,63 @@ def run_cavity_tables(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_fp64_continue(args, w):
+    """One cavity case in FP32 windows (20 convective times each), then its
+    state continued in FP64 (windows of 10): whether a quantity the FP32
+    state has stopped moving is at its steady value, or frozen by the
+    fixed-point quantum at a small time step."""
+    import numpy as np
+    import torch
+    from paper_2202_13449_gb300 import capi, post
+    torch.cuda.set_device(0)
+    capi.lib()
+    Pr, Vc = 0.71, 0.1
+    n, L = w["n"], float(w["n"])
+    xf = capi.tanh_faces(n, L, stretch_to_first_cell(n, L, w["wall"] * L))
+    nu = Vc * L * np.sqrt(Pr / w["Ra"])
+    chi = nu / Pr
+    wmin = float(np.min(np.diff(xf)))
+    dt = min(0.5 * wmin, 0.2 * wmin * wmin / max(nu, chi))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def quantities(s):
+        rho, u, v, T = s.get_state()
+        umax, uy, vmax, vx = post.cavity_centrelines(xf, xf, u, v)
+        pmax, px, py = post.streamfunction_max(xf, xf, u)
+        return {"u_max": round(umax * L / chi, 4), "u_max_y": round(uy, 5),
+                "v_max": round(vmax * L / chi, 3), "Nu_half": round(s.nusselt(capi.NU_HALF), 5),
+                "psi_max": round(pmax / chi, 5)}
+
+    windows = {"fp32": [], "fp64": []}
+    chunk = int(round(20.0 * (L / Vc) / dt))
+    s = capi.Solver(xf, xf, capi.FP32)
+    s.set_params(w["Ra"], Pr, Vc, 0.0)
+    s.set_stream(stream)
+    s.autotune(32)
+    for _ in range(w["w32"]):
+        s.step(chunk)
+        windows["fp32"].append(quantities(s))
+    st = s.get_state()
+    s.close()
+    d = capi.Solver(xf, xf, capi.FP64)
+    d.set_params(w["Ra"], Pr, Vc, 0.0)
+    d.set_stream(stream)
+    d.set_state(*st)
+    d.autotune(4)
+    for _ in range(w["w64"]):
+        d.step(chunk // 2)
+        windows["fp64"].append(quantities(d))
+    d.close()
+    print(json.dumps({"metric": "Table 3 quantities after FP32 and FP64 windows", "value": None,
+                      "unit": None, "n_gpus": 1, "dtype": "f32 then f64",
+                      "data": "synthetic (seeded; no dataset)",
+                      "config": {"workload": args.workload, "description": w["desc"], "dt": dt,
+                                 "steps_per_fp32_window": chunk,
+                                 "steps_per_fp64_window": chunk // 2},
+                      "windows": windows}), flush=True)
+
+
 def curv_case(inputs, w):
     """The Section 4.3 cylinder: mesh, physics and the free-stream state."""
     import numpy as np
@@ -1514,6 +1577,8 @@ def run_ours(args, w):
         return run_table4(args, w)
     if w.get("kind") == "cavity_tables":
         return run_cavity_tables(args, w)
+    if w.get("kind") == "fp64_continue":
+        return run_fp64_continue(args, w)
     if w.get("kind") == "cubic":
         return run_cubic(args, w)
     if w.get("kind") == "schemes":
@@ -2060,7 +2125,7 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         if w.get("kind") in ("accuracy", "rb_steady", "schemes", "table6", "table4",
-                             "cavity_tables"):
+                             "cavity_tables", "fp64_continue"):
             print(json.dumps({"impl": "reference", "unavailable": "this run measures accuracy or "
                               "time to a steady state of the GPU path; the oracle's rate is the "
                               "rb1024x512 / cavity512 reference lines"}))
