@@ -178,7 +178,7 @@ WORKLOADS = {
              "V_c = 0.1): windows of 20 convective times in FP32 from the conduction state, "
              "then the FP32 state continued in FP64 (exact conversion) in windows of 10, with "
              "the Table 3 quantities after every window",
-        Ra=1e8, n=400, wall=0.0002, w32=11, w64=3, kind="fp64_continue"),
+        Ra=1e8, n=400, wall=0.0002, w32=11, w64=8, kind="fp64_continue"),
     "table4": dict(
         desc="Table 4 of Section 4.3 on this GPU: mean Nusselt number (Eq. 73) and separation "
              "angle on the heated cylinder at Re = 20, Pr = 0.7, Gr = 0, 100, 800, 1600, each run "
