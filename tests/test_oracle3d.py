@@ -511,3 +511,20 @@ def test_square_duct_flow_converges_to_the_series_solution(d3):
         assert np.max(np.abs(s[1] - s[1][:, :, :1])) == 0.0
     assert errs[1] < 0.03, errs
     assert errs[0] / errs[1] > 3.2, errs
+
+
+@pytest.mark.parametrize("phi,L", [(0.0, 8.0), (1.5, 37.0)])
+def test_conduction_nusselt_numbers_are_one(d3, phi, L):
+    """The conduction state (T linear in x from the cold wall to the hot
+    one, at rest) carries the heat chi dT / L through every x-plane, so the
+    wall number of Eq. 76, the middle-line number of Eq. 75 and the
+    mid-plane number are all 1 exactly, on uniform and stretched meshes and
+    for a box side other than the cell count (a dropped or misplaced length,
+    area or chi fails this)."""
+    n = 8
+    p = d3.cubic_cavity(n, 1e4, phi=phi, L=L)
+    st = inputs.conduction_state3(p.xf, p.yf, p.zf)
+    for side in (0, 1):
+        assert -d3.nusselt(p, st, side) == pytest.approx(1.0, abs=1e-12)
+        assert -d3.nusselt(p, st, side, mid=True) == pytest.approx(1.0, abs=1e-12)
+    assert -d3.nusselt(p, st, d3.MID_PLANE_X) == pytest.approx(1.0, abs=1e-12)
