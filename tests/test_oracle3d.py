@@ -528,3 +528,29 @@ def test_conduction_nusselt_numbers_are_one(d3, phi, L):
         assert -d3.nusselt(p, st, side) == pytest.approx(1.0, abs=1e-12)
         assert -d3.nusselt(p, st, side, mid=True) == pytest.approx(1.0, abs=1e-12)
     assert -d3.nusselt(p, st, d3.MID_PLANE_X) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_residual_is_relative_l2_change_of_speed_and_temperature(d3):
+    """The residual a 3D step returns equals R12 evaluated here from the
+    states before and after it: cell speeds |u| = sqrt(u^2 + v^2 + w^2), a
+    plain sum over cells, the new state's norm as the denominator (the L2
+    analogue of Eq. 65, as in 2D); componentwise differences or the old
+    norm would give other numbers on these states."""
+    n = 6
+    p = d3.cubic_cavity(n, 1e4, phi=1.2)
+    st = inputs.perturbed_state3(n, n, n, seed=31)
+    for _ in range(2):
+        st1, res, rc = d3.step(p, st, 1)
+        assert rc == 0
+        m0 = np.sqrt(st[1] ** 2 + st[2] ** 2 + st[3] ** 2)
+        m1 = np.sqrt(st1[1] ** 2 + st1[2] ** 2 + st1[3] ** 2)
+        ru = np.sqrt(np.sum((m1 - m0) ** 2)) / np.sqrt(np.sum(m1 ** 2))
+        rT = np.sqrt(np.sum((st1[4] - st[4]) ** 2)) / np.sqrt(np.sum(st1[4] ** 2))
+        assert res[0] == pytest.approx(ru, rel=1e-13, abs=0)
+        assert res[1] == pytest.approx(rT, rel=1e-13, abs=0)
+        comp = np.sqrt(np.sum(sum((st1[q] - st[q]) ** 2 for q in (1, 2, 3)))) / np.sqrt(
+            np.sum(m1 ** 2))
+        old_den = np.sqrt(np.sum((m1 - m0) ** 2)) / np.sqrt(np.sum(m0 ** 2))
+        for alt in (comp, old_den, ru ** 2):
+            assert abs(alt - ru) > 1e-3 * ru
+        st = st1

@@ -250,3 +250,30 @@ def test_poiseuille_converges_at_second_order_on_a_sheared_mesh(cv):
         np.testing.assert_allclose(s[1], s0[1], rtol=1e-10, atol=1e-16)
     assert errs[1] < 0.011
     assert 3.6 < errs[0] / errs[1] < 4.4, errs
+
+
+def test_residual_is_relative_l2_change_of_speed_and_temperature(cv):
+    """The residual a curvilinear step returns equals R12 evaluated here from
+    the states before and after it (cell speeds, plain sums over cells, the
+    new state's norm as the denominator, as on rectilinear meshes); the
+    componentwise and old-norm readings differ on these states."""
+    X, Y = o_mesh(24, 10, 1.0, 3.0)
+    p = cv.ProblemC(X=X, Y=Y, nu=0.02, chi=0.028, beta_g=1e-3, dt=0.02, kappa=0.9,
+                    gdir=(0.0, 1.0), bc_kind=(cv.PERIODIC, cv.PERIODIC, cv.DIRICHLET, cv.DIRICHLET),
+                    bc_T=(0, 0, 1.0, 0.0))
+    nj, ni = p.shape
+    st = inputs.perturbed_state(ni, nj, seed=82)
+    for _ in range(2):
+        st1, res, rc = cv.step(p, st, 1)
+        assert rc == 0
+        m0, m1 = np.hypot(st[1], st[2]), np.hypot(st1[1], st1[2])
+        ru = np.sqrt(np.sum((m1 - m0) ** 2)) / np.sqrt(np.sum(m1 ** 2))
+        rT = np.sqrt(np.sum((st1[3] - st[3]) ** 2)) / np.sqrt(np.sum(st1[3] ** 2))
+        assert res[0] == pytest.approx(ru, rel=1e-13, abs=0)
+        assert res[1] == pytest.approx(rT, rel=1e-13, abs=0)
+        comp = np.sqrt(np.sum((st1[1] - st[1]) ** 2 + (st1[2] - st[2]) ** 2)) / np.sqrt(
+            np.sum(m1 ** 2))
+        old_den = np.sqrt(np.sum((m1 - m0) ** 2)) / np.sqrt(np.sum(m0 ** 2))
+        for alt in (comp, old_den, ru ** 2):
+            assert abs(alt - ru) > 1e-3 * ru
+        st = st1
