@@ -449,7 +449,9 @@ def run_batch(args, w):
     if args.schedule == "auto":
         sched = b.autotune(16)
     else:
-        sched = (SCHED_NAMES.index(args.schedule.split(":")[0]), 0, 0.0)
+        name, _, rows = args.schedule.partition(":")
+        sched = (SCHED_NAMES.index(name), int(rows or 0), 0.0)
+        b.set_schedule(sched[0], sched[1])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         flush.zero_()

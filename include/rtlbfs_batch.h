@@ -124,6 +124,13 @@ int rtlbfs_batch_nusselt(rtlbfs_batch_t b, int slot, int which, double* nu);
 /* Free a slot and its device memory. */
 int rtlbfs_batch_remove(rtlbfs_batch_t b, int slot);
 
+/* Schedule of the batch's step launches, as rtlbfs_set_schedule of
+ * include/rtlbfs.h: kernel 0 = warp-marching strips of chunk_rows rows,
+ * 1 = shared-memory tiles of height chunk_rows (0: the default of each),
+ * 2 is refused for a batch (the persistent kernel takes one cavity).
+ * ERR_ARG on other values. */
+int rtlbfs_batch_set_schedule(rtlbfs_batch_t b, int kernel, int chunk_rows);
+
 /* Pick the step schedule for the current set of slots (see rtlbfs_autotune). */
 int rtlbfs_batch_autotune(rtlbfs_batch_t b, int steps, int* kernel, int* chunk_rows,
                           double* ms_per_step);

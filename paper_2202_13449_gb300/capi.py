@@ -109,6 +109,7 @@ _SIGS = {
     "rtlbfs_batch_set_state_raw": (C.c_int, [_vp, C.c_int, _vp, C.c_double]),
     "rtlbfs_batch_get_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
     "rtlbfs_batch_arm_many": (C.c_int, [_vp, C.c_int, _vp, C.c_double, C.c_long]),
+    "rtlbfs_batch_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
     "rtlbfs_batch_set_states_raw": (C.c_int, [_vp, C.c_int, _vp, _vp, _dp]),
     "rtlbfs_batch_arm": (C.c_int, [_vp, C.c_int, C.c_double, C.c_long]),
     "rtlbfs_batch_step": (C.c_int, [_vp, C.c_long]),
@@ -592,6 +593,11 @@ class Batch:
 
     def arm(self, slot, tol, max_steps):
         self._check(lib().rtlbfs_batch_arm(self._h, slot, float(tol), int(max_steps)), "batch_arm")
+
+    def set_schedule(self, kernel: int = 0, chunk_rows: int = 0):
+        """Step kernel (0 marching, 1 tiles) and its rows per unit / tile height."""
+        self._check(lib().rtlbfs_batch_set_schedule(self._h, int(kernel), int(chunk_rows)),
+                    "batch_set_schedule")
 
     def arm_many(self, slots, tol, max_steps):
         """arm() for several slots in one launch."""

@@ -228,6 +228,14 @@ int rtlbfs_batch_remove(rtlbfs_batch_t b, int slot)
     return bfinish(b, b->eng->remove(slot));
 }
 
+int rtlbfs_batch_set_schedule(rtlbfs_batch_t b, int kernel, int chunk_rows)
+{
+    if (!b || kernel == 2) return RTLBFS_ERR_ARG;
+    int rc = b->eng->set_kernel(kernel);
+    if (rc == RTLBFS_OK) rc = b->eng->set_chunk_rows(chunk_rows);
+    return bfinish(b, rc);
+}
+
 int rtlbfs_batch_autotune(rtlbfs_batch_t b, int steps, int* kernel, int* chunk_rows,
                           double* ms_per_step)
 {

@@ -281,3 +281,29 @@ def test_batch_arm_many_equals_arming_each_slot():
             np.testing.assert_array_equal(m.get_state(s_m)[q], a.get_state(s_a)[q])
     a.close()
     m.close()
+
+
+def test_batch_schedule_is_settable():
+    """rtlbfs_batch_set_schedule: the tile kernel and the marching kernel
+    advance a batch to the same fields (FP64: the same arithmetic up to the
+    order of a few sums); the persistent kernel is refused for a batch."""
+    out = []
+    for kernel, rows in ((0, 32), (1, 8)):
+        b = capi.Batch(capi.FP64, 8)
+        slots = []
+        for nx, ny, phi, Ra, seed in SPECS:
+            xf = capi.tanh_faces(nx, float(nx), phi)
+            yf = capi.tanh_faces(ny, float(nx) * ny / nx, phi)
+            s = b.add(xf, yf, Ra, 0.71, 0.1, 0.0)
+            b.set_state(s, *inputs.perturbed_state(nx, ny, seed=seed))
+            b.arm(s, 0.0, 10)
+            slots.append(s)
+        b.set_schedule(kernel, rows)
+        with pytest.raises(capi.RTLBFSError):
+            b.set_schedule(2, 0)
+        b.step(10)
+        out.append([b.get_state(s) for s in slots])
+        b.close()
+    for sa, sb in zip(*out):
+        for q in range(4):
+            assert rel(sb[q], sa[q], 1e-3) < 1e-12
