@@ -324,8 +324,9 @@ __device__ __forceinline__ void tile_sums(const TileSmem<P, TX, TY, NT>& sm, dou
 // the phase's remainder: the halo ring of the load, the gradient ring, the
 // east face column and north face row of the tile.  The remainders go to the
 // lowest threads, so they keep as few warps as possible busy for the extra
-// round.  With CW = 16 or 32 lanes of a warp read consecutive records: no
-// bank conflicts.
+// round; the north face row starts on the warp after the east column's, so
+// no warp computes two faces more than the others.  With CW = 16 or 32
+// lanes of a warp read consecutive records: no bank conflicts.
 template <class P, int TX, int TY, int NT, int SCHEME, bool LDCG>
 __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const CavityDesc* dp,
                                           int i0, int j0,
@@ -519,6 +520,11 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
         using XF = std::true_type;
         using YF = std::false_type;
         constexpr int TQ = (TX + TY + NT - 1) / NT;  // rounds of the east/north faces
+        // the north row starts at the first warp past the east column where
+        // the rounds leave room: the two remainders then fall on different
+        // warps, and no warp computes two faces more than the others
+        constexpr int EW = (TY + 31) / 32 * 32;
+        constexpr int YOFF = EW + TX <= TQ * NT ? EW : TY;
 #pragma unroll(UNROLL)
         for (int k = 0; k < CPT + TQ; ++k) {
             int fc = tc + k * CW, fr = tr;
@@ -534,7 +540,7 @@ __device__ __forceinline__ void tile_step(TileSmem<P, TX, TY, NT>& sm, const Cav
         for (int k = 0; k < CPT + TQ; ++k) {
             int fc = tc + k * CW, fr = tr;
             if (k >= CPT) {
-                const int t = tid + (k - CPT) * NT - TY;
+                const int t = tid + (k - CPT) * NT - YOFF;
                 if (t >= TX) break;
                 if (t < 0) continue;
                 fc = t;
