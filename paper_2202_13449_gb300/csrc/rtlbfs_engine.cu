@@ -2,6 +2,7 @@
 // buffers, the tile list of the batched step kernel, CUDA graphs of step
 // launches, run control and the FP64 reductions.
 #include "rtlbfs_engine.h"
+#include "rtlbfs_worklist.h"
 
 #include <algorithm>
 #include <cmath>
@@ -647,25 +648,6 @@ int Engine::pick_tile_height() const
     return best_h;
 }
 
-// Tiles whose halo reaches past the mesh edge take the ghost-resolution
-// path and run longer; spaced evenly through the cavity's part of the list,
-// they are spread over the SMs instead of several landing on one.
-static void spread_edge_tiles(std::vector<int4>& t, int b, int nx, int ny, int h)
-{
-    std::vector<int4> edge, inner;
-    for (int k = b; k < (int)t.size(); ++k) {
-        const int4 u = t[k];
-        const bool in = u.y >= 2 && u.z >= 2 && u.y + kTileX + 2 <= nx && u.z + h + 2 <= ny;
-        (in ? inner : edge).push_back(u);
-    }
-    const long long ne = (long long)edge.size(), n = ne + (long long)inner.size();
-    size_t ie = 0, ii = 0;
-    for (long long k = 0; k < n; ++k) {
-        const bool take_edge = (k + 1) * ne / n > k * ne / n;
-        t[b + k] = take_edge ? edge[ie++] : inner[ii++];
-    }
-}
-
 int Engine::rebuild_tiles()
 {
     std::vector<int4> t;
@@ -684,9 +666,17 @@ int Engine::rebuild_tiles()
             c.ntiles = tx * ty;
             for (int j = 0; j < ty; ++j)
                 for (int i = 0; i < tx; ++i) t.push_back(make_int4(s, i * kTileX, j * tile_h_, 0));
-            // the persistent kernel finds a tile's neighbours by its index in
-            // row-major order: only the launch-per-step kernel takes the spread
-            if (kernel_ == 1) spread_edge_tiles(t, c.first_tile, c.nx, c.ny, tile_h_);
+            // Tiles whose halo reaches past the mesh edge take the ghost-resolution
+            // path and run longer: spaced evenly through the cavity's part of the
+            // list, they are spread over the SMs instead of several landing on one.
+            // The persistent kernel finds a tile's neighbours by its index in
+            // row-major order: only the launch-per-step kernel takes the spread.
+            if (kernel_ == 1) {
+                const int nx = c.nx, ny = c.ny, th = tile_h_;
+                spread_units(t, (std::size_t)c.first_tile, [=](const int4& u) {
+                    return !(u.y >= 2 && u.z >= 2 && u.y + kTileX + 2 <= nx && u.z + th + 2 <= ny);
+                });
+            }
         }
     } else {
         // warp-marching units: strips of kStrip columns, chunks of H rows.
