@@ -319,8 +319,12 @@ void rtlbfs_destroy(rtlbfs_t h);
  * that live in the caller's buffers rather than in a handle.  It computes
  * what rtlbfs_nusselt computes (same selectors `which`, same FP64
  * arithmetic) and allocates nothing: no cudaMalloc, cudaFree or allocating
- * library call.  Host arrays (xf, yf, bc_*) are read before the call
- * returns; the work is queued on `stream`.
+ * library call.  bc_kind, bc_T and bc_u are read before the call returns;
+ * xf and yf too when they are pageable memory (malloc, new, numpy): the
+ * runtime stages such a copy before returning.  From pinned memory the
+ * copies read xf and yf when they run on `stream`, so keep pinned arrays
+ * unchanged until the stream has passed this call.  The work is queued on
+ * `stream`.
  *
  *   nx, ny         cells, each at most 8192 (larger: RTLBFS_ERR_ARG)
  *   xf, yf         host face coordinates (nx+1, ny+1), strictly ascending

@@ -967,8 +967,11 @@ int Engine::arm_many(int n, const int* slots, long long nsteps, double tol)
     if (n == 0) return RTLBFS_OK;
     int rc = grow_lists(n);
     if (rc) return rc;
-    // pageable source: staged before the call returns, ordered on the stream
-    CK(cudaMemcpyAsync(d_slot_list_, slots, sizeof(int) * n, cudaMemcpyHostToDevice, stream_));
+    // copied from a pageable copy of the caller's array, which the runtime
+    // stages before the call returns: the caller's array may be pinned, and
+    // is free for reuse on return either way
+    const std::vector<int> sl(slots, slots + n);
+    CK(cudaMemcpyAsync(d_slot_list_, sl.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream_));
     CK(launch_arm_list(stream_, d_ctl_, d_slot_list_, n, nsteps, tol));
     g_launches++;
     return RTLBFS_OK;
