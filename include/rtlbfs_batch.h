@@ -94,7 +94,10 @@ int rtlbfs_batch_set_state_raw(rtlbfs_batch_t b, int slot, const void* records, 
  * synchronises once, so with pinned buffers the copies run back to back
  * as DMA.  Arguments are checked before any copy: ERR_ARG for n < 0, a
  * null array, a slot not in use, a null record pointer or (set) a bad
- * unit; nothing is copied then.
+ * unit; nothing is copied then.  On ERR_CUDA from set, the states and run
+ * records of the listed slots are undefined (some copies may have run);
+ * set them again before stepping.  A slot listed twice takes the records
+ * of its last entry.
  */
 int rtlbfs_batch_get_states_raw(rtlbfs_batch_t b, int n, const int* slots, void* const* records,
                                 double* T_units);
