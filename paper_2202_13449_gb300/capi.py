@@ -228,6 +228,17 @@ def _f64(a, n: int) -> np.ndarray:
     return out
 
 
+def _raw_out(out, nbytes: int) -> np.ndarray:
+    """`out` as an array the library may write nbytes into: C-contiguous,
+    writable and large enough (the library writes through a bare pointer)."""
+    a = np.asarray(out)
+    if not (a.flags.c_contiguous and a.flags.writeable):
+        raise ValueError("the output buffer must be C-contiguous and writable")
+    if a.nbytes < nbytes:
+        raise ValueError(f"the output buffer holds {a.nbytes} bytes, {nbytes} are needed")
+    return a
+
+
 def tanh_faces(n: int, L: float, phi: float) -> np.ndarray:
     """Eq. 74 face coordinates from the library (host-only entry point)."""
     out = np.empty(n + 1)
@@ -441,8 +452,8 @@ class Solver:
         """(records, T_unit): the state's cell records as a uint8 array (or
         into `out`, any writable buffer of raw_bytes() bytes, e.g. a pinned
         torch tensor's numpy view) and the temperature unit."""
-        if out is None:
-            out = np.empty(self.raw_bytes(), dtype=np.uint8)
+        nb = self.raw_bytes()
+        out = np.empty(nb, dtype=np.uint8) if out is None else _raw_out(out, nb)
         tu = C.c_double()
         self._check(lib().rtlbfs_get_state_raw(self._h, _vp(out.ctypes.data), C.byref(tu)),
                     "get_state_raw")
@@ -496,6 +507,7 @@ class Batch:
         self.max_slots = max_slots
         self.precision = precision
         self.shapes = {}
+        self._nbytes = {}  # raw_bytes of each slot in use (fixed until it is removed)
 
     def _check(self, rc, what):
         if rc:
@@ -520,6 +532,7 @@ class Batch:
         self._check(lib().rtlbfs_batch_add(self._h, len(xf) - 1, len(yf) - 1, _ptr(xf), _ptr(yf),
                                            Ra, Pr, Ma, dt, C.byref(s)), "batch_add")
         self.shapes[s.value] = (len(yf) - 1, len(xf) - 1)
+        self._nbytes.pop(s.value, None)
         return int(s.value)
 
     def set_bc(self, slot, side, kind, T_wall=0.0, u_wall=0.0):
@@ -544,14 +557,19 @@ class Batch:
         return tuple(out)
 
     def raw_bytes(self, slot) -> int:
-        return int(lib().rtlbfs_batch_state_raw_bytes(self._h, int(slot)))
+        nb = self._nbytes.get(slot)
+        if nb is None:
+            nb = int(lib().rtlbfs_batch_state_raw_bytes(self._h, int(slot)))
+            if nb:
+                self._nbytes[slot] = nb
+        return nb
 
     def get_state_raw(self, slot, out=None):
         """(records, T_unit) of a slot: its cell records as a uint8 array (or
         into `out`, any writable buffer of raw_bytes(slot) bytes) and the
         temperature unit."""
-        if out is None:
-            out = np.empty(self.raw_bytes(slot), dtype=np.uint8)
+        nb = self.raw_bytes(slot)  # 0: not a slot in use, refused by the library
+        out = np.empty(nb, dtype=np.uint8) if out is None else _raw_out(out, nb)
         tu = C.c_double()
         self._check(lib().rtlbfs_batch_get_state_raw(self._h, int(slot), _vp(out.ctypes.data),
                                                      C.byref(tu)), "batch_get_state_raw")
@@ -568,8 +586,11 @@ class Batch:
         """Records of several slots in one call, into the writable buffers
         outs[k] (raw_bytes(slots[k]) bytes each); returns their T_units."""
         n = len(slots)
+        if len(outs) != n:
+            raise ValueError(f"{n} slots but {len(outs)} output buffers")
         sl = np.ascontiguousarray(slots, dtype=np.int32)
-        ptrs = (_vp * n)(*[_vp(np.asarray(o).ctypes.data) for o in outs])
+        arrs = [_raw_out(o, self.raw_bytes(s)) for s, o in zip(slots, outs)]
+        ptrs = (_vp * n)(*[_vp(a.ctypes.data) for a in arrs])
         tu = np.empty(n)
         self._check(lib().rtlbfs_batch_get_states_raw(self._h, n, _vp(sl.ctypes.data),
                                                       C.cast(ptrs, _vp), _ptr(tu)),
@@ -579,6 +600,8 @@ class Batch:
     def set_states_raw(self, slots, recs, T_units):
         """Restore several slots' records in one call."""
         n = len(slots)
+        if len(recs) != n or len(T_units) != n:
+            raise ValueError(f"{n} slots but {len(recs)} record buffers and {len(T_units)} units")
         sl = np.ascontiguousarray(slots, dtype=np.int32)
         arrs = [np.ascontiguousarray(r).view(np.uint8).reshape(-1) for r in recs]
         for s, a in zip(slots, arrs):
@@ -624,6 +647,7 @@ class Batch:
     def remove(self, slot):
         self._check(lib().rtlbfs_batch_remove(self._h, slot), "batch_remove")
         self.shapes.pop(slot, None)
+        self._nbytes.pop(slot, None)
 
     def autotune(self, steps=32):
         k, r, ms = C.c_int(0), C.c_int(0), C.c_double(0)

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every function
 declared in include/rtlbfs.h, and its host-only entry points agree with the
-oracle; argument errors come back as status codes."""
+oracle; argument errors come back as status codes, and the binding checks the
+buffers the library writes into."""
 import ctypes as C
 
 import numpy as np
@@ -59,3 +60,17 @@ def test_op_counts_of_the_tlbfs_stage():
     assert face_t > 1.5 * face_r  # nine equilibria and their moments per face
     with pytest.raises(capi.RTLBFSError):
         capi.op_counts(2)
+
+
+def test_raw_output_buffers_are_checked_before_the_library_writes():
+    """The state-record readers write through a bare pointer: the binding
+    refuses a buffer that is too small, strided or read-only."""
+    ok = np.zeros(64, dtype=np.uint8)
+    assert capi._raw_out(ok, 64) is not None
+    assert capi._raw_out(np.zeros(8), 64).nbytes == 64  # any dtype, counted in bytes
+    assert capi._raw_out(bytearray(80), 64).nbytes == 80
+    ro = np.zeros(64, dtype=np.uint8)
+    ro.flags.writeable = False
+    for bad in (np.zeros(63, dtype=np.uint8), np.zeros((8, 16), dtype=np.uint8)[:, ::2], ro):
+        with pytest.raises(ValueError):
+            capi._raw_out(bad, 64)
